@@ -1,0 +1,171 @@
+"""Seeded synthetic inputs for the MRT-LBKM combustion step.
+
+This module is shared by the tests, the benchmark and the smoke check. It holds
+only initial fields and parameters (no arithmetic of the kinetic model), so the
+oracle and the CUDA path stay independent of each other. Every workload is an
+analytic initial-value problem of the kind the paper runs in Sec. IV:
+
+* ``riemann``    -- Sod-type shock tube, no reaction (Sec. IV.B).
+* ``detonation`` -- 1-D detonation driven by a Chapman-Jouguet state (Sec. IV.A).
+* ``reactive2d`` -- 2-D periodic reactive field of random Fourier modes.
+* ``batched``    -- many 1-D detonations of uneven length and differing S, Q.
+* ``adjoint``    -- 1-D detonation whose target is a run with perturbed S, Q.
+
+Default velocity set: a 16-velocity model of four orbits (axis, diagonal, axis,
+diagonal) with speeds (2.7, 2.2, 1.2, 1.0) and eta (5, 0, 3, 0). The paper's
+24-velocity set cut to its first two rings gives a singular 16x16 M (rank 14),
+so the 16-velocity model uses four orbits with their own speeds instead.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED_BASE = 14116697
+
+DEFAULT_ORBITS = dict(orbit_kind=(0, 1, 0, 1), orbit_speed=(2.7, 2.2, 1.2, 1.0),
+                      orbit_eta=(5.0, 0.0, 3.0, 0.0))
+
+
+def cj_state(Q: float, gamma: float, rho0: float = 1.0, p0: float = 1.0):
+    """Chapman-Jouguet detonation into a gas at rest (rho0, p0) with heat release Q
+    per unit mass (ideal gas, specific internal energy p/((gamma-1) rho)).
+
+    Returns (D_cj, rho, u, p, T) of the burnt state, T = p/rho. Closed form of the
+    Rayleigh line tangent to the equilibrium Hugoniot (CJ theory cited in Sec. IV.A).
+    """
+    c0sq = gamma * p0 / rho0
+    q = (gamma * gamma - 1.0) * Q / c0sq
+    M2 = 1.0 + q + math.sqrt((1.0 + q) ** 2 - 1.0)
+    Dcj = math.sqrt(M2 * c0sq)
+    p = p0 * (1.0 + gamma * M2) / (1.0 + gamma)
+    rho = rho0 * (gamma + 1.0) * M2 / (1.0 + gamma * M2)
+    u = Dcj * (1.0 - rho0 / rho)
+    return Dcj, rho, u, p, p / rho
+
+
+def von_neumann_pressure(Q: float, gamma: float, rho0: float = 1.0, p0: float = 1.0):
+    """Pressure behind a non-reacting shock moving at the CJ speed (ZND spike)."""
+    c0sq = gamma * p0 / rho0
+    Dcj = cj_state(Q, gamma, rho0, p0)[0]
+    M2 = Dcj * Dcj / c0sq
+    return p0 * (2.0 * gamma * M2 - (gamma - 1.0)) / (gamma + 1.0)
+
+
+def _base(**kw):
+    d = dict(DEFAULT_ORBITS)
+    d.update(gamma=1.4, Q=0.0, omega1=0.0, omega2=0.0, T_ig=1.1, bc_x=1, bc_y=0, ny=1)
+    d.update(kw)
+    return d
+
+
+def riemann(nx=400, steps=1000, run="A", interface=None):
+    """Sod shock tube on nx cells: left rho=1, p=1; right rho=0.125, p=0.1; u=0.
+    Run A: all S = 1e5 (single-relaxation limit). Run B: S uniform in [0.8e5, 1.2e5]."""
+    rng = np.random.default_rng(SEED_BASE + 1)
+    S = np.full(16, 1e5) if run == "A" else rng.uniform(0.8e5, 1.2e5, 16)
+    iface = nx // 2 if interface is None else interface
+    rho = np.where(np.arange(nx) < iface, 1.0, 0.125)[None, :]
+    T = np.where(np.arange(nx) < iface, 1.0, 0.8)[None, :]
+    zero = np.zeros((1, nx))
+    return dict(params=_base(nx=nx, S=S, dx=1e-3, dt=1e-5), steps=steps,
+                fields=dict(rho=rho, ux=zero, uy=zero.copy(), T=T, lam=zero.copy()),
+                name="riemann%s_nx%d" % (run, nx))
+
+
+def detonation(nx=16384, steps=20000, driver=50, Q=1.0, S=None, dx=1e-4, dt=2e-6,
+               omega1=2e4, gamma=1.4):
+    """1-D detonation: CJ burnt state (lambda=1) in the first `driver` cells, unburnt
+    premix rho=1, T=1, u=0, lambda=0 ahead. S_5..S_7 = 1e4, the others 1e5 (Sec. IV.A)."""
+    if S is None:
+        S = np.full(16, 1e5)
+        S[4:7] = 1e4
+    _, rcj, ucj, _, Tcj = cj_state(Q, gamma)
+    burnt = np.arange(nx) < driver
+    f = dict(rho=np.where(burnt, rcj, 1.0)[None, :], ux=np.where(burnt, ucj, 0.0)[None, :],
+             uy=np.zeros((1, nx)), T=np.where(burnt, Tcj, 1.0)[None, :],
+             lam=np.where(burnt, 1.0, 0.0)[None, :])
+    return dict(params=_base(nx=nx, S=np.asarray(S, float), Q=Q, omega1=omega1, T_ig=1.1,
+                             dx=dx, dt=dt, gamma=gamma),
+                steps=steps, fields=f, name="detonation_nx%d" % nx)
+
+
+def _modes(rng, nmodes, kmax):
+    ks = []
+    while len(ks) < nmodes:
+        k = rng.integers(-kmax, kmax + 1, size=2)
+        if 1 <= math.hypot(*k) <= kmax:
+            ks.append(k)
+    return np.array(ks), rng.uniform(0, 1, nmodes), rng.uniform(0, 2 * np.pi, nmodes)
+
+
+def _mode_sum(ks, amp, ph, nx, ny, deriv=None):
+    """sum_m a_m cos(2 pi (kx x/nx + ky y/ny) + theta_m) on the grid, or its x / y
+    derivative in grid units, built from separable cos/sin products."""
+    out = np.zeros((ny, nx))
+    xs, ys = np.arange(nx) / nx, np.arange(ny) / ny
+    for (kx, ky), a, th in zip(ks, amp, ph):
+        ax = 2 * np.pi * kx * xs + th
+        ay = 2 * np.pi * ky * ys
+        c = np.cos(ay)[:, None] * np.cos(ax)[None, :] - np.sin(ay)[:, None] * np.sin(ax)[None, :]
+        if deriv is None:
+            out += a * c
+        else:
+            s = np.sin(ay)[:, None] * np.cos(ax)[None, :] + np.cos(ay)[:, None] * np.sin(ax)[None, :]
+            kk = kx if deriv == "x" else ky
+            out -= a * kk * s
+    return out
+
+
+def reactive2d(n=4096, steps=500, T_ig=1.0, seed_offset=3):
+    """2-D periodic reactive field on n x n cells: rho, T = 1 + 0.05 phi/max|phi| with phi
+    a sum of 32 random Fourier modes (1 <= |k| <= 16), solenoidal u of peak 0.1 from a
+    second mode set, lambda ~ U[0, 0.2], S ~ U[1e4, 1e5], Q = 1, k = 2e4.
+    T_ig defaults to 1.0: with T <= 1.05 the paper's 1.1 would leave the field inert."""
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    kmax = min(16, n // 4)
+    fields = {}
+    for name in ("rho", "T"):
+        phi = _mode_sum(*_modes(rng, 32, kmax), n, n)
+        fields[name] = 1.0 + 0.05 * phi / np.abs(phi).max()
+    ks, amp, ph = _modes(rng, 32, kmax)
+    ux = _mode_sum(ks, amp, ph, n, n, deriv="y")
+    uy = -_mode_sum(ks, amp, ph, n, n, deriv="x")
+    umax = np.sqrt(ux * ux + uy * uy).max()
+    fields["ux"], fields["uy"] = 0.1 * ux / umax, 0.1 * uy / umax
+    fields["lam"] = rng.uniform(0.0, 0.2, (n, n))
+    S = rng.uniform(1e4, 1e5, 16)
+    return dict(params=_base(nx=n, ny=n, S=S, Q=1.0, omega1=2e4, T_ig=T_ig, dx=1e-3,
+                             dt=5e-6, bc_x=0, bc_y=0),
+                steps=steps, fields=fields, name="reactive2d_%dx%d" % (n, n))
+
+
+def batched(n_instances=512, steps=5000, nx_min=1024, nx_max=65536, driver=50):
+    """Many 1-D detonations: nx log-uniform in [nx_min, nx_max] (multiple of 4), S_k
+    log-uniform in [1e4, 1e6] per instance, Q ~ U[0.5, 2] with the CJ driver state of
+    each instance's own Q, dx = 1e-4, dt = 1e-6."""
+    rng = np.random.default_rng(SEED_BASE + 4)
+    nxs = np.exp(rng.uniform(np.log(nx_min), np.log(nx_max), n_instances))
+    nxs = (np.round(nxs / 4) * 4).astype(np.int64)
+    S = np.exp(rng.uniform(np.log(1e4), np.log(1e6), (n_instances, 16)))
+    Q = rng.uniform(0.5, 2.0, n_instances)
+    insts = []
+    for i in range(n_instances):
+        d = detonation(nx=int(nxs[i]), steps=steps, driver=driver, Q=float(Q[i]), S=S[i],
+                       dx=1e-4, dt=1e-6)
+        insts.append(d)
+    return dict(instances=insts, steps=steps, nx=nxs, S=S, Q=Q,
+                name="batched_%d" % n_instances)
+
+
+def adjoint(nx=8192, steps=4000):
+    """Detonation of nx cells (structure and parameters of ``detonation``) and a
+    target run with S_k (1 + 0.05 xi_k), Q * 1.05, xi ~ N(0, 1)."""
+    rng = np.random.default_rng(SEED_BASE + 5)
+    base = detonation(nx=nx, steps=steps)
+    xi = rng.standard_normal(16)
+    S_t = base["params"]["S"] * (1.0 + 0.05 * xi)
+    target = detonation(nx=nx, steps=steps, Q=1.05, S=S_t)
+    return dict(base=base, target=target, w_tne=1.0, checkpoint_every=64,
+                name="adjoint_nx%d" % nx)
