@@ -1,0 +1,355 @@
+"""Throughput benchmark of the fused MRT-LBKM step on GB300.
+
+Workload: the 2-D periodic reactive field of 4096 x 4096 cells (32 random
+Fourier modes in rho and T, solenoidal u of peak 0.1, lambda ~ U[0, 0.2],
+S ~ U[1e4, 1e5], Q = 1, k = 2e4), FP32 state with FP64 conserved-moment
+recovery and FP64 grid-wide TNE reductions on every step. A step is one launch
+of the fused kernel over the whole grid (stencil, collision, reaction, Euler
+update, TNE). The state (1.14 GB per copy) is larger than L2, so no flush is
+needed between steps.
+
+Prints one JSON line: Mcell-updates/s (cells x steps / time), the roofline of
+the step kernel against the measured HBM copy bandwidth, an end-to-end figure
+through the C ABI with host buffers, the CPU oracle timed on the host cores,
+and SM clocks sampled during the timed region.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbkm_inputs as li  # noqa: E402
+
+N_CELLS_SIDE = 4096
+BYTES_PER_CELL = {"f32": 136, "f64": 272}  # read + write of 16 f + lambda
+METRIC = "Mcell-updates/s (16 f_i)"
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_tag):
+    """dram bytes per launch from the committed ncu summary, if it matches the current
+    kernel source (sha256 line); else None."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "step_kernel_reactive2d.md")
+    src = os.path.join(ROOT, "paper_1411_6697_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(src, f), "rb").read())
+    digest = h.hexdigest()
+    try:
+        lines = open(prof).read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for line in lines:
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("source_sha256") != digest:
+        return None
+    try:
+        return float(kv.get("traffic_bytes_per_launch_%s" % kernel_tag))
+    except (TypeError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_solver(cfg, precision, recovery, stream=None, tne_every=1):
+    from paper_1411_6697_gb300 import lbkm
+    p = cfg["params"]
+    return lbkm.Solver(nx=p["nx"], ny=p["ny"], precision=precision, recovery=recovery,
+                       gamma=p["gamma"], orbit_kind=p["orbit_kind"], orbit_speed=p["orbit_speed"],
+                       orbit_eta=p["orbit_eta"], S=p["S"], Q=p["Q"], omega1=p["omega1"],
+                       omega2=p["omega2"], T_ig=p["T_ig"], dx=p["dx"], dy=p["dx"], dt=p["dt"],
+                       bc=(p["bc_x"], p["bc_y"]), tne_every=tne_every,
+                       tne_capacity=4096, stream=stream)
+
+
+def time_steps(solver, stream, steps):
+    """CUDA-event time of `steps` fused steps on the solver's stream (ms)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    solver.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def cpu_oracle_rate(budget_s=12.0, side=1024):
+    """The FP64 oracle, as it stands, on a side x side window generated with the same
+    recipe; steps chosen to fill about budget_s seconds. Returns (Mcell/s, desc, cores)."""
+    from oracle import oracle
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    cfg = li.reactive2d(n=side, steps=1)
+    p = dict(cfg["params"])
+    nx, ny = p.pop("nx"), p.pop("ny")
+    ob = oracle.Oracle(nx, ny, **p)
+    fl = cfg["fields"]
+    f = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
+    t0 = time.perf_counter()
+    f, lam = ob.run(f, fl["lam"], 1)
+    one = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    ob.run(f, lam, steps)
+    dt = time.perf_counter() - t0
+    rate = nx * ny * steps / dt / 1e6
+    desc = "FP64 C oracle (OpenMP, %d threads) on a %dx%d window of the same recipe, %d steps, " \
+           "%.1f s" % (int(os.environ["OMP_NUM_THREADS"]), side, side, steps, dt)
+    return rate, desc, int(os.environ["OMP_NUM_THREADS"])
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, a bounded window per step."""
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    side = 384
+    cfg = li.reactive2d(n=side, steps=1)
+    p = dict(cfg["params"])
+    nx, ny = p.pop("nx"), p.pop("ny")
+    ob = oracle.Oracle(nx, ny, **p)
+    fl = cfg["fields"]
+    f = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
+    lam = fl["lam"]
+    for _ in range(args.warmup):
+        f, lam = ob.run(f, lam, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, lam = ob.run(f, lam, 1)
+    dt = time.perf_counter() - t0
+    value = nx * ny * args.steps / dt / 1e6
+    sample = "%dx%d window of the reactive2d recipe per step (FP64 oracle, %s threads)" % (
+        side, side, os.environ["OMP_NUM_THREADS"])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mcell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "reactive2d_4096x4096 (sampled window)", "window": side},
+            "cpu_baseline": {"value": value, "unit": "Mcell-updates/s",
+                             "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--recovery", default="f64", choices=["f64", "df32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--side", type=int, default=N_CELLS_SIDE)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    rank, local, world = _env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    from paper_1411_6697_gb300 import lbkm
+    prec = lbkm.F32 if args.precision == "f32" else lbkm.F64
+    rec = lbkm.RECOVER_F64 if args.recovery == "f64" else lbkm.RECOVER_DF32
+    cfg = li.reactive2d(n=args.side, steps=500)
+    n = args.side * args.side
+    stream = torch.cuda.Stream()
+    solver = make_solver(cfg, prec, rec, stream=stream)
+    fl = cfg["fields"]
+    solver.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    with torch.cuda.stream(stream):
+        if args.warmup:
+            solver.step(args.warmup)
+        solver.sync()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            ms = time_steps(solver, stream, args.steps)
+        solver.sync()
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * n * args.steps / (ms_max * 1e-3) / 1e6
+    per_launch_ms = ms / args.steps
+    tag = "f32" if prec == lbkm.F32 else "f64"
+    alg_bytes = BYTES_PER_CELL[tag] * n
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    traffic = profile_traffic(tag + ("_df32" if rec == lbkm.RECOVER_DF32 else ""))
+
+    # end to end through the C ABI with pinned host buffers: H2D of the initial fields,
+    # the steps, D2H of the macroscopic fields and of the TNE history
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(
+        np.broadcast_to(fl[k], (args.side, args.side)))).pin_memory() for k in fl}
+    outs = {k: torch.empty((args.side, args.side), dtype=torch.float64).pin_memory()
+            for k in ("rho", "ux", "uy", "T", "p", "lam")}
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        solver.init_fields(pinned["rho"], pinned["ux"], pinned["uy"], pinned["T"],
+                           pinned["lam"])
+        solver.step(e2e_steps)
+        solver.macros(out=outs)
+        hist = solver.tne_history(max_records=e2e_steps)
+    t_e2e = time.perf_counter() - t0
+    e2e_value = n * e2e_steps / t_e2e / 1e6
+    h2d = 5 * n * 8
+    d2h = 6 * n * 8 + len(hist) * 8 * 67
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": tag, "data": "synthetic",
+        "config": {"workload": "reactive2d_%dx%d" % (args.side, args.side),
+                   "cells_per_gpu": n, "precision": tag,
+                   "conserved_moment_recovery": args.recovery,
+                   "tne": "every step, FP64 grid-wide reduction",
+                   "l2": "state %.2f GB per copy > L2 (129 MB): no flush" % (
+                       17 * n * (4 if tag == "f32" else 8) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "kernel": "step_kernel (%s)" % tag,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": {"value": e2e_value, "unit": "Mcell-updates/s",
+                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+                "note": "init_fields from pinned host + %d steps + macros to pinned host + "
+                        "TNE history" % e2e_steps},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+
+    if rank == 0 and not args.no_variants:
+        var = {}
+        for name, pr, rc in (("f32_recover_f64", lbkm.F32, lbkm.RECOVER_F64),
+                             ("f32_recover_df32", lbkm.F32, lbkm.RECOVER_DF32),
+                             ("f64_plain", lbkm.F64, lbkm.RECOVER_F64)):
+            if pr == prec and rc == rec:
+                var[name] = value / world
+                continue
+            s2 = make_solver(cfg, pr, rc, stream=stream)
+            s2.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+            with torch.cuda.stream(stream):
+                s2.step(3)
+                k = 20 if pr == lbkm.F32 else 4
+                t = time_steps(s2, stream, k)
+            var[name] = n * k / (t * 1e-3) / 1e6
+            s2.close()
+        line["variants_mcell_per_s"] = var
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, desc, cores = cpu_oracle_rate()
+        line["cpu_baseline"] = {"value": rate, "unit": "Mcell-updates/s", "cores": cores,
+                                "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

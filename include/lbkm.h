@@ -1,0 +1,198 @@
+/*
+ * lbkm.h -- C ABI of the GB300 (sm_103a) implementation of the two-dimensional
+ * multiple-relaxation-time lattice Boltzmann kinetic model for combustion of
+ * Xu, Lin, Zhang and Li (arXiv:1411.6697).
+ *
+ * One time step updates, in every cell, the 16 discrete distribution functions
+ * f_i and the reaction progress lambda:
+ *   - moments f_hat = M f, macros rho, u, T (Sec. II, Eqs. (5)-(7), rows m_1..m_16
+ *     of M listed after Eq. (16));
+ *   - analytic equilibrium moments f_hat^eq (list after Eq. (16); f_hat^eq_14 and
+ *     f_hat^eq_16 carry the factor T of Eq. (11));
+ *   - relaxation in moment space with the diagonal rates R_k (= S_k here), the
+ *     modification terms A_hat_8, A_hat_9 (Eqs. (3)-(4), sign as in the
+ *     Chapman-Enskog form Eq. (29)) and the chemical term
+ *     C_hat_k = (d f_hat^eq_k/dT) dT/dt|_C, dT/dt|_C = 2 Q lambda'/(D+I)
+ *     (Eqs. (19)-(23));
+ *   - back-transform Omega = M^-1 Omega_hat (M^-1 fixed before the main loop,
+ *     Sec. II and Sec. V);
+ *   - NND finite differences of v_i f_i in space (Sec. II) and forward Euler in
+ *     time; lambda follows Eq. (28) with m = n = 1, its time part integrated
+ *     exactly over dt where T > T_ig and its advection by NND interface values;
+ *   - on request, the thermodynamic non-equilibrium (TNE) measures of the state
+ *     being stepped, Delta_k = f_hat_k - f_hat^eq_k and d = sqrt(sum Delta_k^2)
+ *     (Sec. VI, Eqs. (90)-(91)), reduced over the grid on the fly.
+ *
+ * Velocity model: 16 velocities in four orbits of four (kind 0 = axis set
+ * cyc(+-1, 0), kind 1 = diagonal set (+-1, +-1)), each orbit with its own speed
+ * and eta: the D2V24 construction of Sec. II (Eqs. (25)-(27)) reduced to the 16
+ * velocities that Sec. VII allows. A non-singular 16x16 M needs exactly two
+ * orbits of each kind; the library takes them in the order axis, diagonal,
+ * axis, diagonal. Velocities inside an orbit: (1,0),(0,1),(-1,0),(0,-1) and
+ * (1,1),(-1,1),(-1,-1),(1,-1), times the orbit speed.
+ *
+ * Conventions
+ *   - Every call returns an lbkm_status; nothing is thrown across the ABI.
+ *     lbkm_last_error() gives a message for the last failing call on a handle.
+ *   - The handle owns its device buffers. Caller arrays are borrowed for the
+ *     duration of a call only.
+ *   - Host field arrays are FP64, row-major [ny][nx]. With on_device != 0 the
+ *     pointers are device pointers (FP64, same layout) on the handle's device.
+ *   - lbkm_step() is asynchronous on the handle's stream; device-side failures
+ *     (non-finite or non-positive rho or T) surface as LBKM_EUNSTABLE at the
+ *     next synchronising call (lbkm_macros, lbkm_tne, lbkm_sync, ...).
+ *   - Calls on one handle are not thread-safe. Different handles are
+ *     independent.
+ */
+#ifndef LBKM_H
+#define LBKM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBKM_NV 16 /* discrete velocities = moments */
+
+typedef struct lbkm* lbkm_t; /* opaque, owned by the library */
+
+typedef enum {
+    LBKM_OK = 0,
+    LBKM_EINVAL = 1,    /* bad argument or parameter set */
+    LBKM_ENOMEM = 2,    /* device or host allocation failed */
+    LBKM_ECUDA = 3,     /* CUDA runtime error (message in lbkm_last_error) */
+    LBKM_ESINGULAR = 4, /* the velocity set gives a singular M */
+    LBKM_EUNSTABLE = 5, /* a cell reached non-finite or non-positive rho or T */
+    LBKM_ETIMEOUT = 6,  /* a bounded device-side wait gave up */
+    LBKM_ESTATE = 7     /* call out of order (e.g. step before init_fields) */
+} lbkm_status;
+
+typedef enum {
+    LBKM_F64 = 0, /* plain form: state and all arithmetic in FP64 */
+    LBKM_F32 = 1  /* state and bulk arithmetic in FP32; conserved-moment
+                     recovery and TNE reductions as set by lbkm_recovery */
+} lbkm_precision;
+
+typedef enum {
+    LBKM_RECOVER_F64 = 0,  /* rho, rho u, rho[(D+I)T+u^2] and rho, u, T in FP64 */
+    LBKM_RECOVER_DF32 = 1  /* same quantities in double-float (pairs of FP32 with
+                              error-free transforms), ~48-bit significand, run on
+                              the FP32 pipes */
+} lbkm_recovery;
+
+typedef enum { LBKM_BC_PERIODIC = 0, LBKM_BC_ZERO_GRADIENT = 1 } lbkm_bc;
+
+typedef struct {
+    int32_t nx, ny;        /* grid; ny = 1 for one-dimensional runs */
+    int32_t precision;     /* lbkm_precision */
+    int32_t recovery;      /* lbkm_recovery, used by LBKM_F32 only */
+    double gamma;          /* specific-heat ratio; I = 2/(gamma-1) - D (Sec. III) */
+    double Pr;             /* if > 0: S_8 = S_9 = Pr * S_5 (Pr = R_kappa/R_mu,
+                              Sec. III, needs S_5 = S_6 = S_7); if <= 0: S as given */
+    int32_t orbit_kind[4]; /* must be {0, 1, 0, 1} (axis, diagonal, axis, diagonal) */
+    double orbit_speed[4]; /* v of each orbit (> 0) */
+    double orbit_eta[4];   /* eta of each orbit (>= 0) */
+    double S[16];          /* relaxation rates R_1..R_16 (R_1..R_4 accepted, unused,
+                              Sec. III); require dt * max(S_5..S_16) < 2 */
+    double Q;              /* heat release per unit mass (Eq. (18)) */
+    double omega1, omega2; /* Cochran rate constants of Eq. (28), m = n = 1 */
+    double T_ig;           /* reaction only where T > T_ig (Sec. II) */
+    double dx, dy, dt;     /* grid spacing and time step */
+    int32_t bc_x, bc_y;    /* lbkm_bc for each direction */
+    int32_t tne_every;     /* 0: no on-the-fly TNE; k > 0: reduce the TNE of the
+                              input state of every k-th step into the history */
+    int32_t tne_capacity;  /* records kept in the device history ring (>= 1) */
+} lbkm_params;
+
+/* Grid-wide TNE measures of one state (Sec. VI). Sums are weighted by dx*dy;
+ * min and max are unweighted. Index k-1 holds Delta_k; Delta_1..Delta_4 are 0. */
+typedef struct {
+    double sum[16], abs_sum[16], min[16], max[16];
+    double d_sum, d2_sum; /* sum of d and of d^2, d = sqrt(sum_k Delta_k^2) */
+    int64_t step;         /* step index of the state the record describes */
+} lbkm_tne_global;
+
+/* Fill *p with defaults: D2V16 orbits (axis 2.7/eta 5, diagonal 2.2/eta 0,
+ * axis 1.2/eta 3, diagonal 1.0/eta 0), gamma 1.4, S_k = 1e5, Q = 0, T_ig = 1.1,
+ * dx = dy = 1e-3, dt = 1e-5, zero-gradient x, periodic y, LBKM_F64, TNE off,
+ * tne_capacity 1. nx, ny are set to 0 and must be filled in. */
+void lbkm_default_params(lbkm_params* p);
+
+/* Validate p, build M (rows m_1..m_16), invert it in block form and keep the
+ * model constants for kernel-parameter (constant-bank) delivery, allocate the
+ * two device copies of the state [17][ny][pitch] (f_1..f_16, lambda) and the
+ * reduction buffers. cuda_stream: a cudaStream_t (NULL = legacy default stream)
+ * on the current device; the handle launches all its work there.
+ * Errors: LBKM_EINVAL (bad sizes or parameters, message names the field),
+ * LBKM_ESINGULAR, LBKM_ENOMEM, LBKM_ECUDA. On error *out is NULL. */
+lbkm_status lbkm_create(const lbkm_params* p, void* cuda_stream, lbkm_t* out);
+
+/* Release every device and host resource of h (NULL is ignored). Synchronises
+ * the handle's stream first. */
+void lbkm_destroy(lbkm_t h);
+
+/* Change the stream later work is launched on. */
+lbkm_status lbkm_set_stream(lbkm_t h, void* cuda_stream);
+
+/* Equilibrium start, f = M^-1 f_hat^eq(rho, u, T) (Eq. (16)), and lambda.
+ * rho, ux, uy, T, lambda: [ny][nx] FP64, host (on_device = 0) or device.
+ * lambda may be NULL (then lambda = 0). Resets the step counter to 0 and the
+ * TNE history. Errors: LBKM_EINVAL (NULL field), LBKM_ECUDA. */
+lbkm_status lbkm_init_fields(lbkm_t h, const double* rho, const double* ux, const double* uy,
+                             const double* T, const double* lambda, int on_device);
+
+/* Advance n >= 0 time steps, asynchronously on the handle's stream. Each step
+ * is one fused kernel (stencil, collision, reaction, Euler update and, when due,
+ * the TNE reduction). Repeated chunks are replayed from a CUDA graph.
+ * Errors: LBKM_ESTATE (no init_fields yet), LBKM_EINVAL (n < 0), LBKM_ECUDA. */
+lbkm_status lbkm_step(lbkm_t h, int64_t n);
+
+/* Wait for the handle's stream and check the device status word.
+ * Errors: LBKM_EUNSTABLE, LBKM_ECUDA. */
+lbkm_status lbkm_sync(lbkm_t h);
+
+/* Number of steps taken since lbkm_init_fields / lbkm_set_state. */
+int64_t lbkm_steps_taken(lbkm_t h);
+
+/* Macroscopic fields of the current state (Eqs. (5)-(7)): rho, u_x, u_y, T,
+ * p = rho T and lambda, each [ny][nx] FP64, host or device; NULL pointers are
+ * skipped. Synchronises. Errors: LBKM_ESTATE, LBKM_EUNSTABLE, LBKM_ECUDA. */
+lbkm_status lbkm_macros(lbkm_t h, double* rho, double* ux, double* uy, double* T, double* p,
+                        double* lambda, int on_device);
+
+/* TNE of the current state (Sec. VI): delta, if not NULL, receives
+ * Delta_1..Delta_16 as [16][ny][nx] FP64 (host or device, Delta_1..4 = 0);
+ * g, if not NULL, receives the grid-wide record (host memory). Synchronises. */
+lbkm_status lbkm_tne(lbkm_t h, double* delta, lbkm_tne_global* g, int on_device);
+
+/* Copy up to max_records of the on-the-fly TNE records, oldest first, to out
+ * (host). *n_out receives how many were copied. Records older than
+ * tne_capacity steps are overwritten. Synchronises. */
+lbkm_status lbkm_tne_history(lbkm_t h, lbkm_tne_global* out, int32_t max_records,
+                             int32_t* n_out);
+
+/* Bytes of one state snapshot (17 planes of nx*ny values in the handle's
+ * precision, FP64 or FP32, row-major, f_1..f_16 then lambda, followed by the
+ * int64 step counter). */
+size_t lbkm_state_bytes(lbkm_t h);
+
+/* Checkpoint / resume: copy the current state to dst or load it from src
+ * (lbkm_state_bytes() bytes, host or device). set_state clears the status word
+ * and the TNE history. Errors: LBKM_EINVAL, LBKM_ESTATE, LBKM_ECUDA. */
+lbkm_status lbkm_get_state(lbkm_t h, void* dst, int on_device);
+lbkm_status lbkm_set_state(lbkm_t h, const void* src, int on_device);
+
+/* Message of the last failing call on h (or of the last failing lbkm_create
+ * when h is NULL). Never NULL. */
+const char* lbkm_last_error(lbkm_t h);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t lbkm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBKM_H */

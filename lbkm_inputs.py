@@ -102,20 +102,18 @@ def _modes(rng, nmodes, kmax):
 
 def _mode_sum(ks, amp, ph, nx, ny, deriv=None):
     """sum_m a_m cos(2 pi (kx x/nx + ky y/ny) + theta_m) on the grid, or its x / y
-    derivative in grid units, built from separable cos/sin products."""
-    out = np.zeros((ny, nx))
+    derivative in grid units. cos(A + B) = cos A cos B - sin A sin B makes the sum
+    two rank-32 products of per-axis tables."""
     xs, ys = np.arange(nx) / nx, np.arange(ny) / ny
-    for (kx, ky), a, th in zip(ks, amp, ph):
-        ax = 2 * np.pi * kx * xs + th
-        ay = 2 * np.pi * ky * ys
-        c = np.cos(ay)[:, None] * np.cos(ax)[None, :] - np.sin(ay)[:, None] * np.sin(ax)[None, :]
-        if deriv is None:
-            out += a * c
-        else:
-            s = np.sin(ay)[:, None] * np.cos(ax)[None, :] + np.cos(ay)[:, None] * np.sin(ax)[None, :]
-            kk = kx if deriv == "x" else ky
-            out -= a * kk * s
-    return out
+    ax = 2 * np.pi * np.outer(ks[:, 0], xs) + ph[:, None]   # [m, nx]
+    ay = 2 * np.pi * np.outer(ks[:, 1], ys)                  # [m, ny]
+    cx, sx, cy, sy = np.cos(ax), np.sin(ax), np.cos(ay), np.sin(ay)
+    if deriv is None:
+        w = amp
+        return (cy.T * w) @ cx - (sy.T * w) @ sx
+    w = amp * (ks[:, 0] if deriv == "x" else ks[:, 1])
+    # d/dk of cos(A + B) = -sin(A + B) = -(sin B cos A + cos B sin A)
+    return -((sy.T * w) @ cx + (cy.T * w) @ sx)
 
 
 def reactive2d(n=4096, steps=500, T_ig=1.0, seed_offset=3):

@@ -1,0 +1,475 @@
+// api.cu -- the C ABI declared in include/lbkm.h.
+//
+// A handle owns two device copies of the state, laid out as 17 planes
+// (f_1..f_16, lambda) of ny rows with a pitch that is a multiple of 32
+// elements, plus the TNE partial buffer, the on-the-fly TNE history ring and a
+// small block of device counters. lbkm_step launches one fused step kernel per
+// time step; chunks of GRAPH_CHUNK steps are captured once into a CUDA graph
+// and replayed, so control crosses from host to device once per chunk.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/lbkm.h"
+#include "kernels.cuh"
+#include "model.h"
+
+using namespace lbk;
+
+namespace {
+constexpr int GRAPH_CHUNK = 32; // even, so a replay leaves the ping-pong index unchanged
+thread_local std::string g_create_error;
+}
+
+struct lbkm {
+    lbkm_params p;
+    HostModel hm;
+    ModelConst<double> Kd;
+    ModelConst<float> Kf;
+    int precision, recovery;
+    bool two_d;
+    int nx, ny, pitch;
+    size_t elem, plane_elems, state_bytes_dev;
+    cudaStream_t stream;
+    cudaStream_t capture_stream;
+    void* buf[2];
+    int cur;
+    double* partials;
+    int grid, tgrid;
+    DevCounters* ctr;
+    TneRecord* hist;
+    TneRecord* tne_out;
+    bool initialized;
+    int64_t host_steps;
+    cudaGraphExec_t graph[2];
+    std::string err;
+};
+
+namespace {
+
+lbkm_status fail(lbkm_t h, lbkm_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(h, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? LBKM_ENOMEM : LBKM_ECUDA,   \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+const void* model_ptr(const lbkm* h)
+{
+    return h->precision == 0 ? (const void*)&h->Kd : (const void*)&h->Kf;
+}
+
+StepLaunch step_args(const lbkm* h, int from)
+{
+    StepLaunch a;
+    a.in = h->buf[from];
+    a.out = h->buf[1 - from];
+    a.partials = h->partials;
+    a.ctr = h->ctr;
+    a.hist = h->hist;
+    a.hist_cap = h->p.tne_capacity;
+    a.tne_every = h->p.tne_every;
+    a.grid = h->grid;
+    a.cell_area = h->p.dx * h->p.dy;
+    return a;
+}
+
+lbkm_status check_status(lbkm_t h)
+{
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    int st = 0;
+    CUDA_TRY(h, cudaMemcpy(&st, &h->ctr->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & 1)
+        return fail(h, LBKM_EUNSTABLE,
+                    "a cell reached a non-finite or non-positive density or temperature");
+    return LBKM_OK;
+}
+
+void release(lbkm* h)
+{
+    for (int i = 0; i < 2; i++)
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+    cudaFree(h->partials);
+    cudaFree(h->ctr);
+    cudaFree(h->hist);
+    cudaFree(h->tne_out);
+}
+
+} // namespace
+
+extern "C" {
+
+void lbkm_default_params(lbkm_params* p)
+{
+    memset(p, 0, sizeof(*p));
+    p->precision = LBKM_F64;
+    p->recovery = LBKM_RECOVER_F64;
+    p->gamma = 1.4;
+    p->Pr = 0.0;
+    const int32_t kind[4] = {0, 1, 0, 1};
+    const double speed[4] = {2.7, 2.2, 1.2, 1.0}, eta[4] = {5.0, 0.0, 3.0, 0.0};
+    for (int o = 0; o < 4; o++) {
+        p->orbit_kind[o] = kind[o];
+        p->orbit_speed[o] = speed[o];
+        p->orbit_eta[o] = eta[o];
+    }
+    for (int k = 0; k < 16; k++) p->S[k] = 1e5;
+    p->T_ig = 1.1;
+    p->dx = p->dy = 1e-3;
+    p->dt = 1e-5;
+    p->bc_x = LBKM_BC_ZERO_GRADIENT;
+    p->bc_y = LBKM_BC_PERIODIC;
+    p->tne_capacity = 1;
+}
+
+lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
+{
+    if (!out) return fail(nullptr, LBKM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!pin) return fail(nullptr, LBKM_EINVAL, "params is NULL");
+    lbkm_params p = *pin;
+    if (p.nx < 1 || p.ny < 1) return fail(nullptr, LBKM_EINVAL, "nx and ny must be >= 1");
+    if (p.nx > (1 << 28) || p.ny > (1 << 28) || (double)p.nx * p.ny > 4e9)
+        return fail(nullptr, LBKM_EINVAL, "grid too large");
+    if (p.precision != LBKM_F64 && p.precision != LBKM_F32)
+        return fail(nullptr, LBKM_EINVAL, "precision must be LBKM_F64 or LBKM_F32");
+    if (p.recovery != LBKM_RECOVER_F64 && p.recovery != LBKM_RECOVER_DF32)
+        return fail(nullptr, LBKM_EINVAL, "recovery must be LBKM_RECOVER_F64 or _DF32");
+    if (!(p.gamma > 1.0 && p.gamma <= 2.0))
+        return fail(nullptr, LBKM_EINVAL, "gamma must lie in (1, 2] (I = 2/(gamma-1) - 2 >= 0)");
+    for (int o = 0; o < 4; o++) {
+        if (!(p.orbit_speed[o] > 0.0)) return fail(nullptr, LBKM_EINVAL, "orbit_speed must be > 0");
+        if (!(p.orbit_eta[o] >= 0.0)) return fail(nullptr, LBKM_EINVAL, "orbit_eta must be >= 0");
+    }
+    if (!(p.dx > 0 && p.dy > 0 && p.dt > 0))
+        return fail(nullptr, LBKM_EINVAL, "dx, dy, dt must be > 0");
+    if (p.bc_x < 0 || p.bc_x > 1 || p.bc_y < 0 || p.bc_y > 1)
+        return fail(nullptr, LBKM_EINVAL, "bc_x, bc_y must be LBKM_BC_PERIODIC or _ZERO_GRADIENT");
+    if (p.Pr > 0) p.S[7] = p.S[8] = p.Pr * p.S[4];
+    double smax = 0;
+    for (int k = 4; k < 16; k++) {
+        if (!(p.S[k] > 0)) return fail(nullptr, LBKM_EINVAL, "S_%d must be > 0", k + 1);
+        if (p.S[k] > smax) smax = p.S[k];
+    }
+    if (!(p.dt * smax < 2.0))
+        return fail(nullptr, LBKM_EINVAL,
+                    "dt * max(S_5..S_16) = %g: forward Euler relaxation needs < 2", p.dt * smax);
+    double vmax = 0;
+    for (int o = 0; o < 4; o++) vmax = fmax(vmax, p.orbit_speed[o]);
+    double cfl = vmax * p.dt * (1.0 / p.dx + (p.ny > 1 ? 1.0 / p.dy : 0.0));
+    if (!(cfl <= 1.0))
+        return fail(nullptr, LBKM_EINVAL, "CFL number %g of the fastest velocity exceeds 1", cfl);
+    if (!(p.omega1 >= 0 && p.omega2 >= 0))
+        return fail(nullptr, LBKM_EINVAL, "omega1, omega2 must be >= 0");
+    if (p.tne_every < 0 || p.tne_capacity < 1)
+        return fail(nullptr, LBKM_EINVAL, "tne_every must be >= 0 and tne_capacity >= 1");
+
+    lbkm* h = new lbkm();
+    h->p = p;
+    char err[256] = {0};
+    if (build_host_model(p.orbit_kind, p.orbit_speed, p.orbit_eta, p.gamma, &h->hm, err,
+                         sizeof(err)) != 0) {
+        delete h;
+        bool kind = strstr(err, "orbit_kind") != nullptr;
+        return fail(nullptr, kind ? LBKM_EINVAL : LBKM_ESINGULAR, "%s", err);
+    }
+    h->precision = p.precision;
+    h->recovery = p.recovery;
+    h->two_d = p.ny > 1;
+    h->nx = p.nx;
+    h->ny = p.ny;
+    h->pitch = (p.nx + 31) / 32 * 32;
+    h->elem = p.precision == LBKM_F64 ? 8 : 4;
+    h->plane_elems = (size_t)h->ny * h->pitch;
+    h->state_bytes_dev = (size_t)NPLANE * h->plane_elems * h->elem;
+    fill_model_const<double>(h->hm, p.S, p.Q, p.omega1, p.omega2, p.T_ig, p.dx, p.dy, p.dt, p.nx,
+                             p.ny, h->pitch, p.bc_x, p.bc_y, &h->Kd);
+    fill_model_const<float>(h->hm, p.S, p.Q, p.omega1, p.omega2, p.T_ig, p.dx, p.dy, p.dt, p.nx,
+                            p.ny, h->pitch, p.bc_x, p.bc_y, &h->Kf);
+    h->stream = (cudaStream_t)cuda_stream;
+
+    auto bail = [&](cudaError_t e, const char* what) {
+        std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+        release(h);
+        delete h;
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? LBKM_ENOMEM : LBKM_ECUDA, "%s",
+                    m.c_str());
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->buf[0], h->state_bytes_dev)) != cudaSuccess) return bail(e, "state A");
+    if ((e = cudaMalloc(&h->buf[1], h->state_bytes_dev)) != cudaSuccess) return bail(e, "state B");
+    if ((e = cudaMemset(h->buf[0], 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemset(h->buf[1], 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
+    h->grid = step_grid(h->precision, h->recovery, h->two_d, h->nx, h->ny);
+    if (h->grid < 1) return bail(cudaGetLastError(), "step grid");
+    h->tgrid = tne_grid(h->nx, h->ny);
+    int pg = h->grid > h->tgrid ? h->grid : h->tgrid;
+    if ((e = cudaMalloc(&h->partials, sizeof(double) * TNE_PART * (size_t)pg)) != cudaSuccess)
+        return bail(e, "partials");
+    if ((e = cudaMalloc(&h->ctr, sizeof(DevCounters))) != cudaSuccess) return bail(e, "counters");
+    if ((e = cudaMemset(h->ctr, 0, sizeof(DevCounters))) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMalloc(&h->hist, sizeof(TneRecord) * (size_t)p.tne_capacity)) != cudaSuccess)
+        return bail(e, "history");
+    if ((e = cudaMalloc(&h->tne_out, sizeof(TneRecord))) != cudaSuccess) return bail(e, "tne out");
+    if ((e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(e, "capture stream");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "synchronize");
+    *out = h;
+    return LBKM_OK;
+}
+
+void lbkm_destroy(lbkm_t h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+}
+
+lbkm_status lbkm_set_stream(lbkm_t h, void* s)
+{
+    if (!h) return LBKM_EINVAL;
+    h->stream = (cudaStream_t)s;
+    return LBKM_OK;
+}
+
+lbkm_status lbkm_init_fields(lbkm_t h, const double* rho, const double* ux, const double* uy,
+                             const double* T, const double* lambda, int on_device)
+{
+    if (!h) return LBKM_EINVAL;
+    if (!rho || !ux || !uy || !T) return fail(h, LBKM_EINVAL, "rho, ux, uy and T are required");
+    const size_t n = (size_t)h->nx * h->ny, nb = n * sizeof(double);
+    double* tmp = nullptr;
+    const double *r = rho, *u = ux, *v = uy, *t = T, *l = lambda;
+    if (!on_device) {
+        CUDA_TRY(h, cudaMallocAsync((void**)&tmp, nb * 5, h->stream));
+        const double* src[5] = {rho, ux, uy, T, lambda};
+        for (int k = 0; k < 5; k++) {
+            if (!src[k]) continue;
+            CUDA_TRY(h, cudaMemcpyAsync(tmp + k * n, src[k], nb, cudaMemcpyHostToDevice, h->stream));
+        }
+        r = tmp;
+        u = tmp + n;
+        v = tmp + 2 * n;
+        t = tmp + 3 * n;
+        l = lambda ? tmp + 4 * n : nullptr;
+    }
+    h->cur = 0;
+    CUDA_TRY(h, launch_init(h->precision, h->Kd, r, u, v, t, l, h->buf[0], h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->ctr, 0, sizeof(DevCounters), h->stream));
+    if (tmp) CUDA_TRY(h, cudaFreeAsync(tmp, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->initialized = true;
+    h->host_steps = 0;
+    return LBKM_OK;
+}
+
+lbkm_status lbkm_step(lbkm_t h, int64_t n)
+{
+    if (!h) return LBKM_EINVAL;
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_step before lbkm_init_fields");
+    if (n < 0) return fail(h, LBKM_EINVAL, "n must be >= 0");
+    const void* K = model_ptr(h);
+    while (n >= GRAPH_CHUNK) {
+        cudaGraphExec_t& ex = h->graph[h->cur];
+        if (!ex) {
+            cudaGraph_t g;
+            CUDA_TRY(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+            int c = h->cur;
+            cudaError_t le = cudaSuccess;
+            for (int s = 0; s < GRAPH_CHUNK && le == cudaSuccess; s++) {
+                le = launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, c),
+                                 h->capture_stream);
+                c = 1 - c;
+            }
+            cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &g);
+            if (le != cudaSuccess || ce != cudaSuccess) {
+                if (ce == cudaSuccess) cudaGraphDestroy(g);
+                return fail(h, LBKM_ECUDA, "graph capture: %s",
+                            cudaGetErrorString(le != cudaSuccess ? le : ce));
+            }
+            cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess)
+                return fail(h, LBKM_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+        }
+        CUDA_TRY(h, cudaGraphLaunch(ex, h->stream));
+        n -= GRAPH_CHUNK;
+        h->host_steps += GRAPH_CHUNK;
+    }
+    for (; n > 0; n--) {
+        CUDA_TRY(h, launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, h->cur),
+                                h->stream));
+        h->cur = 1 - h->cur;
+        h->host_steps++;
+    }
+    return LBKM_OK;
+}
+
+lbkm_status lbkm_sync(lbkm_t h)
+{
+    if (!h) return LBKM_EINVAL;
+    return check_status(h);
+}
+
+int64_t lbkm_steps_taken(lbkm_t h) { return h ? h->host_steps : -1; }
+
+lbkm_status lbkm_macros(lbkm_t h, double* rho, double* ux, double* uy, double* T, double* p,
+                        double* lambda, int on_device)
+{
+    if (!h) return LBKM_EINVAL;
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_macros before lbkm_init_fields");
+    const size_t n = (size_t)h->nx * h->ny, nb = n * sizeof(double);
+    double* outs[6] = {rho, ux, uy, T, p, lambda};
+    double* dev[6] = {rho, ux, uy, T, p, lambda};
+    double* tmp = nullptr;
+    if (!on_device) {
+        CUDA_TRY(h, cudaMallocAsync((void**)&tmp, nb * 6, h->stream));
+        for (int k = 0; k < 6; k++) dev[k] = outs[k] ? tmp + k * n : nullptr;
+    }
+    CUDA_TRY(h, launch_macros(h->precision, h->Kd, h->buf[h->cur], dev[0], dev[1], dev[2], dev[3],
+                              dev[4], dev[5], h->stream));
+    if (!on_device) {
+        for (int k = 0; k < 6; k++)
+            if (outs[k])
+                CUDA_TRY(h, cudaMemcpyAsync(outs[k], dev[k], nb, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(h, cudaFreeAsync(tmp, h->stream));
+    }
+    return check_status(h);
+}
+
+static void record_to_global(const TneRecord& r, lbkm_tne_global* g)
+{
+    memcpy(g->sum, r.sum, sizeof(g->sum));
+    memcpy(g->abs_sum, r.abs_sum, sizeof(g->abs_sum));
+    memcpy(g->min, r.min, sizeof(g->min));
+    memcpy(g->max, r.max, sizeof(g->max));
+    g->d_sum = r.d_sum;
+    g->d2_sum = r.d2_sum;
+    g->step = r.step;
+}
+
+lbkm_status lbkm_tne(lbkm_t h, double* delta, lbkm_tne_global* g, int on_device)
+{
+    if (!h) return LBKM_EINVAL;
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_tne before lbkm_init_fields");
+    const size_t n = (size_t)h->nx * h->ny, nb = 16 * n * sizeof(double);
+    double* dd = delta;
+    double* tmp = nullptr;
+    if (delta && !on_device) {
+        CUDA_TRY(h, cudaMallocAsync((void**)&tmp, nb, h->stream));
+        dd = tmp;
+    }
+    CUDA_TRY(h, launch_tne(h->precision, h->Kd, h->buf[h->cur], dd, h->partials, h->tgrid, h->ctr,
+                           h->tne_out, h->p.dx * h->p.dy, h->stream));
+    if (tmp) {
+        CUDA_TRY(h, cudaMemcpyAsync(delta, tmp, nb, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(h, cudaFreeAsync(tmp, h->stream));
+    }
+    TneRecord r;
+    CUDA_TRY(h, cudaMemcpyAsync(&r, h->tne_out, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+    lbkm_status st = check_status(h);
+    if (st != LBKM_OK) return st;
+    if (g) record_to_global(r, g);
+    return LBKM_OK;
+}
+
+lbkm_status lbkm_tne_history(lbkm_t h, lbkm_tne_global* out, int32_t max_records, int32_t* n_out)
+{
+    if (!h || !n_out || (max_records > 0 && !out)) return LBKM_EINVAL;
+    *n_out = 0;
+    lbkm_status st = check_status(h);
+    if (st != LBKM_OK) return st;
+    DevCounters c;
+    CUDA_TRY(h, cudaMemcpy(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    const int cap = h->p.tne_capacity;
+    int64_t have = c.hist_count < cap ? c.hist_count : cap;
+    int64_t take = have < max_records ? have : max_records;
+    for (int64_t k = 0; k < take; k++) {
+        int64_t idx = (c.hist_count - have + k) % cap;
+        TneRecord r;
+        CUDA_TRY(h, cudaMemcpy(&r, h->hist + idx, sizeof(r), cudaMemcpyDeviceToHost));
+        record_to_global(r, out + k);
+    }
+    *n_out = (int32_t)take;
+    return LBKM_OK;
+}
+
+size_t lbkm_state_bytes(lbkm_t h)
+{
+    if (!h) return 0;
+    return (size_t)NPLANE * h->nx * h->ny * h->elem + sizeof(int64_t);
+}
+
+lbkm_status lbkm_get_state(lbkm_t h, void* dst, int on_device)
+{
+    if (!h || !dst) return LBKM_EINVAL;
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_get_state before lbkm_init_fields");
+    const size_t row = (size_t)h->nx * h->elem, plane = row * h->ny;
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int pl = 0; pl < NPLANE; pl++)
+        CUDA_TRY(h, cudaMemcpy2DAsync((char*)dst + pl * plane, row,
+                                      (char*)h->buf[h->cur] + pl * h->plane_elems * h->elem,
+                                      h->pitch * h->elem, row, h->ny, k, h->stream));
+    int64_t s = h->host_steps;
+    CUDA_TRY(h, cudaMemcpyAsync((char*)dst + NPLANE * plane, &s, sizeof(s),
+                                on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+                                h->stream));
+    return check_status(h);
+}
+
+lbkm_status lbkm_set_state(lbkm_t h, const void* src, int on_device)
+{
+    if (!h || !src) return LBKM_EINVAL;
+    const size_t row = (size_t)h->nx * h->elem, plane = row * h->ny;
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    h->cur = 0;
+    for (int pl = 0; pl < NPLANE; pl++)
+        CUDA_TRY(h, cudaMemcpy2DAsync((char*)h->buf[0] + pl * h->plane_elems * h->elem,
+                                      h->pitch * h->elem, (const char*)src + pl * plane, row, row,
+                                      h->ny, k, h->stream));
+    int64_t s = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&s, (const char*)src + NPLANE * plane, sizeof(s),
+                                on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                                h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    DevCounters c;
+    memset(&c, 0, sizeof(c));
+    c.step = s;
+    CUDA_TRY(h, cudaMemcpy(h->ctr, &c, sizeof(c), cudaMemcpyHostToDevice));
+    h->host_steps = s;
+    h->initialized = true;
+    return LBKM_OK;
+}
+
+const char* lbkm_last_error(lbkm_t h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+int32_t lbkm_version(void) { return 100; }
+
+} // extern "C"

@@ -1,0 +1,597 @@
+// kernels.cu -- CUDA kernels of the MRT-LBKM step for sm_103a.
+//
+// step_kernel: one fused forward-Euler stage. Each block walks tiles of
+// TX x TY cells (grid-stride loop, grid = SMs x resident blocks). Per tile it
+//   1. stages the 17 planes (f_1..f_16, lambda) of the tile plus a 2-cell halo
+//      in shared memory (coalesced row loads, boundary condition applied by
+//      index mapping);
+//   2. recovers rho, u, T of the tile and a 1-cell ring (needed by grad u) from
+//      the conserved moments, in FP64 or double-float;
+//   3. per cell: moments by butterflies + sector blocks, f_hat^eq, Delta_k,
+//      A_hat_8/9 (Eqs. (3)-(4)), reaction (Eq. (28)), C_hat (Eqs. (19)-(23)),
+//      Omega = M^-1 Omega_hat, NND flux differences of v_i f_i from shared
+//      memory, Euler update, lambda update; each f_i is read once from HBM and
+//      written once;
+//   4. when the TNE of this step is due, accumulates Delta_k statistics
+//      (warp shuffles, then FP64 per warp), and the last block to finish
+//      reduces the per-block partials in a fixed order (deterministic).
+// The plain FP64 form instantiates the same kernel with R = double.
+#include <float.h>
+
+#include "cell.cuh"
+#include "kernels.cuh"
+
+namespace lbk {
+
+namespace {
+
+constexpr int NSUM = 2 * TNE_K + 2; // sums: Delta, |Delta|, d, d^2
+constexpr int NMM = 2 * TNE_K;      // min, max
+
+template <typename R, bool TWO_D, int TX, int TY>
+struct Cfg {
+    static constexpr int H = TWO_D ? 2 : 0;  // halo rows of f (NND radius)
+    static constexpr int H1 = TWO_D ? 1 : 0; // ring rows of macros (grad u)
+    static constexpr int SW = TX + 4, SH = TY + 2 * H, PS = SW * SH;
+    static constexpr int RW = TX + 2, RH = TY + 2 * H1, RS = RW * RH;
+    static constexpr int NT = TX * TY, NW = NT / 32;
+    static constexpr size_t off_mac = ((size_t)NPLANE * PS * sizeof(R) + 15) / 16 * 16;
+    static constexpr size_t off_Td = off_mac + 4 * RS * sizeof(R);
+    static constexpr size_t off_off = (off_Td + RS * sizeof(double) + 15) / 16 * 16;
+    static constexpr size_t off_tsum = off_off;
+    static constexpr size_t off_tmm = off_tsum + (size_t)NW * NSUM * sizeof(double);
+    static constexpr size_t smem = off_tmm + (size_t)NW * NMM * sizeof(R);
+};
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename R>
+__device__ __forceinline__ R warp_min(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = rmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <typename R>
+__device__ __forceinline__ R warp_max(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = rmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename R>
+__device__ __forceinline__ R big_value();
+template <>
+__device__ __forceinline__ float big_value<float>() { return FLT_MAX; }
+template <>
+__device__ __forceinline__ double big_value<double>() { return DBL_MAX; }
+
+// Last block of a launch: reduce the per-block partials (fixed order) into a
+// TNE record. Called by every thread of that block.
+__device__ void finish_tne(const double* partials, int nblocks, TneRecord* rec, int64_t step,
+                           double area)
+{
+    __shared__ double res[TNE_PART];
+    for (int q = threadIdx.x; q < TNE_PART; q += blockDim.x) {
+        double acc;
+        if (q < 2 * TNE_K || q >= 4 * TNE_K) {
+            acc = 0.0;
+            for (int b = 0; b < nblocks; b++) acc += __ldcg(partials + (size_t)b * TNE_PART + q);
+            acc *= area;
+        } else if (q < 3 * TNE_K) {
+            acc = DBL_MAX;
+            for (int b = 0; b < nblocks; b++)
+                acc = fmin(acc, __ldcg(partials + (size_t)b * TNE_PART + q));
+        } else {
+            acc = -DBL_MAX;
+            for (int b = 0; b < nblocks; b++)
+                acc = fmax(acc, __ldcg(partials + (size_t)b * TNE_PART + q));
+        }
+        res[q] = acc;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 16; k += blockDim.x) {
+        bool z = k < 4;
+        rec->sum[k] = z ? 0.0 : res[k - 4];
+        rec->abs_sum[k] = z ? 0.0 : res[TNE_K + k - 4];
+        rec->min[k] = z ? 0.0 : res[2 * TNE_K + k - 4];
+        rec->max[k] = z ? 0.0 : res[3 * TNE_K + k - 4];
+    }
+    if (threadIdx.x == 0) {
+        rec->d_sum = res[4 * TNE_K];
+        rec->d2_sum = res[4 * TNE_K + 1];
+        rec->step = step;
+    }
+}
+
+template <typename R, int REC, bool TWO_D, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+    step_kernel(const ModelConst<R> K, const StepLaunch a)
+{
+    using C = Cfg<R, TWO_D, TX, TY>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    R* sf = reinterpret_cast<R*>(smem);
+    R* smac = reinterpret_cast<R*>(smem + C::off_mac); // rho, ux, uy, T  [4][RH][RW]
+    double* sTd = reinterpret_cast<double*>(smem + C::off_Td);
+    double* tsum = reinterpret_cast<double*>(smem + C::off_tsum);
+    R* tmm = reinterpret_cast<R*>(smem + C::off_tmm);
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = tid / TX;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nx = K.nx, ny = K.ny, pitch = K.pitch;
+    const int64_t plane = K.plane;
+    const R* __restrict__ in = static_cast<const R*>(a.in);
+    R* __restrict__ out = static_cast<R*>(a.out);
+
+    const int64_t step = a.ctr->step;
+    const bool do_tne = a.tne_every > 0 && (step % a.tne_every) == 0;
+    if (do_tne) {
+        for (int i = tid; i < C::NW * NSUM; i += C::NT) tsum[i] = 0.0;
+        for (int i = tid; i < C::NW * NMM; i += C::NT)
+            tmm[i] = (i % NMM) < TNE_K ? big_value<R>() : -big_value<R>();
+    }
+    int bad = 0;
+
+    const int tiles_x = (nx + TX - 1) / TX;
+    const int tiles_y = (ny + TY - 1) / TY;
+    const int ntiles = tiles_x * tiles_y;
+
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
+        __syncthreads();
+        // 1. stage f and lambda with halo
+        for (int idx = tid; idx < NPLANE * C::PS; idx += C::NT) {
+            const int p = idx / C::PS;
+            const int rem = idx - p * C::PS;
+            const int r = rem / C::SW, c = rem - r * C::SW;
+            const int gx = map_index(x0 - 2 + c, nx, K.bc_x);
+            const int gy = TWO_D ? map_index(y0 - C::H + r, ny, K.bc_y) : y0;
+            sf[idx] = in[p * plane + (int64_t)gy * pitch + gx];
+        }
+        __syncthreads();
+        // 2. macros of the tile and its ring
+        for (int idx = tid; idx < C::RS; idx += C::NT) {
+            const int r = idx / C::RW, c = idx - r * C::RW;
+            const int s = (r + C::H - C::H1) * C::SW + c + 1;
+            R fl[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) fl[i] = sf[i * C::PS + s];
+            double rho, ux, uy, T;
+            if constexpr (REC == 1)
+                recover_df32(K.cd, K.wd, K.inv_DId, reinterpret_cast<const float*>(fl), rho, ux,
+                             uy, T);
+            else
+                recover_f64(K.cd, K.wd, K.inv_DId, fl, rho, ux, uy, T);
+            smac[idx] = (R)rho;
+            smac[C::RS + idx] = (R)ux;
+            smac[2 * C::RS + idx] = (R)uy;
+            smac[3 * C::RS + idx] = (R)T;
+            sTd[idx] = T;
+        }
+        __syncthreads();
+
+        // 3. the cell update
+        const int gx = x0 + lx, gy = y0 + ly;
+        const bool active = gx < nx && gy < ny;
+        R Dk[TNE_K];
+        if (active) {
+            const int c0 = (ly + C::H) * C::SW + lx + 2;
+            const int m0 = (ly + C::H1) * C::RW + lx + 1;
+            R f[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) f[i] = sf[i * C::PS + c0];
+            const R lam0 = sf[16 * C::PS + c0];
+            const R rho = smac[m0], ux = smac[C::RS + m0], uy = smac[2 * C::RS + m0];
+            const R T = smac[3 * C::RS + m0];
+            const double Td = sTd[m0];
+            if (!(rho > R(0)) || !(Td > 0.0) || !isfinite(ux + uy + Td + (double)rho)) bad = 1;
+
+            R m[16], q[16];
+            forward_moments(K, f, m);
+            feq_moments(K.DI, rho, ux, uy, T, q);
+#pragma unroll
+            for (int k = 0; k < TNE_K; k++) Dk[k] = m[k + 4] - q[k + 4];
+
+            const R* sux = smac + C::RS;
+            const R* suy = smac + 2 * C::RS;
+            const R dux_dx = (sux[m0 + 1] - sux[m0 - 1]) * K.half_inv_dx;
+            const R duy_dx = (suy[m0 + 1] - suy[m0 - 1]) * K.half_inv_dx;
+            R dux_dy = R(0), duy_dy = R(0);
+            if constexpr (TWO_D) {
+                dux_dy = (sux[m0 + C::RW] - sux[m0 - C::RW]) * K.half_inv_dy;
+                duy_dy = (suy[m0 + C::RW] - suy[m0 - C::RW]) * K.half_inv_dy;
+            }
+            const R theta = (dux_dx + duy_dy) * K.inv_DI;
+            const R shear = duy_dx + dux_dy;
+            const R rT = rho * T;
+            const R A8 = rT * K.A8c * (R(4) * ux * (dux_dx - theta) + R(2) * uy * shear);
+            const R A9 = rT * K.A9c * (R(4) * uy * (duy_dy - theta) + R(2) * ux * shear);
+
+            R dlam = R(0);
+            if (Td > K.T_igd) dlam = reaction_increment(lam0, K.omega1 * rT, K.omega2 * rT, K.dt);
+            const R cr = dlam * K.chem;
+
+            R dq[16], Om[16], W[16];
+            dfeq_dT(K.DI, rho, ux, uy, T, dq);
+            Om[0] = Om[1] = Om[2] = R(0);
+            Om[3] = dq[3] * cr;
+#pragma unroll
+            for (int k = 4; k < 16; k++) Om[k] = fma(-K.S[k], Dk[k - 4], dq[k] * cr);
+            Om[7] += A8;
+            Om[8] += A9;
+            inverse_moments(K, Om, W);
+
+            // NND flux differences (compile-time upwind side per velocity)
+            const R* s0 = sf + c0;
+#define FV(i, ox, oy) s0[(i) * C::PS + (oy) * C::SW + (ox)]
+#define PX(i) nnd_pos(FV(i, -2, 0), FV(i, -1, 0), FV(i, 0, 0), FV(i, 1, 0))
+#define NX(i) nnd_neg(FV(i, -1, 0), FV(i, 0, 0), FV(i, 1, 0), FV(i, 2, 0))
+#define PY(i) nnd_pos(FV(i, 0, -2), FV(i, 0, -1), FV(i, 0, 0), FV(i, 0, 1))
+#define NY(i) nnd_neg(FV(i, 0, -1), FV(i, 0, 0), FV(i, 0, 1), FV(i, 0, 2))
+            R adv[16];
+#pragma unroll
+            for (int o = 0; o < 2; o++) { // axis orbits 0, 2
+                const int i0 = 8 * o;
+                const R cx = K.c[2 * o] * K.inv_dx, cy = K.c[2 * o] * K.inv_dy;
+                adv[i0 + 0] = cx * PX(i0 + 0);
+                adv[i0 + 2] = -cx * NX(i0 + 2);
+                if constexpr (TWO_D) {
+                    adv[i0 + 1] = cy * PY(i0 + 1);
+                    adv[i0 + 3] = -cy * NY(i0 + 3);
+                } else {
+                    adv[i0 + 1] = adv[i0 + 3] = R(0);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 2; o++) { // diagonal orbits 1, 3
+                const int i0 = 4 + 8 * o;
+                const R cx = K.c[2 * o + 1] * K.inv_dx, cy = K.c[2 * o + 1] * K.inv_dy;
+                R x0p = cx * PX(i0 + 0), x1n = cx * NX(i0 + 1), x2n = cx * NX(i0 + 2),
+                  x3p = cx * PX(i0 + 3);
+                R y0p = R(0), y1p = R(0), y2n = R(0), y3n = R(0);
+                if constexpr (TWO_D) {
+                    y0p = cy * PY(i0 + 0);
+                    y1p = cy * PY(i0 + 1);
+                    y2n = cy * NY(i0 + 2);
+                    y3n = cy * NY(i0 + 3);
+                }
+                adv[i0 + 0] = x0p + y0p;
+                adv[i0 + 1] = y1p - x1n;
+                adv[i0 + 2] = -(x2n + y2n);
+                adv[i0 + 3] = x3p - y3n;
+            }
+            const int64_t g = (int64_t)gy * pitch + gx;
+#pragma unroll
+            for (int i = 0; i < 16; i++) out[i * plane + g] = f[i] + K.dt * (W[i] - adv[i]);
+
+            // lambda: u . grad(lambda) with NND interface values, reaction, clamp
+            R la = ux > R(0) ? ux * PX(16) : (ux < R(0) ? ux * NX(16) : R(0));
+            la *= K.inv_dx;
+            if constexpr (TWO_D) {
+                R lb = uy > R(0) ? uy * PY(16) : (uy < R(0) ? uy * NY(16) : R(0));
+                la += lb * K.inv_dy;
+            }
+#undef FV
+#undef PX
+#undef NX
+#undef PY
+#undef NY
+            R ln = lam0 - K.dt * la + dlam;
+            ln = ln < R(0) ? R(0) : (ln > R(1) ? R(1) : ln);
+            out[16 * plane + g] = ln;
+        }
+
+        // 4. TNE statistics of this tile (all lanes take part in the shuffles)
+        if (do_tne) {
+            R d2 = R(0);
+#pragma unroll
+            for (int k = 0; k < TNE_K; k++) {
+                if (!active) Dk[k] = R(0);
+                d2 += Dk[k] * Dk[k];
+            }
+#pragma unroll
+            for (int k = 0; k < TNE_K; k++) {
+                R s = warp_sum(Dk[k]);
+                R sa = warp_sum(Dk[k] < R(0) ? -Dk[k] : Dk[k]);
+                R mn = warp_min(active ? Dk[k] : big_value<R>());
+                R mx = warp_max(active ? Dk[k] : -big_value<R>());
+                if (lane == 0) {
+                    tsum[warp * NSUM + k] += (double)s;
+                    tsum[warp * NSUM + TNE_K + k] += (double)sa;
+                    tmm[warp * NMM + k] = rmin(tmm[warp * NMM + k], mn);
+                    tmm[warp * NMM + TNE_K + k] = rmax(tmm[warp * NMM + TNE_K + k], mx);
+                }
+            }
+            R sd = warp_sum(sqrt(d2)), sd2 = warp_sum(d2);
+            if (lane == 0) {
+                tsum[warp * NSUM + 2 * TNE_K] += (double)sd;
+                tsum[warp * NSUM + 2 * TNE_K + 1] += (double)sd2;
+            }
+        }
+    }
+
+    // end of step: status, TNE partials, arrival count; the last block finishes
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(&a.ctr->status, 1);
+    if (do_tne) {
+        double* part = a.partials + (size_t)blockIdx.x * TNE_PART;
+        for (int q = tid; q < NSUM; q += C::NT) {
+            double s = 0.0;
+            for (int w = 0; w < C::NW; w++) s += tsum[w * NSUM + q];
+            part[q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K)] = s;
+        }
+        for (int q = tid; q < NMM; q += C::NT) {
+            R v = tmm[q];
+            for (int w = 1; w < C::NW; w++)
+                v = q < TNE_K ? rmin(v, tmm[w * NMM + q]) : rmax(v, tmm[w * NMM + q]);
+            part[2 * TNE_K + q] = (double)v;
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    __shared__ unsigned int s_last;
+    if (tid == 0) s_last = (atomicAdd(&a.ctr->arrivals, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (do_tne) {
+            const int64_t slot = a.ctr->hist_count % a.hist_cap;
+            finish_tne(a.partials, gridDim.x, a.hist + slot, step, a.cell_area);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (do_tne) a.ctr->hist_count += 1;
+            a.ctr->step = step + 1;
+            a.ctr->arrivals = 0u;
+        }
+    }
+}
+
+template <typename R, int REC, bool TWO_D, int TX, int TY>
+struct StepKernel {
+    using C = Cfg<R, TWO_D, TX, TY>;
+    // opt in to the dynamic shared memory once per process, before any capture
+    static cudaError_t prepare()
+    {
+        static cudaError_t done = cudaFuncSetAttribute(
+            step_kernel<R, REC, TWO_D, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)C::smem);
+        return done;
+    }
+    static int grid(int nx, int ny)
+    {
+        static int per_sm = -1, sms = -1;
+        if (per_sm < 0) {
+            if (prepare() != cudaSuccess) return -1;
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per_sm, step_kernel<R, REC, TWO_D, TX, TY>, C::NT, C::smem) != cudaSuccess)
+                return -1;
+            if (per_sm < 1) per_sm = 1;
+        }
+        long tiles = (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+        long g = (long)per_sm * sms;
+        return (int)(tiles < g ? tiles : g);
+    }
+    static cudaError_t launch(const void* K, const StepLaunch& a, cudaStream_t s)
+    {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+        step_kernel<R, REC, TWO_D, TX, TY><<<a.grid, C::NT, C::smem, s>>>(
+            *static_cast<const ModelConst<R>*>(K), a);
+        return cudaGetLastError();
+    }
+};
+
+// tile shapes: 2-D 32 x 8 cells, 1-D 64 cells
+template <typename R, int REC>
+using K2D = StepKernel<R, REC, true, 32, 8>;
+template <typename R, int REC>
+using K1D = StepKernel<R, REC, false, 64, 1>;
+
+// ------------------------------------------------------------ init, macros, TNE
+template <typename R>
+__global__ void init_kernel(const ModelConst<double> K, const double* rho, const double* ux,
+                            const double* uy, const double* T, const double* lam, R* state)
+{
+    const int64_t n = (int64_t)K.nx * K.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(c / K.nx), x = (int)(c - (int64_t)y * K.nx);
+        double q[16], f[16];
+        feq_moments(K.DI, rho[c], ux[c], uy[c], T[c], q);
+        inverse_moments(K, q, f);
+        const int64_t g = (int64_t)y * K.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 16; i++) state[i * K.plane + g] = (R)f[i];
+        state[16 * K.plane + g] = (R)(lam ? lam[c] : 0.0);
+    }
+}
+
+template <typename R>
+__global__ void macros_kernel(const ModelConst<double> K, const R* state, double* rho,
+                              double* ux, double* uy, double* T, double* p, double* lam)
+{
+    const int64_t n = (int64_t)K.nx * K.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(c / K.nx), x = (int)(c - (int64_t)y * K.nx);
+        const int64_t g = (int64_t)y * K.pitch + x;
+        R f[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) f[i] = state[i * K.plane + g];
+        double r, u, v, t;
+        recover_f64(K.cd, K.wd, K.inv_DId, f, r, u, v, t);
+        if (rho) rho[c] = r;
+        if (ux) ux[c] = u;
+        if (uy) uy[c] = v;
+        if (T) T[c] = t;
+        if (p) p[c] = r * t;
+        if (lam) lam[c] = (double)state[16 * K.plane + g];
+    }
+}
+
+constexpr int TNE_THREADS = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(TNE_THREADS)
+    tne_kernel(const ModelConst<double> K, const R* state, double* delta, double* partials,
+               DevCounters* ctr, TneRecord* out, double area)
+{
+    __shared__ double ssum[TNE_THREADS / 32][NSUM];
+    __shared__ double smm[TNE_THREADS / 32][NMM];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc[NSUM], mn[TNE_K], mx[TNE_K];
+    for (int q = 0; q < NSUM; q++) acc[q] = 0.0;
+    for (int k = 0; k < TNE_K; k++) mn[k] = DBL_MAX, mx[k] = -DBL_MAX;
+    const int64_t n = (int64_t)K.nx * K.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(c / K.nx), x = (int)(c - (int64_t)y * K.nx);
+        const int64_t g = (int64_t)y * K.pitch + x;
+        double f[16], m[16], q[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) f[i] = (double)state[i * K.plane + g];
+        forward_moments(K, f, m);
+        const double r = m[0], u = m[1] / r, v = m[2] / r;
+        const double t = (m[3] / r - (u * u + v * v)) * K.inv_DId;
+        feq_moments(K.DI, r, u, v, t, q);
+        double d2 = 0.0;
+        for (int k = 0; k < 16; k++) {
+            double D = k < 4 ? 0.0 : m[k] - q[k];
+            if (delta) delta[k * n + c] = D;
+            if (k >= 4) {
+                acc[k - 4] += D;
+                acc[TNE_K + k - 4] += fabs(D);
+                mn[k - 4] = fmin(mn[k - 4], D);
+                mx[k - 4] = fmax(mx[k - 4], D);
+                d2 += D * D;
+            }
+        }
+        acc[2 * TNE_K] += sqrt(d2);
+        acc[2 * TNE_K + 1] += d2;
+    }
+    for (int q = 0; q < NSUM; q++) {
+        double s = warp_sum(acc[q]);
+        if (lane == 0) ssum[warp][q] = s;
+    }
+    for (int k = 0; k < TNE_K; k++) {
+        double a = warp_min(mn[k]), b = warp_max(mx[k]);
+        if (lane == 0) smm[warp][k] = a, smm[warp][TNE_K + k] = b;
+    }
+    __syncthreads();
+    double* part = partials + (size_t)blockIdx.x * TNE_PART;
+    if (threadIdx.x < NSUM) {
+        double s = 0.0;
+        for (int w = 0; w < TNE_THREADS / 32; w++) s += ssum[w][threadIdx.x];
+        const int q = threadIdx.x;
+        part[q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K)] = s;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + NMM) {
+        const int q = threadIdx.x - 32;
+        double v = smm[0][q];
+        for (int w = 1; w < TNE_THREADS / 32; w++)
+            v = q < TNE_K ? fmin(v, smm[w][q]) : fmax(v, smm[w][q]);
+        part[2 * TNE_K + q] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ unsigned int s_last;
+    if (threadIdx.x == 0) s_last = (atomicAdd(&ctr->arrivals, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finish_tne(partials, gridDim.x, out, ctr->step, area);
+        __syncthreads();
+        if (threadIdx.x == 0) ctr->arrivals = 0u;
+    }
+}
+
+int sm_count()
+{
+    static int sms = -1;
+    if (sms < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return sms;
+}
+
+int elementwise_grid(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)sm_count() * 16;
+    return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
+} // namespace
+
+int step_grid(int precision, int recovery, bool two_d, int nx, int ny)
+{
+    if (precision == 0)
+        return two_d ? K2D<double, 0>::grid(nx, ny) : K1D<double, 0>::grid(nx, ny);
+    if (recovery == 1)
+        return two_d ? K2D<float, 1>::grid(nx, ny) : K1D<float, 1>::grid(nx, ny);
+    return two_d ? K2D<float, 0>::grid(nx, ny) : K1D<float, 0>::grid(nx, ny);
+}
+
+cudaError_t launch_step(int precision, int recovery, bool two_d, const void* K,
+                        const StepLaunch& a, cudaStream_t s)
+{
+    if (precision == 0)
+        return two_d ? K2D<double, 0>::launch(K, a, s) : K1D<double, 0>::launch(K, a, s);
+    if (recovery == 1)
+        return two_d ? K2D<float, 1>::launch(K, a, s) : K1D<float, 1>::launch(K, a, s);
+    return two_d ? K2D<float, 0>::launch(K, a, s) : K1D<float, 0>::launch(K, a, s);
+}
+
+cudaError_t launch_init(int precision, const ModelConst<double>& Kd, const double* rho,
+                        const double* ux, const double* uy, const double* T, const double* lam,
+                        void* state, cudaStream_t s)
+{
+    const int64_t n = (int64_t)Kd.nx * Kd.ny;
+    const int g = elementwise_grid(n, 256);
+    if (precision == 0)
+        init_kernel<double><<<g, 256, 0, s>>>(Kd, rho, ux, uy, T, lam, (double*)state);
+    else
+        init_kernel<float><<<g, 256, 0, s>>>(Kd, rho, ux, uy, T, lam, (float*)state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macros(int precision, const ModelConst<double>& Kd, const void* state,
+                          double* rho, double* ux, double* uy, double* T, double* p,
+                          double* lam, cudaStream_t s)
+{
+    const int64_t n = (int64_t)Kd.nx * Kd.ny;
+    const int g = elementwise_grid(n, 256);
+    if (precision == 0)
+        macros_kernel<double><<<g, 256, 0, s>>>(Kd, (const double*)state, rho, ux, uy, T, p, lam);
+    else
+        macros_kernel<float><<<g, 256, 0, s>>>(Kd, (const float*)state, rho, ux, uy, T, p, lam);
+    return cudaGetLastError();
+}
+
+int tne_grid(int nx, int ny) { return elementwise_grid((int64_t)nx * ny, TNE_THREADS); }
+
+cudaError_t launch_tne(int precision, const ModelConst<double>& Kd, const void* state,
+                       double* delta, double* partials, int grid, DevCounters* ctr,
+                       TneRecord* out, double area, cudaStream_t s)
+{
+    if (precision == 0)
+        tne_kernel<double><<<grid, TNE_THREADS, 0, s>>>(Kd, (const double*)state, delta,
+                                                        partials, ctr, out, area);
+    else
+        tne_kernel<float><<<grid, TNE_THREADS, 0, s>>>(Kd, (const float*)state, delta, partials,
+                                                       ctr, out, area);
+    return cudaGetLastError();
+}
+
+} // namespace lbk

@@ -1,0 +1,57 @@
+// kernels.cuh -- launch interface between the C ABI and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "model.h"
+
+namespace lbk {
+
+// Device-side bookkeeping shared by the kernels of one handle.
+struct DevCounters {
+    int64_t step;          // steps taken (advanced by the last block of each step)
+    int64_t hist_count;    // TNE records written so far
+    unsigned int arrivals; // blocks of the current launch that finished (reset by the last)
+    int status;            // bit 0: non-finite or non-positive rho or T seen
+    int pad;
+};
+
+// One on-the-fly TNE record, laid out like lbkm_tne_global.
+struct TneRecord {
+    double sum[16], abs_sum[16], min[16], max[16];
+    double d_sum, d2_sum;
+    int64_t step;
+};
+
+struct StepLaunch {
+    const void* in;      // state at t_n  [17][ny][pitch]
+    void* out;           // state at t_n+1
+    double* partials;    // [grid][TNE_PART]
+    DevCounters* ctr;
+    TneRecord* hist;     // ring of hist_cap records
+    int hist_cap;
+    int tne_every;       // 0 = off
+    int grid;            // blocks launched
+    double cell_area;    // dx * dy
+};
+
+// precision: 0 = FP64, 1 = FP32; recovery: 0 = FP64, 1 = double-float (FP32 only)
+cudaError_t launch_step(int precision, int recovery, bool two_d, const void* K,
+                        const StepLaunch& a, cudaStream_t s);
+// Blocks to launch for a step on this grid (multiple of the SM count times the
+// resident blocks per SM, capped by the number of tiles).
+int step_grid(int precision, int recovery, bool two_d, int nx, int ny);
+
+cudaError_t launch_init(int precision, const ModelConst<double>& Kd, const double* rho,
+                        const double* ux, const double* uy, const double* T, const double* lam,
+                        void* state, cudaStream_t s);
+cudaError_t launch_macros(int precision, const ModelConst<double>& Kd, const void* state,
+                          double* rho, double* ux, double* uy, double* T, double* p,
+                          double* lam, cudaStream_t s);
+// TNE fields (optional) and grid-wide record of a state, all FP64.
+cudaError_t launch_tne(int precision, const ModelConst<double>& Kd, const void* state,
+                       double* delta, double* partials, int grid, DevCounters* ctr,
+                       TneRecord* out, double cell_area, cudaStream_t s);
+int tne_grid(int nx, int ny);
+
+} // namespace lbk

@@ -1,0 +1,302 @@
+"""Python binding of the C ABI in include/lbkm.h (argument marshalling only).
+
+Every step of the model runs in the CUDA library ``_lib/libpaper_lbkm.so``;
+this module converts arguments (NumPy arrays for host data, torch CUDA tensors
+for device data, torch streams) and raises on error codes. There is no CPU
+fallback: if the library is missing or fails to load, importing the binding
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpaper_lbkm.so")
+
+F64, F32 = 0, 1
+RECOVER_F64, RECOVER_DF32 = 0, 1
+BC_PERIODIC, BC_ZERO_GRADIENT = 0, 1
+
+STATUS = {0: "LBKM_OK", 1: "LBKM_EINVAL", 2: "LBKM_ENOMEM", 3: "LBKM_ECUDA",
+          4: "LBKM_ESINGULAR", 5: "LBKM_EUNSTABLE", 6: "LBKM_ETIMEOUT", 7: "LBKM_ESTATE"}
+
+EXPORTED = ["lbkm_default_params", "lbkm_create", "lbkm_destroy", "lbkm_set_stream",
+            "lbkm_init_fields", "lbkm_step", "lbkm_sync", "lbkm_steps_taken", "lbkm_macros",
+            "lbkm_tne", "lbkm_tne_history", "lbkm_state_bytes", "lbkm_get_state",
+            "lbkm_set_state", "lbkm_last_error", "lbkm_version"]
+
+
+class LbkmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("recovery", ctypes.c_int32),
+        ("gamma", ctypes.c_double), ("Pr", ctypes.c_double),
+        ("orbit_kind", ctypes.c_int32 * 4), ("orbit_speed", ctypes.c_double * 4),
+        ("orbit_eta", ctypes.c_double * 4), ("S", ctypes.c_double * 16),
+        ("Q", ctypes.c_double), ("omega1", ctypes.c_double), ("omega2", ctypes.c_double),
+        ("T_ig", ctypes.c_double),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dt", ctypes.c_double),
+        ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+        ("tne_every", ctypes.c_int32), ("tne_capacity", ctypes.c_int32),
+    ]
+
+
+class TneGlobal(ctypes.Structure):
+    _fields_ = [("sum", ctypes.c_double * 16), ("abs_sum", ctypes.c_double * 16),
+                ("min", ctypes.c_double * 16), ("max", ctypes.c_double * 16),
+                ("d_sum", ctypes.c_double), ("d2_sum", ctypes.c_double),
+                ("step", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {"sum": np.array(self.sum[:]), "abs_sum": np.array(self.abs_sum[:]),
+                "min": np.array(self.min[:]), "max": np.array(self.max[:]),
+                "d_sum": self.d_sum, "d2_sum": self.d2_sum, "step": int(self.step)}
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("CUDA library %s is missing: run __graft_entry__.build() "
+                          "(nvcc, sm_103a) first; there is no CPU fallback" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    H = ctypes.c_void_p
+    lib.lbkm_default_params.argtypes = [ctypes.POINTER(Params)]
+    lib.lbkm_default_params.restype = None
+    lib.lbkm_create.argtypes = [ctypes.POINTER(Params), _vp, ctypes.POINTER(H)]
+    lib.lbkm_destroy.argtypes = [H]
+    lib.lbkm_destroy.restype = None
+    lib.lbkm_set_stream.argtypes = [H, _vp]
+    lib.lbkm_init_fields.argtypes = [H, _vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+    lib.lbkm_step.argtypes = [H, ctypes.c_int64]
+    lib.lbkm_sync.argtypes = [H]
+    lib.lbkm_steps_taken.argtypes = [H]
+    lib.lbkm_steps_taken.restype = ctypes.c_int64
+    lib.lbkm_macros.argtypes = [H] + [_vp] * 6 + [ctypes.c_int]
+    lib.lbkm_tne.argtypes = [H, _vp, ctypes.POINTER(TneGlobal), ctypes.c_int]
+    lib.lbkm_tne_history.argtypes = [H, ctypes.POINTER(TneGlobal), ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_int32)]
+    lib.lbkm_state_bytes.argtypes = [H]
+    lib.lbkm_state_bytes.restype = ctypes.c_size_t
+    lib.lbkm_get_state.argtypes = [H, _vp, ctypes.c_int]
+    lib.lbkm_set_state.argtypes = [H, _vp, ctypes.c_int]
+    lib.lbkm_last_error.argtypes = [H]
+    lib.lbkm_last_error.restype = ctypes.c_char_p
+    lib.lbkm_version.restype = ctypes.c_int32
+    for name in ("lbkm_create", "lbkm_set_stream", "lbkm_init_fields", "lbkm_step", "lbkm_sync",
+                 "lbkm_macros", "lbkm_tne", "lbkm_tne_history", "lbkm_get_state",
+                 "lbkm_set_state"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().lbkm_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k in ("orbit_kind", "orbit_speed", "orbit_eta", "S"):
+            arr = getattr(p, k)
+            vals = np.broadcast_to(np.asarray(v), (len(arr),))
+            for i in range(len(arr)):
+                arr[i] = vals[i].item()
+        elif k == "bc":
+            p.bc_x, p.bc_y = v
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+class Solver:
+    """One MRT-LBKM grid on the GPU (a handle of the C ABI)."""
+
+    def __init__(self, params: Params = None, stream=None, **kw):
+        lib = load()
+        self._lib = lib
+        self.params = params if params is not None else default_params(**kw)
+        self.nx, self.ny = int(self.params.nx), int(self.params.ny)
+        h = ctypes.c_void_p()
+        rc = lib.lbkm_create(ctypes.byref(self.params), ctypes.c_void_p(_stream_ptr(stream)),
+                             ctypes.byref(h))
+        if rc != 0:
+            raise LbkmError(rc, lib.lbkm_last_error(None).decode())
+        self._h = h
+
+    # ------------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise LbkmError(rc, self._lib.lbkm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbkm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------
+    def _field(self, a, keep):
+        shape = (self.ny, self.nx)
+        if a is None:
+            return None, 0
+        if _is_torch(a):
+            import torch
+            t = a.to(dtype=torch.float64).expand(shape).contiguous()
+            keep.append(t)
+            return t.data_ptr(), 1 if t.is_cuda else 0
+        arr = np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), shape))
+        keep.append(arr)
+        return arr.ctypes.data, 0
+
+    def init_fields(self, rho, ux, uy, T, lam=None):
+        keep = []
+        ptrs, dev = [], set()
+        for a in (rho, ux, uy, T, lam):
+            p, d = self._field(a, keep)
+            ptrs.append(p)
+            if a is not None:
+                dev.add(d)
+        if len(dev) != 1:
+            raise ValueError("fields must be all host arrays or all CUDA tensors")
+        self._check(self._lib.lbkm_init_fields(self._h, *[ctypes.c_void_p(p) for p in ptrs],
+                                               dev.pop()))
+
+    def step(self, n=1):
+        self._check(self._lib.lbkm_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._lib.lbkm_sync(self._h))
+
+    @property
+    def steps_taken(self):
+        return int(self._lib.lbkm_steps_taken(self._h))
+
+    def macros(self, device=False, out=None):
+        """rho, ux, uy, T, p, lambda of the current state; with out (a dict of
+        preallocated host or CUDA tensors/arrays) the results land there."""
+        names = ("rho", "ux", "uy", "T", "p", "lam")
+        if out is not None:
+            ptrs = [(out[k].data_ptr() if _is_torch(out[k]) else out[k].ctypes.data)
+                    if k in out else None for k in names]
+            self._check(self._lib.lbkm_macros(self._h, *[ctypes.c_void_p(p) for p in ptrs],
+                                              1 if device else 0))
+            return out
+        if device:
+            import torch
+            out = {k: torch.empty((self.ny, self.nx), dtype=torch.float64, device="cuda")
+                   for k in names}
+            ptrs = [out[k].data_ptr() for k in names]
+        else:
+            out = {k: np.empty((self.ny, self.nx)) for k in names}
+            ptrs = [out[k].ctypes.data for k in names]
+        self._check(self._lib.lbkm_macros(self._h, *[ctypes.c_void_p(p) for p in ptrs],
+                                          1 if device else 0))
+        return out
+
+    def tne(self, fields=True, device=False):
+        g = TneGlobal()
+        delta = None
+        ptr = None
+        if fields:
+            if device:
+                import torch
+                delta = torch.empty((16, self.ny, self.nx), dtype=torch.float64, device="cuda")
+                ptr = delta.data_ptr()
+            else:
+                delta = np.empty((16, self.ny, self.nx))
+                ptr = delta.ctypes.data
+        self._check(self._lib.lbkm_tne(self._h, ctypes.c_void_p(ptr), ctypes.byref(g),
+                                       1 if device else 0))
+        return delta, g.as_dict()
+
+    def tne_history(self, max_records=None):
+        cap = int(self.params.tne_capacity) if max_records is None else int(max_records)
+        buf = (TneGlobal * max(cap, 1))()
+        n = ctypes.c_int32()
+        self._check(self._lib.lbkm_tne_history(self._h, buf, cap, ctypes.byref(n)))
+        return [buf[i].as_dict() for i in range(n.value)]
+
+    def state_bytes(self):
+        return int(self._lib.lbkm_state_bytes(self._h))
+
+    def get_state(self, device=False):
+        """State snapshot as bytes: a NumPy uint8 array, or a CUDA uint8 tensor."""
+        if device:
+            import torch
+            buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device="cuda")
+            self._check(self._lib.lbkm_get_state(self._h, ctypes.c_void_p(buf.data_ptr()), 1))
+            return buf
+        buf = np.empty(self.state_bytes(), np.uint8)
+        self._check(self._lib.lbkm_get_state(self._h, ctypes.c_void_p(buf.ctypes.data), 0))
+        return buf
+
+    def set_state(self, buf):
+        if _is_torch(buf):
+            if buf.numel() != self.state_bytes():
+                raise ValueError("state buffer has the wrong size")
+            self._check(self._lib.lbkm_set_state(self._h, ctypes.c_void_p(buf.data_ptr()), 1))
+            return
+        buf = np.ascontiguousarray(buf, np.uint8)
+        if buf.size != self.state_bytes():
+            raise ValueError("state buffer has %d bytes, expected %d" % (buf.size,
+                                                                        self.state_bytes()))
+        self._check(self._lib.lbkm_set_state(self._h, ctypes.c_void_p(buf.ctypes.data), 0))
+
+    def planes_device(self):
+        """Current f_1..f_16 and lambda as a CUDA tensor [17, ny, nx] in the state's dtype."""
+        import torch
+        raw = self.get_state(device=True)
+        dt = torch.float64 if self.params.precision == F64 else torch.float32
+        n = 17 * self.ny * self.nx * (8 if dt == torch.float64 else 4)
+        return raw[:n].view(dt).view(17, self.ny, self.nx)
+
+    def f_planes(self):
+        """Current f_1..f_16 and lambda as FP64 NumPy arrays [17, ny, nx] (from a state copy)."""
+        raw = self.get_state()
+        dt = np.float64 if self.params.precision == F64 else np.float32
+        n = 17 * self.ny * self.nx
+        return np.frombuffer(raw[: n * np.dtype(dt).itemsize].tobytes(), dt).reshape(
+            17, self.ny, self.nx).astype(np.float64)
+
+
+def version():
+    return int(load().lbkm_version())

@@ -1,0 +1,84 @@
+"""The C-ABI library loads and exports every entry point include/lbkm.h declares,
+and the ctypes structures of the binding have the header's layout. CPU only: no
+call here touches a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbkm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1411_6697_gb300 import build
+    build.build()
+    from paper_1411_6697_gb300 import lbkm
+    return lbkm.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbkm_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_1411_6697_gb300 import lbkm
+    assert sorted(lbkm.EXPORTED) == names
+
+
+def test_struct_layout_matches_header(lib):
+    from paper_1411_6697_gb300 import lbkm
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "lbkm.h"
+#define F(s, m) printf(#m " %zu\n", offsetof(s, m));
+int main(void) {
+  printf("params %zu\n", sizeof(lbkm_params));
+  printf("tne %zu\n", sizeof(lbkm_tne_global));
+  F(lbkm_params, gamma) F(lbkm_params, orbit_kind) F(lbkm_params, orbit_speed)
+  F(lbkm_params, S) F(lbkm_params, Q) F(lbkm_params, T_ig) F(lbkm_params, dt)
+  F(lbkm_params, bc_x) F(lbkm_params, tne_capacity)
+  F(lbkm_tne_global, d_sum) F(lbkm_tne_global, step)
+  return 0; }
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "l")
+        subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe])
+        out = dict(line.split() for line in subprocess.check_output([exe]).decode().splitlines())
+    assert int(out["params"]) == ctypes.sizeof(lbkm.Params)
+    assert int(out["tne"]) == ctypes.sizeof(lbkm.TneGlobal)
+    for m in ("gamma", "orbit_kind", "orbit_speed", "S", "Q", "T_ig", "dt", "bc_x",
+              "tne_capacity"):
+        assert int(out[m]) == getattr(lbkm.Params, m).offset, m
+    assert int(out["d_sum"]) == lbkm.TneGlobal.d_sum.offset
+    assert int(out["step"]) == lbkm.TneGlobal.step.offset
+
+
+def test_default_params_are_host_only(lib):
+    from paper_1411_6697_gb300 import lbkm
+    p = lbkm.default_params(nx=10, ny=1)
+    assert p.orbit_kind[:] == [0, 1, 0, 1]
+    assert list(p.orbit_speed) == [2.7, 2.2, 1.2, 1.0]
+    assert p.S[5] == 1e5 and p.tne_capacity == 1 and p.precision == lbkm.F64
+    assert lbkm.version() == 100
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    from paper_1411_6697_gb300 import lbkm
+    monkeypatch.setattr(lbkm, "_lib", None)
+    monkeypatch.setattr(lbkm, "LIB_PATH", "/nonexistent/libpaper_lbkm.so")
+    with pytest.raises(ImportError):
+        lbkm.load()

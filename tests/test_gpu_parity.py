@@ -1,0 +1,269 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Same seeded inputs on both sides; element-wise comparison by relative L2 per
+field: <= 1e-12 for the FP64 form, <= 2e-5 for the FP32 forms. Grids span
+several tiles and a ragged tail (tiles are 32 x 8 cells in 2-D, 64 in 1-D).
+"""
+import numpy as np
+import pytest
+
+import lbkm_inputs as li
+from gpu_common import TOL, make_oracle, rel_l2, solver, state_bytes
+from paper_1411_6697_gb300 import lbkm
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [(lbkm.F64, 0), (lbkm.F32, 0), (lbkm.F32, 1)]
+PID = ["f64", "f32", "f32-df"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "the -m gpu tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def mixed_2d(nx, ny, bc=(0, 0), seed=0, reactive=True):
+    """A 2-D non-uniform state with shear, compression, heat release and unequal R_k."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx)[None, :] / nx
+    y = np.arange(ny)[:, None] / ny
+    fields = dict(
+        rho=1 + 0.1 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) + 0 * x,
+        ux=0.2 * np.cos(2 * np.pi * y) + 0.05 * np.sin(4 * np.pi * x),
+        uy=-0.15 * np.sin(2 * np.pi * x) + 0.05 * np.cos(2 * np.pi * y),
+        T=1.1 + 0.15 * np.cos(2 * np.pi * (x + y)) + 0 * x,
+        lam=rng.uniform(0, 0.6, (ny, nx)))
+    params = dict(li.DEFAULT_ORBITS, nx=nx, ny=ny, gamma=1.4, S=rng.uniform(5e3, 1e5, 16),
+                  Q=1.0 if reactive else 0.0, omega1=2e3, omega2=300.0, T_ig=1.1, dx=1e-3,
+                  dt=1e-5, bc_x=bc[0], bc_y=bc[1])
+    return params, fields
+
+
+def start(params, fields, prec, rec, noise_seed=None, **kw):
+    """Solver and oracle at the same start state; with noise_seed the state is a
+    perturbed (non-equilibrium) f, loaded through lbkm_set_state."""
+    ob = make_oracle(params)
+    f = ob.init(fields["rho"], fields["ux"], fields["uy"], fields["T"])
+    lam = np.broadcast_to(fields["lam"], f.shape[1:]).copy()
+    s = solver(params, prec, rec, **kw)
+    if noise_seed is None:
+        s.init_fields(fields["rho"], fields["ux"], fields["uy"], fields["T"], fields["lam"])
+        if prec == lbkm.F32:
+            planes = s.f_planes()  # oracle starts from the same FP32-rounded state
+            f, lam = planes[:16].copy(), planes[16].copy()
+    else:
+        rng = np.random.default_rng(noise_seed)
+        f = f * (1 + 2e-3 * rng.standard_normal(f.shape))
+        if prec == lbkm.F32:
+            f = f.astype(np.float32).astype(np.float64)
+            lam = lam.astype(np.float32).astype(np.float64)
+        s.set_state(state_bytes(np.concatenate([f, lam[None]]), prec))
+    return s, ob, f, lam
+
+
+# ------------------------------------------------------------------ init, macros
+@pytest.mark.parametrize("prec", [lbkm.F64, lbkm.F32], ids=["f64", "f32"])
+def test_init_is_discrete_equilibrium(prec):
+    params, fields = mixed_2d(37, 11)
+    s = solver(params, prec)
+    s.init_fields(fields["rho"], fields["ux"], fields["uy"], fields["T"], fields["lam"])
+    ob = make_oracle(params)
+    f = ob.init(fields["rho"], fields["ux"], fields["uy"], fields["T"])
+    got = s.f_planes()
+    tol = 1e-13 if prec == lbkm.F64 else 1e-7
+    for i in range(16):
+        assert rel_l2(got[i], f[i]) < tol, i
+    m = s.macros()
+    for k in ("rho", "ux", "uy", "T"):
+        assert rel_l2(m[k], np.broadcast_to(fields[k], m[k].shape)) < (
+            1e-13 if prec == lbkm.F64 else 1e-6), k
+    assert np.array_equal(m["p"], m["rho"] * m["T"])
+
+
+# ------------------------------------------------------------------ fused step, 2-D
+@pytest.mark.parametrize("prec,rec", PRECS, ids=PID)
+@pytest.mark.parametrize("nx,ny,bc", [(70, 37, (0, 0)), (45, 19, (1, 1)), (33, 9, (1, 0))])
+def test_step_2d_nonequilibrium_parity(prec, rec, nx, ny, bc):
+    params, fields = mixed_2d(nx, ny, bc=bc, seed=nx)
+    s, ob, f, lam = start(params, fields, prec, rec, noise_seed=ny)
+    steps = 25
+    s.step(steps)
+    f_ref, lam_ref = ob.run(f, lam, steps)
+    got = s.f_planes()
+    for i in range(16):
+        assert rel_l2(got[i], f_ref[i]) <= TOL[prec], ("f", i + 1, rel_l2(got[i], f_ref[i]))
+    assert rel_l2(got[16], lam_ref) <= TOL[prec]
+    m, mr = s.macros(), ob.macros(f_ref)
+    for k in ("rho", "ux", "uy", "T", "p"):
+        assert rel_l2(m[k], mr[k]) <= TOL[prec], (k, rel_l2(m[k], mr[k]))
+    assert lam_ref.max() > lam.max() - 1e-12  # the reaction ran
+
+
+# ------------------------------------------------------------------ configs 1 and 2
+@pytest.mark.parametrize("run", ["A", "B"])
+def test_riemann_full_config_fp64(run):
+    c = li.riemann(nx=400, steps=1000, run=run, interface=200)
+    fl = c["fields"]
+    s = solver(c["params"], lbkm.F64)
+    s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    s.step(c["steps"])
+    ob = make_oracle(c["params"])
+    f, lam = ob.run(ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"]), fl["lam"], c["steps"])
+    m, mr = s.macros(), ob.macros(f)
+    for k in ("rho", "ux", "T", "p"):
+        assert rel_l2(m[k], mr[k]) <= 1e-12, (k, rel_l2(m[k], mr[k]))
+    assert rel_l2(s.f_planes()[:16], f) <= 1e-12
+
+
+@pytest.fixture(scope="module")
+def detonation_ref():
+    """Oracle run of the full 1-D detonation (16384 cells), kept at 2000 and 20000 steps."""
+    c = li.detonation(nx=16384, steps=20000)
+    fl = c["fields"]
+    ob = make_oracle(c["params"])
+    f0 = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
+    f1, l1 = ob.run(f0, fl["lam"], 2000)
+    f2, l2 = ob.run(f1, l1, 18000)
+    return c, ob, {2000: (f1, l1), 20000: (f2, l2)}
+
+
+@pytest.mark.parametrize("prec,rec", PRECS, ids=PID)
+@pytest.mark.parametrize("steps", [2000, 20000])
+def test_detonation_full_config(detonation_ref, prec, rec, steps):
+    c, ob, ref = detonation_ref
+    fl = c["fields"]
+    s = solver(c["params"], prec, rec)
+    s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    s.step(steps)
+    f, lam = ref[steps]
+    m, mr = s.macros(), ob.macros(f)
+    errs = {k: rel_l2(m[k], mr[k]) for k in ("rho", "ux", "T", "p")}
+    errs["lam"] = rel_l2(m["lam"], lam)
+    print("detonation", steps, "prec", prec, rec, errs)
+    tol = TOL[prec]
+    if prec == lbkm.F32 and steps == 20000:
+        # long FP32 runs: the error against the FP64 oracle is reported, bounded loosely
+        tol = 5e-3
+    for k, e in errs.items():
+        assert e <= tol, (k, e)
+
+
+# ------------------------------------------------------------------ full 2-D size, sampled
+@pytest.mark.parametrize("prec,rec", [(lbkm.F32, 0), (lbkm.F32, 1)], ids=["f32", "f32-df"])
+def test_reactive2d_full_size_sampled(prec, rec):
+    """4096 x 4096 periodic reactive field, 3 steps: sampled cells against the oracle run
+    on a periodic patch around each sample (the update has radius 2 per step)."""
+    import torch
+    c = li.reactive2d(n=4096, steps=3)
+    fl = c["fields"]
+    s = solver(c["params"], prec, rec)
+    s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    steps = c["steps"]
+    s.step(steps)
+    planes = s.planes_device()
+    n = 4096
+    rng = np.random.default_rng(42)
+    samples = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (1, 2)] + [
+        tuple(rng.integers(0, n, 2)) for _ in range(15)]
+    R = 2 * steps + 2
+    p = dict(c["params"])
+    p.update(nx=2 * R + 1, ny=2 * R + 1, bc_x=1, bc_y=1)
+    ob = make_oracle(p)
+    for (yy, xx) in samples:
+        iy = np.arange(yy - R, yy + R + 1) % n
+        ix = np.arange(xx - R, xx + R + 1) % n
+        patch = {k: fl[k][np.ix_(iy, ix)] for k in fl}
+        f = ob.init(patch["rho"], patch["ux"], patch["uy"], patch["T"])
+        f, lam = ob.run(f, patch["lam"], steps)
+        want = np.concatenate([f[:, R, R], [lam[R, R]]])
+        got = planes[:, yy, xx].double().cpu().numpy()
+        assert np.abs(got - want).max() <= 2e-5 * np.abs(want).max(), (yy, xx)
+    del torch
+
+
+# ------------------------------------------------------------------ TNE
+@pytest.mark.parametrize("prec,rec", PRECS, ids=PID)
+def test_tne_fields_and_on_the_fly_records(prec, rec):
+    params, fields = mixed_2d(40, 17, seed=3)
+    steps = 6
+    s, ob, f, lam = start(params, fields, prec, rec, noise_seed=5, tne_every=1, tne_capacity=16)
+    s.step(steps)
+    hist = s.tne_history()
+    assert [h["step"] for h in hist] == list(range(steps))
+    fs, ls = f, lam
+    for k in range(steps):
+        _, rec_ref = ob.tne(fs, fields=False)
+        h = hist[k]
+        scale = rec_ref["abs_sum"].max()
+        tol = 1e-12 if prec == lbkm.F64 else 2e-5
+        assert np.abs(h["sum"] - rec_ref["sum"]).max() <= tol * scale, k
+        assert np.abs(h["abs_sum"] - rec_ref["abs_sum"]).max() <= tol * scale, k
+        mscale = max(np.abs(rec_ref["min"]).max(), np.abs(rec_ref["max"]).max())
+        assert np.abs(h["min"] - rec_ref["min"]).max() <= tol * mscale, k
+        assert np.abs(h["max"] - rec_ref["max"]).max() <= tol * mscale, k
+        assert abs(h["d_sum"] - rec_ref["d_sum"]) <= tol * rec_ref["d_sum"]
+        assert abs(h["d2_sum"] - rec_ref["d2_sum"]) <= tol * rec_ref["d2_sum"]
+        fs, ls = ob.step(fs, ls)
+    # lbkm_tne on the current state (FP64 arithmetic on the stored state)
+    delta, g = s.tne(fields=True)
+    cur = s.f_planes()[:16]
+    dref, gref = ob.tne(cur)
+    assert np.abs(delta - dref).max() <= 1e-12 * np.abs(dref).max()
+    assert np.abs(g["abs_sum"] - gref["abs_sum"]).max() <= 1e-12 * gref["abs_sum"].max()
+    assert np.all(delta[:4] == 0)
+
+
+# ------------------------------------------------------------------ runtime behaviour
+def test_graph_chunks_equal_single_steps():
+    params, fields = mixed_2d(50, 20, seed=9)
+    a = solver(params, lbkm.F64, tne_every=3, tne_capacity=64)
+    b = solver(params, lbkm.F64, tne_every=3, tne_capacity=64)
+    for s in (a, b):
+        s.init_fields(fields["rho"], fields["ux"], fields["uy"], fields["T"], fields["lam"])
+    a.step(71)  # two 32-step graph replays + 7 single launches
+    for _ in range(71):
+        b.step(1)
+    assert np.array_equal(a.get_state(), b.get_state())
+    ha, hb = a.tne_history(), b.tne_history()
+    assert len(ha) == 24 and [h["step"] for h in ha] == list(range(0, 71, 3))
+    assert all(np.array_equal(x["sum"], y["sum"]) for x, y in zip(ha, hb))
+
+
+def test_checkpoint_resume_is_bitwise():
+    params, fields = mixed_2d(33, 12, seed=4)
+    a = solver(params, lbkm.F32)
+    a.init_fields(fields["rho"], fields["ux"], fields["uy"], fields["T"], fields["lam"])
+    a.step(40)
+    mid = a.get_state()
+    a.step(40)
+    b = solver(params, lbkm.F32)
+    b.set_state(mid)
+    assert b.steps_taken == 40
+    b.step(40)
+    assert np.array_equal(a.get_state(), b.get_state())
+
+
+def test_zero_steps_and_tiny_grids():
+    for nx, ny in ((1, 1), (3, 1), (2, 2), (5, 3)):
+        params, fields = mixed_2d(nx, ny, bc=(0, 0), seed=nx + ny)
+        s, ob, f, lam = start(params, fields, lbkm.F64, 0, noise_seed=1)
+        s.step(0)
+        assert np.allclose(s.f_planes()[:16], f, rtol=0, atol=0)
+        s.step(7)
+        f_ref, lam_ref = ob.run(f, lam, 7)
+        assert rel_l2(s.f_planes()[:16], f_ref) <= 1e-12, (nx, ny)
+
+
+def test_nonfinite_state_is_reported():
+    params, fields = mixed_2d(20, 4, seed=2)
+    s, ob, f, lam = start(params, fields, lbkm.F64, 0)
+    f = f.copy()
+    f[3, 2, 5] = np.nan
+    s.set_state(state_bytes(np.concatenate([f, lam[None]]), lbkm.F64))
+    s.step(1)
+    with pytest.raises(lbkm.LbkmError) as e:
+        s.sync()
+    assert e.value.code == 5

@@ -1,0 +1,48 @@
+"""Host-side validation of lbkm_create: every rejection happens before any CUDA call,
+so these run without a GPU (stream 0 is passed explicitly)."""
+import pytest
+
+from paper_1411_6697_gb300 import lbkm
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1411_6697_gb300 import build
+    build.build()
+
+
+def create(**kw):
+    base = dict(nx=16, ny=1)
+    base.update(kw)
+    return lbkm.Solver(stream=0, **base)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(nx=0), 1),
+    (dict(ny=0), 1),
+    (dict(precision=7), 1),
+    (dict(recovery=3), 1),
+    (dict(gamma=1.0), 1),
+    (dict(gamma=2.5), 1),
+    (dict(dt=3e-5), 1),                       # dt * S = 3 >= 2: Euler relaxation unstable
+    (dict(dx=1e-5), 1),                        # CFL 2.7 > 1
+    (dict(orbit_kind=(0, 0, 1, 1)), 1),        # order must be axis, diag, axis, diag
+    (dict(orbit_speed=(2.7, -1.0, 1.2, 1.0)), 1),
+    (dict(bc=(2, 0)), 1),
+    (dict(tne_every=-1), 1),
+    (dict(tne_capacity=0), 1),
+    (dict(omega1=-1.0), 1),
+    # the paper's first two rings (shared speed and eta): singular M
+    (dict(orbit_speed=(2.7, 2.7, 2.2, 2.2), orbit_eta=(5.0, 5.0, 3.0, 3.0)), 4),
+])
+def test_invalid_parameters_are_rejected(kw, code):
+    with pytest.raises(lbkm.LbkmError) as e:
+        create(**kw)
+    assert e.value.code == code
+    assert str(e.value)
+
+
+def test_pr_sets_heat_conduction_rates():
+    p = lbkm.default_params(nx=4, ny=1, Pr=0.5, S=[1e4] * 16)
+    # the override happens inside lbkm_create; the stored copy keeps the caller's values
+    assert p.Pr == 0.5 and p.S[7] == 1e4
