@@ -120,20 +120,29 @@ def test_riemann_full_config_fp64(run):
 
 @pytest.fixture(scope="module")
 def detonation_ref():
-    """Oracle run of the full 1-D detonation (16384 cells), kept at 2000 and 20000 steps."""
+    """Oracle run of the full 1-D detonation (16384 cells), kept at 2000 and 20000 steps,
+    and the oracle's own spread at 20000 steps: the same run from an initial f perturbed
+    by 1e-15 (relative). The ignition switch T > T_ig is a hard threshold, so rounding
+    differences of that size grow to ~1e-6 over 20000 steps whatever the implementation;
+    that spread, not 1e-12, is the attainable FP64 bound for the long run."""
     c = li.detonation(nx=16384, steps=20000)
     fl = c["fields"]
     ob = make_oracle(c["params"])
     f0 = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
     f1, l1 = ob.run(f0, fl["lam"], 2000)
     f2, l2 = ob.run(f1, l1, 18000)
-    return c, ob, {2000: (f1, l1), 20000: (f2, l2)}
+    fp = f0 * (1 + 1e-15 * np.random.default_rng(0).standard_normal(f0.shape))
+    fp, lp = ob.run(fp, fl["lam"], 20000)
+    m2, mp = ob.macros(f2), ob.macros(fp)
+    spread = {k: rel_l2(mp[k], m2[k]) for k in ("rho", "ux", "T", "p")}
+    spread["lam"] = rel_l2(lp, l2)
+    return c, ob, {2000: (f1, l1), 20000: (f2, l2)}, spread
 
 
 @pytest.mark.parametrize("prec,rec", PRECS, ids=PID)
 @pytest.mark.parametrize("steps", [2000, 20000])
 def test_detonation_full_config(detonation_ref, prec, rec, steps):
-    c, ob, ref = detonation_ref
+    c, ob, ref, spread = detonation_ref
     fl = c["fields"]
     s = solver(c["params"], prec, rec)
     s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
@@ -142,13 +151,14 @@ def test_detonation_full_config(detonation_ref, prec, rec, steps):
     m, mr = s.macros(), ob.macros(f)
     errs = {k: rel_l2(m[k], mr[k]) for k in ("rho", "ux", "T", "p")}
     errs["lam"] = rel_l2(m["lam"], lam)
-    print("detonation", steps, "prec", prec, rec, errs)
-    tol = TOL[prec]
-    if prec == lbkm.F32 and steps == 20000:
-        # long FP32 runs: the error against the FP64 oracle is reported, bounded loosely
-        tol = 5e-3
+    print("detonation", steps, "prec", prec, rec, errs, "oracle spread", spread)
     for k, e in errs.items():
-        assert e <= tol, (k, e)
+        tol = TOL[prec]
+        if steps == 20000:
+            # past the ignition-switch events the bound is the oracle's own spread
+            # (FP64), or FP32 rounding amplified by the same switch events
+            tol = max(tol, 20 * spread[k]) if prec == lbkm.F64 else 5e-4
+        assert e <= tol, (k, e, tol)
 
 
 # ------------------------------------------------------------------ full 2-D size, sampled
@@ -194,18 +204,23 @@ def test_tne_fields_and_on_the_fly_records(prec, rec):
     hist = s.tne_history()
     assert [h["step"] for h in hist] == list(range(steps))
     fs, ls = f, lam
+    area = params["dx"] * params["dx"]
     for k in range(steps):
         _, rec_ref = ob.tne(fs, fields=False)
         h = hist[k]
-        scale = rec_ref["abs_sum"].max()
+        # Delta_k = f_hat_k - f_hat^eq_k cancels several digits, so its rounding error
+        # scales with |f_hat_k|, the magnitude of the moments it is taken from
+        fh = np.abs(np.einsum("ki,iyx->kyx", ob.M, fs))
         tol = 1e-12 if prec == lbkm.F64 else 2e-5
-        assert np.abs(h["sum"] - rec_ref["sum"]).max() <= tol * scale, k
-        assert np.abs(h["abs_sum"] - rec_ref["abs_sum"]).max() <= tol * scale, k
-        mscale = max(np.abs(rec_ref["min"]).max(), np.abs(rec_ref["max"]).max())
-        assert np.abs(h["min"] - rec_ref["min"]).max() <= tol * mscale, k
-        assert np.abs(h["max"] - rec_ref["max"]).max() <= tol * mscale, k
-        assert abs(h["d_sum"] - rec_ref["d_sum"]) <= tol * rec_ref["d_sum"]
-        assert abs(h["d2_sum"] - rec_ref["d2_sum"]) <= tol * rec_ref["d2_sum"]
+        sscale = fh.sum(axis=(1, 2)) * area
+        mscale = fh.max(axis=(1, 2))
+        assert np.all(np.abs(h["sum"] - rec_ref["sum"]) <= tol * sscale), k
+        assert np.all(np.abs(h["abs_sum"] - rec_ref["abs_sum"]) <= tol * sscale), k
+        assert np.all(np.abs(h["min"] - rec_ref["min"]) <= tol * mscale), k
+        assert np.all(np.abs(h["max"] - rec_ref["max"]) <= tol * mscale), k
+        dscale = np.sqrt((fh[4:] ** 2).sum(axis=0)).sum() * area
+        assert abs(h["d_sum"] - rec_ref["d_sum"]) <= tol * dscale
+        assert abs(h["d2_sum"] - rec_ref["d2_sum"]) <= tol * dscale * mscale[4:].max()
         fs, ls = ob.step(fs, ls)
     # lbkm_tne on the current state (FP64 arithmetic on the stored state)
     delta, g = s.tne(fields=True)
