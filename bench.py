@@ -53,17 +53,24 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+STEP_KERNEL_SOURCES = ("kernels.cu", "cell.cuh", "kernels.cuh", "model.h")
+
+
+def step_kernel_digest():
+    """sha256 over the sources that define the step kernel."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1411_6697_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in STEP_KERNEL_SOURCES:
+        h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()
+
+
 def profile_traffic(kernel_tag):
     """dram bytes per launch from the committed ncu summary, if it matches the current
     kernel source (sha256 line); else None."""
-    import hashlib
     prof = os.path.join(ROOT, "profiles", "step_kernel_reactive2d.md")
-    src = os.path.join(ROOT, "paper_1411_6697_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(src, f), "rb").read())
-    digest = h.hexdigest()
+    digest = step_kernel_digest()
     try:
         lines = open(prof).read().splitlines()
     except OSError:
