@@ -184,6 +184,26 @@ size_t lbkm_state_bytes(lbkm_t h);
 lbkm_status lbkm_get_state(lbkm_t h, void* dst, int on_device);
 lbkm_status lbkm_set_state(lbkm_t h, const void* src, int on_device);
 
+/* TNE record of a caller-owned state, allocating nothing (the paper has no
+ * counterpart; this is an interface for callers that cannot allocate device
+ * memory, e.g. because their own pool already holds all of it, or because a
+ * latency-bound loop must not pay cudaMalloc's implicit synchronisation).
+ * No handle is needed: p gives the model (nx, ny, precision, gamma, orbits,
+ * dx, dy; the rest is ignored), state is a device array of 17 planes [ny][pitch]
+ * in p->precision (f_1..f_16, lambda; the layout lbkm_get_state writes with
+ * pitch = nx), delta is NULL or a device array [16][ny][nx] FP64, and out is a
+ * device pointer to one lbkm_tne_global (step is set to -1). The call is
+ * asynchronous on cuda_stream. Scratch: a fixed device array inside the library
+ * (about 0.8 MB on every GPU that loads it, kept until the process exits),
+ * shared by all calls: calls that overlap on the GPU race, so serialise them
+ * (one stream, or events). The first call on a device looks up the scratch
+ * address with that device current; make that first call before any stream
+ * capture. Limit: nx * ny <= 16,777,216 cells; larger grids return
+ * LBKM_EINVAL. Errors: LBKM_EINVAL, LBKM_ESINGULAR, LBKM_ECUDA, with the
+ * message in lbkm_last_error(NULL). */
+lbkm_status lbkm_tne_noalloc(const lbkm_params* p, const void* state, int64_t pitch,
+                             double* delta, lbkm_tne_global* out, void* cuda_stream);
+
 /* Message of the last failing call on h (or of the last failing lbkm_create
  * when h is NULL). Never NULL. */
 const char* lbkm_last_error(lbkm_t h);

@@ -473,3 +473,8 @@ const char* lbkm_last_error(lbkm_t h)
 int32_t lbkm_version(void) { return 100; }
 
 } // extern "C"
+
+namespace lbk {
+// Message for lbkm_last_error(NULL) from entry points that take no handle.
+void set_handleless_error(const char* msg) { g_create_error = msg; }
+} // namespace lbk

@@ -26,7 +26,7 @@ STATUS = {0: "LBKM_OK", 1: "LBKM_EINVAL", 2: "LBKM_ENOMEM", 3: "LBKM_ECUDA",
 EXPORTED = ["lbkm_default_params", "lbkm_create", "lbkm_destroy", "lbkm_set_stream",
             "lbkm_init_fields", "lbkm_step", "lbkm_sync", "lbkm_steps_taken", "lbkm_macros",
             "lbkm_tne", "lbkm_tne_history", "lbkm_state_bytes", "lbkm_get_state",
-            "lbkm_set_state", "lbkm_last_error", "lbkm_version"]
+            "lbkm_set_state", "lbkm_last_error", "lbkm_version", "lbkm_tne_noalloc"]
 
 
 class LbkmError(RuntimeError):
@@ -99,6 +99,8 @@ def load():
     lib.lbkm_last_error.argtypes = [H]
     lib.lbkm_last_error.restype = ctypes.c_char_p
     lib.lbkm_version.restype = ctypes.c_int32
+    lib.lbkm_tne_noalloc.argtypes = [ctypes.POINTER(Params), _vp, ctypes.c_int64, _vp, _vp, _vp]
+    lib.lbkm_tne_noalloc.restype = ctypes.c_int
     for name in ("lbkm_create", "lbkm_set_stream", "lbkm_init_fields", "lbkm_step", "lbkm_sync",
                  "lbkm_macros", "lbkm_tne", "lbkm_tne_history", "lbkm_get_state",
                  "lbkm_set_state"):
@@ -296,6 +298,17 @@ class Solver:
         n = 17 * self.ny * self.nx
         return np.frombuffer(raw[: n * np.dtype(dt).itemsize].tobytes(), dt).reshape(
             17, self.ny, self.nx).astype(np.float64)
+
+
+def tne_noalloc(params: Params, state_ptr: int, pitch: int, delta_ptr, out_ptr: int, stream=None):
+    """lbkm_tne_noalloc: TNE record of a caller-owned device state, allocating nothing.
+    All pointers are device addresses; out receives one lbkm_tne_global (536 bytes)."""
+    lib = load()
+    rc = lib.lbkm_tne_noalloc(ctypes.byref(params), ctypes.c_void_p(state_ptr), int(pitch),
+                              ctypes.c_void_p(delta_ptr), ctypes.c_void_p(out_ptr),
+                              ctypes.c_void_p(_stream_ptr(stream)))
+    if rc != 0:
+        raise LbkmError(rc, lib.lbkm_last_error(None).decode())
 
 
 def version():
