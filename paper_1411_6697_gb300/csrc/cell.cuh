@@ -43,12 +43,14 @@ __device__ __forceinline__ R nnd_neg(R qm1, R q0, R qp1, R qp2)
     return d2 - R(0.5) * (minmod(d2, d3) - minmod(d1, d2));
 }
 
-template <typename R, int N>
-__device__ __forceinline__ void matvec(const R* A, const R* x, R* y)
+// y = A x for an N x N block A of coefficients (type T) acting on lanes of type L
+// (a scalar, or a pair of cells packed for FFMA2).
+template <int N, typename T, typename L>
+__device__ __forceinline__ void matvec(const T* A, const L* x, L* y)
 {
 #pragma unroll
     for (int r = 0; r < N; r++) {
-        R s = A[r * N] * x[0];
+        L s = A[r * N] * x[0];
 #pragma unroll
         for (int c = 1; c < N; c++) s = fma(A[r * N + c], x[c], s);
         y[r] = s;
@@ -57,32 +59,32 @@ __device__ __forceinline__ void matvec(const R* A, const R* x, R* y)
 
 // f (velocity space, orbit-major) -> the 16 moments in the standard order
 // m1..m16 (0-based index k-1), by butterflies and the sector blocks.
-template <typename R>
-__device__ __forceinline__ void forward_moments(const ModelConst<R>& K, const R* f, R* m)
+template <typename R, typename L>
+__device__ __forceinline__ void forward_moments(const ModelConst<R>& K, const L* f, L* m)
 {
     // axis orbits 0 (f0..f3) and 2 (f8..f11)
-    R sx0 = f[0] + f[2], sy0 = f[1] + f[3], ax0 = f[0] - f[2], ay0 = f[1] - f[3];
-    R sx2 = f[8] + f[10], sy2 = f[9] + f[11], ax2 = f[8] - f[10], ay2 = f[9] - f[11];
+    L sx0 = f[0] + f[2], sy0 = f[1] + f[3], ax0 = f[0] - f[2], ay0 = f[1] - f[3];
+    L sx2 = f[8] + f[10], sy2 = f[9] + f[11], ax2 = f[8] - f[10], ay2 = f[9] - f[11];
     // diagonal orbits 1 (f4..f7) and 3 (f12..f15)
-    R s01 = f[4] + f[5], d01 = f[4] - f[5], s23 = f[6] + f[7], d23 = f[6] - f[7];
-    R e1 = s01 + s23, ay1 = s01 - s23, ax1 = d01 - d23, o1 = d01 + d23;
-    R t01 = f[12] + f[13], u01 = f[12] - f[13], t23 = f[14] + f[15], u23 = f[14] - f[15];
-    R e3 = t01 + t23, ay3 = t01 - t23, ax3 = u01 - u23, o3 = u01 + u23;
+    L s01 = f[4] + f[5], d01 = f[4] - f[5], s23 = f[6] + f[7], d23 = f[6] - f[7];
+    L e1 = s01 + s23, ay1 = s01 - s23, ax1 = d01 - d23, o1 = d01 + d23;
+    L t01 = f[12] + f[13], u01 = f[12] - f[13], t23 = f[14] + f[15], u23 = f[14] - f[15];
+    L e3 = t01 + t23, ay3 = t01 - t23, ax3 = u01 - u23, o3 = u01 + u23;
 
-    R es[4] = {sx0 + sy0, sx2 + sy2, e1, e3}, ea[2] = {sx0 - sy0, sx2 - sy2};
-    R xo[4] = {ax0, ax2, ax1, ax3}, yo[4] = {ay0, ay2, ay1, ay3}, oo[2] = {o1, o3};
-    R pes[4], pea[2], px[4], py[4], po[2];
-    matvec<R, 4>(K.Bes, es, pes);
-    matvec<R, 2>(K.Bea, ea, pea);
-    matvec<R, 4>(K.Bodd, xo, px);
-    matvec<R, 4>(K.Bodd, yo, py);
-    matvec<R, 2>(K.Boo, oo, po);
+    L es[4] = {sx0 + sy0, sx2 + sy2, e1, e3}, ea[2] = {sx0 - sy0, sx2 - sy2};
+    L xo[4] = {ax0, ax2, ax1, ax3}, yo[4] = {ay0, ay2, ay1, ay3}, oo[2] = {o1, o3};
+    L pes[4], pea[2], px[4], py[4], po[2];
+    matvec<4>(K.Bes, es, pes);
+    matvec<2>(K.Bea, ea, pea);
+    matvec<4>(K.Bodd, xo, px);
+    matvec<4>(K.Bodd, yo, py);
+    matvec<2>(K.Boo, oo, po);
     m[0] = pes[0];
     m[3] = pes[1];
-    m[4] = R(0.5) * (pes[2] + pea[0]);
-    m[6] = R(0.5) * (pes[2] - pea[0]);
-    m[13] = R(0.5) * (pes[3] + pea[1]);
-    m[15] = R(0.5) * (pes[3] - pea[1]);
+    m[4] = L(0.5f) * (pes[2] + pea[0]);
+    m[6] = L(0.5f) * (pes[2] - pea[0]);
+    m[13] = L(0.5f) * (pes[3] + pea[1]);
+    m[15] = L(0.5f) * (pes[3] - pea[1]);
     m[1] = px[0];
     m[7] = px[1];
     m[9] = px[2];
@@ -96,24 +98,24 @@ __device__ __forceinline__ void forward_moments(const ModelConst<R>& K, const R*
 }
 
 // moments (standard order) -> velocity space: Omega = M^-1 Omega_hat.
-template <typename R>
-__device__ __forceinline__ void inverse_moments(const ModelConst<R>& K, const R* mh, R* f)
+template <typename R, typename L>
+__device__ __forceinline__ void inverse_moments(const ModelConst<R>& K, const L* mh, L* f)
 {
-    R es[4] = {mh[0], mh[3], mh[4] + mh[6], mh[13] + mh[15]};
-    R ea[2] = {mh[4] - mh[6], mh[13] - mh[15]};
-    R xo[4] = {mh[1], mh[7], mh[9], mh[11]};
-    R yo[4] = {mh[2], mh[8], mh[12], mh[10]};
-    R oo[2] = {mh[5], mh[14]};
-    R pes[4], pea[2], px[4], py[4], po[2];
-    matvec<R, 4>(K.Ies, es, pes);
-    matvec<R, 2>(K.Iea, ea, pea);
-    matvec<R, 4>(K.Iodd, xo, px);
-    matvec<R, 4>(K.Iodd, yo, py);
-    matvec<R, 2>(K.Ioo, oo, po);
+    L es[4] = {mh[0], mh[3], mh[4] + mh[6], mh[13] + mh[15]};
+    L ea[2] = {mh[4] - mh[6], mh[13] - mh[15]};
+    L xo[4] = {mh[1], mh[7], mh[9], mh[11]};
+    L yo[4] = {mh[2], mh[8], mh[12], mh[10]};
+    L oo[2] = {mh[5], mh[14]};
+    L pes[4], pea[2], px[4], py[4], po[2];
+    matvec<4>(K.Ies, es, pes);
+    matvec<2>(K.Iea, ea, pea);
+    matvec<4>(K.Iodd, xo, px);
+    matvec<4>(K.Iodd, yo, py);
+    matvec<2>(K.Ioo, oo, po);
     // axis orbits
 #pragma unroll
     for (int a = 0; a < 2; a++) {
-        R pp = pes[a] + pea[a], pm = pes[a] - pea[a];
+        L pp = pes[a] + pea[a], pm = pes[a] - pea[a];
         f[8 * a + 0] = pp + px[a];
         f[8 * a + 2] = pp - px[a];
         f[8 * a + 1] = pm + py[a];
@@ -122,8 +124,8 @@ __device__ __forceinline__ void inverse_moments(const ModelConst<R>& K, const R*
     // diagonal orbits
 #pragma unroll
     for (int d = 0; d < 2; d++) {
-        R e = pes[2 + d], X = px[2 + d], Y = py[2 + d], o = po[d];
-        R eo = e + o, em = e - o, xp = X + Y, xm = X - Y;
+        L e = pes[2 + d], X = px[2 + d], Y = py[2 + d], o = po[d];
+        L eo = e + o, em = e - o, xp = X + Y, xm = X - Y;
         f[4 + 8 * d + 0] = eo + xp;
         f[4 + 8 * d + 1] = em - xm;
         f[4 + 8 * d + 2] = eo - xp;

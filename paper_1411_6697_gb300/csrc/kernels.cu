@@ -20,13 +20,11 @@
 
 #include "cell.cuh"
 #include "kernels.cuh"
+#include "reduce.cuh"
 
 namespace lbk {
 
 namespace {
-
-constexpr int NSUM = 2 * TNE_K + 2; // sums: Delta, |Delta|, d, d^2
-constexpr int NMM = 2 * TNE_K;      // min, max
 
 template <typename R, bool TWO_D, int TX, int TY>
 struct Cfg {
@@ -42,73 +40,6 @@ struct Cfg {
     static constexpr size_t off_tmm = off_tsum + (size_t)NW * NSUM * sizeof(double);
     static constexpr size_t smem = off_tmm + (size_t)NW * NMM * sizeof(R);
 };
-
-template <typename R>
-__device__ __forceinline__ R warp_sum(R v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-template <typename R>
-__device__ __forceinline__ R warp_min(R v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = rmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-template <typename R>
-__device__ __forceinline__ R warp_max(R v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = rmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-template <typename R>
-__device__ __forceinline__ R big_value();
-template <>
-__device__ __forceinline__ float big_value<float>() { return FLT_MAX; }
-template <>
-__device__ __forceinline__ double big_value<double>() { return DBL_MAX; }
-
-// Last block of a launch: reduce the per-block partials (fixed order) into a
-// TNE record. Called by every thread of that block.
-__device__ void finish_tne(const double* partials, int nblocks, TneRecord* rec, int64_t step,
-                           double area)
-{
-    __shared__ double res[TNE_PART];
-    for (int q = threadIdx.x; q < TNE_PART; q += blockDim.x) {
-        double acc;
-        if (q < 2 * TNE_K || q >= 4 * TNE_K) {
-            acc = 0.0;
-            for (int b = 0; b < nblocks; b++) acc += __ldcg(partials + (size_t)b * TNE_PART + q);
-            acc *= area;
-        } else if (q < 3 * TNE_K) {
-            acc = DBL_MAX;
-            for (int b = 0; b < nblocks; b++)
-                acc = fmin(acc, __ldcg(partials + (size_t)b * TNE_PART + q));
-        } else {
-            acc = -DBL_MAX;
-            for (int b = 0; b < nblocks; b++)
-                acc = fmax(acc, __ldcg(partials + (size_t)b * TNE_PART + q));
-        }
-        res[q] = acc;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 16; k += blockDim.x) {
-        bool z = k < 4;
-        rec->sum[k] = z ? 0.0 : res[k - 4];
-        rec->abs_sum[k] = z ? 0.0 : res[TNE_K + k - 4];
-        rec->min[k] = z ? 0.0 : res[2 * TNE_K + k - 4];
-        rec->max[k] = z ? 0.0 : res[3 * TNE_K + k - 4];
-    }
-    if (threadIdx.x == 0) {
-        rec->d_sum = res[4 * TNE_K];
-        rec->d2_sum = res[4 * TNE_K + 1];
-        rec->step = step;
-    }
-}
 
 template <typename R, int REC, bool TWO_D, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY)
@@ -538,9 +469,8 @@ int step_grid(int precision, int recovery, bool two_d, int nx, int ny)
 {
     if (precision == 0)
         return two_d ? K2D<double, 0>::grid(nx, ny) : K1D<double, 0>::grid(nx, ny);
-    if (recovery == 1)
-        return two_d ? K2D<float, 1>::grid(nx, ny) : K1D<float, 1>::grid(nx, ny);
-    return two_d ? K2D<float, 0>::grid(nx, ny) : K1D<float, 0>::grid(nx, ny);
+    if (two_d) return march_grid(recovery, nx, ny);
+    return recovery == 1 ? K1D<float, 1>::grid(nx, ny) : K1D<float, 0>::grid(nx, ny);
 }
 
 cudaError_t launch_step(int precision, int recovery, bool two_d, const void* K,
@@ -548,9 +478,8 @@ cudaError_t launch_step(int precision, int recovery, bool two_d, const void* K,
 {
     if (precision == 0)
         return two_d ? K2D<double, 0>::launch(K, a, s) : K1D<double, 0>::launch(K, a, s);
-    if (recovery == 1)
-        return two_d ? K2D<float, 1>::launch(K, a, s) : K1D<float, 1>::launch(K, a, s);
-    return two_d ? K2D<float, 0>::launch(K, a, s) : K1D<float, 0>::launch(K, a, s);
+    if (two_d) return launch_march(recovery, *static_cast<const ModelConst<float>*>(K), a, s);
+    return recovery == 1 ? K1D<float, 1>::launch(K, a, s) : K1D<float, 0>::launch(K, a, s);
 }
 
 cudaError_t launch_init(int precision, const ModelConst<double>& Kd, const double* rho,

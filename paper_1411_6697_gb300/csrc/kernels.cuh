@@ -54,4 +54,9 @@ cudaError_t launch_tne(int precision, const ModelConst<double>& Kd, const void* 
                        TneRecord* out, double cell_area, cudaStream_t s);
 int tne_grid(int nx, int ny);
 
+// FP32 2-D step: y-marching strips, two cells per thread (march.cu)
+int march_grid(int recovery, int nx, int ny);
+cudaError_t launch_march(int recovery, const ModelConst<float>& K, const StepLaunch& a,
+                         cudaStream_t s);
+
 } // namespace lbk

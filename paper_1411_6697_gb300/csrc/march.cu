@@ -1,0 +1,539 @@
+// march.cu -- the FP32 2-D step kernel: y-marching strips, two cells per thread.
+//
+// A block of 64 threads owns a strip of 128 columns x `strip_rows` rows and
+// marches up it one row per iteration. Thread t updates the cells (x0+2t, y)
+// and (x0+2t+1, y) together, so most arithmetic runs as packed FP32 pairs
+// (FFMA2 / FADD2 / FMUL2, sm_100+).
+//
+// Shared memory keeps a ring of 7 staged rows (the 17 planes f_1..f_16,
+// lambda of rows y-2..y+2 plus 2 rows prefetched ahead, each 128 + 8 columns
+// wide) filled by 16-byte cp.async copies, and a ring of 4 macro rows (rho, u,
+// T of rows y-1..y+2, with one halo column on each side for grad u). Per
+// iteration: wait for row y+2, one __syncthreads, issue the copy of row y+4,
+// recover rho, u, T of row y+2 from its conserved moments, update row y. The
+// conserved-moment recovery is either FP64 (REC = 0) or double-float on the
+// FP32 pipes (REC = 1); the ignition test T > T_ig is taken in that precision.
+// The TNE statistics of the updated state's input (Delta_5..Delta_16, Sec. VI)
+// accumulate in registers and are reduced per strip into FP64.
+#include <float.h>
+
+#include "cell.cuh"
+#include "kernels.cuh"
+#include "reduce.cuh"
+#include "vec2.cuh"
+
+namespace lbk {
+
+namespace {
+
+constexpr int MT = 64;         // threads per block
+constexpr int NWM = MT / 32;   // warps per block
+constexpr int BW = 2 * MT;     // columns per strip
+constexpr int RW = BW + 8;     // staged row: x0-4 .. x0+BW+3 (16-byte aligned chunks)
+constexpr int CHUNKS = RW / 4; // 16-byte chunks per plane row
+constexpr int ROW_CHUNKS = NPLANE * CHUNKS;
+constexpr int PF = 2;          // staged rows in flight beyond y+2
+constexpr int NRING = 5 + PF;  // staged rows kept
+constexpr int MRING = 4;       // macro rows kept
+constexpr int MW = BW + 4;     // macro row: x0-2 .. x0+BW+1, own cells at even offsets
+constexpr size_t OFF_MAC = (size_t)NRING * NPLANE * RW * 4;
+constexpr size_t OFF_IGN = OFF_MAC + (size_t)4 * MRING * MW * 4;
+constexpr size_t OFF_TSUM = (OFF_IGN + (size_t)MRING * BW + 15) / 16 * 16;
+constexpr size_t OFF_TMM = OFF_TSUM + (size_t)NWM * NSUM * 8;
+constexpr size_t MARCH_SMEM = OFF_TMM + (size_t)NWM * NMM * 4;
+
+__device__ __forceinline__ void cp16(void* dst, const void* src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ int ring_slot(int r) { return (r + NRING) % NRING; }
+__device__ __forceinline__ int mac_slot(int r) { return (r + MRING) & (MRING - 1); }
+
+// Stage row r (boundary-mapped) of all 17 planes, columns x0-4 .. x0+BW+3.
+__device__ __forceinline__ void issue_row(const float* __restrict__ in, float* ring, int r,
+                                          int x0, const ModelConst<float>& K)
+{
+    const int gy = map_index(r, K.ny, K.bc_y);
+    const float* rowp = in + (int64_t)gy * K.pitch;
+    float* slot = ring + (size_t)ring_slot(r) * NPLANE * RW;
+    for (int c = threadIdx.x; c < ROW_CHUNKS; c += MT) {
+        const int p = c / CHUNKS, ch = c - p * CHUNKS;
+        const int x = x0 - 4 + 4 * ch;
+        float* dst = slot + p * RW + 4 * ch;
+        const float* src = rowp + p * K.plane;
+        if (x >= 0 && x + 4 <= K.nx) {
+            cp16(dst, src + x);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++) dst[e] = src[map_index(x + e, K.nx, K.bc_x)];
+        }
+    }
+}
+
+struct DfConst {
+    float ch[4], cl[4], wh[4], wl[4], idh, idl, tigh, tigl;
+};
+
+__device__ __forceinline__ void split(double v, float& h, float& l)
+{
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+// Double-float recovery of rho, u, T for a pair of cells (Eqs. (5)-(7)): exact
+// butterflies by TwoSum, conserved moments as hi + lo, u and T by corrected
+// quotients. Returns the FP32-rounded values and the ignition decisions.
+__device__ __forceinline__ void recover_pair_df(const V2* f, const DfConst& C, V2& rho, V2& ux,
+                                                V2& uy, V2& T, bool& ig0, bool& ig1, bool& ok0,
+                                                bool& ok1)
+{
+    D2 P[2], E[2], AX[4], AY[4]; // sector slots: axis0, axis2 | diag1, diag3
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        const int b = 8 * a;
+        D2 s02 = two_sum(f[b], f[b + 2]), s13 = two_sum(f[b + 1], f[b + 3]);
+        AX[a] = two_sum(f[b], -f[b + 2]);
+        AY[a] = two_sum(f[b + 1], -f[b + 3]);
+        P[a] = d_add(s02, s13);
+    }
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+        const int b = 4 + 8 * d;
+        D2 s01 = two_sum(f[b], f[b + 1]), d01 = two_sum(f[b], -f[b + 1]);
+        D2 s23 = two_sum(f[b + 2], f[b + 3]), d23 = two_sum(f[b + 2], -f[b + 3]);
+        E[d] = d_add(s01, s23);
+        AY[2 + d] = d_add(s01, d_neg(s23));
+        AX[2 + d] = d_add(d01, d_neg(d23));
+    }
+    // slot -> orbit: 0 -> 0, 1 -> 2, 2 -> 1, 3 -> 3
+    const D2 m1 = d_add(d_add(P[0], P[1]), d_add(E[0], E[1]));
+    const D2 m2 = d_add(d_add(d_mul_c(AX[0], C.ch[0], C.cl[0]), d_mul_c(AX[1], C.ch[2], C.cl[2])),
+                        d_add(d_mul_c(AX[2], C.ch[1], C.cl[1]), d_mul_c(AX[3], C.ch[3], C.cl[3])));
+    const D2 m3 = d_add(d_add(d_mul_c(AY[0], C.ch[0], C.cl[0]), d_mul_c(AY[1], C.ch[2], C.cl[2])),
+                        d_add(d_mul_c(AY[2], C.ch[1], C.cl[1]), d_mul_c(AY[3], C.ch[3], C.cl[3])));
+    const D2 m4 = d_add(d_add(d_mul_c(P[0], C.wh[0], C.wl[0]), d_mul_c(P[1], C.wh[2], C.wl[2])),
+                        d_add(d_mul_c(E[0], C.wh[1], C.wl[1]), d_mul_c(E[1], C.wh[3], C.wl[3])));
+    const V2 rb(__frcp_rn(m1.hi.x()), __frcp_rn(m1.hi.y()));
+    const D2 vx = d_div(m2, m1, rb), vy = d_div(m3, m1, rb), e = d_div(m4, m1, rb);
+    const D2 t = d_mul_c(d_add(e, d_neg(d_add(d_sqr(vx), d_sqr(vy)))), C.idh, C.idl);
+    rho = m1.hi;
+    ux = vx.hi;
+    uy = vy.hi;
+    T = t.hi;
+    ig0 = t.hi.x() > C.tigh || (t.hi.x() == C.tigh && t.lo.x() > C.tigl);
+    ig1 = t.hi.y() > C.tigh || (t.hi.y() == C.tigh && t.lo.y() > C.tigl);
+    ok0 = m1.hi.x() > 0.0f && t.hi.x() > 0.0f && t.hi.x() <= FLT_MAX;
+    ok1 = m1.hi.y() > 0.0f && t.hi.y() > 0.0f && t.hi.y() <= FLT_MAX;
+}
+
+// Plain FP32 velocity of one cell (halo columns, used only inside grad u).
+__device__ __forceinline__ void velocity_f32(const float* f, const ModelConst<float>& K,
+                                             float& ux, float& uy)
+{
+    float rho = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; i++) rho += f[i];
+    const float jx = K.c[0] * (f[0] - f[2]) + K.c[2] * (f[8] - f[10]) +
+                     K.c[1] * (f[4] - f[5] - f[6] + f[7]) + K.c[3] * (f[12] - f[13] - f[14] + f[15]);
+    const float jy = K.c[0] * (f[1] - f[3]) + K.c[2] * (f[9] - f[11]) +
+                     K.c[1] * (f[4] + f[5] - f[6] - f[7]) + K.c[3] * (f[12] + f[13] - f[14] - f[15]);
+    ux = jx / rho;
+    uy = jy / rho;
+}
+
+template <int REC>
+__device__ __forceinline__ void row_macros(const float* ring, float* mac, unsigned char* ign,
+                                           int r, const ModelConst<float>& K, const DfConst& C,
+                                           int& bad, bool act0, bool act1)
+{
+    const int tid = threadIdx.x;
+    const float* slot = ring + (size_t)ring_slot(r) * NPLANE * RW;
+    const int ms = mac_slot(r);
+    const int lx = 2 * tid + 4;
+    V2 f[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) f[i] = V2(*reinterpret_cast<const float2*>(slot + i * RW + lx));
+    V2 rho, ux, uy, T;
+    bool ig0, ig1, ok0, ok1;
+    if constexpr (REC == 1) {
+        recover_pair_df(f, C, rho, ux, uy, T, ig0, ig1, ok0, ok1);
+    } else {
+        float a[16], b[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) a[i] = f[i].x(), b[i] = f[i].y();
+        double r0, u0, v0, t0, r1, u1, v1, t1;
+        recover_f64(K.cd, K.wd, K.inv_DId, a, r0, u0, v0, t0);
+        recover_f64(K.cd, K.wd, K.inv_DId, b, r1, u1, v1, t1);
+        rho = V2((float)r0, (float)r1);
+        ux = V2((float)u0, (float)u1);
+        uy = V2((float)v0, (float)v1);
+        T = V2((float)t0, (float)t1);
+        ig0 = t0 > K.T_igd;
+        ig1 = t1 > K.T_igd;
+        ok0 = r0 > 0.0 && t0 > 0.0 && t0 <= DBL_MAX;
+        ok1 = r1 > 0.0 && t1 > 0.0 && t1 <= DBL_MAX;
+    }
+    if ((act0 && !ok0) || (act1 && !ok1)) bad = 1;
+    const int mi = 2 * tid + 2;
+    *reinterpret_cast<float2*>(mac + (0 * MRING + ms) * MW + mi) = rho.v;
+    *reinterpret_cast<float2*>(mac + (1 * MRING + ms) * MW + mi) = ux.v;
+    *reinterpret_cast<float2*>(mac + (2 * MRING + ms) * MW + mi) = uy.v;
+    *reinterpret_cast<float2*>(mac + (3 * MRING + ms) * MW + mi) = T.v;
+    ign[ms * BW + 2 * tid] = ig0;
+    ign[ms * BW + 2 * tid + 1] = ig1;
+    // halo columns x0-1 and x0+BW: velocity only (grad u)
+    if (tid == 0 || tid == MT - 1) {
+        const int hx = tid == 0 ? 3 : BW + 4;
+        const int hm = tid == 0 ? 1 : BW + 2;
+        float g[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) g[i] = slot[i * RW + hx];
+        float hu, hv;
+        velocity_f32(g, K, hu, hv);
+        mac[(1 * MRING + ms) * MW + hm] = hu;
+        mac[(2 * MRING + ms) * MW + hm] = hv;
+    }
+}
+
+// NND flux differences of a pair of cells (x, x+1) along x, from q_{x-2..x+3}.
+struct Q6 {
+    float a, b, c, d, e, g; // x-2, x-1, x, x+1, x+2, x+3
+};
+__device__ __forceinline__ Q6 load6(const float* row, int lx)
+{
+    const float2 A = *reinterpret_cast<const float2*>(row + lx - 2);
+    const float2 B = *reinterpret_cast<const float2*>(row + lx);
+    const float2 Cc = *reinterpret_cast<const float2*>(row + lx + 2);
+    return {A.x, A.y, B.x, B.y, Cc.x, Cc.y};
+}
+// upwind side v > 0: (d1 + (mm(d1,d2) - mm(d0,d1))/2) for both cells
+__device__ __forceinline__ V2 nnd_pos_x(const Q6& q)
+{
+    const float d0 = q.b - q.a, d1 = q.c - q.b, d2 = q.d - q.c, d3 = q.e - q.d;
+    const float m01 = mm1(d0, d1), m12 = mm1(d1, d2), m23 = mm1(d2, d3);
+    return fma(V2(0.5f), V2(m12, m23) - V2(m01, m12), V2(d1, d2));
+}
+// upwind side v < 0: (d2 - (mm(d2,d3) - mm(d1,d2))/2) for both cells
+__device__ __forceinline__ V2 nnd_neg_x(const Q6& q)
+{
+    const float d1 = q.c - q.b, d2 = q.d - q.c, d3 = q.e - q.d, d4 = q.g - q.e;
+    const float m12 = mm1(d1, d2), m23 = mm1(d2, d3), m34 = mm1(d3, d4);
+    return fma(V2(-0.5f), V2(m23, m34) - V2(m12, m23), V2(d2, d3));
+}
+__device__ __forceinline__ V2 ldv(const float* p) { return V2(*reinterpret_cast<const float2*>(p)); }
+// along y from rows y-2..y+1 (v > 0) or y-1..y+2 (v < 0), packed over the pair
+__device__ __forceinline__ V2 nnd_pos_y(V2 qm2, V2 qm1, V2 q0, V2 qp1)
+{
+    const V2 d0 = qm1 - qm2, d1 = q0 - qm1, d2 = qp1 - q0;
+    return fma(V2(0.5f), mm2(d1, d2) - mm2(d0, d1), d1);
+}
+__device__ __forceinline__ V2 nnd_neg_y(V2 qm1, V2 q0, V2 qp1, V2 qp2)
+{
+    const V2 d1 = q0 - qm1, d2 = qp1 - q0, d3 = qp2 - qp1;
+    return fma(V2(-0.5f), mm2(d2, d3) - mm2(d1, d2), d2);
+}
+
+template <int REC>
+__global__ void __launch_bounds__(MT, 3)
+    march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* ring = reinterpret_cast<float*>(smem);
+    float* mac = reinterpret_cast<float*>(smem + OFF_MAC);
+    unsigned char* ign = smem + OFF_IGN;
+    double* tsum = reinterpret_cast<double*>(smem + OFF_TSUM);
+    float* tmm = reinterpret_cast<float*>(smem + OFF_TMM);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nx = K.nx, ny = K.ny;
+    const float* __restrict__ in = static_cast<const float*>(a.in);
+    float* __restrict__ out = static_cast<float*>(a.out);
+
+    DfConst C;
+#pragma unroll
+    for (int o = 0; o < 4; o++) {
+        split(K.cd[o], C.ch[o], C.cl[o]);
+        split(K.wd[o], C.wh[o], C.wl[o]);
+    }
+    split(K.inv_DId, C.idh, C.idl);
+    split(K.T_igd, C.tigh, C.tigl);
+
+    const int64_t step = a.ctr->step;
+    const bool do_tne = a.tne_every > 0 && (step % a.tne_every) == 0;
+    if (do_tne) {
+        for (int i = tid; i < NWM * NSUM; i += MT) tsum[i] = 0.0;
+        for (int i = tid; i < NWM * NMM; i += MT) tmm[i] = (i % NMM) < TNE_K ? FLT_MAX : -FLT_MAX;
+    }
+    float tmin[TNE_K], tmax[TNE_K];
+#pragma unroll
+    for (int k = 0; k < TNE_K; k++) tmin[k] = FLT_MAX, tmax[k] = -FLT_MAX;
+    int bad = 0;
+
+    const int nsx = (nx + BW - 1) / BW, nsy = (ny + strip_rows - 1) / strip_rows;
+    const int nstrips = nsx * nsy;
+    const int lx = 2 * tid + 4;  // own cells in a staged row
+    const int mi = 2 * tid + 2;  // own cells in a macro row
+    const float dt = K.dt;
+
+    for (int s = blockIdx.x; s < nstrips; s += gridDim.x) {
+        const int x0 = (s / nsy) * BW, y0 = (s % nsy) * strip_rows;
+        const int yend = y0 + strip_rows < ny ? y0 + strip_rows : ny;
+        const int cx = x0 + 2 * tid;
+        const bool act0 = cx < nx, act1 = cx + 1 < nx;
+        float tsm[NSUM];
+#pragma unroll
+        for (int q = 0; q < NSUM; q++) tsm[q] = 0.f;
+
+        __syncthreads(); // the previous strip is done with the rings
+        for (int r = y0 - 2; r <= y0 + 1 + PF; r++) {
+            if (r <= yend + 1) issue_row(in, ring, r, x0, K);
+            cp_commit();
+        }
+        cp_wait<PF>(); // rows y0-2 .. y0+1 have landed
+        __syncthreads();
+        for (int r = y0 - 1; r <= y0 + 1; r++) row_macros<REC>(ring, mac, ign, r, K, C, bad, act0, act1);
+
+        for (int y = y0; y < yend; y++) {
+            cp_wait<PF - 1>(); // row y+2 has landed
+            __syncthreads();
+            if (y + 2 + PF <= yend + 1) issue_row(in, ring, y + 2 + PF, x0, K);
+            cp_commit();
+            if (y + 2 <= yend) row_macros<REC>(ring, mac, ign, y + 2, K, C, bad, act0, act1);
+
+            // ---------------- update of row y ----------------
+            const float* r0 = ring + (size_t)ring_slot(y) * NPLANE * RW;
+            const float* rm1 = ring + (size_t)ring_slot(y - 1) * NPLANE * RW;
+            const float* rm2 = ring + (size_t)ring_slot(y - 2) * NPLANE * RW;
+            const float* rp1 = ring + (size_t)ring_slot(y + 1) * NPLANE * RW;
+            const float* rp2 = ring + (size_t)ring_slot(y + 2) * NPLANE * RW;
+            const int ms = mac_slot(y), msm = mac_slot(y - 1), msp = mac_slot(y + 1);
+            V2 f[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) f[i] = ldv(r0 + i * RW + lx);
+            const V2 lam0 = ldv(r0 + 16 * RW + lx);
+            const V2 rho = ldv(mac + (0 * MRING + ms) * MW + mi);
+            const V2 ux = ldv(mac + (1 * MRING + ms) * MW + mi);
+            const V2 uy = ldv(mac + (2 * MRING + ms) * MW + mi);
+            const V2 T = ldv(mac + (3 * MRING + ms) * MW + mi);
+            const bool ig0 = ign[ms * BW + 2 * tid], ig1 = ign[ms * BW + 2 * tid + 1];
+
+            // moments, equilibrium, non-equilibrium parts
+            V2 m[16], q[16], D[TNE_K];
+            forward_moments(K, f, m);
+            feq_moments(V2(K.DI), rho, ux, uy, T, q);
+#pragma unroll
+            for (int k = 0; k < TNE_K; k++) D[k] = m[k + 4] - q[k + 4];
+
+            // grad u: x from the macro row (halo columns included), y from rows y+-1
+            const float* uxr = mac + (1 * MRING + ms) * MW;
+            const float* uyr = mac + (2 * MRING + ms) * MW;
+            const float2 uxl = *reinterpret_cast<const float2*>(uxr + mi - 2);
+            const float2 uxh = *reinterpret_cast<const float2*>(uxr + mi + 2);
+            const float2 uyl = *reinterpret_cast<const float2*>(uyr + mi - 2);
+            const float2 uyh = *reinterpret_cast<const float2*>(uyr + mi + 2);
+            const V2 dux_dx = (V2(ux.y(), uxh.x) - V2(uxl.y, ux.x())) * K.half_inv_dx;
+            const V2 duy_dx = (V2(uy.y(), uyh.x) - V2(uyl.y, uy.x())) * K.half_inv_dx;
+            const V2 dux_dy = (ldv(mac + (1 * MRING + msp) * MW + mi) -
+                               ldv(mac + (1 * MRING + msm) * MW + mi)) * K.half_inv_dy;
+            const V2 duy_dy = (ldv(mac + (2 * MRING + msp) * MW + mi) -
+                               ldv(mac + (2 * MRING + msm) * MW + mi)) * K.half_inv_dy;
+            const V2 theta = (dux_dx + duy_dy) * K.inv_DI;
+            const V2 shear = duy_dx + dux_dy;
+            const V2 rT = rho * T;
+            const V2 A8 = (rT * K.A8c) * fma(V2(4.f) * ux, dux_dx - theta, V2(2.f) * uy * shear);
+            const V2 A9 = (rT * K.A9c) * fma(V2(4.f) * uy, duy_dy - theta, V2(2.f) * ux * shear);
+
+            // reaction over dt (Eq. (28)), decided by the recovered T
+            float dl0 = 0.f, dl1 = 0.f;
+            if (ig0) dl0 = reaction_increment(lam0.x(), K.omega1 * rT.x(), K.omega2 * rT.x(), dt);
+            if (ig1) dl1 = reaction_increment(lam0.y(), K.omega1 * rT.y(), K.omega2 * rT.y(), dt);
+            const V2 dlam(dl0, dl1);
+            const V2 cr = dlam * K.chem;
+
+            // collision in moment space and back
+            V2 dq[16], Om[16], W[16];
+            dfeq_dT(V2(K.DI), rho, ux, uy, T, dq);
+            Om[0] = Om[1] = Om[2] = V2(0.f);
+            Om[3] = dq[3] * cr;
+#pragma unroll
+            for (int k = 4; k < 16; k++) Om[k] = fma(V2(-K.S[k]), D[k - 4], dq[k] * cr);
+            Om[7] += A8;
+            Om[8] += A9;
+            inverse_moments(K, Om, W);
+
+            // NND flux differences, upwind side fixed per velocity
+            V2 adv[16];
+#pragma unroll
+            for (int o = 0; o < 2; o++) { // axis orbits 0, 2
+                const int i0 = 8 * o;
+                const float cxs = K.c[2 * o] * K.inv_dx, cys = K.c[2 * o] * K.inv_dy;
+                adv[i0 + 0] = cxs * nnd_pos_x(load6(r0 + (i0 + 0) * RW, lx));
+                adv[i0 + 2] = -cxs * nnd_neg_x(load6(r0 + (i0 + 2) * RW, lx));
+                adv[i0 + 1] = cys * nnd_pos_y(ldv(rm2 + (i0 + 1) * RW + lx), ldv(rm1 + (i0 + 1) * RW + lx),
+                                              f[i0 + 1], ldv(rp1 + (i0 + 1) * RW + lx));
+                adv[i0 + 3] = -cys * nnd_neg_y(ldv(rm1 + (i0 + 3) * RW + lx), f[i0 + 3],
+                                               ldv(rp1 + (i0 + 3) * RW + lx), ldv(rp2 + (i0 + 3) * RW + lx));
+            }
+#pragma unroll
+            for (int o = 0; o < 2; o++) { // diagonal orbits 1, 3
+                const int i0 = 4 + 8 * o;
+                const float cxs = K.c[2 * o + 1] * K.inv_dx, cys = K.c[2 * o + 1] * K.inv_dy;
+#define PY(i) nnd_pos_y(ldv(rm2 + (i) * RW + lx), ldv(rm1 + (i) * RW + lx), f[i], ldv(rp1 + (i) * RW + lx))
+#define NY(i) nnd_neg_y(ldv(rm1 + (i) * RW + lx), f[i], ldv(rp1 + (i) * RW + lx), ldv(rp2 + (i) * RW + lx))
+                adv[i0 + 0] = fma(cxs, nnd_pos_x(load6(r0 + (i0 + 0) * RW, lx)), cys * PY(i0 + 0));
+                adv[i0 + 1] = fma(cys, PY(i0 + 1), -cxs * nnd_neg_x(load6(r0 + (i0 + 1) * RW, lx)));
+                adv[i0 + 2] = -(fma(cxs, nnd_neg_x(load6(r0 + (i0 + 2) * RW, lx)), cys * NY(i0 + 2)));
+                adv[i0 + 3] = fma(cxs, nnd_pos_x(load6(r0 + (i0 + 3) * RW, lx)), -cys * NY(i0 + 3));
+            }
+            // lambda: u . grad(lambda) with NND interface values
+            const Q6 lq = load6(r0 + 16 * RW, lx);
+            const V2 lpx = nnd_pos_x(lq), lnx = nnd_neg_x(lq);
+            const V2 lpy = PY(16), lny = NY(16);
+#undef PY
+#undef NY
+            const V2 lax(ux.x() > 0.f ? lpx.x() : lnx.x(), ux.y() > 0.f ? lpx.y() : lnx.y());
+            const V2 lay(uy.x() > 0.f ? lpy.x() : lny.x(), uy.y() > 0.f ? lpy.y() : lny.y());
+            const V2 ladv = fma(ux * K.inv_dx, lax, uy * K.inv_dy * lay);
+            V2 ln = fma(V2(-dt), ladv, lam0) + dlam;
+            ln = vmin(vmax(ln, V2(0.f)), V2(1.f));
+
+            // Euler update and store (two adjacent cells per thread)
+            const int64_t g = (int64_t)y * K.pitch + cx;
+            if (act1) {
+#pragma unroll
+                for (int i = 0; i < 16; i++)
+                    *reinterpret_cast<float2*>(out + i * K.plane + g) = fma(V2(dt), W[i] - adv[i], f[i]).v;
+                *reinterpret_cast<float2*>(out + 16 * K.plane + g) = ln.v;
+            } else if (act0) {
+#pragma unroll
+                for (int i = 0; i < 16; i++) out[i * K.plane + g] = fma(V2(dt), W[i] - adv[i], f[i]).x();
+                out[16 * K.plane + g] = ln.x();
+            }
+
+            // TNE statistics of the state being stepped (Eqs. (90)-(91))
+            if (do_tne) {
+                const float w0 = act0 ? 1.f : 0.f, w1 = act1 ? 1.f : 0.f;
+                V2 d2(0.f);
+#pragma unroll
+                for (int k = 0; k < TNE_K; k++) {
+                    const V2 Dk = D[k] * V2(w0, w1);
+                    d2 = fma(Dk, Dk, d2);
+                    tsm[k] += Dk.x() + Dk.y();
+                    tsm[TNE_K + k] += fabsf(Dk.x()) + fabsf(Dk.y());
+                    tmin[k] = fminf(tmin[k], fminf(act0 ? Dk.x() : FLT_MAX, act1 ? Dk.y() : FLT_MAX));
+                    tmax[k] = fmaxf(tmax[k], fmaxf(act0 ? Dk.x() : -FLT_MAX, act1 ? Dk.y() : -FLT_MAX));
+                }
+                tsm[2 * TNE_K] += sqrtf(d2.x()) + sqrtf(d2.y());
+                tsm[2 * TNE_K + 1] += d2.x() + d2.y();
+            }
+        }
+        cp_wait<0>();
+        if (do_tne) { // per strip: warp sums in FP32, then FP64 per warp
+#pragma unroll
+            for (int q = 0; q < NSUM; q++) {
+                const float v = warp_sum(tsm[q]);
+                if (lane == 0) tsum[warp * NSUM + q] += (double)v;
+            }
+        }
+    }
+
+    // end of step: status, TNE partials, arrival count; the last block finishes
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(&a.ctr->status, 1);
+    if (do_tne) {
+#pragma unroll
+        for (int k = 0; k < TNE_K; k++) {
+            const float mn = warp_min(tmin[k]), mx = warp_max(tmax[k]);
+            if (lane == 0) {
+                tmm[warp * NMM + k] = mn;
+                tmm[warp * NMM + TNE_K + k] = mx;
+            }
+        }
+        __syncthreads();
+        double* part = a.partials + (size_t)blockIdx.x * TNE_PART;
+        for (int q = tid; q < NSUM; q += MT) {
+            double sacc = 0.0;
+            for (int w = 0; w < NWM; w++) sacc += tsum[w * NSUM + q];
+            part[q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K)] = sacc;
+        }
+        for (int q = tid; q < NMM; q += MT) {
+            float v = tmm[q];
+            for (int w = 1; w < NWM; w++)
+                v = q < TNE_K ? fminf(v, tmm[w * NMM + q]) : fmaxf(v, tmm[w * NMM + q]);
+            part[2 * TNE_K + q] = (double)v;
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    __shared__ unsigned int s_last;
+    if (tid == 0) s_last = (atomicAdd(&a.ctr->arrivals, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (do_tne) {
+            const int64_t slot = a.ctr->hist_count % a.hist_cap;
+            finish_tne(a.partials, gridDim.x, a.hist + slot, step, a.cell_area);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (do_tne) a.ctr->hist_count += 1;
+            a.ctr->step = step + 1;
+            a.ctr->arrivals = 0u;
+        }
+    }
+}
+
+template <int REC>
+cudaError_t march_prepare()
+{
+    static cudaError_t done = cudaFuncSetAttribute(
+        march_kernel<REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MARCH_SMEM);
+    return done;
+}
+
+} // namespace
+
+int march_strip_rows(int ny)
+{
+    return ny >= 4096 ? 32 : (ny >= 64 ? 32 : ny);
+}
+
+int march_grid(int recovery, int nx, int ny)
+{
+    cudaError_t e = recovery == 1 ? march_prepare<1>() : march_prepare<0>();
+    if (e != cudaSuccess) return -1;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = recovery == 1
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<1>, MT, MARCH_SMEM)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<0>, MT, MARCH_SMEM);
+    if (e != cudaSuccess) return -1;
+    if (per_sm < 1) per_sm = 1;
+    const int rows = march_strip_rows(ny);
+    const long strips = (long)((nx + BW - 1) / BW) * ((ny + rows - 1) / rows);
+    const long g = (long)per_sm * sms;
+    return (int)(strips < g ? strips : g);
+}
+
+cudaError_t launch_march(int recovery, const ModelConst<float>& K, const StepLaunch& a,
+                         cudaStream_t s)
+{
+    cudaError_t e = recovery == 1 ? march_prepare<1>() : march_prepare<0>();
+    if (e != cudaSuccess) return e;
+    const int rows = march_strip_rows(K.ny);
+    if (recovery == 1)
+        march_kernel<1><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+    else
+        march_kernel<0><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+    return cudaGetLastError();
+}
+
+} // namespace lbk

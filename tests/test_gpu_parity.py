@@ -85,7 +85,8 @@ def test_init_is_discrete_equilibrium(prec):
 
 # ------------------------------------------------------------------ fused step, 2-D
 @pytest.mark.parametrize("prec,rec", PRECS, ids=PID)
-@pytest.mark.parametrize("nx,ny,bc", [(70, 37, (0, 0)), (45, 19, (1, 1)), (33, 9, (1, 0))])
+@pytest.mark.parametrize("nx,ny,bc", [(70, 37, (0, 0)), (45, 19, (1, 1)), (33, 9, (1, 0)),
+                                      (300, 77, (0, 0)), (262, 40, (1, 1)), (130, 3, (0, 1))])
 def test_step_2d_nonequilibrium_parity(prec, rec, nx, ny, bc):
     params, fields = mixed_2d(nx, ny, bc=bc, seed=nx)
     s, ob, f, lam = start(params, fields, prec, rec, noise_seed=ny)
