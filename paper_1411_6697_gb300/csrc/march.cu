@@ -396,7 +396,10 @@ __global__ void __launch_bounds__(MT, 3)
             // lambda: u . grad(lambda) with NND interface values
             const Q6 lq = load6(r0 + 16 * RW, lx);
             const V2 lpx = nnd_pos_x(lq), lnx = nnd_neg_x(lq);
-            const V2 lpy = PY(16), lny = NY(16);
+            const V2 lpy = nnd_pos_y(ldv(rm2 + 16 * RW + lx), ldv(rm1 + 16 * RW + lx), lam0,
+                                     ldv(rp1 + 16 * RW + lx));
+            const V2 lny = nnd_neg_y(ldv(rm1 + 16 * RW + lx), lam0, ldv(rp1 + 16 * RW + lx),
+                                     ldv(rp2 + 16 * RW + lx));
 #undef PY
 #undef NY
             const V2 lax(ux.x() > 0.f ? lpx.x() : lnx.x(), ux.y() > 0.f ? lpx.y() : lnx.y());
