@@ -57,25 +57,33 @@ __device__ __forceinline__ void cp_wait()
 __device__ __forceinline__ int ring_slot(int r) { return (r + NRING) % NRING; }
 __device__ __forceinline__ int mac_slot(int r) { return (r + MRING) & (MRING - 1); }
 
-// Stage row r (boundary-mapped) of all 17 planes, columns x0-4 .. x0+BW+3.
+// Stage row r (boundary-mapped) of all 17 planes, columns x0-4 .. x0+BW+3: chunks
+// 0..31 of each plane by one warp (lane = chunk), chunks 32..33 by the first 34
+// threads.
+__device__ __forceinline__ void stage_chunk(const float* rowp, float* slot, int p, int ch, int x0,
+                                            const ModelConst<float>& K)
+{
+    const int x = x0 - 4 + 4 * ch;
+    float* dst = slot + p * RW + 4 * ch;
+    const float* src = rowp + p * K.plane;
+    if (x >= 0 && x + 4 <= K.nx) {
+        cp16(dst, src + x);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++) dst[e] = src[map_index(x + e, K.nx, K.bc_x)];
+    }
+}
 __device__ __forceinline__ void issue_row(const float* __restrict__ in, float* ring, int r,
                                           int x0, const ModelConst<float>& K)
 {
+    static_assert(CHUNKS == 34 && NWM == 2, "staging layout assumes 34 chunks and 2 warps");
     const int gy = map_index(r, K.ny, K.bc_y);
     const float* rowp = in + (int64_t)gy * K.pitch;
     float* slot = ring + (size_t)ring_slot(r) * NPLANE * RW;
-    for (int c = threadIdx.x; c < ROW_CHUNKS; c += MT) {
-        const int p = c / CHUNKS, ch = c - p * CHUNKS;
-        const int x = x0 - 4 + 4 * ch;
-        float* dst = slot + p * RW + 4 * ch;
-        const float* src = rowp + p * K.plane;
-        if (x >= 0 && x + 4 <= K.nx) {
-            cp16(dst, src + x);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; e++) dst[e] = src[map_index(x + e, K.nx, K.bc_x)];
-        }
-    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int p = w; p < NPLANE; p += NWM) stage_chunk(rowp, slot, p, lane, x0, K);
+    if (threadIdx.x < 2 * NPLANE)
+        stage_chunk(rowp, slot, threadIdx.x >> 1, 32 + (threadIdx.x & 1), x0, K);
 }
 
 struct DfConst {
@@ -149,22 +157,28 @@ __device__ __forceinline__ void velocity_f32(const float* f, const ModelConst<fl
     uy = jy / rho;
 }
 
+struct MacRow {
+    V2 rho, ux, uy, T;
+    bool ig0, ig1;
+    float hu, hv; // velocity of the halo column (threads 0 and MT-1)
+};
+
+// rho, u, T of the thread's two cells of staged row r, kept in registers until
+// store_macros so that the update of an earlier row can run in between.
 template <int REC>
-__device__ __forceinline__ void row_macros(const float* ring, float* mac, unsigned char* ign,
-                                           int r, const ModelConst<float>& K, const DfConst& C,
-                                           int& bad, bool act0, bool act1)
+__device__ __forceinline__ MacRow row_macros(const float* ring, int r, const ModelConst<float>& K,
+                                             const DfConst& C, int& bad, bool act0, bool act1)
 {
     const int tid = threadIdx.x;
     const float* slot = ring + (size_t)ring_slot(r) * NPLANE * RW;
-    const int ms = mac_slot(r);
     const int lx = 2 * tid + 4;
     V2 f[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) f[i] = V2(*reinterpret_cast<const float2*>(slot + i * RW + lx));
-    V2 rho, ux, uy, T;
-    bool ig0, ig1, ok0, ok1;
+    MacRow o;
+    bool ok0, ok1;
     if constexpr (REC == 1) {
-        recover_pair_df(f, C, rho, ux, uy, T, ig0, ig1, ok0, ok1);
+        recover_pair_df(f, C, o.rho, o.ux, o.uy, o.T, o.ig0, o.ig1, ok0, ok1);
     } else {
         float a[16], b[16];
 #pragma unroll
@@ -172,34 +186,42 @@ __device__ __forceinline__ void row_macros(const float* ring, float* mac, unsign
         double r0, u0, v0, t0, r1, u1, v1, t1;
         recover_f64(K.cd, K.wd, K.inv_DId, a, r0, u0, v0, t0);
         recover_f64(K.cd, K.wd, K.inv_DId, b, r1, u1, v1, t1);
-        rho = V2((float)r0, (float)r1);
-        ux = V2((float)u0, (float)u1);
-        uy = V2((float)v0, (float)v1);
-        T = V2((float)t0, (float)t1);
-        ig0 = t0 > K.T_igd;
-        ig1 = t1 > K.T_igd;
+        o.rho = V2((float)r0, (float)r1);
+        o.ux = V2((float)u0, (float)u1);
+        o.uy = V2((float)v0, (float)v1);
+        o.T = V2((float)t0, (float)t1);
+        o.ig0 = t0 > K.T_igd;
+        o.ig1 = t1 > K.T_igd;
         ok0 = r0 > 0.0 && t0 > 0.0 && t0 <= DBL_MAX;
         ok1 = r1 > 0.0 && t1 > 0.0 && t1 <= DBL_MAX;
     }
     if ((act0 && !ok0) || (act1 && !ok1)) bad = 1;
-    const int mi = 2 * tid + 2;
-    *reinterpret_cast<float2*>(mac + (0 * MRING + ms) * MW + mi) = rho.v;
-    *reinterpret_cast<float2*>(mac + (1 * MRING + ms) * MW + mi) = ux.v;
-    *reinterpret_cast<float2*>(mac + (2 * MRING + ms) * MW + mi) = uy.v;
-    *reinterpret_cast<float2*>(mac + (3 * MRING + ms) * MW + mi) = T.v;
-    ign[ms * BW + 2 * tid] = ig0;
-    ign[ms * BW + 2 * tid + 1] = ig1;
-    // halo columns x0-1 and x0+BW: velocity only (grad u)
-    if (tid == 0 || tid == MT - 1) {
+    o.hu = o.hv = 0.f;
+    if (tid == 0 || tid == MT - 1) { // halo columns x0-1 and x0+BW: velocity only
         const int hx = tid == 0 ? 3 : BW + 4;
-        const int hm = tid == 0 ? 1 : BW + 2;
         float g[16];
 #pragma unroll
         for (int i = 0; i < 16; i++) g[i] = slot[i * RW + hx];
-        float hu, hv;
-        velocity_f32(g, K, hu, hv);
-        mac[(1 * MRING + ms) * MW + hm] = hu;
-        mac[(2 * MRING + ms) * MW + hm] = hv;
+        velocity_f32(g, K, o.hu, o.hv);
+    }
+    return o;
+}
+
+__device__ __forceinline__ void store_macros(float* mac, unsigned char* ign, int r, const MacRow& o)
+{
+    const int tid = threadIdx.x;
+    const int ms = mac_slot(r);
+    const int mi = 2 * tid + 2;
+    *reinterpret_cast<float2*>(mac + (0 * MRING + ms) * MW + mi) = o.rho.v;
+    *reinterpret_cast<float2*>(mac + (1 * MRING + ms) * MW + mi) = o.ux.v;
+    *reinterpret_cast<float2*>(mac + (2 * MRING + ms) * MW + mi) = o.uy.v;
+    *reinterpret_cast<float2*>(mac + (3 * MRING + ms) * MW + mi) = o.T.v;
+    ign[ms * BW + 2 * tid] = o.ig0;
+    ign[ms * BW + 2 * tid + 1] = o.ig1;
+    if (tid == 0 || tid == MT - 1) {
+        const int hm = tid == 0 ? 1 : BW + 2;
+        mac[(1 * MRING + ms) * MW + hm] = o.hu;
+        mac[(2 * MRING + ms) * MW + hm] = o.hv;
     }
 }
 
@@ -299,14 +321,16 @@ __global__ void __launch_bounds__(MT, 3)
         }
         cp_wait<PF>(); // rows y0-2 .. y0+1 have landed
         __syncthreads();
-        for (int r = y0 - 1; r <= y0 + 1; r++) row_macros<REC>(ring, mac, ign, r, K, C, bad, act0, act1);
+        for (int r = y0 - 1; r <= y0 + 1; r++)
+            store_macros(mac, ign, r, row_macros<REC>(ring, r, K, C, bad, act0, act1));
 
         for (int y = y0; y < yend; y++) {
             cp_wait<PF - 1>(); // row y+2 has landed
             __syncthreads();
             if (y + 2 + PF <= yend + 1) issue_row(in, ring, y + 2 + PF, x0, K);
             cp_commit();
-            if (y + 2 <= yend) row_macros<REC>(ring, mac, ign, y + 2, K, C, bad, act0, act1);
+            // macros of row y+2 (stored after the update of row y, which does not read them)
+            const MacRow next = row_macros<REC>(ring, y + 2, K, C, bad, act0, act1);
 
             // ---------------- update of row y ----------------
             const float* r0 = ring + (size_t)ring_slot(y) * NPLANE * RW;
@@ -369,30 +393,6 @@ __global__ void __launch_bounds__(MT, 3)
             Om[8] += A9;
             inverse_moments(K, Om, W);
 
-            // NND flux differences, upwind side fixed per velocity
-            V2 adv[16];
-#pragma unroll
-            for (int o = 0; o < 2; o++) { // axis orbits 0, 2
-                const int i0 = 8 * o;
-                const float cxs = K.c[2 * o] * K.inv_dx, cys = K.c[2 * o] * K.inv_dy;
-                adv[i0 + 0] = cxs * nnd_pos_x(load6(r0 + (i0 + 0) * RW, lx));
-                adv[i0 + 2] = -cxs * nnd_neg_x(load6(r0 + (i0 + 2) * RW, lx));
-                adv[i0 + 1] = cys * nnd_pos_y(ldv(rm2 + (i0 + 1) * RW + lx), ldv(rm1 + (i0 + 1) * RW + lx),
-                                              f[i0 + 1], ldv(rp1 + (i0 + 1) * RW + lx));
-                adv[i0 + 3] = -cys * nnd_neg_y(ldv(rm1 + (i0 + 3) * RW + lx), f[i0 + 3],
-                                               ldv(rp1 + (i0 + 3) * RW + lx), ldv(rp2 + (i0 + 3) * RW + lx));
-            }
-#pragma unroll
-            for (int o = 0; o < 2; o++) { // diagonal orbits 1, 3
-                const int i0 = 4 + 8 * o;
-                const float cxs = K.c[2 * o + 1] * K.inv_dx, cys = K.c[2 * o + 1] * K.inv_dy;
-#define PY(i) nnd_pos_y(ldv(rm2 + (i) * RW + lx), ldv(rm1 + (i) * RW + lx), f[i], ldv(rp1 + (i) * RW + lx))
-#define NY(i) nnd_neg_y(ldv(rm1 + (i) * RW + lx), f[i], ldv(rp1 + (i) * RW + lx), ldv(rp2 + (i) * RW + lx))
-                adv[i0 + 0] = fma(cxs, nnd_pos_x(load6(r0 + (i0 + 0) * RW, lx)), cys * PY(i0 + 0));
-                adv[i0 + 1] = fma(cys, PY(i0 + 1), -cxs * nnd_neg_x(load6(r0 + (i0 + 1) * RW, lx)));
-                adv[i0 + 2] = -(fma(cxs, nnd_neg_x(load6(r0 + (i0 + 2) * RW, lx)), cys * NY(i0 + 2)));
-                adv[i0 + 3] = fma(cxs, nnd_pos_x(load6(r0 + (i0 + 3) * RW, lx)), -cys * NY(i0 + 3));
-            }
             // lambda: u . grad(lambda) with NND interface values
             const Q6 lq = load6(r0 + 16 * RW, lx);
             const V2 lpx = nnd_pos_x(lq), lnx = nnd_neg_x(lq);
@@ -400,26 +400,51 @@ __global__ void __launch_bounds__(MT, 3)
                                      ldv(rp1 + 16 * RW + lx));
             const V2 lny = nnd_neg_y(ldv(rm1 + 16 * RW + lx), lam0, ldv(rp1 + 16 * RW + lx),
                                      ldv(rp2 + 16 * RW + lx));
-#undef PY
-#undef NY
             const V2 lax(ux.x() > 0.f ? lpx.x() : lnx.x(), ux.y() > 0.f ? lpx.y() : lnx.y());
             const V2 lay(uy.x() > 0.f ? lpy.x() : lny.x(), uy.y() > 0.f ? lpy.y() : lny.y());
             const V2 ladv = fma(ux * K.inv_dx, lax, uy * K.inv_dy * lay);
             V2 ln = fma(V2(-dt), ladv, lam0) + dlam;
             ln = vmin(vmax(ln, V2(0.f)), V2(1.f));
 
-            // Euler update and store (two adjacent cells per thread)
+            // NND flux differences (upwind side fixed per velocity), Euler update, store
             const int64_t g = (int64_t)y * K.pitch + cx;
-            if (act1) {
+            auto put = [&](int i, V2 adv) {
+                const V2 v = fma(V2(dt), W[i] - adv, f[i]);
+                if (act1)
+                    *reinterpret_cast<float2*>(out + i * K.plane + g) = v.v;
+                else if (act0)
+                    out[i * K.plane + g] = v.x();
+            };
+#define PX(i) nnd_pos_x(load6(r0 + (i) * RW, lx))
+#define NX(i) nnd_neg_x(load6(r0 + (i) * RW, lx))
+#define PY(i) nnd_pos_y(ldv(rm2 + (i) * RW + lx), ldv(rm1 + (i) * RW + lx), f[i], ldv(rp1 + (i) * RW + lx))
+#define NY(i) nnd_neg_y(ldv(rm1 + (i) * RW + lx), f[i], ldv(rp1 + (i) * RW + lx), ldv(rp2 + (i) * RW + lx))
 #pragma unroll
-                for (int i = 0; i < 16; i++)
-                    *reinterpret_cast<float2*>(out + i * K.plane + g) = fma(V2(dt), W[i] - adv[i], f[i]).v;
-                *reinterpret_cast<float2*>(out + 16 * K.plane + g) = ln.v;
-            } else if (act0) {
-#pragma unroll
-                for (int i = 0; i < 16; i++) out[i * K.plane + g] = fma(V2(dt), W[i] - adv[i], f[i]).x();
-                out[16 * K.plane + g] = ln.x();
+            for (int o = 0; o < 2; o++) { // axis orbits 0, 2
+                const int i0 = 8 * o;
+                const float cxs = K.c[2 * o] * K.inv_dx, cys = K.c[2 * o] * K.inv_dy;
+                put(i0 + 0, cxs * PX(i0 + 0));
+                put(i0 + 1, cys * PY(i0 + 1));
+                put(i0 + 2, -cxs * NX(i0 + 2));
+                put(i0 + 3, -cys * NY(i0 + 3));
             }
+#pragma unroll
+            for (int o = 0; o < 2; o++) { // diagonal orbits 1, 3
+                const int i0 = 4 + 8 * o;
+                const float cxs = K.c[2 * o + 1] * K.inv_dx, cys = K.c[2 * o + 1] * K.inv_dy;
+                put(i0 + 0, fma(cxs, PX(i0 + 0), cys * PY(i0 + 0)));
+                put(i0 + 1, fma(cys, PY(i0 + 1), -cxs * NX(i0 + 1)));
+                put(i0 + 2, -(fma(cxs, NX(i0 + 2), cys * NY(i0 + 2))));
+                put(i0 + 3, fma(cxs, PX(i0 + 3), -cys * NY(i0 + 3)));
+            }
+#undef PX
+#undef NX
+#undef PY
+#undef NY
+            if (act1)
+                *reinterpret_cast<float2*>(out + 16 * K.plane + g) = ln.v;
+            else if (act0)
+                out[16 * K.plane + g] = ln.x();
 
             // TNE statistics of the state being stepped (Eqs. (90)-(91))
             if (do_tne) {
@@ -437,6 +462,7 @@ __global__ void __launch_bounds__(MT, 3)
                 tsm[2 * TNE_K] += sqrtf(d2.x()) + sqrtf(d2.y());
                 tsm[2 * TNE_K + 1] += d2.x() + d2.y();
             }
+            store_macros(mac, ign, y + 2, next);
         }
         cp_wait<0>();
         if (do_tne) { // per strip: warp sums in FP32, then FP64 per warp
@@ -503,27 +529,56 @@ cudaError_t march_prepare()
 
 } // namespace
 
-int march_strip_rows(int ny)
+// Blocks resident on the whole GPU, and the strip height: the number of strips
+// per column of the grid is chosen so that the strips fill whole waves of the
+// resident blocks while each strip stays long compared with its 3-row
+// prologue (rows staged and macros recovered before the first update).
+namespace {
+int resident_blocks(int recovery)
 {
-    return ny >= 4096 ? 32 : (ny >= 64 ? 32 : ny);
+    static int cache[2] = {-1, -1};
+    int& c = cache[recovery & 1];
+    if (c < 0) {
+        cudaError_t e = recovery == 1 ? march_prepare<1>() : march_prepare<0>();
+        if (e != cudaSuccess) return -1;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = recovery == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &per_sm, march_kernel<1>, MT, MARCH_SMEM)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &per_sm, march_kernel<0>, MT, MARCH_SMEM);
+        if (e != cudaSuccess) return -1;
+        c = (per_sm < 1 ? 1 : per_sm) * sms;
+    }
+    return c;
+}
+} // namespace
+
+void march_plan(int recovery, int nx, int ny, int* grid, int* strip_rows)
+{
+    const int G = resident_blocks(recovery);
+    const int nsx = (nx + BW - 1) / BW;
+    long best_cost = -1;
+    int best_rows = ny;
+    for (int nsy = 1; nsy <= ny; nsy++) {
+        const int rows = (ny + nsy - 1) / nsy;
+        if (rows < 8 && nsy > 1) break;
+        const long strips = (long)nsx * ((ny + rows - 1) / rows);
+        const long waves = (strips + G - 1) / G;
+        const long cost = waves * (rows + 3);
+        if (best_cost < 0 || cost < best_cost) best_cost = cost, best_rows = rows;
+    }
+    const long strips = (long)nsx * ((ny + best_rows - 1) / best_rows);
+    *grid = G < 0 ? -1 : (int)(strips < G ? strips : G);
+    *strip_rows = best_rows;
 }
 
 int march_grid(int recovery, int nx, int ny)
 {
-    cudaError_t e = recovery == 1 ? march_prepare<1>() : march_prepare<0>();
-    if (e != cudaSuccess) return -1;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = recovery == 1
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<1>, MT, MARCH_SMEM)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<0>, MT, MARCH_SMEM);
-    if (e != cudaSuccess) return -1;
-    if (per_sm < 1) per_sm = 1;
-    const int rows = march_strip_rows(ny);
-    const long strips = (long)((nx + BW - 1) / BW) * ((ny + rows - 1) / rows);
-    const long g = (long)per_sm * sms;
-    return (int)(strips < g ? strips : g);
+    int g, r;
+    march_plan(recovery, nx, ny, &g, &r);
+    return g;
 }
 
 cudaError_t launch_march(int recovery, const ModelConst<float>& K, const StepLaunch& a,
@@ -531,7 +586,9 @@ cudaError_t launch_march(int recovery, const ModelConst<float>& K, const StepLau
 {
     cudaError_t e = recovery == 1 ? march_prepare<1>() : march_prepare<0>();
     if (e != cudaSuccess) return e;
-    const int rows = march_strip_rows(K.ny);
+    int g, rows;
+    march_plan(recovery, K.nx, K.ny, &g, &rows);
+    if (g != a.grid) return cudaErrorInvalidConfiguration; // partial buffers sized for a.grid
     if (recovery == 1)
         march_kernel<1><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
     else
