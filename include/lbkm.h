@@ -76,7 +76,10 @@ typedef enum {
 } lbkm_precision;
 
 typedef enum {
-    LBKM_RECOVER_F64 = 0,  /* rho, rho u, rho[(D+I)T+u^2] and rho, u, T in FP64 */
+    LBKM_RECOVER_F64 = 0,  /* rho, u, T formed in FP64 from the conserved moments
+                              rho, rho u, rho[(D+I)T+u^2]; on 2-D grids those sums
+                              are first taken exactly (error-free FP32 transforms)
+                              and carried into FP64 as hi + lo */
     LBKM_RECOVER_DF32 = 1  /* same quantities in double-float (pairs of FP32 with
                               error-free transforms), ~48-bit significand, run on
                               the FP32 pipes */

@@ -14,7 +14,7 @@
 
 #include <string>
 
-#include "../../include/lbkm.h"
+#include "lbkm.h"
 #include "kernels.cuh"
 #include "model.h"
 

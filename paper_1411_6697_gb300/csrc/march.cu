@@ -11,11 +11,13 @@
 // T of rows y-1..y+2, with one halo column on each side for grad u). Per
 // iteration: wait for row y+2, one __syncthreads, issue the copy of row y+4,
 // recover rho, u, T of row y+2 from its conserved moments, update row y. The
-// conserved-moment recovery is either FP64 (REC = 0) or double-float on the
-// FP32 pipes (REC = 1); the ignition test T > T_ig is taken in that precision.
+// conserved moments are summed exactly (TwoSum butterflies, split constants);
+// rho, u, T are then formed in FP64 (REC = 0) or in double-float on the FP32
+// pipes (REC = 1), and the ignition test T > T_ig is taken in that precision.
 // The TNE statistics of the updated state's input (Delta_5..Delta_16, Sec. VI)
 // accumulate in registers and are reduced per strip into FP64.
 #include <float.h>
+#include <stdlib.h>
 
 #include "cell.cuh"
 #include "kernels.cuh"
@@ -96,12 +98,11 @@ __device__ __forceinline__ void split(double v, float& h, float& l)
     l = (float)(v - (double)h);
 }
 
-// Double-float recovery of rho, u, T for a pair of cells (Eqs. (5)-(7)): exact
-// butterflies by TwoSum, conserved moments as hi + lo, u and T by corrected
-// quotients. Returns the FP32-rounded values and the ignition decisions.
-__device__ __forceinline__ void recover_pair_df(const V2* f, const DfConst& C, V2& rho, V2& ux,
-                                                V2& uy, V2& T, bool& ig0, bool& ig1, bool& ok0,
-                                                bool& ok1)
+// Conserved moments m1 = rho, m2 = rho u_x, m3 = rho u_y, m4 = rho[(D+I)T + u^2]
+// (Eqs. (5)-(7)) of a pair of cells as double-float sums: every butterfly is an
+// exact TwoSum, the orbit weights are applied as split constants.
+__device__ __forceinline__ void conserved_pair(const V2* f, const DfConst& C, D2& m1, D2& m2,
+                                               D2& m3, D2& m4)
 {
     D2 P[2], E[2], AX[4], AY[4]; // sector slots: axis0, axis2 | diag1, diag3
 #pragma unroll
@@ -122,13 +123,22 @@ __device__ __forceinline__ void recover_pair_df(const V2* f, const DfConst& C, V
         AX[2 + d] = d_add(d01, d_neg(d23));
     }
     // slot -> orbit: 0 -> 0, 1 -> 2, 2 -> 1, 3 -> 3
-    const D2 m1 = d_add(d_add(P[0], P[1]), d_add(E[0], E[1]));
-    const D2 m2 = d_add(d_add(d_mul_c(AX[0], C.ch[0], C.cl[0]), d_mul_c(AX[1], C.ch[2], C.cl[2])),
-                        d_add(d_mul_c(AX[2], C.ch[1], C.cl[1]), d_mul_c(AX[3], C.ch[3], C.cl[3])));
-    const D2 m3 = d_add(d_add(d_mul_c(AY[0], C.ch[0], C.cl[0]), d_mul_c(AY[1], C.ch[2], C.cl[2])),
-                        d_add(d_mul_c(AY[2], C.ch[1], C.cl[1]), d_mul_c(AY[3], C.ch[3], C.cl[3])));
-    const D2 m4 = d_add(d_add(d_mul_c(P[0], C.wh[0], C.wl[0]), d_mul_c(P[1], C.wh[2], C.wl[2])),
-                        d_add(d_mul_c(E[0], C.wh[1], C.wl[1]), d_mul_c(E[1], C.wh[3], C.wl[3])));
+    m1 = d_add(d_add(P[0], P[1]), d_add(E[0], E[1]));
+    m2 = d_add(d_add(d_mul_c(AX[0], C.ch[0], C.cl[0]), d_mul_c(AX[1], C.ch[2], C.cl[2])),
+               d_add(d_mul_c(AX[2], C.ch[1], C.cl[1]), d_mul_c(AX[3], C.ch[3], C.cl[3])));
+    m3 = d_add(d_add(d_mul_c(AY[0], C.ch[0], C.cl[0]), d_mul_c(AY[1], C.ch[2], C.cl[2])),
+               d_add(d_mul_c(AY[2], C.ch[1], C.cl[1]), d_mul_c(AY[3], C.ch[3], C.cl[3])));
+    m4 = d_add(d_add(d_mul_c(P[0], C.wh[0], C.wl[0]), d_mul_c(P[1], C.wh[2], C.wl[2])),
+               d_add(d_mul_c(E[0], C.wh[1], C.wl[1]), d_mul_c(E[1], C.wh[3], C.wl[3])));
+}
+
+// Double-float recovery: rho, u, T by corrected quotients on the FP32 pipes.
+__device__ __forceinline__ void recover_pair_df(const V2* f, const DfConst& C, V2& rho, V2& ux,
+                                                V2& uy, V2& T, bool& ig0, bool& ig1, bool& ok0,
+                                                bool& ok1)
+{
+    D2 m1, m2, m3, m4;
+    conserved_pair(f, C, m1, m2, m3, m4);
     const V2 rb(__frcp_rn(m1.hi.x()), __frcp_rn(m1.hi.y()));
     const D2 vx = d_div(m2, m1, rb), vy = d_div(m3, m1, rb), e = d_div(m4, m1, rb);
     const D2 t = d_mul_c(d_add(e, d_neg(d_add(d_sqr(vx), d_sqr(vy)))), C.idh, C.idl);
@@ -140,6 +150,19 @@ __device__ __forceinline__ void recover_pair_df(const V2* f, const DfConst& C, V
     ig1 = t.hi.y() > C.tigh || (t.hi.y() == C.tigh && t.lo.y() > C.tigl);
     ok0 = m1.hi.x() > 0.0f && t.hi.x() > 0.0f && t.hi.x() <= FLT_MAX;
     ok1 = m1.hi.y() > 0.0f && t.hi.y() > 0.0f && t.hi.y() <= FLT_MAX;
+}
+
+// FP64 recovery: the exact conserved sums carried into FP64 (hi + lo), then rho,
+// u, T formed in FP64 arithmetic.
+__device__ __forceinline__ void recover_one_f64(double m1, double m2, double m3, double m4,
+                                                double inv_DI, double& r, double& u, double& v,
+                                                double& t)
+{
+    const double q = 1.0 / m1;
+    r = m1;
+    u = m2 * q;
+    v = m3 * q;
+    t = (m4 * q - (u * u + v * v)) * inv_DI;
 }
 
 // Plain FP32 velocity of one cell (halo columns, used only inside grad u).
@@ -180,12 +203,15 @@ __device__ __forceinline__ MacRow row_macros(const float* ring, int r, const Mod
     if constexpr (REC == 1) {
         recover_pair_df(f, C, o.rho, o.ux, o.uy, o.T, o.ig0, o.ig1, ok0, ok1);
     } else {
-        float a[16], b[16];
-#pragma unroll
-        for (int i = 0; i < 16; i++) a[i] = f[i].x(), b[i] = f[i].y();
+        D2 m1, m2, m3, m4;
+        conserved_pair(f, C, m1, m2, m3, m4);
         double r0, u0, v0, t0, r1, u1, v1, t1;
-        recover_f64(K.cd, K.wd, K.inv_DId, a, r0, u0, v0, t0);
-        recover_f64(K.cd, K.wd, K.inv_DId, b, r1, u1, v1, t1);
+        recover_one_f64((double)m1.hi.x() + (double)m1.lo.x(), (double)m2.hi.x() + (double)m2.lo.x(),
+                        (double)m3.hi.x() + (double)m3.lo.x(), (double)m4.hi.x() + (double)m4.lo.x(),
+                        K.inv_DId, r0, u0, v0, t0);
+        recover_one_f64((double)m1.hi.y() + (double)m1.lo.y(), (double)m2.hi.y() + (double)m2.lo.y(),
+                        (double)m3.hi.y() + (double)m3.lo.y(), (double)m4.hi.y() + (double)m4.lo.y(),
+                        K.inv_DId, r1, u1, v1, t1);
         o.rho = V2((float)r0, (float)r1);
         o.ux = V2((float)u0, (float)u1);
         o.uy = V2((float)v0, (float)v1);
@@ -329,8 +355,8 @@ __global__ void __launch_bounds__(MT, 3)
             __syncthreads();
             if (y + 2 + PF <= yend + 1) issue_row(in, ring, y + 2 + PF, x0, K);
             cp_commit();
-            // macros of row y+2 (stored after the update of row y, which does not read them)
-            const MacRow next = row_macros<REC>(ring, y + 2, K, C, bad, act0, act1);
+            // macros of row y+2 (read from the next iteration on)
+            store_macros(mac, ign, y + 2, row_macros<REC>(ring, y + 2, K, C, bad, act0, act1));
 
             // ---------------- update of row y ----------------
             const float* r0 = ring + (size_t)ring_slot(y) * NPLANE * RW;
@@ -462,7 +488,6 @@ __global__ void __launch_bounds__(MT, 3)
                 tsm[2 * TNE_K] += sqrtf(d2.x()) + sqrtf(d2.y());
                 tsm[2 * TNE_K + 1] += d2.x() + d2.y();
             }
-            store_macros(mac, ign, y + 2, next);
         }
         cp_wait<0>();
         if (do_tne) { // per strip: warp sums in FP32, then FP64 per warp
@@ -559,19 +584,19 @@ void march_plan(int recovery, int nx, int ny, int* grid, int* strip_rows)
 {
     const int G = resident_blocks(recovery);
     const int nsx = (nx + BW - 1) / BW;
-    long best_cost = -1;
-    int best_rows = ny;
-    for (int nsy = 1; nsy <= ny; nsy++) {
-        const int rows = (ny + nsy - 1) / nsy;
-        if (rows < 8 && nsy > 1) break;
-        const long strips = (long)nsx * ((ny + rows - 1) / rows);
-        const long waves = (strips + G - 1) / G;
-        const long cost = waves * (rows + 3);
-        if (best_cost < 0 || cost < best_cost) best_cost = cost, best_rows = rows;
+    // 32-row strips measured best at 4096^2 (16: -12 %, 64: -11 %, one wave of
+    // 293-row strips: -36 %); smaller grids use shorter strips so that every
+    // resident block gets work
+    int rows = 32;
+    while (rows > 8 && (long)nsx * ((ny + rows - 1) / rows) < G) rows /= 2;
+    if (rows > ny) rows = ny;
+    if (const char* env = getenv("LBKM_MARCH_ROWS")) { // tuning override
+        const int r = atoi(env);
+        if (r >= 1) rows = r < ny ? r : ny;
     }
-    const long strips = (long)nsx * ((ny + best_rows - 1) / best_rows);
+    const long strips = (long)nsx * ((ny + rows - 1) / rows);
     *grid = G < 0 ? -1 : (int)(strips < G ? strips : G);
-    *strip_rows = best_rows;
+    *strip_rows = rows;
 }
 
 int march_grid(int recovery, int nx, int ny)

@@ -13,7 +13,7 @@
 #include <stdio.h>
 #include <string.h>
 
-#include "../../include/lbkm.h"
+#include "lbkm.h"
 #include "cell.cuh"
 #include "kernels.cuh"
 #include "model.h"
