@@ -154,12 +154,15 @@ __device__ __forceinline__ void recover_pair_df(const V2* f, const DfConst& C, V
 
 // FP64 recovery: the exact conserved sums carried into FP64 (hi + lo), then rho,
 // u, T formed in FP64 arithmetic.
-__device__ __forceinline__ void recover_one_f64(double m1, double m2, double m3, double m4,
-                                                double inv_DI, double& r, double& u, double& v,
+// 1/m1 from an FP32 reciprocal refined by two FP64 Newton steps (each doubles the
+// correct bits: 24 -> 48 -> full FP64), then u and T in FP64.
+__device__ __forceinline__ void recover_one_f64(float seed_of, double m1, double m2, double m3,
+                                                double m4, double inv_DI, double& u, double& v,
                                                 double& t)
 {
-    const double q = 1.0 / m1;
-    r = m1;
+    double q = (double)__frcp_rn(seed_of);
+    q = ::fma(q, ::fma(-m1, q, 1.0), q);
+    q = ::fma(q, ::fma(-m1, q, 1.0), q);
     u = m2 * q;
     v = m3 * q;
     t = (m4 * q - (u * u + v * v)) * inv_DI;
@@ -205,14 +208,16 @@ __device__ __forceinline__ MacRow row_macros(const float* ring, int r, const Mod
     } else {
         D2 m1, m2, m3, m4;
         conserved_pair(f, C, m1, m2, m3, m4);
-        double r0, u0, v0, t0, r1, u1, v1, t1;
-        recover_one_f64((double)m1.hi.x() + (double)m1.lo.x(), (double)m2.hi.x() + (double)m2.lo.x(),
+        double u0, v0, t0, u1, v1, t1;
+        const double r0 = (double)m1.hi.x() + (double)m1.lo.x();
+        const double r1 = (double)m1.hi.y() + (double)m1.lo.y();
+        recover_one_f64(m1.hi.x(), r0, (double)m2.hi.x() + (double)m2.lo.x(),
                         (double)m3.hi.x() + (double)m3.lo.x(), (double)m4.hi.x() + (double)m4.lo.x(),
-                        K.inv_DId, r0, u0, v0, t0);
-        recover_one_f64((double)m1.hi.y() + (double)m1.lo.y(), (double)m2.hi.y() + (double)m2.lo.y(),
+                        K.inv_DId, u0, v0, t0);
+        recover_one_f64(m1.hi.y(), r1, (double)m2.hi.y() + (double)m2.lo.y(),
                         (double)m3.hi.y() + (double)m3.lo.y(), (double)m4.hi.y() + (double)m4.lo.y(),
-                        K.inv_DId, r1, u1, v1, t1);
-        o.rho = V2((float)r0, (float)r1);
+                        K.inv_DId, u1, v1, t1);
+        o.rho = m1.hi; // the exact sum rounded to FP32
         o.ux = V2((float)u0, (float)u1);
         o.uy = V2((float)v0, (float)v1);
         o.T = V2((float)t0, (float)t1);
