@@ -207,6 +207,42 @@ lbkm_status lbkm_set_state(lbkm_t h, const void* src, int on_device);
 lbkm_status lbkm_tne_noalloc(const lbkm_params* p, const void* state, int64_t pitch,
                              double* delta, lbkm_tne_global* out, void* cuda_stream);
 
+/* Many independent 1-D instances of uneven length in one handle (zero-gradient
+ * boundaries per instance), advanced together by one persistent kernel per
+ * chunk of steps (replayed from a CUDA graph). p gives everything the instances
+ * share (velocity set, gamma, Pr, omega2, T_ig, dx, dt; precision must be
+ * LBKM_F32, tne_every 0); p->nx, p->ny, p->bc_x are ignored. inst_nx[i]: cells
+ * of instance i (a multiple of 4, >= 4). inst_S ([n][16]), inst_Q ([n]),
+ * inst_omega1 ([n]): per-instance rates, heat release and rate constant, or
+ * NULL to use p->S, p->Q, p->omega1 for all. The fields of lbkm_init_fields,
+ * lbkm_macros, lbkm_tne and the state of lbkm_get_state are the instances
+ * concatenated in order (nx = sum inst_nx, ny = 1). Errors as lbkm_create. */
+lbkm_status lbkm_create_batched(const lbkm_params* p, int32_t n_instances,
+                                const int32_t* inst_nx, const double* inst_S,
+                                const double* inst_Q, const double* inst_omega1,
+                                void* cuda_stream, lbkm_t* out);
+
+/* Number of instances of h (1 for a single grid). */
+int32_t lbkm_instances(lbkm_t h);
+
+/* TNE record (Sec. VI) of each instance of a batched handle, FP64, into out
+ * (host, lbkm_instances(h) records, step = -1). Synchronises. */
+lbkm_status lbkm_tne_instances(lbkm_t h, lbkm_tne_global* out);
+
+/* Choose the block size and the number of resident blocks of the persistent
+ * kernel by timing trial_steps steps of each candidate on the handle's own
+ * state, which is restored afterwards. chosen (3 ints, may be NULL) receives
+ * threads per block, blocks per SM and blocks. Synchronises. Single grids keep
+ * their fixed plan (chosen = 0). */
+lbkm_status lbkm_autotune(lbkm_t h, int32_t trial_steps, int32_t* chosen);
+
+/* Bound of each grid-barrier wait of the persistent kernel (default 2 s). A
+ * wait that runs out sets the status word; the next synchronising call returns
+ * LBKM_ETIMEOUT and the kernel has returned instead of hanging.
+ * phantom_blocks > 0 makes the barrier wait for blocks that do not exist: for
+ * testing that path only. */
+lbkm_status lbkm_set_wait_limit(lbkm_t h, int64_t timeout_ns, int32_t phantom_blocks);
+
 /* Message of the last failing call on h (or of the last failing lbkm_create
  * when h is NULL). Never NULL. */
 const char* lbkm_last_error(lbkm_t h);

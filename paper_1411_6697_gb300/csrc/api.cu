@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "lbkm.h"
 #include "kernels.cuh"
@@ -47,6 +48,19 @@ struct lbkm {
     int64_t host_steps;
     cudaGraphExec_t graph[2];
     std::string err;
+    // batched 1-D instances
+    bool batched;
+    int n_inst;
+    std::vector<int32_t> inst_nx;
+    InstParam* d_inst;
+    BatchItem* d_items;
+    int nitems;
+    unsigned* d_bar;
+    int bt;          // threads per block of the persistent kernel
+    int bgrid;       // blocks of the persistent kernel
+    long long wait_ns;
+    int phantom;
+    TneRecord* d_inst_tne;
 };
 
 namespace {
@@ -98,6 +112,9 @@ lbkm_status check_status(lbkm_t h)
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     int st = 0;
     CUDA_TRY(h, cudaMemcpy(&st, &h->ctr->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & 2)
+        return fail(h, LBKM_ETIMEOUT,
+                    "a grid barrier wait of the persistent kernel ran out of time");
     if (st & 1)
         return fail(h, LBKM_EUNSTABLE,
                     "a cell reached a non-finite or non-positive density or temperature");
@@ -115,6 +132,42 @@ void release(lbkm* h)
     cudaFree(h->ctr);
     cudaFree(h->hist);
     cudaFree(h->tne_out);
+    cudaFree(h->d_inst);
+    cudaFree(h->d_items);
+    cudaFree(h->d_bar);
+    cudaFree(h->d_inst_tne);
+}
+
+// Work items of the batched kernel for segments of `seg` cells.
+cudaError_t build_items(lbkm* h, int seg)
+{
+    std::vector<BatchItem> items;
+    for (int i = 0; i < h->n_inst; i++)
+        for (int x0 = 0; x0 < h->inst_nx[i]; x0 += seg) items.push_back({i, x0});
+    cudaFree(h->d_items);
+    h->d_items = nullptr;
+    cudaError_t e = cudaMalloc(&h->d_items, sizeof(BatchItem) * items.size());
+    if (e != cudaSuccess) return e;
+    h->nitems = (int)items.size();
+    return cudaMemcpy(h->d_items, items.data(), sizeof(BatchItem) * items.size(),
+                      cudaMemcpyHostToDevice);
+}
+
+BatchLaunch batch_args(const lbkm* h, int nsteps)
+{
+    BatchLaunch b;
+    b.buf[0] = h->buf[0];
+    b.buf[1] = h->buf[1];
+    b.cur = h->cur;
+    b.inst = h->d_inst;
+    b.items = h->d_items;
+    b.nitems = h->nitems;
+    b.ctr = h->ctr;
+    b.bar = h->d_bar;
+    b.nsteps = nsteps;
+    b.phantom_blocks = h->phantom;
+    b.wait_ns = h->wait_ns;
+    return b;
 }
 
 } // namespace
@@ -291,6 +344,43 @@ lbkm_status lbkm_step(lbkm_t h, int64_t n)
     if (!h) return LBKM_EINVAL;
     if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_step before lbkm_init_fields");
     if (n < 0) return fail(h, LBKM_EINVAL, "n must be >= 0");
+    if (h->batched) {
+        // one persistent launch per chunk of steps, replayed from a CUDA graph
+        while (n >= GRAPH_CHUNK) {
+            cudaGraphExec_t& ex = h->graph[h->cur];
+            if (!ex) {
+                cudaGraph_t g;
+                CUDA_TRY(h, cudaStreamBeginCapture(h->capture_stream,
+                                                   cudaStreamCaptureModeThreadLocal));
+                cudaError_t le = cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned),
+                                                 h->capture_stream);
+                if (le == cudaSuccess)
+                    le = launch_batch(h->recovery, h->bt, h->Kf, batch_args(h, GRAPH_CHUNK),
+                                      h->bgrid, h->capture_stream);
+                cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &g);
+                if (le != cudaSuccess || ce != cudaSuccess) {
+                    if (ce == cudaSuccess) cudaGraphDestroy(g);
+                    return fail(h, LBKM_ECUDA, "graph capture of the persistent kernel: %s",
+                                cudaGetErrorString(le != cudaSuccess ? le : ce));
+                }
+                cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+                cudaGraphDestroy(g);
+                if (ie != cudaSuccess)
+                    return fail(h, LBKM_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+            }
+            CUDA_TRY(h, cudaGraphLaunch(ex, h->stream));
+            n -= GRAPH_CHUNK;
+            h->host_steps += GRAPH_CHUNK;
+        }
+        if (n > 0) {
+            CUDA_TRY(h, cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
+            CUDA_TRY(h, launch_batch(h->recovery, h->bt, h->Kf, batch_args(h, (int)n), h->bgrid,
+                                     h->stream));
+            h->cur ^= (int)(n & 1);
+            h->host_steps += n;
+        }
+        return LBKM_OK;
+    }
     const void* K = model_ptr(h);
     while (n >= GRAPH_CHUNK) {
         cudaGraphExec_t& ex = h->graph[h->cur];
@@ -461,6 +551,207 @@ lbkm_status lbkm_set_state(lbkm_t h, const void* src, int on_device)
     CUDA_TRY(h, cudaMemcpy(h->ctr, &c, sizeof(c), cudaMemcpyHostToDevice));
     h->host_steps = s;
     h->initialized = true;
+    return LBKM_OK;
+}
+
+lbkm_status lbkm_create_batched(const lbkm_params* pin, int32_t n_instances,
+                                const int32_t* inst_nx, const double* inst_S,
+                                const double* inst_Q, const double* inst_omega1,
+                                void* cuda_stream, lbkm_t* out)
+{
+    if (!out) return fail(nullptr, LBKM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!pin || !inst_nx || n_instances < 1)
+        return fail(nullptr, LBKM_EINVAL, "params, inst_nx and n_instances >= 1 are required");
+    if (pin->precision != LBKM_F32)
+        return fail(nullptr, LBKM_EINVAL, "batched instances run in LBKM_F32");
+    if (pin->tne_every != 0)
+        return fail(nullptr, LBKM_EINVAL,
+                    "tne_every must be 0 for batched instances (use lbkm_tne_instances)");
+    int64_t total = 0;
+    for (int i = 0; i < n_instances; i++) {
+        if (inst_nx[i] < 4 || inst_nx[i] % 4 != 0)
+            return fail(nullptr, LBKM_EINVAL, "instance %d: nx must be a multiple of 4 and >= 4",
+                        i);
+        total += inst_nx[i];
+    }
+    if (total > (1 << 28)) return fail(nullptr, LBKM_EINVAL, "too many cells in total");
+    lbkm_params q = *pin;
+    q.nx = (int32_t)total;
+    q.ny = 1;
+    q.bc_x = LBKM_BC_ZERO_GRADIENT;
+    std::vector<InstParam> ip(n_instances);
+    const double DI = 2.0 + (2.0 / (pin->gamma - 1.0) - 2.0);
+    int64_t off = 0;
+    for (int i = 0; i < n_instances; i++) {
+        double S[16];
+        for (int k = 0; k < 16; k++) S[k] = inst_S ? inst_S[16 * i + k] : pin->S[k];
+        if (pin->Pr > 0) S[7] = S[8] = pin->Pr * S[4];
+        double smax = 0;
+        for (int k = 4; k < 16; k++) {
+            if (!(S[k] > 0)) return fail(nullptr, LBKM_EINVAL, "instance %d: S must be > 0", i);
+            smax = fmax(smax, S[k]);
+        }
+        if (!(pin->dt * smax < 2.0))
+            return fail(nullptr, LBKM_EINVAL, "instance %d: dt * max S = %g must be < 2", i,
+                        pin->dt * smax);
+        const double Q = inst_Q ? inst_Q[i] : pin->Q;
+        const double om1 = inst_omega1 ? inst_omega1[i] : pin->omega1;
+        if (!(om1 >= 0)) return fail(nullptr, LBKM_EINVAL, "instance %d: omega1 < 0", i);
+        for (int k = 0; k < 16; k++) ip[i].S[k] = (float)S[k];
+        ip[i].A8c = (float)((S[4] - S[7]) / S[4]);
+        ip[i].A9c = (float)((S[6] - S[8]) / S[6]);
+        ip[i].chem = (float)(2.0 * Q / (DI * pin->dt));
+        ip[i].om1 = (float)om1;
+        ip[i].om2 = (float)pin->omega2;
+        ip[i].nx = inst_nx[i];
+        ip[i].off = off;
+        off += inst_nx[i];
+    }
+    lbkm_t h = nullptr;
+    lbkm_status st = lbkm_create(&q, cuda_stream, &h);
+    if (st != LBKM_OK) return st;
+    h->batched = true;
+    h->n_inst = n_instances;
+    h->inst_nx.assign(inst_nx, inst_nx + n_instances);
+    h->wait_ns = 2000000000LL;
+    h->phantom = 0;
+    cudaError_t e = cudaMalloc(&h->d_inst, sizeof(InstParam) * n_instances);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_inst, ip.data(), sizeof(InstParam) * n_instances,
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_bar, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(h->d_bar, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_inst_tne, sizeof(TneRecord) * n_instances);
+    int sms = 0, dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    h->bt = 128;
+    const int per_sm = batch_max_blocks(h->recovery, h->bt);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    h->bgrid = per_sm * sms;
+    if (e == cudaSuccess) e = build_items(h, batch_segment(h->bt));
+    if (e != cudaSuccess) {
+        std::string m = cudaGetErrorString(e);
+        lbkm_destroy(h);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? LBKM_ENOMEM : LBKM_ECUDA,
+                    "batched set-up: %s", m.c_str());
+    }
+    *out = h;
+    return LBKM_OK;
+}
+
+int32_t lbkm_instances(lbkm_t h) { return h ? (h->batched ? h->n_inst : 1) : 0; }
+
+lbkm_status lbkm_tne_instances(lbkm_t h, lbkm_tne_global* out)
+{
+    if (!h || !out) return LBKM_EINVAL;
+    if (!h->batched) return fail(h, LBKM_EINVAL, "lbkm_tne_instances needs a batched handle");
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_tne_instances before init");
+    CUDA_TRY(h, launch_tne_instances(h->precision, h->Kd, h->buf[h->cur], h->d_inst, h->n_inst,
+                                     h->d_inst_tne, h->p.dx * h->p.dy, h->stream));
+    std::vector<TneRecord> r(h->n_inst);
+    CUDA_TRY(h, cudaMemcpyAsync(r.data(), h->d_inst_tne, sizeof(TneRecord) * h->n_inst,
+                                cudaMemcpyDeviceToHost, h->stream));
+    lbkm_status st = check_status(h);
+    if (st != LBKM_OK) return st;
+    for (int i = 0; i < h->n_inst; i++) record_to_global(r[i], out + i);
+    return LBKM_OK;
+}
+
+static void drop_graphs(lbkm_t h)
+{
+    for (int i = 0; i < 2; i++)
+        if (h->graph[i]) {
+            cudaGraphExecDestroy(h->graph[i]);
+            h->graph[i] = nullptr;
+        }
+}
+
+lbkm_status lbkm_set_wait_limit(lbkm_t h, int64_t timeout_ns, int32_t phantom_blocks)
+{
+    if (!h || timeout_ns < 1 || phantom_blocks < 0) return LBKM_EINVAL;
+    h->wait_ns = timeout_ns;
+    h->phantom = phantom_blocks;
+    drop_graphs(h);
+    return LBKM_OK;
+}
+
+lbkm_status lbkm_autotune(lbkm_t h, int32_t trial_steps, int32_t* chosen)
+{
+    if (!h || trial_steps < 1) return LBKM_EINVAL;
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_autotune before init");
+    if (!h->batched) {
+        if (chosen) chosen[0] = chosen[1] = chosen[2] = 0;
+        return LBKM_OK; // single grids use their fixed plan
+    }
+    int sms = 0, dev = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    // keep the state and counters; every trial starts from them
+    void* saved = nullptr;
+    CUDA_TRY(h, cudaMalloc(&saved, h->state_bytes_dev));
+    DevCounters c0;
+    const int cur0 = h->cur;
+    const int64_t steps0 = h->host_steps;
+    cudaError_t e = cudaMemcpy(saved, h->buf[cur0], h->state_bytes_dev, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(&c0, h->ctr, sizeof(c0), cudaMemcpyDeviceToHost);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    float best = -1.f;
+    int best_bt = h->bt, best_grid = h->bgrid;
+    const int bts[2] = {64, 128};
+    for (int t = 0; t < 2 && e == cudaSuccess; t++) {
+        const int maxb = batch_max_blocks(h->recovery, bts[t]);
+        for (int bps = 1; bps <= maxb && e == cudaSuccess; bps++) {
+            h->bt = bts[t];
+            h->bgrid = bps * sms;
+            e = build_items(h, batch_segment(h->bt));
+            if (e != cudaSuccess) break;
+            h->cur = cur0;
+            e = cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream);
+            if (e == cudaSuccess)
+                e = launch_batch(h->recovery, h->bt, h->Kf, batch_args(h, 1), h->bgrid, h->stream);
+            h->cur = cur0 ^ 1;
+            if (e == cudaSuccess) e = cudaEventRecord(ev0, h->stream);
+            if (e == cudaSuccess)
+                e = launch_batch(h->recovery, h->bt, h->Kf, batch_args(h, trial_steps), h->bgrid,
+                                 h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+            if (e == cudaSuccess && (best < 0.f || ms < best)) {
+                best = ms;
+                best_bt = h->bt;
+                best_grid = h->bgrid;
+            }
+            // back to the saved state
+            h->cur = cur0;
+            if (e == cudaSuccess)
+                e = cudaMemcpy(h->buf[cur0], saved, h->state_bytes_dev, cudaMemcpyDeviceToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(h->ctr, &c0, sizeof(c0), cudaMemcpyHostToDevice);
+        }
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    cudaFree(saved);
+    h->host_steps = steps0;
+    h->cur = cur0;
+    h->bt = best_bt;
+    h->bgrid = best_grid;
+    if (e == cudaSuccess) e = build_items(h, batch_segment(h->bt));
+    drop_graphs(h);
+    if (e != cudaSuccess) return fail(h, LBKM_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    lbkm_status st = check_status(h);
+    if (st != LBKM_OK) return st;
+    if (chosen) {
+        chosen[0] = h->bt;
+        chosen[1] = h->bgrid / (sms > 0 ? sms : 1);
+        chosen[2] = h->bgrid;
+    }
     return LBKM_OK;
 }
 

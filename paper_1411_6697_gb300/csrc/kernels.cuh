@@ -54,6 +54,38 @@ cudaError_t launch_tne(int precision, const ModelConst<double>& Kd, const void* 
                        TneRecord* out, double cell_area, cudaStream_t s);
 int tne_grid(int nx, int ny);
 
+// Batched 1-D instances (batch.cu): per-instance parameters, work items and the
+// arguments of one persistent launch.
+struct InstParam {
+    float S[16];
+    float A8c, A9c, chem, om1, om2; // (S5-S8)/S5, (S7-S9)/S7, 2Q/((D+I)dt), omega1, omega2
+    int32_t nx;
+    int64_t off; // first cell of the instance in the flat layout
+};
+struct BatchItem {
+    int32_t inst, x0; // instance and first cell of the segment
+};
+struct BatchLaunch {
+    void* buf[2];
+    int cur;             // buffer holding the input of the first step
+    const InstParam* inst;
+    const BatchItem* items;
+    int nitems;
+    DevCounters* ctr;
+    unsigned* bar;       // grid barrier: arrivals, generation
+    int nsteps;
+    int phantom_blocks;  // > 0 only to test the bounded barrier wait
+    long long wait_ns;   // bound of each barrier wait
+};
+int batch_segment(int block_threads);
+int batch_max_blocks(int recovery, int block_threads);
+cudaError_t launch_batch(int recovery, int block_threads, const ModelConst<float>& K,
+                         const BatchLaunch& b, int grid, cudaStream_t s);
+// grid-wide TNE record of every instance (one block per instance, FP64)
+cudaError_t launch_tne_instances(int precision, const ModelConst<double>& Kd, const void* state,
+                                 const InstParam* inst, int n_inst, TneRecord* out,
+                                 double area, cudaStream_t s);
+
 // FP32 2-D step: y-marching strips, two cells per thread (march.cu)
 int march_grid(int recovery, int nx, int ny);
 cudaError_t launch_march(int recovery, const ModelConst<float>& K, const StepLaunch& a,

@@ -26,7 +26,9 @@ STATUS = {0: "LBKM_OK", 1: "LBKM_EINVAL", 2: "LBKM_ENOMEM", 3: "LBKM_ECUDA",
 EXPORTED = ["lbkm_default_params", "lbkm_create", "lbkm_destroy", "lbkm_set_stream",
             "lbkm_init_fields", "lbkm_step", "lbkm_sync", "lbkm_steps_taken", "lbkm_macros",
             "lbkm_tne", "lbkm_tne_history", "lbkm_state_bytes", "lbkm_get_state",
-            "lbkm_set_state", "lbkm_last_error", "lbkm_version", "lbkm_tne_noalloc"]
+            "lbkm_set_state", "lbkm_last_error", "lbkm_version", "lbkm_tne_noalloc",
+            "lbkm_create_batched", "lbkm_instances", "lbkm_tne_instances", "lbkm_autotune",
+            "lbkm_set_wait_limit"]
 
 
 class LbkmError(RuntimeError):
@@ -101,6 +103,17 @@ def load():
     lib.lbkm_version.restype = ctypes.c_int32
     lib.lbkm_tne_noalloc.argtypes = [ctypes.POINTER(Params), _vp, ctypes.c_int64, _vp, _vp, _vp]
     lib.lbkm_tne_noalloc.restype = ctypes.c_int
+    lib.lbkm_create_batched.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, _vp, _vp, _vp,
+                                        _vp, _vp, ctypes.POINTER(H)]
+    lib.lbkm_create_batched.restype = ctypes.c_int
+    lib.lbkm_instances.argtypes = [H]
+    lib.lbkm_instances.restype = ctypes.c_int32
+    lib.lbkm_tne_instances.argtypes = [H, ctypes.POINTER(TneGlobal)]
+    lib.lbkm_tne_instances.restype = ctypes.c_int
+    lib.lbkm_autotune.argtypes = [H, ctypes.c_int32, _vp]
+    lib.lbkm_autotune.restype = ctypes.c_int
+    lib.lbkm_set_wait_limit.argtypes = [H, ctypes.c_int64, ctypes.c_int32]
+    lib.lbkm_set_wait_limit.restype = ctypes.c_int
     for name in ("lbkm_create", "lbkm_set_stream", "lbkm_init_fields", "lbkm_step", "lbkm_sync",
                  "lbkm_macros", "lbkm_tne", "lbkm_tne_history", "lbkm_get_state",
                  "lbkm_set_state"):
@@ -152,6 +165,57 @@ class Solver:
         if rc != 0:
             raise LbkmError(rc, lib.lbkm_last_error(None).decode())
         self._h = h
+
+    @classmethod
+    def batched(cls, inst_nx, inst_S=None, inst_Q=None, inst_omega1=None, params=None,
+                stream=None, **kw):
+        """Many 1-D instances in one handle (lbkm_create_batched); fields are the
+        instances concatenated in order."""
+        self = cls.__new__(cls)
+        lib = load()
+        self._lib = lib
+        kw.setdefault("precision", F32)
+        self.params = params if params is not None else default_params(**kw)
+        nxs = np.ascontiguousarray(inst_nx, dtype=np.int32)
+        keep = [nxs]
+
+        def arr(a, shape):
+            if a is None:
+                return None
+            b = np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), shape))
+            keep.append(b)
+            return b.ctypes.data
+        h = ctypes.c_void_p()
+        rc = lib.lbkm_create_batched(ctypes.byref(self.params), len(nxs),
+                                     ctypes.c_void_p(nxs.ctypes.data),
+                                     ctypes.c_void_p(arr(inst_S, (len(nxs), 16))),
+                                     ctypes.c_void_p(arr(inst_Q, (len(nxs),))),
+                                     ctypes.c_void_p(arr(inst_omega1, (len(nxs),))),
+                                     ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h))
+        if rc != 0:
+            raise LbkmError(rc, lib.lbkm_last_error(None).decode())
+        self._h = h
+        self.nx, self.ny = int(nxs.sum()), 1
+        self.inst_nx = nxs.copy()
+        return self
+
+    @property
+    def instances(self):
+        return int(self._lib.lbkm_instances(self._h))
+
+    def tne_instances(self):
+        n = self.instances
+        buf = (TneGlobal * n)()
+        self._check(self._lib.lbkm_tne_instances(self._h, buf))
+        return [buf[i].as_dict() for i in range(n)]
+
+    def autotune(self, trial_steps=3):
+        out = (ctypes.c_int32 * 3)()
+        self._check(self._lib.lbkm_autotune(self._h, int(trial_steps), out))
+        return tuple(out)
+
+    def set_wait_limit(self, timeout_ns, phantom_blocks=0):
+        self._check(self._lib.lbkm_set_wait_limit(self._h, int(timeout_ns), int(phantom_blocks)))
 
     # ------------------------------------------------------------------
     def _check(self, rc):

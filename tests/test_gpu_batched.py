@@ -1,0 +1,105 @@
+"""Batched 1-D instances in one persistent launch (lbkm_create_batched): parity of
+every instance with the FP64 oracle run of that instance alone, per-instance TNE,
+the autotuner, and the bounded grid-barrier wait."""
+import numpy as np
+import pytest
+
+import lbkm_inputs as li
+from gpu_common import make_oracle, rel_l2
+from paper_1411_6697_gb300 import lbkm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "the -m gpu tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def small_batch(n=6, steps=40, nx_max=600):
+    """Uneven instances, several spanning more than one 256-cell segment."""
+    return li.batched(n_instances=n, steps=steps, nx_min=64, nx_max=nx_max, driver=12)
+
+
+def make_batched(cfg, recovery=0):
+    p0 = cfg["instances"][0]["params"]
+    shared = {k: p0[k] for k in ("gamma", "orbit_kind", "orbit_speed", "orbit_eta", "omega1",
+                                 "omega2", "T_ig", "dx", "dt")}
+    s = lbkm.Solver.batched(cfg["nx"], inst_S=cfg["S"], inst_Q=cfg["Q"], recovery=recovery,
+                            dy=p0["dx"], **shared)
+    fields = {k: np.concatenate([d["fields"][k] for d in cfg["instances"]], axis=1)
+              for k in ("rho", "ux", "uy", "T", "lam")}
+    s.init_fields(fields["rho"], fields["ux"], fields["uy"], fields["T"], fields["lam"])
+    return s
+
+
+def split(a, nxs):
+    return np.split(a, np.cumsum(nxs)[:-1], axis=-1)
+
+
+@pytest.mark.parametrize("recovery", [0, 1], ids=["f64rec", "df32"])
+def test_batched_instances_match_oracle(recovery):
+    cfg = small_batch()
+    s = make_batched(cfg, recovery)
+    assert s.instances == len(cfg["nx"])
+    s.step(cfg["steps"])  # one 32-step graph replay + 8 steps in a direct launch
+    planes = s.f_planes()
+    m = s.macros()
+    for i, (inst, nx) in enumerate(zip(cfg["instances"], cfg["nx"])):
+        ob = make_oracle(inst["params"])
+        fl = inst["fields"]
+        f0 = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
+        # the oracle starts from the same FP32-rounded initial state
+        f0 = f0.astype(np.float32).astype(np.float64)
+        f, lam = ob.run(f0, fl["lam"], cfg["steps"])
+        got = split(planes, cfg["nx"])[i]
+        assert rel_l2(got[:16], f) <= 2e-5, (i, nx, rel_l2(got[:16], f))
+        assert rel_l2(got[16], lam) <= 2e-5
+        mr = ob.macros(f)
+        for k in ("rho", "ux", "T"):
+            assert rel_l2(split(m[k], cfg["nx"])[i], mr[k]) <= 2e-5, (i, k)
+
+
+def test_batched_tne_per_instance():
+    cfg = small_batch(n=4, steps=20)
+    s = make_batched(cfg)
+    s.step(cfg["steps"])
+    recs = s.tne_instances()
+    planes = s.f_planes()
+    for i, inst in enumerate(cfg["instances"]):
+        ob = make_oracle(inst["params"])
+        _, ref = ob.tne(split(planes, cfg["nx"])[i][:16], fields=False)
+        scale = ref["abs_sum"].max()
+        assert np.abs(recs[i]["sum"] - ref["sum"]).max() <= 1e-12 * scale
+        assert np.abs(recs[i]["abs_sum"] - ref["abs_sum"]).max() <= 1e-12 * scale
+        assert np.allclose(recs[i]["min"], ref["min"], rtol=1e-12, atol=1e-15)
+        assert np.allclose(recs[i]["max"], ref["max"], rtol=1e-12, atol=1e-15)
+
+
+def test_autotune_keeps_state_and_results():
+    cfg = small_batch(n=5, steps=8)
+    a = make_batched(cfg)
+    b = make_batched(cfg)
+    before = a.get_state()
+    chosen = a.autotune(trial_steps=2)
+    assert chosen[0] in (64, 128) and chosen[1] >= 1 and chosen[2] >= 1
+    assert np.array_equal(a.get_state(), before) and a.steps_taken == 0
+    a.step(8)
+    b.step(8)
+    pa, pb = a.f_planes(), b.f_planes()
+    assert rel_l2(pa, pb) <= 1e-6  # segment boundaries may differ with the block size
+
+
+def test_barrier_wait_runs_out_and_reports():
+    """A barrier told to wait for a block that does not exist gives up after 5 ms:
+    the kernel returns and the host sees LBKM_ETIMEOUT."""
+    cfg = small_batch(n=3, steps=2)
+    s = make_batched(cfg)
+    s.set_wait_limit(5_000_000, phantom_blocks=1)
+    s.step(1)
+    with pytest.raises(lbkm.LbkmError) as e:
+        s.sync()
+    assert e.value.code == 6
