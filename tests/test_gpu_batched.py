@@ -75,8 +75,11 @@ def test_batched_tne_per_instance():
         scale = ref["abs_sum"].max()
         assert np.abs(recs[i]["sum"] - ref["sum"]).max() <= 1e-12 * scale
         assert np.abs(recs[i]["abs_sum"] - ref["abs_sum"]).max() <= 1e-12 * scale
-        assert np.allclose(recs[i]["min"], ref["min"], rtol=1e-12, atol=1e-15)
-        assert np.allclose(recs[i]["max"], ref["max"], rtol=1e-12, atol=1e-15)
+        # components that vanish in 1-D (Delta_6, Delta_9, ...) are rounding noise on
+        # both sides, so min/max are compared on the record's overall scale
+        mscale = max(np.abs(ref["min"]).max(), np.abs(ref["max"]).max())
+        assert np.abs(recs[i]["min"] - ref["min"]).max() <= 1e-12 * mscale
+        assert np.abs(recs[i]["max"] - ref["max"]).max() <= 1e-12 * mscale
 
 
 def test_autotune_keeps_state_and_results():
