@@ -230,6 +230,107 @@ def run_reference(args):
     return 0
 
 
+def _shared_params(p0):
+    return {k: p0[k] for k in ("gamma", "orbit_kind", "orbit_speed", "orbit_eta", "omega1",
+                               "omega2", "T_ig", "dx", "dt")}
+
+
+def run_batched(args):
+    """Config 4: 512 1-D detonations of uneven length in one persistent launch per chunk
+    of steps, FP32; compared with the plain single-instance FP64 form on a sample of the
+    same instances, run one after another."""
+    import torch
+    from paper_1411_6697_gb300 import lbkm
+    rank, local, world = _env_rank()
+    torch.cuda.set_device(local)
+    rec = lbkm.RECOVER_F64 if args.recovery == "f64" else lbkm.RECOVER_DF32
+    cfg = li.batched(n_instances=512, steps=5000)
+    p0 = cfg["instances"][0]["params"]
+    stream = torch.cuda.Stream()
+    s = lbkm.Solver.batched(cfg["nx"], inst_S=cfg["S"], inst_Q=cfg["Q"], recovery=rec,
+                            dy=p0["dx"], stream=stream, **_shared_params(p0))
+    fields = {k: np.concatenate([d["fields"][k] for d in cfg["instances"]], axis=1)
+              for k in ("rho", "ux", "uy", "T", "lam")}
+    s.init_fields(fields["rho"], fields["ux"], fields["uy"], fields["T"], fields["lam"])
+    chosen = s.autotune(trial_steps=3)
+    n = int(np.sum(cfg["nx"]))
+    with torch.cuda.stream(stream):
+        s.step(args.warmup)
+        s.sync()
+        with ClockSampler(local) as clk:
+            ms = time_steps(s, stream, args.steps)
+        s.sync()
+    value = n * args.steps / (ms * 1e-3) / 1e6
+    peak, peak_kind = measured_peak()
+    achieved = BYTES_PER_CELL["f32"] * n / (ms / args.steps * 1e-3) / 1e9
+    # plain single-instance FP64 form on a seeded sample of the instances
+    rng = np.random.default_rng(li.SEED_BASE + 40)
+    sample = rng.choice(len(cfg["nx"]), 24, replace=False)
+    t64 = c64 = 0.0
+    for i in sample:
+        d = cfg["instances"][i]
+        q = d["params"]
+        one = lbkm.Solver(nx=q["nx"], ny=1, precision=lbkm.F64, S=q["S"], Q=q["Q"], bc=(1, 0),
+                          dy=q["dx"], stream=stream, **_shared_params(q))
+        fl = d["fields"]
+        one.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+        with torch.cuda.stream(stream):
+            one.step(3)
+            t64 += time_steps(one, stream, 64) * 1e-3
+        c64 += q["nx"] * 64
+        one.close()
+    plain = c64 / t64 / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batched_512x1d_detonations", "cells": n,
+                       "instances": len(cfg["nx"]), "conserved_moment_recovery": args.recovery,
+                       "autotuned": {"threads": chosen[0], "blocks_per_sm": chosen[1],
+                                     "blocks": chosen[2]},
+                       "l2": "state %.2f GB per copy > L2: no flush" % (17 * n * 4 / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "batch_kernel (f32)",
+                         "algorithmic_bytes_per_launch_step": BYTES_PER_CELL["f32"] * n},
+            "plain_f64_single_instance_mcell_per_s": plain,
+            "speedup_vs_plain_f64": value / plain,
+            "plain_sample": "24 seeded instances, 64 steps each, one after another",
+            "gpu_launches": (args.steps + 31) // 32, "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
+def run_detonation(args):
+    """Config 2: one 1-D detonation of 16384 cells (L2-resident, latency-bound)."""
+    import torch
+    from paper_1411_6697_gb300 import lbkm
+    rank, local, world = _env_rank()
+    torch.cuda.set_device(local)
+    cfg = li.detonation()
+    fl = cfg["fields"]
+    stream = torch.cuda.Stream()
+    out = {}
+    for name, prec in (("f64", lbkm.F64), ("f32", lbkm.F32)):
+        q = cfg["params"]
+        one = lbkm.Solver(nx=q["nx"], ny=1, precision=prec, S=q["S"], Q=q["Q"], bc=(1, 0),
+                          dy=q["dx"], stream=stream, tne_every=1, tne_capacity=4096,
+                          **_shared_params(q))
+        one.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+        with torch.cuda.stream(stream):
+            one.step(args.warmup)
+            ms = time_steps(one, stream, args.steps)
+        out[name] = q["nx"] * args.steps / (ms * 1e-3) / 1e6
+        one.close()
+    line = {"metric": METRIC, "value": out["f32"], "unit": "Mcell-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "detonation_16384x1", "note": "2.2 MB state, L2-resident"},
+            "f64_mcell_per_s": out["f64"]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -241,9 +342,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--side", type=int, default=N_CELLS_SIDE)
+    ap.add_argument("--workload", default="reactive2d",
+                    choices=["reactive2d", "batched", "detonation"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "detonation":
+        return run_detonation(args)
 
     import torch
     import torch.distributed as dist
