@@ -251,17 +251,18 @@ __global__ void __launch_bounds__(TX * TY)
     // end of step: status, TNE partials, arrival count; the last block finishes
     if (__syncthreads_or(bad) && tid == 0) atomicOr(&a.ctr->status, 1);
     if (do_tne) {
-        double* part = a.partials + (size_t)blockIdx.x * TNE_PART;
+        double* part = a.partials + blockIdx.x; // quantity-major, stride gridDim.x
+        const size_t ps = gridDim.x;
         for (int q = tid; q < NSUM; q += C::NT) {
             double s = 0.0;
             for (int w = 0; w < C::NW; w++) s += tsum[w * NSUM + q];
-            part[q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K)] = s;
+            part[ps * (q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K))] = s;
         }
         for (int q = tid; q < NMM; q += C::NT) {
             R v = tmm[q];
             for (int w = 1; w < C::NW; w++)
                 v = q < TNE_K ? rmin(v, tmm[w * NMM + q]) : rmax(v, tmm[w * NMM + q]);
-            part[2 * TNE_K + q] = (double)v;
+            part[ps * (2 * TNE_K + q)] = (double)v;
         }
         __threadfence();
     }
@@ -419,18 +420,19 @@ __global__ void __launch_bounds__(TNE_THREADS)
         if (lane == 0) smm[warp][k] = a, smm[warp][TNE_K + k] = b;
     }
     __syncthreads();
-    double* part = partials + (size_t)blockIdx.x * TNE_PART;
+    double* part = partials + blockIdx.x; // quantity-major, stride gridDim.x
+    const size_t ps = gridDim.x;
     if (threadIdx.x < NSUM) {
         double s = 0.0;
         for (int w = 0; w < TNE_THREADS / 32; w++) s += ssum[w][threadIdx.x];
         const int q = threadIdx.x;
-        part[q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K)] = s;
+        part[ps * (q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K))] = s;
     } else if (threadIdx.x >= 32 && threadIdx.x < 32 + NMM) {
         const int q = threadIdx.x - 32;
         double v = smm[0][q];
         for (int w = 1; w < TNE_THREADS / 32; w++)
             v = q < TNE_K ? fmin(v, smm[w][q]) : fmax(v, smm[w][q]);
-        part[2 * TNE_K + q] = v;
+        part[ps * (2 * TNE_K + q)] = v;
     }
     __threadfence();
     __syncthreads();

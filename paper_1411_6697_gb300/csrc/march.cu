@@ -343,17 +343,18 @@ __global__ void __launch_bounds__(MT, 3)
             }
         }
         __syncthreads();
-        double* part = a.partials + (size_t)blockIdx.x * TNE_PART;
+        double* part = a.partials + blockIdx.x; // quantity-major, stride gridDim.x
+        const size_t ps = gridDim.x;
         for (int q = tid; q < NSUM; q += MT) {
             double sacc = 0.0;
             for (int w = 0; w < NWM; w++) sacc += tsum[w * NSUM + q];
-            part[q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K)] = sacc;
+            part[ps * (q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K))] = sacc;
         }
         for (int q = tid; q < NMM; q += MT) {
             float v = tmm[q];
             for (int w = 1; w < NWM; w++)
                 v = q < TNE_K ? fminf(v, tmm[w * NMM + q]) : fmaxf(v, tmm[w * NMM + q]);
-            part[2 * TNE_K + q] = (double)v;
+            part[ps * (2 * TNE_K + q)] = (double)v;
         }
         __threadfence();
     }

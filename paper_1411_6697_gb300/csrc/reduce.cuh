@@ -43,26 +43,28 @@ __device__ __forceinline__ double big_value<double>() { return DBL_MAX; }
 
 // Last block of a launch: reduce the per-block partials (fixed order) into a
 // TNE record. Called by every thread of that block.
-static __device__ __noinline__ void finish_tne(const double* partials, int nblocks, TneRecord* rec, int64_t step,
-                           double area)
+// Partials are stored quantity-major: partial q of block b at partials[q * nblocks + b].
+// Each quantity is reduced by one warp: lane l combines blocks l, l+32, ... in
+// order, then the lanes combine in a fixed shuffle tree (deterministic).
+static __device__ __noinline__ void finish_tne(const double* partials, int nblocks, TneRecord* rec,
+                                               int64_t step, double area)
 {
     __shared__ double res[TNE_PART];
-    for (int q = threadIdx.x; q < TNE_PART; q += blockDim.x) {
-        double acc;
-        if (q < 2 * TNE_K || q >= 4 * TNE_K) {
-            acc = 0.0;
-            for (int b = 0; b < nblocks; b++) acc += __ldcg(partials + (size_t)b * TNE_PART + q);
-            acc *= area;
-        } else if (q < 3 * TNE_K) {
-            acc = DBL_MAX;
-            for (int b = 0; b < nblocks; b++)
-                acc = fmin(acc, __ldcg(partials + (size_t)b * TNE_PART + q));
-        } else {
-            acc = -DBL_MAX;
-            for (int b = 0; b < nblocks; b++)
-                acc = fmax(acc, __ldcg(partials + (size_t)b * TNE_PART + q));
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = threadIdx.x >> 5; q < TNE_PART; q += nw) {
+        const double* pq = partials + (size_t)q * nblocks;
+        const int kind = (q < 2 * TNE_K || q >= 4 * TNE_K) ? 0 : (q < 3 * TNE_K ? 1 : 2);
+        double acc = kind == 0 ? 0.0 : (kind == 1 ? DBL_MAX : -DBL_MAX);
+        for (int b = lane; b < nblocks; b += 32) {
+            const double v = __ldcg(pq + b);
+            acc = kind == 0 ? acc + v : (kind == 1 ? fmin(acc, v) : fmax(acc, v));
         }
-        res[q] = acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v = __shfl_xor_sync(0xffffffffu, acc, o);
+            acc = kind == 0 ? acc + v : (kind == 1 ? fmin(acc, v) : fmax(acc, v));
+        }
+        if (lane == 0) res[q] = kind == 0 ? acc * area : acc;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < 16; k += blockDim.x) {
