@@ -207,6 +207,36 @@ lbkm_status lbkm_set_state(lbkm_t h, const void* src, int on_device);
 lbkm_status lbkm_tne_noalloc(const lbkm_params* p, const void* state, int64_t pitch,
                              double* delta, lbkm_tne_global* out, void* cuda_stream);
 
+/* Objective of lbkm_grad over N steps from the handle's current state (t = 0):
+ * J = w_mismatch/2 sum_x (rho_N - rho*)^2 dx + w_tne sum_{n<N} sum_x d_n^2 dx dt,
+ * d_n^2 = sum_k Delta_k^2 of the state entering step n (Sec. VI, Eqs. (90)-(91)). */
+typedef struct {
+    const double* rho_target;  /* [nx] host: rho* */
+    double w_mismatch, w_tne;
+    int64_t steps;             /* N >= 1 */
+    int32_t checkpoint_every;  /* a state is kept every this many steps (>= 1) */
+} lbkm_objective;
+
+typedef struct {
+    double J, J_mismatch, J_tne;
+    double dS[16];             /* dJ/dS_1..16 (S_1..4: 0, Sec. III) */
+    double dQ, domega1;        /* dJ/dQ, dJ/domega1 */
+    double* drho0;             /* [nx] host or NULL: dJ/drho of the start, with u, T fixed,
+                                  for a start made by lbkm_init_fields (equilibrium) */
+    double* df0;               /* [16][nx] host or NULL: dJ/df of the start state */
+} lbkm_grad_out;
+
+/* Gradient of J by the discrete adjoint of the FP64 step (reverse mode through
+ * every step, hand-written kernels): the forward run keeps a state every
+ * checkpoint_every steps and each segment is recomputed from its checkpoint
+ * before its steps are reversed, so memory is (N/C + C) states. The ignition
+ * switch T > T_ig stays a hard switch (no derivative through it); minmod and the
+ * lambda clamp follow the branch the forward values take. The handle's state is
+ * left unchanged. Needs an LBKM_F64 handle with ny = 1 and omega2 = 0 (not
+ * batched). Errors: LBKM_EINVAL, LBKM_ESTATE, LBKM_ENOMEM, LBKM_ECUDA,
+ * LBKM_EUNSTABLE. Synchronises. */
+lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* obj, lbkm_grad_out* out);
+
 /* Many independent 1-D instances of uneven length in one handle (zero-gradient
  * boundaries per instance), advanced together by one persistent kernel per
  * chunk of steps (replayed from a CUDA graph). p gives everything the instances

@@ -755,6 +755,166 @@ lbkm_status lbkm_autotune(lbkm_t h, int32_t trial_steps, int32_t* chosen)
     return LBKM_OK;
 }
 
+lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
+{
+    if (!h || !ob || !out) return LBKM_EINVAL;
+    if (h->precision != LBKM_F64 || h->ny != 1 || h->batched)
+        return fail(h, LBKM_EINVAL, "lbkm_grad needs a single LBKM_F64 grid with ny = 1");
+    if (h->p.omega2 != 0.0) return fail(h, LBKM_EINVAL, "lbkm_grad needs omega2 = 0");
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_grad before lbkm_init_fields");
+    if (!ob->rho_target || ob->steps < 1 || ob->checkpoint_every < 1)
+        return fail(h, LBKM_EINVAL, "rho_target, steps >= 1 and checkpoint_every >= 1 needed");
+    const int nx = h->nx;
+    const int64_t N = ob->steps;
+    const int C = ob->checkpoint_every;
+    const int64_t nck = (N + C - 1) / C;
+    const size_t SB = h->state_bytes_dev;
+    const int G = adj_grid(nx);
+    char *ck = nullptr, *seg = nullptr;
+    double *work = nullptr, *mats = nullptr;
+    DevCounters* sctr = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(ck);
+        cudaFree(seg);
+        cudaFree(work);
+        cudaFree(mats);
+        cudaFree(sctr);
+    };
+    // work: mac 4n, mb 16n, loc 6n, gb 2n, fbA/fbB 32n, lbA/lbB 2n, rho_t n, drho0 n,
+    //       pacc NPAR*G, jtne G, jmis G
+    const size_t nwork = (size_t)nx * (4 + 16 + 6 + 2 + 32 + 2 + 1 + 1) + (size_t)(ADJ_NPAR + 2) * G;
+    cudaError_t e = cudaMalloc(&ck, SB * nck);
+    if (e == cudaSuccess) e = cudaMalloc(&seg, SB * (size_t)(C + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&work, sizeof(double) * nwork);
+    if (e == cudaSuccess) e = cudaMalloc(&mats, sizeof(double) * (256 + 256 + 16));
+    if (e == cudaSuccess) e = cudaMalloc(&sctr, sizeof(DevCounters));
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(h, e == cudaErrorMemoryAllocation ? LBKM_ENOMEM : LBKM_ECUDA,
+                    "lbkm_grad allocation: %s", cudaGetErrorString(e));
+    }
+    double* mac = work;
+    double* mb = mac + 4 * (size_t)nx;
+    double* loc = mb + 16 * (size_t)nx;
+    double* gb = loc + 6 * (size_t)nx;
+    double* fbA = gb + 2 * (size_t)nx;
+    double* fbB = fbA + 16 * (size_t)nx;
+    double* lbA = fbB + 16 * (size_t)nx;
+    double* lbB = lbA + nx;
+    double* rho_t = lbB + nx;
+    double* drho0 = rho_t + nx;
+    double* pacc = drho0 + nx;
+    double* jtne = pacc + (size_t)ADJ_NPAR * G;
+    double* jmis = jtne + G;
+    std::vector<double> hm(256 + 256 + 16);
+    memcpy(hm.data(), h->hm.M, 256 * sizeof(double));
+    memcpy(hm.data() + 256, h->hm.Minv, 256 * sizeof(double));
+    {
+        static const int ax[4] = {1, 0, -1, 0}, dg[4] = {1, -1, -1, 1};
+        for (int o = 0; o < 4; o++)
+            for (int q = 0; q < 4; q++)
+                hm[512 + 4 * o + q] = h->hm.c[o] * (h->p.orbit_kind[o] == 0 ? ax[q] : dg[q]);
+    }
+    cudaStream_t st = h->stream;
+    auto S = [&](int64_t k) { return seg + (size_t)k * SB; };
+    auto K_ = [&](int64_t k) { return ck + (size_t)k * SB; };
+#define GT(call)                                                                              \
+    do {                                                                                      \
+        e = (call);                                                                           \
+        if (e != cudaSuccess) {                                                               \
+            cleanup();                                                                        \
+            return fail(h, LBKM_ECUDA, "lbkm_grad: %s: %s", #call, cudaGetErrorString(e));   \
+        }                                                                                     \
+    } while (0)
+    GT(cudaMemcpyAsync(mats, hm.data(), sizeof(double) * hm.size(), cudaMemcpyHostToDevice, st));
+    GT(cudaMemcpyAsync(rho_t, ob->rho_target, sizeof(double) * nx, cudaMemcpyHostToDevice, st));
+    GT(cudaMemsetAsync(pacc, 0, sizeof(double) * (ADJ_NPAR + 2) * G, st));
+    GT(cudaMemsetAsync(sctr, 0, sizeof(DevCounters), st));
+    GT(cudaMemcpyAsync(K_(0), h->buf[h->cur], SB, cudaMemcpyDeviceToDevice, st));
+    StepLaunch sl = step_args(h, 0);
+    sl.ctr = sctr;
+    sl.tne_every = 0;
+    // forward run, keeping a state every C steps
+    for (int64_t n = 0; n < N; n++) {
+        sl.in = n == 0 ? (const void*)K_(0) : (const void*)S(n % 2);
+        sl.out = S((n + 1) % 2);
+        GT(launch_step(0, 0, false, &h->Kd, sl, st));
+        if ((n + 1) % C == 0 && n + 1 < N)
+            GT(cudaMemcpyAsync(K_((n + 1) / C), S((n + 1) % 2), SB, cudaMemcpyDeviceToDevice, st));
+    }
+    AdjArgs a;
+    memset(&a, 0, sizeof(a));
+    a.mac = mac;
+    a.mb = mb;
+    a.loc = loc;
+    a.gb = gb;
+    a.pacc = pacc;
+    a.M = mats;
+    a.Minv = mats + 256;
+    a.vx = mats + 512;
+    a.tne_w = ob->w_tne * h->p.dx * h->p.dt;
+    a.jw = a.tne_w;
+    // seed with the mismatch of the final state
+    a.f = reinterpret_cast<const double*>(S(N % 2));
+    a.fb0 = fbA;
+    a.lb0 = lbA;
+    a.jacc = jmis;
+    GT(launch_adj_seed(h->Kd, a, rho_t, ob->w_mismatch, G, st));
+    a.jacc = jtne;
+    double *fc = fbA, *fn = fbB, *lc = lbA, *ln = lbB;
+    for (int64_t sg = nck - 1; sg >= 0; sg--) {
+        const int64_t n0 = sg * C, n1 = (n0 + C < N) ? n0 + C : N;
+        GT(cudaMemcpyAsync(S(0), K_(sg), SB, cudaMemcpyDeviceToDevice, st));
+        for (int64_t n = n0; n < n1 - 1; n++) {
+            sl.in = S(n - n0);
+            sl.out = S(n - n0 + 1);
+            GT(launch_step(0, 0, false, &h->Kd, sl, st));
+        }
+        for (int64_t n = n1 - 1; n >= n0; n--) {
+            const double* state = reinterpret_cast<const double*>(S(n - n0));
+            GT(launch_macros(0, h->Kd, state, mac, mac + nx, mac + 2 * (size_t)nx,
+                             mac + 3 * (size_t)nx, nullptr, nullptr, st));
+            a.f = state;
+            a.fb1 = fc;
+            a.lb1 = lc;
+            a.fb0 = fn;
+            a.lb0 = ln;
+            GT(launch_adj_step(h->Kd, a, G, st));
+            std::swap(fc, fn);
+            std::swap(lc, ln);
+        }
+    }
+    a.f = reinterpret_cast<const double*>(K_(0));
+    a.fb1 = fc;
+    GT(launch_adj_rho0(h->Kd, a, drho0, G, st));
+    std::vector<double> hp((size_t)(ADJ_NPAR + 2) * G);
+    GT(cudaMemcpyAsync(hp.data(), pacc, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
+    if (out->drho0)
+        GT(cudaMemcpyAsync(out->drho0, drho0, sizeof(double) * nx, cudaMemcpyDeviceToHost, st));
+    if (out->df0)
+        GT(cudaMemcpyAsync(out->df0, fc, sizeof(double) * 16 * nx, cudaMemcpyDeviceToHost, st));
+    GT(cudaStreamSynchronize(st));
+#undef GT
+    int stat = 0;
+    cudaMemcpy(&stat, &sctr->status, sizeof(int), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (stat & 1)
+        return fail(h, LBKM_EUNSTABLE, "the forward run reached a non-physical state");
+    double sums[ADJ_NPAR + 2];
+    for (int q = 0; q < ADJ_NPAR + 2; q++) {
+        double s = 0.0;
+        for (int b = 0; b < G; b++) s += hp[(size_t)q * G + b];
+        sums[q] = s;
+    }
+    for (int k = 0; k < 16; k++) out->dS[k] = k < 4 ? 0.0 : sums[k - 4];
+    out->dQ = sums[12];
+    out->domega1 = sums[13];
+    out->J_tne = sums[ADJ_NPAR];
+    out->J_mismatch = sums[ADJ_NPAR + 1];
+    out->J = out->J_mismatch + out->J_tne;
+    return LBKM_OK;
+}
+
 const char* lbkm_last_error(lbkm_t h)
 {
     if (!h) return g_create_error.c_str();

@@ -86,6 +86,34 @@ cudaError_t launch_tne_instances(int precision, const ModelConst<double>& Kd, co
                                  const InstParam* inst, int n_inst, TneRecord* out,
                                  double area, cudaStream_t s);
 
+// Discrete adjoint of the FP64 1-D step (adjoint.cu).
+constexpr int ADJ_NPAR = 14; // dJ/dS_5..S_16, dJ/dQ, dJ/domega1
+struct AdjArgs {
+    const double* f;     // state n: 17 planes with the handle's pitch
+    const double* mac;   // [4][nx] rho, ux, uy, T of state n
+    const double* fb1;   // dJ/df of state n+1, [16][nx]
+    const double* lb1;   // dJ/dlambda of state n+1, [nx]
+    double* mb;          // [16][nx] pass A -> B: adjoint of the moments
+    double* loc;         // [6][nx] pass A -> B: rho_b, ux_b, uy_b, T_b, lambda_b, clamped lambda_b
+    double* gb;          // [2][nx] pass A -> B: adjoints of du_x/dx, du_y/dx
+    double* fb0;         // dJ/df of state n, [16][nx]
+    double* lb0;         // dJ/dlambda of state n, [nx]
+    double* pacc;        // [ADJ_NPAR][grid] per-block parameter accumulators
+    double* jacc;        // [grid] per-block objective accumulators
+    const double* M;     // [16][16] moment matrix (row = moment)
+    const double* Minv;  // [16][16]
+    const double* vx;    // [16] x-velocities
+    double tne_w;        // w_tne dx dt: Delta_b += 2 tne_w Delta
+    double jw;           // w_tne dx dt for the objective value
+};
+int adj_grid(int nx);
+cudaError_t launch_adj_step(const ModelConst<double>& K, const AdjArgs& a, int grid,
+                            cudaStream_t s);
+cudaError_t launch_adj_seed(const ModelConst<double>& K, const AdjArgs& a, const double* rho_t,
+                            double w, int grid, cudaStream_t s);
+cudaError_t launch_adj_rho0(const ModelConst<double>& K, const AdjArgs& a, double* drho0,
+                            int grid, cudaStream_t s);
+
 // FP32 2-D step: y-marching strips, two cells per thread (march.cu)
 int march_grid(int recovery, int nx, int ny);
 cudaError_t launch_march(int recovery, const ModelConst<float>& K, const StepLaunch& a,

@@ -38,7 +38,7 @@ struct ModelConst {
     R DI, inv_DI;                        // D + I and its inverse
     R omega1, omega2;                    // Cochran constants (Eq. (28))
     R chem;                              // 2 Q / ((D+I) dt): C_hat = dfeq/dT * dlambda * chem
-    R dt, inv_dx, inv_dy, half_inv_dx, half_inv_dy;
+    R dt, inv_dx, inv_dy, half_inv_dx, half_inv_dy, dx_;
     double cd[4], wd[4];                 // speeds and w in FP64 (conserved-moment recovery)
     double inv_DId, T_igd;
     int32_t nx, ny, pitch, bc_x, bc_y;

@@ -219,6 +219,7 @@ void fill_model_const(const HostModel& hm, const double S[16], double Q, double 
     K->inv_dy = (R)(1.0 / dy);
     K->half_inv_dx = (R)(0.5 / dx);
     K->half_inv_dy = (R)(0.5 / dy);
+    K->dx_ = (R)dx;
     K->T_igd = T_ig;
     K->nx = nx;
     K->ny = ny;

@@ -28,7 +28,7 @@ EXPORTED = ["lbkm_default_params", "lbkm_create", "lbkm_destroy", "lbkm_set_stre
             "lbkm_tne", "lbkm_tne_history", "lbkm_state_bytes", "lbkm_get_state",
             "lbkm_set_state", "lbkm_last_error", "lbkm_version", "lbkm_tne_noalloc",
             "lbkm_create_batched", "lbkm_instances", "lbkm_tne_instances", "lbkm_autotune",
-            "lbkm_set_wait_limit"]
+            "lbkm_set_wait_limit", "lbkm_grad"]
 
 
 class LbkmError(RuntimeError):
@@ -50,6 +50,19 @@ class Params(ctypes.Structure):
         ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
         ("tne_every", ctypes.c_int32), ("tne_capacity", ctypes.c_int32),
     ]
+
+
+class Objective(ctypes.Structure):
+    _fields_ = [("rho_target", ctypes.c_void_p), ("w_mismatch", ctypes.c_double),
+                ("w_tne", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("checkpoint_every", ctypes.c_int32)]
+
+
+class GradOut(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_double), ("J_mismatch", ctypes.c_double),
+                ("J_tne", ctypes.c_double), ("dS", ctypes.c_double * 16),
+                ("dQ", ctypes.c_double), ("domega1", ctypes.c_double),
+                ("drho0", ctypes.c_void_p), ("df0", ctypes.c_void_p)]
 
 
 class TneGlobal(ctypes.Structure):
@@ -112,6 +125,8 @@ def load():
     lib.lbkm_tne_instances.restype = ctypes.c_int
     lib.lbkm_autotune.argtypes = [H, ctypes.c_int32, _vp]
     lib.lbkm_autotune.restype = ctypes.c_int
+    lib.lbkm_grad.argtypes = [H, ctypes.POINTER(Objective), ctypes.POINTER(GradOut)]
+    lib.lbkm_grad.restype = ctypes.c_int
     lib.lbkm_set_wait_limit.argtypes = [H, ctypes.c_int64, ctypes.c_int32]
     lib.lbkm_set_wait_limit.restype = ctypes.c_int
     for name in ("lbkm_create", "lbkm_set_stream", "lbkm_init_fields", "lbkm_step", "lbkm_sync",
@@ -213,6 +228,24 @@ class Solver:
         out = (ctypes.c_int32 * 3)()
         self._check(self._lib.lbkm_autotune(self._h, int(trial_steps), out))
         return tuple(out)
+
+    def grad(self, rho_target, steps, w_mismatch=1.0, w_tne=1.0, checkpoint_every=64,
+             want_f0=False):
+        """lbkm_grad: J and dJ/d(S, Q, omega1, rho0 [, f0]) over `steps` steps from the
+        current state (which is left unchanged)."""
+        rt = np.ascontiguousarray(np.broadcast_to(np.asarray(rho_target, np.float64),
+                                                  (self.nx,)))
+        ob = Objective(rt.ctypes.data, float(w_mismatch), float(w_tne), int(steps),
+                       int(checkpoint_every))
+        drho0 = np.zeros(self.nx)
+        df0 = np.zeros((16, self.nx)) if want_f0 else None
+        out = GradOut()
+        out.drho0 = drho0.ctypes.data
+        out.df0 = df0.ctypes.data if want_f0 else None
+        self._check(self._lib.lbkm_grad(self._h, ctypes.byref(ob), ctypes.byref(out)))
+        return {"J": out.J, "J_mismatch": out.J_mismatch, "J_tne": out.J_tne,
+                "dS": np.array(out.dS[:]), "dQ": out.dQ, "domega1": out.domega1,
+                "drho0": drho0, "df0": df0}
 
     def set_wait_limit(self, timeout_ns, phantom_blocks=0):
         self._check(self._lib.lbkm_set_wait_limit(self._h, int(timeout_ns), int(phantom_blocks)))
