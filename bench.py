@@ -331,6 +331,77 @@ def run_detonation(args):
     return 0
 
 
+def run_adjoint(args):
+    """Config 5: dJ/d(S, Q, omega1, rho0) of a 4000-step 1-D detonation of 8192 cells
+    (profile mismatch + integrated TNE), checkpoints every 64 steps, through lbkm_grad;
+    compared with the plain single-instance FP64 forward run that central differences
+    would repeat twice per gradient entry."""
+    import time
+    import torch
+    from paper_1411_6697_gb300 import lbkm
+    rank, local, world = _env_rank()
+    torch.cuda.set_device(local)
+    cfg = li.adjoint()
+    base, tgt = cfg["base"], cfg["target"]
+    q, fl = base["params"], base["fields"]
+    steps = base["steps"]
+    stream = torch.cuda.Stream()
+
+    def solver(p):
+        s = lbkm.Solver(nx=p["nx"], ny=1, precision=lbkm.F64, S=p["S"], Q=p["Q"], bc=(1, 0),
+                        dy=p["dx"], stream=stream, **_shared_params(p))
+        s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+        return s
+
+    # target profile: the run with perturbed S and Q
+    t = solver(tgt["params"])
+    with torch.cuda.stream(stream):
+        t.step(steps)
+        t.sync()
+    rho_t = t.macros()["rho"][0].copy()
+    t.close()
+    # plain FP64 forward of the same length
+    one = solver(q)
+    with torch.cuda.stream(stream):
+        one.step(3)
+        one.sync()
+        ms_fwd = time_steps(one, stream, steps)
+    one.close()
+    s = solver(q)
+    n_grad = max(1, min(args.steps, 3))
+    g = s.grad(rho_t, steps, w_tne=cfg["w_tne"], checkpoint_every=cfg["checkpoint_every"])
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(n_grad):
+            g = s.grad(rho_t, steps, w_tne=cfg["w_tne"],
+                       checkpoint_every=cfg["checkpoint_every"])
+        sec = (time.perf_counter() - t0) / n_grad
+    s.close()
+    nx = q["nx"]
+    n_scalar = 16 + 2               # S_1..S_16, Q, omega1
+    n_entries = n_scalar + nx       # and the initial density field
+    fd = 2 * ms_fwd * 1e-3          # one central difference = two forward runs
+    line = {"metric": METRIC, "value": nx * steps / sec / 1e6,
+            "unit": "Mcell-updates/s (forward-equivalent, per gradient)", "n_gpus": 1,
+            "steps": n_grad, "warmup": 1, "ms_per_step": sec * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "adjoint_8192x1_detonation_4000_steps",
+                       "checkpoint_every": cfg["checkpoint_every"], "w_tne": cfg["w_tne"],
+                       "step": "one lbkm_grad call (forward with checkpoints, replay, "
+                               "reverse sweep), host wall clock"},
+            "J": g["J"], "plain_f64_forward_ms": ms_fwd,
+            "plain_f64_forward_mcell_per_s": nx * steps / (ms_fwd * 1e-3) / 1e6,
+            "gradient_ms": sec * 1e3,
+            "gradient_over_forward": sec / (ms_fwd * 1e-3),
+            "speedup_vs_central_fd_scalars": n_scalar * fd / sec,
+            "speedup_vs_central_fd_all_entries": n_entries * fd / sec,
+            "gradient_entries": n_entries, "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,12 +414,14 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--side", type=int, default=N_CELLS_SIDE)
     ap.add_argument("--workload", default="reactive2d",
-                    choices=["reactive2d", "batched", "detonation"])
+                    choices=["reactive2d", "batched", "detonation", "adjoint"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     if args.workload == "detonation":
         return run_detonation(args)
 

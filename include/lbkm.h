@@ -101,7 +101,7 @@ typedef struct {
                               Sec. III); require dt * max(S_5..S_16) < 2 */
     double Q;              /* heat release per unit mass (Eq. (18)) */
     double omega1, omega2; /* Cochran rate constants of Eq. (28), m = n = 1 */
-    double T_ig;           /* reaction only where T > T_ig (Sec. II) */
+    double T_ig;           /* reaction only where T > T_ig (Sec. II); finite, >= 0 */
     double dx, dy, dt;     /* grid spacing and time step */
     int32_t bc_x, bc_y;    /* lbkm_bc for each direction */
     int32_t tne_every;     /* 0: no on-the-fly TNE; k > 0: reduce the TNE of the

@@ -236,6 +236,8 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
         return fail(nullptr, LBKM_EINVAL, "CFL number %g of the fastest velocity exceeds 1", cfl);
     if (!(p.omega1 >= 0 && p.omega2 >= 0))
         return fail(nullptr, LBKM_EINVAL, "omega1, omega2 must be >= 0");
+    if (!(p.T_ig >= 0.0 && p.T_ig <= 1e300))
+        return fail(nullptr, LBKM_EINVAL, "T_ig must be finite and >= 0");
     if (p.tne_every < 0 || p.tne_capacity < 1)
         return fail(nullptr, LBKM_EINVAL, "tne_every must be >= 0 and tne_capacity >= 1");
 

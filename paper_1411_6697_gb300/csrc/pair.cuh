@@ -22,6 +22,14 @@ __device__ __forceinline__ void cp_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// the hardware reciprocal approximation (about 1 ulp); every use refines it
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 struct DfConst {
     float ch[4], cl[4], wh[4], wl[4], idh, idl, tigh, tigl;
 };
@@ -73,7 +81,7 @@ __device__ __forceinline__ void recover_pair_df(const V2* f, const DfConst& C, V
 {
     D2 m1, m2, m3, m4;
     conserved_pair(f, C, m1, m2, m3, m4);
-    const V2 rb(__frcp_rn(m1.hi.x()), __frcp_rn(m1.hi.y()));
+    const V2 rb(rcp_approx(m1.hi.x()), rcp_approx(m1.hi.y()));
     const D2 vx = d_div(m2, m1, rb), vy = d_div(m3, m1, rb), e = d_div(m4, m1, rb);
     const D2 t = d_mul_c(d_add(e, d_neg(d_add(d_sqr(vx), d_sqr(vy)))), C.idh, C.idl);
     rho = m1.hi;
@@ -86,21 +94,60 @@ __device__ __forceinline__ void recover_pair_df(const V2* f, const DfConst& C, V
     ok1 = m1.hi.y() > 0.0f && t.hi.y() > 0.0f && t.hi.y() <= FLT_MAX;
 }
 
+// Exact binary32 -> binary64 conversion by moving the IEEE-754 fields with integer
+// operations (exponent rebias 127 -> 1023, significand shifted by 29 bits), so the
+// conversion runs on the integer ALU instead of the FP64 unit, which GB300 builds
+// for 1/58 of the FP32 rate. Zeros are built directly; subnormal, infinite and NaN
+// inputs (never produced by a valid state) take the conversion instruction.
+__device__ __forceinline__ double f2d_exact(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e - 1u < 254u) {
+        const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+        return __hiloint2double((int)hi, (int)(b << 29));
+    }
+    if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return (double)x;
+}
+
+// binary64 -> binary32, round to nearest even, by integer operations: the top 23
+// significand bits are kept and the 29 dropped bits decide the rounding (above half:
+// up; exactly half: to even). A carry out of the significand steps the exponent,
+// which also yields infinity on overflow. Results outside the normal binary32 range
+// (zero, subnormal) and infinite or NaN inputs take the conversion instruction.
+__device__ __forceinline__ float d2f_rn(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    if (e < 1 || e > 254) return __double2float_rn(x);
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;
+    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float((hi & 0x80000000u) | (((unsigned)e << 23) + m + up));
+}
+
+// Ordered comparisons of FP64 values through their bit patterns: for a >= 0 (not
+// NaN), x > a exactly when the patterns compare so as signed 64-bit integers.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
 // FP64 recovery: the exact conserved sums carried into FP64 (hi + lo), then rho,
 // u, T formed in FP64 arithmetic.
 // 1/m1 from an FP32 reciprocal refined by two FP64 Newton steps (each doubles the
-// correct bits: 24 -> 48 -> full FP64), then u and T in FP64.
+// correct bits: 22 -> 44 -> full FP64), then u and T in FP64.
 __device__ __forceinline__ void recover_one_f64(float seed_of, double m1, double m2, double m3,
                                                 double m4, double inv_DI, double& u, double& v,
                                                 double& t)
 {
-    double q = (double)__frcp_rn(seed_of);
+    double q = f2d_exact(rcp_approx(seed_of));
     q = ::fma(q, ::fma(-m1, q, 1.0), q);
     q = ::fma(q, ::fma(-m1, q, 1.0), q);
     u = m2 * q;
     v = m3 * q;
     t = (m4 * q - (u * u + v * v)) * inv_DI;
 }
+
+__device__ __forceinline__ double df_to_f64(float hi, float lo) { return f2d_exact(hi) + f2d_exact(lo); }
 
 // rho, u, T of a cell pair from its 16 f: exact conserved sums, then FP64 (REC = 0)
 // or double-float (REC = 1); ig = T > T_ig decided in that precision, ok = rho > 0
@@ -116,22 +163,23 @@ __device__ __forceinline__ void recover_pair(const V2* f, const DfConst& C,
         D2 m1, m2, m3, m4;
         conserved_pair(f, C, m1, m2, m3, m4);
         double u0, v0, t0, u1, v1, t1;
-        const double r0 = (double)m1.hi.x() + (double)m1.lo.x();
-        const double r1 = (double)m1.hi.y() + (double)m1.lo.y();
-        recover_one_f64(m1.hi.x(), r0, (double)m2.hi.x() + (double)m2.lo.x(),
-                        (double)m3.hi.x() + (double)m3.lo.x(), (double)m4.hi.x() + (double)m4.lo.x(),
+        const double r0 = df_to_f64(m1.hi.x(), m1.lo.x());
+        const double r1 = df_to_f64(m1.hi.y(), m1.lo.y());
+        recover_one_f64(m1.hi.x(), r0, df_to_f64(m2.hi.x(), m2.lo.x()),
+                        df_to_f64(m3.hi.x(), m3.lo.x()), df_to_f64(m4.hi.x(), m4.lo.x()),
                         K.inv_DId, u0, v0, t0);
-        recover_one_f64(m1.hi.y(), r1, (double)m2.hi.y() + (double)m2.lo.y(),
-                        (double)m3.hi.y() + (double)m3.lo.y(), (double)m4.hi.y() + (double)m4.lo.y(),
+        recover_one_f64(m1.hi.y(), r1, df_to_f64(m2.hi.y(), m2.lo.y()),
+                        df_to_f64(m3.hi.y(), m3.lo.y()), df_to_f64(m4.hi.y(), m4.lo.y()),
                         K.inv_DId, u1, v1, t1);
         rho = m1.hi; // the exact sum rounded to FP32
-        ux = V2((float)u0, (float)u1);
-        uy = V2((float)v0, (float)v1);
-        T = V2((float)t0, (float)t1);
-        ig0 = t0 > K.T_igd;
-        ig1 = t1 > K.T_igd;
-        ok0 = r0 > 0.0 && t0 > 0.0 && t0 <= DBL_MAX;
-        ok1 = r1 > 0.0 && t1 > 0.0 && t1 <= DBL_MAX;
+        ux = V2(d2f_rn(u0), d2f_rn(u1));
+        uy = V2(d2f_rn(v0), d2f_rn(v1));
+        T = V2(d2f_rn(t0), d2f_rn(t1));
+        const long long tig = dbits(K.T_igd), dmax = dbits(DBL_MAX);
+        ig0 = dbits(t0) > tig;
+        ig1 = dbits(t1) > tig;
+        ok0 = dbits(r0) > 0 && dbits(t0) > 0 && dbits(t0) <= dmax;
+        ok1 = dbits(r1) > 0 && dbits(t1) > 0 && dbits(t1) <= dmax;
     }
 }
 

@@ -20,7 +20,11 @@ def gpu():
 
 
 def problem(nx, steps, omega1, driver):
-    c = li.detonation(nx=nx, steps=steps, driver=driver, omega1=omega1)
+    # the ripple keeps the minmod branches of the f_i away from rounding-level
+    # differences; on flat stretches the gradient would depend on how each side rounds
+    # (without it the oracle's own drho0 near the boundary differs by ~10 % between an
+    # x86 and an Arm host)
+    c = li.detonation(nx=nx, steps=steps, driver=driver, omega1=omega1, ripple=1e-3)
     p = dict(c["params"])
     m = to.Model1D(nx, gamma=p["gamma"], orbit_kind=p["orbit_kind"],
                    orbit_speed=p["orbit_speed"], orbit_eta=p["orbit_eta"], T_ig=p["T_ig"],
@@ -66,7 +70,7 @@ def gpu_grad(c, p, rho_t, steps, w_tne, ck):
     return g
 
 
-def compare(g, r, tol):
+def compare(g, r, tol, tol_rho0=None):
     assert abs(g["J"] - r["J"]) <= tol * abs(r["J"])
     assert abs(g["J_mismatch"] - r["J_mismatch"]) <= tol * abs(r["J_mismatch"])
     sc = np.abs(r["dS"][4:]).max()
@@ -74,7 +78,8 @@ def compare(g, r, tol):
     assert np.all(g["dS"][:4] == 0) and np.abs(r["dS"][:4]).max() == 0.0
     assert abs(g["dQ"] - r["dQ"]) <= tol * abs(r["dQ"])
     assert abs(g["domega1"] - r["domega1"]) <= tol * abs(r["domega1"])
-    assert np.abs(g["drho0"] - r["drho0"]).max() <= tol * np.abs(r["drho0"]).max()
+    t0 = tol if tol_rho0 is None else tol_rho0
+    assert np.abs(g["drho0"] - r["drho0"]).max() <= t0 * np.abs(r["drho0"]).max()
 
 
 @pytest.mark.parametrize("ck", [16, 7, 60])
@@ -93,7 +98,11 @@ def test_adjoint_full_config_size():
     c, p, m, rho_t = problem(nx, steps, omega1=2e4, driver=50)
     r = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0, ck=64)
     g = gpu_grad(c, p, rho_t, steps, w_tne=1.0, ck=64)
-    compare(g, r, 1e-7)
+    # behind the front lambda sits within a few ulp of 1, so the minmod branches of
+    # u.grad(lambda) there are decided by rounding: flipping every such branch whose
+    # arguments are below 1e-15 moves the oracle's own drho0 by 2.9e-7 of its maximum
+    # (and J, dS, dQ, domega1 by < 1e-11), hence the wider elementwise bound on drho0
+    compare(g, r, 1e-7, tol_rho0=2e-6)
 
 
 def test_autograd_function_backward():

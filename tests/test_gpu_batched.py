@@ -106,3 +106,33 @@ def test_barrier_wait_runs_out_and_reports():
     with pytest.raises(lbkm.LbkmError) as e:
         s.sync()
     assert e.value.code == 6
+
+
+@pytest.mark.slow
+def test_batched_full_workload_5000_steps():
+    """All 512 instances (7.8 M cells) for the full 5000 steps in graph-captured chunks:
+    no instance blows up, and the three shortest match their FP64 oracle runs. FP32
+    rounding is amplified by the ignition switch over thousands of steps, so the bound
+    is the larger of 2e-5 and four times the oracle's own drift under a one-ulp FP32
+    perturbation of its initial state."""
+    cfg = li.batched(n_instances=512, steps=5000)
+    s = make_batched(cfg)
+    s.step(cfg["steps"])
+    s.sync()  # raises LbkmError (LBKM_EUNSTABLE) if any cell went non-physical
+    planes = s.f_planes()
+    m = s.macros()
+    assert np.all(m["rho"] > 0) and np.all(m["T"] > 0)
+    rng = np.random.default_rng(li.SEED_BASE + 41)
+    for i in np.argsort(cfg["nx"])[:3]:
+        inst = cfg["instances"][i]
+        ob = make_oracle(inst["params"])
+        fl = inst["fields"]
+        f0 = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"]).astype(np.float32)
+        f_ref, lam_ref = ob.run(f0.astype(np.float64), fl["lam"], cfg["steps"])
+        ulp = np.spacing(np.abs(f0)) * rng.choice([-1.0, 1.0], f0.shape)
+        f_alt, _ = ob.run((f0 + ulp).astype(np.float64), fl["lam"], cfg["steps"])
+        bound = max(2e-5, 4.0 * rel_l2(f_alt, f_ref))
+        got = split(planes, cfg["nx"])[i]
+        err = rel_l2(got[:16], f_ref)
+        assert err <= bound, (int(i), err, bound)
+        assert rel_l2(got[16], lam_ref) <= max(2e-5, 4.0 * bound)
