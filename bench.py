@@ -53,24 +53,30 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-STEP_KERNEL_SOURCES = ("kernels.cu", "cell.cuh", "kernels.cuh", "model.h")
+# the FP32 2-D step runs march_kernel (march.cu); FP64 and 1-D grids run step_kernel
+STEP_KERNEL_SOURCES = {
+    "march": ("march.cu", "pair.cuh", "vec2.cuh", "reduce.cuh", "cell.cuh", "kernels.cuh",
+              "model.h"),
+    "step": ("kernels.cu", "cell.cuh", "kernels.cuh", "model.h", "reduce.cuh"),
+}
+PROFILE = {"march": "march_kernel_reactive2d.md", "step": "step_kernel_reactive2d.md"}
 
 
-def step_kernel_digest():
+def step_kernel_digest(kernel="march"):
     """sha256 over the sources that define the step kernel."""
     import hashlib
     src = os.path.join(ROOT, "paper_1411_6697_gb300", "csrc")
     h = hashlib.sha256()
-    for f in STEP_KERNEL_SOURCES:
+    for f in STEP_KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(src, f), "rb").read())
     return h.hexdigest()
 
 
-def profile_traffic(kernel_tag):
+def profile_traffic(kernel, kernel_tag):
     """dram bytes per launch from the committed ncu summary, if it matches the current
     kernel source (sha256 line); else None."""
-    prof = os.path.join(ROOT, "profiles", "step_kernel_reactive2d.md")
-    digest = step_kernel_digest()
+    prof = os.path.join(ROOT, "profiles", PROFILE[kernel])
+    digest = step_kernel_digest(kernel)
     try:
         lines = open(prof).read().splitlines()
     except OSError:
@@ -463,7 +469,8 @@ def main():
     alg_bytes = BYTES_PER_CELL[tag] * n
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-    traffic = profile_traffic(tag + ("_df32" if rec == lbkm.RECOVER_DF32 else ""))
+    kernel = "march" if (prec == lbkm.F32 and args.side > 1) else "step"
+    traffic = profile_traffic(kernel, tag + ("_df32" if rec == lbkm.RECOVER_DF32 else ""))
 
     # end to end through the C ABI with pinned host buffers: H2D of the initial fields,
     # the steps, D2H of the macroscopic fields and of the TNE history
@@ -499,7 +506,8 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": peak_kind, "kernel": "step_kernel (%s)" % tag,
+                     "peak_kind": peak_kind, "kernel": ("march_kernel<%d> (f32)" % rec) if kernel == "march"
+                     else "step_kernel (%s)" % tag,
                      "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": {"value": e2e_value, "unit": "Mcell-updates/s",
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,

@@ -198,9 +198,10 @@ __global__ void __launch_bounds__(BT)
                 const V2 rT = rho * T;
                 const V2 A8 = (rT * par[16]) * fma(V2(4.f) * ux, dux_dx - theta, V2(2.f) * uy * duy_dx);
                 const V2 A9 = (rT * par[17]) * fma(V2(4.f) * uy, -theta, V2(2.f) * ux * duy_dx);
-                float dl0 = 0.f, dl1 = 0.f;
-                if (ign[2 * tid]) dl0 = reaction_increment(lam0.x(), par[19] * rT.x(), par[20] * rT.x(), dt);
-                if (ign[2 * tid + 1]) dl1 = reaction_increment(lam0.y(), par[19] * rT.y(), par[20] * rT.y(), dt);
+                // both cells evaluated, then selected: no divergent branch
+                const float ri0 = reaction_increment(lam0.x(), par[19] * rT.x(), par[20] * rT.x(), dt);
+                const float ri1 = reaction_increment(lam0.y(), par[19] * rT.y(), par[20] * rT.y(), dt);
+                const float dl0 = ign[2 * tid] ? ri0 : 0.f, dl1 = ign[2 * tid + 1] ? ri1 : 0.f;
                 const V2 dlam(dl0, dl1);
                 const V2 cr = dlam * par[18];
                 V2 dq[16], Om[16], W[16];

@@ -18,11 +18,12 @@ template <typename R>
 __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 
 // minmod of the NND scheme: 0 unless a and b share a sign, else the one of
-// smaller magnitude. Written as max(min(a,b),0) + min(max(a,b),0).
+// smaller magnitude -- which is the median of a, b and 0, written as
+// max(min(a,b), min(max(a,b),0)).
 template <typename R>
 __device__ __forceinline__ R minmod(R a, R b)
 {
-    return rmax(rmin(a, b), R(0)) + rmin(rmax(a, b), R(0));
+    return rmax(rmin(a, b), rmin(rmax(a, b), R(0)));
 }
 
 // (H_{j+1/2} - H_{j-1/2}) / v of the NND flux of F = v q for v > 0, from

@@ -169,8 +169,11 @@ __global__ void __launch_bounds__(MT, 3)
         const int cx = x0 + 2 * tid;
         const bool act0 = cx < nx, act1 = cx + 1 < nx;
         float tsm[NSUM];
+        V2 tsp[TNE_K], td2(0.f);
 #pragma unroll
         for (int q = 0; q < NSUM; q++) tsm[q] = 0.f;
+#pragma unroll
+        for (int k = 0; k < TNE_K; k++) tsp[k] = V2(0.f);
 
         __syncthreads(); // the previous strip is done with the rings
         for (int r = y0 - 2; r <= y0 + 1 + PF; r++) {
@@ -234,9 +237,10 @@ __global__ void __launch_bounds__(MT, 3)
             const V2 A9 = (rT * K.A9c) * fma(V2(4.f) * uy, duy_dy - theta, V2(2.f) * ux * shear);
 
             // reaction over dt (Eq. (28)), decided by the recovered T
-            float dl0 = 0.f, dl1 = 0.f;
-            if (ig0) dl0 = reaction_increment(lam0.x(), K.omega1 * rT.x(), K.omega2 * rT.x(), dt);
-            if (ig1) dl1 = reaction_increment(lam0.y(), K.omega1 * rT.y(), K.omega2 * rT.y(), dt);
+            // (evaluated for both cells and selected: no divergent branch)
+            const float ri0 = reaction_increment(lam0.x(), K.omega1 * rT.x(), K.omega2 * rT.x(), dt);
+            const float ri1 = reaction_increment(lam0.y(), K.omega1 * rT.y(), K.omega2 * rT.y(), dt);
+            const float dl0 = ig0 ? ri0 : 0.f, dl1 = ig1 ? ri1 : 0.f;
             const V2 dlam(dl0, dl1);
             const V2 cr = dlam * K.chem;
 
@@ -304,25 +308,43 @@ __global__ void __launch_bounds__(MT, 3)
             else if (act0)
                 out[16 * K.plane + g] = ln.x();
 
-            // TNE statistics of the state being stepped (Eqs. (90)-(91))
+            // TNE statistics of the state being stepped (Eqs. (90)-(91)); sums of Delta_k
+            // and d^2 accumulate as packed pairs, folded at the end of the strip
             if (do_tne) {
-                const float w0 = act0 ? 1.f : 0.f, w1 = act1 ? 1.f : 0.f;
-                V2 d2(0.f);
+                if (act1) {
+                    V2 d2(0.f);
 #pragma unroll
-                for (int k = 0; k < TNE_K; k++) {
-                    const V2 Dk = D[k] * V2(w0, w1);
-                    d2 = fma(Dk, Dk, d2);
-                    tsm[k] += Dk.x() + Dk.y();
-                    tsm[TNE_K + k] += fabsf(Dk.x()) + fabsf(Dk.y());
-                    tmin[k] = fminf(tmin[k], fminf(act0 ? Dk.x() : FLT_MAX, act1 ? Dk.y() : FLT_MAX));
-                    tmax[k] = fmaxf(tmax[k], fmaxf(act0 ? Dk.x() : -FLT_MAX, act1 ? Dk.y() : -FLT_MAX));
+                    for (int k = 0; k < TNE_K; k++) {
+                        const V2 Dk = D[k];
+                        d2 = fma(Dk, Dk, d2);
+                        tsp[k] += Dk;
+                        tsm[TNE_K + k] += fabsf(Dk.x()) + fabsf(Dk.y());
+                        tmin[k] = fminf(tmin[k], fminf(Dk.x(), Dk.y()));
+                        tmax[k] = fmaxf(tmax[k], fmaxf(Dk.x(), Dk.y()));
+                    }
+                    tsm[2 * TNE_K] += sqrt_approx(d2.x()) + sqrt_approx(d2.y());
+                    td2 += d2;
+                } else if (act0) {
+                    float d2 = 0.f;
+#pragma unroll
+                    for (int k = 0; k < TNE_K; k++) {
+                        const float Dk = D[k].x();
+                        d2 = fmaf(Dk, Dk, d2);
+                        tsp[k] += V2(Dk, 0.f);
+                        tsm[TNE_K + k] += fabsf(Dk);
+                        tmin[k] = fminf(tmin[k], Dk);
+                        tmax[k] = fmaxf(tmax[k], Dk);
+                    }
+                    tsm[2 * TNE_K] += sqrt_approx(d2);
+                    td2 += V2(d2, 0.f);
                 }
-                tsm[2 * TNE_K] += sqrtf(d2.x()) + sqrtf(d2.y());
-                tsm[2 * TNE_K + 1] += d2.x() + d2.y();
             }
         }
         cp_wait<0>();
         if (do_tne) { // per strip: warp sums in FP32, then FP64 per warp
+#pragma unroll
+            for (int k = 0; k < TNE_K; k++) tsm[k] = tsp[k].x() + tsp[k].y();
+            tsm[2 * TNE_K + 1] = td2.x() + td2.y();
 #pragma unroll
             for (int q = 0; q < NSUM; q++) {
                 const float v = warp_sum(tsm[q]);

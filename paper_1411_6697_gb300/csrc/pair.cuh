@@ -30,6 +30,15 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// the hardware square-root approximation (relative error about 2^-23), for the
+// TNE measure d = sqrt(sum_k Delta_k^2), which is reported, never fed back
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 struct DfConst {
     float ch[4], cl[4], wh[4], wl[4], idh, idl, tigh, tigl;
 };

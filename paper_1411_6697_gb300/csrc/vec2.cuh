@@ -10,6 +10,8 @@ struct V2 {
     float2 v;
     __device__ __forceinline__ V2() {}
     __device__ __forceinline__ V2(float2 a) : v(a) {}
+    // lane c of the pair (c a compile-time constant after unrolling)
+    __device__ __forceinline__ float operator[](int c) const { return c ? v.y : v.x; }
     __device__ __forceinline__ V2(float a, float b) : v(make_float2(a, b)) {}
     __device__ __forceinline__ explicit V2(float a) : v(make_float2(a, a)) {}
     __device__ __forceinline__ float x() const { return v.x; }
@@ -40,9 +42,10 @@ __device__ __forceinline__ V2 vmin(V2 a, V2 b) { return V2(fminf(a.v.x, b.v.x), 
 __device__ __forceinline__ V2 vmax(V2 a, V2 b) { return V2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
 __device__ __forceinline__ V2 vabs(V2 a) { return V2(fabsf(a.v.x), fabsf(a.v.y)); }
 
+// minmod(a, b) is the median of a, b and 0: four min/max operations, no arithmetic
 __device__ __forceinline__ float mm1(float a, float b)
 {
-    return fmaxf(fminf(a, b), 0.0f) + fminf(fmaxf(a, b), 0.0f);
+    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
 }
 __device__ __forceinline__ V2 mm2(V2 a, V2 b) { return V2(mm1(a.v.x, b.v.x), mm1(a.v.y, b.v.y)); }
 

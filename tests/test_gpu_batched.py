@@ -111,10 +111,10 @@ def test_barrier_wait_runs_out_and_reports():
 @pytest.mark.slow
 def test_batched_full_workload_5000_steps():
     """All 512 instances (7.8 M cells) for the full 5000 steps in graph-captured chunks:
-    no instance blows up, and the three shortest match their FP64 oracle runs. FP32
-    rounding is amplified by the ignition switch over thousands of steps, so the bound
-    is the larger of 2e-5 and four times the oracle's own drift under a one-ulp FP32
-    perturbation of its initial state."""
+    no instance blows up, and the three shortest match their FP64 oracle runs. Storing
+    the state in FP32 every step costs accuracy that grows with the step count (and the
+    ignition switch amplifies it), so the bound is the larger of 2e-5 and four times the
+    error of the oracle itself when its state is rounded to FP32 after every step."""
     cfg = li.batched(n_instances=512, steps=5000)
     s = make_batched(cfg)
     s.step(cfg["steps"])
@@ -122,17 +122,20 @@ def test_batched_full_workload_5000_steps():
     planes = s.f_planes()
     m = s.macros()
     assert np.all(m["rho"] > 0) and np.all(m["T"] > 0)
-    rng = np.random.default_rng(li.SEED_BASE + 41)
     for i in np.argsort(cfg["nx"])[:3]:
         inst = cfg["instances"][i]
         ob = make_oracle(inst["params"])
         fl = inst["fields"]
-        f0 = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"]).astype(np.float32)
-        f_ref, lam_ref = ob.run(f0.astype(np.float64), fl["lam"], cfg["steps"])
-        ulp = np.spacing(np.abs(f0)) * rng.choice([-1.0, 1.0], f0.shape)
-        f_alt, _ = ob.run((f0 + ulp).astype(np.float64), fl["lam"], cfg["steps"])
-        bound = max(2e-5, 4.0 * rel_l2(f_alt, f_ref))
+        f0 = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"]).astype(np.float32).astype(np.float64)
+        f_ref, lam_ref = ob.run(f0, fl["lam"], cfg["steps"])
+        f_st, lam_st = f0, np.asarray(fl["lam"], np.float64)
+        for _ in range(cfg["steps"]):  # FP32 storage of the state, FP64 arithmetic
+            f_st, lam_st = ob.run(f_st, lam_st, 1)
+            f_st = f_st.astype(np.float32).astype(np.float64)
+            lam_st = lam_st.astype(np.float32).astype(np.float64)
+        bound = max(2e-5, 4.0 * rel_l2(f_st, f_ref))
+        lbound = max(2e-5, 4.0 * rel_l2(lam_st, lam_ref))
         got = split(planes, cfg["nx"])[i]
-        err = rel_l2(got[:16], f_ref)
+        err, lerr = rel_l2(got[:16], f_ref), rel_l2(got[16], lam_ref)
         assert err <= bound, (int(i), err, bound)
-        assert rel_l2(got[16], lam_ref) <= max(2e-5, 4.0 * bound)
+        assert lerr <= lbound, (int(i), lerr, lbound)
