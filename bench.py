@@ -59,7 +59,7 @@ STEP_KERNEL_SOURCES = {
               "model.h"),
     "step": ("kernels.cu", "cell.cuh", "kernels.cuh", "model.h", "reduce.cuh"),
 }
-PROFILE = {"march": "march_kernel_reactive2d.md", "step": "step_kernel_reactive2d.md"}
+PROFILE = {"march": "march_kernel_reactive2d.md", "step": "step_kernel_fp64.md"}
 
 
 def step_kernel_digest(kernel="march"):

@@ -10,6 +10,7 @@ analytic initial-value problem of the kind the paper runs in Sec. IV:
 * ``reactive2d`` -- 2-D periodic reactive field of random Fourier modes.
 * ``batched``    -- many 1-D detonations of uneven length and differing S, Q.
 * ``adjoint``    -- 1-D detonation whose target is a run with perturbed S, Q.
+* ``lax``, ``sjogreen`` -- the other two shock tubes of Sec. IV.B.
 
 Default velocity set: a 16-velocity model of four orbits (axis, diagonal, axis,
 diagonal) with speeds (2.7, 2.2, 1.2, 1.0) and eta (5, 0, 3, 0). The paper's
@@ -72,6 +73,40 @@ def riemann(nx=400, steps=1000, run="A", interface=None):
     return dict(params=_base(nx=nx, S=S, dx=1e-3, dt=1e-5), steps=steps,
                 fields=dict(rho=rho, ux=zero, uy=zero.copy(), T=T, lam=zero.copy()),
                 name="riemann%s_nx%d" % (run, nx))
+
+
+def _shock_tube(nx, steps, dx, dt, gamma, S, left, right, name):
+    """Two constant states (rho, T, u_x) meeting at the middle of the grid."""
+    x = np.arange(nx)
+    L = x < nx // 2
+    rho = np.where(L, left[0], right[0])[None, :]
+    T = np.where(L, left[1], right[1])[None, :]
+    ux = np.where(L, left[2], right[2])[None, :]
+    zero = np.zeros((1, nx))
+    return dict(params=_base(nx=nx, S=np.asarray(S, float), dx=dx, dt=dt, gamma=gamma),
+                steps=steps, fields=dict(rho=rho, ux=ux, uy=zero, T=T, lam=zero.copy()),
+                name=name, left=left, right=right)
+
+
+def lax(nx=2000, steps=15000):
+    """Lax shock tube (Sec. IV.B): (rho, T, u_x) = (0.445, 7.928, 0.698) | (0.5, 1.142, 0)
+    on [-1, 1], dx = 1e-3, dt = 1e-5, t = 0.15, I = 1 (gamma = 5/3), R_5..R_7 = 2e4,
+    R_8 = R_9 = 8e4, other R = 1e5."""
+    S = np.full(16, 1e5)
+    S[4:7] = 2e4
+    S[7:9] = 8e4
+    return _shock_tube(nx, steps, 1e-3, 1e-5, 5.0 / 3.0, S, (0.445, 7.928, 0.698),
+                       (0.5, 1.142, 0.0), "lax_nx%d" % nx)
+
+
+def sjogreen(nx=500, steps=1500):
+    """Sjogreen's problem (Sec. IV.B): (rho, T, u_x) = (1, 0.5, -1.2) | (1, 0.5, 1.2) on
+    [-0.5, 0.5], dx = 2e-3, dt = 2e-5, t = 0.03, I = 4 (gamma = 4/3), R_8 = R_9 = 2e4,
+    other R = 5e4."""
+    S = np.full(16, 5e4)
+    S[7:9] = 2e4
+    return _shock_tube(nx, steps, 2e-3, 2e-5, 4.0 / 3.0, S, (1.0, 0.5, -1.2),
+                       (1.0, 0.5, 1.2), "sjogreen_nx%d" % nx)
 
 
 def detonation(nx=16384, steps=20000, driver=50, Q=1.0, S=None, dx=1e-4, dt=2e-6,

@@ -41,6 +41,8 @@ struct ModelConst {
     R dt, inv_dx, inv_dy, half_inv_dx, half_inv_dy, dx_;
     double cd[4], wd[4];                 // speeds and w in FP64 (conserved-moment recovery)
     double inv_DId, T_igd;
+    // the same four FP64 quantities split as hi + lo FP32 pairs (double-float recovery)
+    float cdh[4], cdl[4], wdh[4], wdl[4], idh, idl, tigh, tigl;
     int32_t nx, ny, pitch, bc_x, bc_y;
     int32_t pad_;
     int64_t plane;                       // elements per plane = ny * pitch

@@ -221,6 +221,16 @@ void fill_model_const(const HostModel& hm, const double S[16], double Q, double 
     K->half_inv_dy = (R)(0.5 / dy);
     K->dx_ = (R)dx;
     K->T_igd = T_ig;
+    auto split = [](double v, float& h, float& l) {
+        h = (float)v;
+        l = (float)(v - (double)h);
+    };
+    for (int k = 0; k < 4; k++) {
+        split(K->cd[k], K->cdh[k], K->cdl[k]);
+        split(K->wd[k], K->wdh[k], K->wdl[k]);
+    }
+    split(K->inv_DId, K->idh, K->idl);
+    split(K->T_igd, K->tigh, K->tigl);
     K->nx = nx;
     K->ny = ny;
     K->pitch = pitch;

@@ -43,12 +43,6 @@ struct DfConst {
     float ch[4], cl[4], wh[4], wl[4], idh, idl, tigh, tigl;
 };
 
-__device__ __forceinline__ void split(double v, float& h, float& l)
-{
-    h = (float)v;
-    l = (float)(v - (double)h);
-}
-
 // Conserved moments m1 = rho, m2 = rho u_x, m3 = rho u_y, m4 = rho[(D+I)T + u^2]
 // (Eqs. (5)-(7)) of a pair of cells as double-float sums: every butterfly is an
 // exact TwoSum, the orbit weights are applied as split constants.
@@ -192,17 +186,22 @@ __device__ __forceinline__ void recover_pair(const V2* f, const DfConst& C,
     }
 }
 
-// Split constants of the conserved-moment recovery, from the FP64 model constants.
+// Split constants of the conserved-moment recovery (split on the host, so they stay
+// constant-bank operands instead of registers).
 __device__ __forceinline__ DfConst df_constants(const ModelConst<float>& K)
 {
     DfConst C;
 #pragma unroll
     for (int o = 0; o < 4; o++) {
-        split(K.cd[o], C.ch[o], C.cl[o]);
-        split(K.wd[o], C.wh[o], C.wl[o]);
+        C.ch[o] = K.cdh[o];
+        C.cl[o] = K.cdl[o];
+        C.wh[o] = K.wdh[o];
+        C.wl[o] = K.wdl[o];
     }
-    split(K.inv_DId, C.idh, C.idl);
-    split(K.T_igd, C.tigh, C.tigl);
+    C.idh = K.idh;
+    C.idl = K.idl;
+    C.tigh = K.tigh;
+    C.tigl = K.tigl;
     return C;
 }
 

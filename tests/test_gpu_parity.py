@@ -119,6 +119,28 @@ def test_riemann_full_config_fp64(run):
     assert rel_l2(s.f_planes()[:16], f) <= 1e-12
 
 
+@pytest.mark.parametrize("which", ["lax", "sjogreen"])
+@pytest.mark.parametrize("prec", [lbkm.F64, lbkm.F32], ids=["f64", "f32"])
+def test_lax_sjogreen_full_runs(which, prec):
+    """Lax (15000 steps, I = 1) and Sjogreen (1500 steps, I = 4) shock tubes of Sec. IV.B
+    run to the paper's end times, every field against the oracle."""
+    c = getattr(li, which)()
+    fl = c["fields"]
+    s = solver(c["params"], prec)
+    s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    s.step(c["steps"])
+    ob = make_oracle(c["params"])
+    f0 = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
+    if prec == lbkm.F32:  # the FP32 run starts from the FP32-rounded state
+        f0 = f0.astype(np.float32).astype(np.float64)
+    f, lam = ob.run(f0, fl["lam"], c["steps"])
+    m, mr = s.macros(), ob.macros(f)
+    tol = TOL[prec]
+    for k in ("rho", "ux", "T", "p"):
+        assert rel_l2(m[k], mr[k]) <= tol, (k, rel_l2(m[k], mr[k]))
+    assert rel_l2(s.f_planes()[:16], f) <= tol
+
+
 @pytest.fixture(scope="module")
 def detonation_ref():
     """Oracle run of the full 1-D detonation (16384 cells), kept at 2000 and 20000 steps,
