@@ -5,12 +5,16 @@
 // and (x0+2t+1, y) together, so most arithmetic runs as packed FP32 pairs
 // (FFMA2 / FADD2 / FMUL2, sm_100+).
 //
-// Shared memory keeps a ring of 7 staged rows (the 17 planes f_1..f_16,
-// lambda of rows y-2..y+2 plus 2 rows prefetched ahead, each 128 + 8 columns
-// wide) filled by 16-byte cp.async copies, and a ring of 4 macro rows (rho, u,
-// T of rows y-1..y+2, with one halo column on each side for grad u). Per
-// iteration: wait for row y+2, one __syncthreads, issue the copy of row y+4,
-// recover rho, u, T of row y+2 from its conserved moments, update row y. The
+// Shared memory keeps the staged rows (128 + 4 columns, filled by 16- and 8-byte
+// cp.async copies) of the 17 planes in rings sized by what each plane still
+// needs: the y-stencil of a plane with v_y > 0 reads rows y-2..y+1, with v_y < 0
+// rows y-1..y+2, with v_y = 0 only row y, lambda rows y-2..y+2; every plane also
+// holds row y+2 (recovered this iteration) and the prefetched row y+3. That is
+// 88 staged plane-rows instead of 17 x 7, which lets four blocks share an SM.
+// A ring of 4 macro rows holds rho, u, T of rows y-1..y+2 (with one halo column
+// on each side for grad u). Per iteration: wait for row y+2, one __syncthreads,
+// issue the copy of row y+3, recover rho, u, T of row y+2 from its conserved
+// moments, update row y. The
 // conserved moments are summed exactly (TwoSum butterflies, split constants);
 // rho, u, T are then formed in FP64 (REC = 0) or in double-float on the FP32
 // pipes (REC = 1), and the ignition test T > T_ig is taken in that precision.
@@ -32,50 +36,135 @@ namespace {
 constexpr int MT = 64;         // threads per block
 constexpr int NWM = MT / 32;   // warps per block
 constexpr int BW = 2 * MT;     // columns per strip
-constexpr int RW = BW + 8;     // staged row: x0-4 .. x0+BW+3 (16-byte aligned chunks)
-constexpr int CHUNKS = RW / 4; // 16-byte chunks per plane row
-constexpr int ROW_CHUNKS = NPLANE * CHUNKS;
-constexpr int PF = 2;          // staged rows in flight beyond y+2
-constexpr int NRING = 5 + PF;  // staged rows kept
+constexpr int RW = BW + 4;     // staged row: x0-2 .. x0+BW+1
+constexpr int PF = 1;          // staged rows in flight beyond y+2
 constexpr int MRING = 4;       // macro rows kept
 constexpr int MW = BW + 4;     // macro row: x0-2 .. x0+BW+1, own cells at even offsets
-constexpr size_t OFF_MAC = (size_t)NRING * NPLANE * RW * 4;
+
+// plane classes by the sign of v_y (orbits 0 and 2 are axis orbits, 1 and 3
+// diagonal): rows kept = rows the y-stencil reads below y+2, plus y+2 and y+3
+enum { C_UP = 0, C_DN = 1, C_FLAT = 2, C_LAM = 3 };
+constexpr int NROWS[4] = {6, 5, 4, 6};   // y-2..y+3, y-1..y+3, y..y+3, y-2..y+3
+constexpr int NPL[4] = {6, 6, 4, 1};     // planes per class
+__host__ __device__ constexpr int pclass(int p)
+{
+    return p == 16 ? C_LAM
+                   : ((p & 3) == 0 || (p & 3) == 2) && ((p >> 2) & 1) == 0
+                         ? C_FLAT
+                         : (((p >> 2) & 1) == 0 ? ((p & 3) == 1 ? C_UP : C_DN)
+                                                 : ((p & 3) < 2 ? C_UP : C_DN));
+}
+// index of plane p within its class, planes in increasing order (o = orbit,
+// k = velocity within the orbit)
+__host__ __device__ constexpr int pindex(int p)
+{
+    const int o = p >> 2, k = p & 3;
+    return p == 16 ? 0
+                   : pclass(p) == C_FLAT ? (o >> 1) * 2 + (k >> 1)
+                                         : (o >> 1) * 3 + ((o & 1) ? (pclass(p) == C_UP ? 1 + k : k - 1) : 0);
+}
+__host__ __device__ constexpr bool class_layout_ok()
+{
+    int seen[4][8] = {};
+    for (int p = 0; p < NPLANE; p++) {
+        const int c = pclass(p), i = pindex(p);
+        if (i < 0 || i >= NPL[c] || seen[c][i]) return false;
+        seen[c][i] = 1;
+    }
+    return true;
+}
+static_assert(class_layout_ok(), "every plane has its own slot in its class");
+
+// ring base (floats) of each class; the whole ring starts 2 floats into shared
+// memory so that every row base is 2 mod 4 floats and column x0 (element 2 of a
+// staged row) sits on a 16-byte boundary
+constexpr int CBASE0 = 2;
+constexpr int CBASE1 = CBASE0 + NROWS[0] * NPL[0] * RW;
+constexpr int CBASE2 = CBASE1 + NROWS[1] * NPL[1] * RW;
+constexpr int CBASE3 = CBASE2 + NROWS[2] * NPL[2] * RW;
+constexpr int RING_FLOATS = CBASE3 + NROWS[3] * NPL[3] * RW;
+static_assert(RW % 4 == 0 && CBASE1 % 4 == 2 && CBASE2 % 4 == 2 && CBASE3 % 4 == 2,
+              "row bases must be 2 mod 4 floats");
+static_assert(pclass(1) == C_UP && pclass(3) == C_DN && pclass(0) == C_FLAT && pclass(2) == C_FLAT &&
+                  pclass(4) == C_UP && pclass(5) == C_UP && pclass(6) == C_DN && pclass(7) == C_DN &&
+                  pclass(8) == C_FLAT && pclass(9) == C_UP && pclass(11) == C_DN &&
+                  pclass(13) == C_UP && pclass(14) == C_DN && pindex(15) == 5 && pindex(10) == 3,
+              "plane classes follow the orbit layout axis, diagonal, axis, diagonal");
+
+constexpr size_t OFF_MAC = ((size_t)RING_FLOATS * 4 + 15) / 16 * 16;
 constexpr size_t OFF_IGN = OFF_MAC + (size_t)4 * MRING * MW * 4;
 constexpr size_t OFF_TSUM = (OFF_IGN + (size_t)MRING * BW + 15) / 16 * 16;
 constexpr size_t OFF_TMM = OFF_TSUM + (size_t)NWM * NSUM * 8;
 constexpr size_t MARCH_SMEM = OFF_TMM + (size_t)NWM * NMM * 4;
+static_assert(MARCH_SMEM <= 56 * 1024, "four blocks per SM need <= 56 KB each");
 
-__device__ __forceinline__ int ring_slot(int r) { return (r + NRING) % NRING; }
 __device__ __forceinline__ int mac_slot(int r) { return (r + MRING) & (MRING - 1); }
 
-// Stage row r (boundary-mapped) of all 17 planes, columns x0-4 .. x0+BW+3: chunks
-// 0..31 of each plane by one warp (lane = chunk), chunks 32..33 by the first 34
-// threads.
-__device__ __forceinline__ void stage_chunk(const float* rowp, float* slot, int p, int ch, int x0,
-                                            const ModelConst<float>& K)
+// start of the staged row r of class c
+template <int CL>
+__device__ __forceinline__ float* class_row(float* ring, int r)
 {
-    const int x = x0 - 4 + 4 * ch;
-    float* dst = slot + p * RW + 4 * ch;
-    const float* src = rowp + p * K.plane;
-    if (x >= 0 && x + 4 <= K.nx) {
-        cp16(dst, src + x);
-    } else {
-#pragma unroll
-        for (int e = 0; e < 4; e++) dst[e] = src[map_index(x + e, K.nx, K.bc_x)];
-    }
+    constexpr int N = NROWS[CL], np = NPL[CL];
+    constexpr int base = CL == 0 ? CBASE0 : CL == 1 ? CBASE1 : CL == 2 ? CBASE2 : CBASE3;
+    return ring + base + ((r + 8 * N) % N) * np * RW;
 }
-__device__ __forceinline__ void issue_row(const float* __restrict__ in, float* ring, int r,
-                                          int x0, const ModelConst<float>& K)
+// the staged row r of plane p (p a compile-time constant after unrolling)
+__device__ __forceinline__ float* plane_row(float* ring, int p, int r)
 {
-    static_assert(CHUNKS == 34 && NWM == 2, "staging layout assumes 34 chunks and 2 warps");
+    const int c = pclass(p);
+    float* b = c == C_UP ? class_row<C_UP>(ring, r)
+                         : c == C_DN ? class_row<C_DN>(ring, r)
+                                     : c == C_FLAT ? class_row<C_FLAT>(ring, r) : class_row<C_LAM>(ring, r);
+    return b + pindex(p) * RW;
+}
+
+__device__ __forceinline__ void cp8(void* dst, const void* src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+
+// Stage row r (boundary-mapped) of the planes whose class is in `mask`, columns
+// x0-2 .. x0+BW+1: the 32 16-byte chunks of columns x0 .. x0+BW-1 of a plane by
+// one warp (lane = chunk), the two 8-byte edges (x0-2, x0-1 and x0+BW, x0+BW+1)
+// of all planes by the first 34 threads. Chunks that leave the grid are gathered
+// element by element through the boundary map.
+__device__ __forceinline__ void issue_row(const float* __restrict__ in, float* ring, int r,
+                                          int x0, const ModelConst<float>& K, unsigned mask)
+{
+    static_assert(BW == 128 && NWM == 2, "staging layout assumes 32 chunks per row and 2 warps");
     const int gy = map_index(r, K.ny, K.bc_y);
     const float* rowp = in + (int64_t)gy * K.pitch;
-    float* slot = ring + (size_t)ring_slot(r) * NPLANE * RW;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int p = w; p < NPLANE; p += NWM) stage_chunk(rowp, slot, p, lane, x0, K);
-    if (threadIdx.x < 2 * NPLANE)
-        stage_chunk(rowp, slot, threadIdx.x >> 1, 32 + (threadIdx.x & 1), x0, K);
+#pragma unroll
+    for (int p = 0; p < NPLANE; p++) {
+        if ((p & 1) != w || !((mask >> pclass(p)) & 1u)) continue;
+        float* dst = plane_row(ring, p, r) + 2 + 4 * lane;
+        const float* src = rowp + p * K.plane;
+        const int x = x0 + 4 * lane;
+        if (x + 4 <= K.nx) {
+            cp16(dst, src + x);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++) dst[e] = src[map_index(x + e, K.nx, K.bc_x)];
+        }
+    }
+    if (threadIdx.x < 2 * NPLANE) {
+        const int p = threadIdx.x >> 1, side = threadIdx.x & 1;
+        if ((mask >> pclass(p)) & 1u) {
+            float* dst = plane_row(ring, p, r) + (side ? BW + 2 : 0);
+            const float* src = rowp + p * K.plane;
+            const int x = side ? x0 + BW : x0 - 2;
+            if (x >= 0 && x + 2 <= K.nx) {
+                cp8(dst, src + x);
+            } else {
+                dst[0] = src[map_index(x, K.nx, K.bc_x)];
+                dst[1] = src[map_index(x + 1, K.nx, K.bc_x)];
+            }
+        }
+    }
 }
+constexpr unsigned ALL_CLASSES = 0xfu;
 
 struct MacRow {
     V2 rho, ux, uy, T;
@@ -90,21 +179,21 @@ __device__ __forceinline__ MacRow row_macros(const float* ring, int r, const Mod
                                              const DfConst& C, int& bad, bool act0, bool act1)
 {
     const int tid = threadIdx.x;
-    const float* slot = ring + (size_t)ring_slot(r) * NPLANE * RW;
-    const int lx = 2 * tid + 4;
+    float* rg = const_cast<float*>(ring);
+    const int lx = 2 * tid + 2;
     V2 f[16];
 #pragma unroll
-    for (int i = 0; i < 16; i++) f[i] = V2(*reinterpret_cast<const float2*>(slot + i * RW + lx));
+    for (int i = 0; i < 16; i++) f[i] = V2(*reinterpret_cast<const float2*>(plane_row(rg, i, r) + lx));
     MacRow o;
     bool ok0, ok1;
     recover_pair<REC>(f, C, K, o.rho, o.ux, o.uy, o.T, o.ig0, o.ig1, ok0, ok1);
     if ((act0 && !ok0) || (act1 && !ok1)) bad = 1;
     o.hu = o.hv = 0.f;
     if (tid == 0 || tid == MT - 1) { // halo columns x0-1 and x0+BW: velocity only
-        const int hx = tid == 0 ? 3 : BW + 4;
+        const int hx = tid == 0 ? 1 : BW + 2;
         float g[16];
 #pragma unroll
-        for (int i = 0; i < 16; i++) g[i] = slot[i * RW + hx];
+        for (int i = 0; i < 16; i++) g[i] = plane_row(rg, i, r)[hx];
         velocity_f32(g, K, o.hu, o.hv);
     }
     return o;
@@ -129,11 +218,11 @@ __device__ __forceinline__ void store_macros(float* mac, unsigned char* ign, int
 }
 
 template <int REC>
-__global__ void __launch_bounds__(MT, 3)
+__global__ void __launch_bounds__(MT, 4)
     march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    float* ring = reinterpret_cast<float*>(smem);
+    float* ring = reinterpret_cast<float*>(smem);  // class rings from float 2 on (see CBASE0)
     float* mac = reinterpret_cast<float*>(smem + OFF_MAC);
     unsigned char* ign = smem + OFF_IGN;
     double* tsum = reinterpret_cast<double*>(smem + OFF_TSUM);
@@ -159,7 +248,7 @@ __global__ void __launch_bounds__(MT, 3)
 
     const int nsx = (nx + BW - 1) / BW, nsy = (ny + strip_rows - 1) / strip_rows;
     const int nstrips = nsx * nsy;
-    const int lx = 2 * tid + 4;  // own cells in a staged row
+    const int lx = 2 * tid + 2;  // own cells in a staged row
     const int mi = 2 * tid + 2;  // own cells in a macro row
     const float dt = K.dt;
 
@@ -176,8 +265,11 @@ __global__ void __launch_bounds__(MT, 3)
         for (int k = 0; k < TNE_K; k++) tsp[k] = V2(0.f);
 
         __syncthreads(); // the previous strip is done with the rings
+        // rows y0-2 .. y0+2: row y0-2 only for the classes whose stencil reaches it
         for (int r = y0 - 2; r <= y0 + 1 + PF; r++) {
-            if (r <= yend + 1) issue_row(in, ring, r, x0, K);
+            if (r <= yend + 1)
+                issue_row(in, ring, r, x0, K,
+                          r == y0 - 2 ? ((1u << C_UP) | (1u << C_LAM)) : ALL_CLASSES);
             cp_commit();
         }
         cp_wait<PF>(); // rows y0-2 .. y0+1 have landed
@@ -188,22 +280,26 @@ __global__ void __launch_bounds__(MT, 3)
         for (int y = y0; y < yend; y++) {
             cp_wait<PF - 1>(); // row y+2 has landed
             __syncthreads();
-            if (y + 2 + PF <= yend + 1) issue_row(in, ring, y + 2 + PF, x0, K);
+            if (y + 2 + PF <= yend + 1) issue_row(in, ring, y + 2 + PF, x0, K, ALL_CLASSES);
             cp_commit();
             // macros of row y+2 (read from the next iteration on)
             store_macros(mac, ign, y + 2, row_macros<REC>(ring, y + 2, K, C, bad, act0, act1));
 
             // ---------------- update of row y ----------------
-            const float* r0 = ring + (size_t)ring_slot(y) * NPLANE * RW;
-            const float* rm1 = ring + (size_t)ring_slot(y - 1) * NPLANE * RW;
-            const float* rm2 = ring + (size_t)ring_slot(y - 2) * NPLANE * RW;
-            const float* rp1 = ring + (size_t)ring_slot(y + 1) * NPLANE * RW;
-            const float* rp2 = ring + (size_t)ring_slot(y + 2) * NPLANE * RW;
+            // row y of every plane; rows y-2..y+1 of the v_y > 0 class, y-1..y+2 of the
+            // v_y < 0 class, y-2..y+2 of lambda
+            const float* up_m2 = class_row<C_UP>(ring, y - 2);
+            const float* up_m1 = class_row<C_UP>(ring, y - 1);
+            const float* up_p1 = class_row<C_UP>(ring, y + 1);
+            const float* dn_m1 = class_row<C_DN>(ring, y - 1);
+            const float* dn_p1 = class_row<C_DN>(ring, y + 1);
+            const float* dn_p2 = class_row<C_DN>(ring, y + 2);
+            const float* lm = class_row<C_LAM>(ring, y);
             const int ms = mac_slot(y), msm = mac_slot(y - 1), msp = mac_slot(y + 1);
             V2 f[16];
 #pragma unroll
-            for (int i = 0; i < 16; i++) f[i] = ldv(r0 + i * RW + lx);
-            const V2 lam0 = ldv(r0 + 16 * RW + lx);
+            for (int i = 0; i < 16; i++) f[i] = ldv(plane_row(ring, i, y) + lx);
+            const V2 lam0 = ldv(lm + lx);
             const V2 rho = ldv(mac + (0 * MRING + ms) * MW + mi);
             const V2 ux = ldv(mac + (1 * MRING + ms) * MW + mi);
             const V2 uy = ldv(mac + (2 * MRING + ms) * MW + mi);
@@ -256,12 +352,14 @@ __global__ void __launch_bounds__(MT, 3)
             inverse_moments(K, Om, W);
 
             // lambda: u . grad(lambda) with NND interface values
-            const Q6 lq = load6(r0 + 16 * RW, lx);
+            const Q6 lq = load6(lm, lx);
+            const float* lm_m2 = class_row<C_LAM>(ring, y - 2);
+            const float* lm_m1 = class_row<C_LAM>(ring, y - 1);
+            const float* lm_p1 = class_row<C_LAM>(ring, y + 1);
+            const float* lm_p2 = class_row<C_LAM>(ring, y + 2);
             const V2 lpx = nnd_pos_x(lq), lnx = nnd_neg_x(lq);
-            const V2 lpy = nnd_pos_y(ldv(rm2 + 16 * RW + lx), ldv(rm1 + 16 * RW + lx), lam0,
-                                     ldv(rp1 + 16 * RW + lx));
-            const V2 lny = nnd_neg_y(ldv(rm1 + 16 * RW + lx), lam0, ldv(rp1 + 16 * RW + lx),
-                                     ldv(rp2 + 16 * RW + lx));
+            const V2 lpy = nnd_pos_y(ldv(lm_m2 + lx), ldv(lm_m1 + lx), lam0, ldv(lm_p1 + lx));
+            const V2 lny = nnd_neg_y(ldv(lm_m1 + lx), lam0, ldv(lm_p1 + lx), ldv(lm_p2 + lx));
             const V2 lax(ux.x() > 0.f ? lpx.x() : lnx.x(), ux.y() > 0.f ? lpx.y() : lnx.y());
             const V2 lay(uy.x() > 0.f ? lpy.x() : lny.x(), uy.y() > 0.f ? lpy.y() : lny.y());
             const V2 ladv = fma(ux * K.inv_dx, lax, uy * K.inv_dy * lay);
@@ -277,10 +375,12 @@ __global__ void __launch_bounds__(MT, 3)
                 else if (act0)
                     out[i * K.plane + g] = v.x();
             };
-#define PX(i) nnd_pos_x(load6(r0 + (i) * RW, lx))
-#define NX(i) nnd_neg_x(load6(r0 + (i) * RW, lx))
-#define PY(i) nnd_pos_y(ldv(rm2 + (i) * RW + lx), ldv(rm1 + (i) * RW + lx), f[i], ldv(rp1 + (i) * RW + lx))
-#define NY(i) nnd_neg_y(ldv(rm1 + (i) * RW + lx), f[i], ldv(rp1 + (i) * RW + lx), ldv(rp2 + (i) * RW + lx))
+#define PX(i) nnd_pos_x(load6(plane_row(ring, (i), y), lx))
+#define NX(i) nnd_neg_x(load6(plane_row(ring, (i), y), lx))
+#define PY(i) nnd_pos_y(ldv(up_m2 + pindex(i) * RW + lx), ldv(up_m1 + pindex(i) * RW + lx), f[i], \
+                        ldv(up_p1 + pindex(i) * RW + lx))
+#define NY(i) nnd_neg_y(ldv(dn_m1 + pindex(i) * RW + lx), f[i], ldv(dn_p1 + pindex(i) * RW + lx), \
+                        ldv(dn_p2 + pindex(i) * RW + lx))
 #pragma unroll
             for (int o = 0; o < 2; o++) { // axis orbits 0, 2
                 const int i0 = 8 * o;

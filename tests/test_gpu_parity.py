@@ -7,6 +7,7 @@ several tiles and a ragged tail (tiles are 32 x 8 cells in 2-D, 64 in 1-D).
 import numpy as np
 import pytest
 
+import exact_riemann as er
 import lbkm_inputs as li
 from gpu_common import TOL, make_oracle, rel_l2, solver, state_bytes
 from paper_1411_6697_gb300 import lbkm
@@ -122,23 +123,54 @@ def test_riemann_full_config_fp64(run):
 @pytest.mark.parametrize("which", ["lax", "sjogreen"])
 @pytest.mark.parametrize("prec", [lbkm.F64, lbkm.F32], ids=["f64", "f32"])
 def test_lax_sjogreen_full_runs(which, prec):
-    """Lax (15000 steps, I = 1) and Sjogreen (1500 steps, I = 4) shock tubes of Sec. IV.B
-    run to the paper's end times, every field against the oracle."""
+    """Lax (15000 steps, I = 1) and Sjogreen (1500 steps, I = 4) shock tubes of Sec. IV.B,
+    every field against the oracle: at an early horizon (before perturbations grow) to
+    the plain tolerance, and at the paper's end time to the larger of that tolerance and
+    a multiple of the oracle's own drift under a perturbation of the size of one
+    rounding of the precision (1e-15 for FP64, 1e-7 for FP32). Both problems amplify
+    such perturbations (Sjogreen's near-vacuum centre most: 1e-7 grows to ~3e-3), so the
+    end-time comparison is only as sharp as the problem allows."""
     c = getattr(li, which)()
     fl = c["fields"]
+    early = {"lax": 1000, "sjogreen": 200}[which]
     s = solver(c["params"], prec)
     s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
-    s.step(c["steps"])
     ob = make_oracle(c["params"])
     f0 = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
     if prec == lbkm.F32:  # the FP32 run starts from the FP32-rounded state
         f0 = f0.astype(np.float32).astype(np.float64)
-    f, lam = ob.run(f0, fl["lam"], c["steps"])
-    m, mr = s.macros(), ob.macros(f)
     tol = TOL[prec]
+    s.step(early)
+    f, lam = ob.run(f0, fl["lam"], early)
+    m, mr = s.macros(), ob.macros(f)
     for k in ("rho", "ux", "T", "p"):
-        assert rel_l2(m[k], mr[k]) <= tol, (k, rel_l2(m[k], mr[k]))
+        assert rel_l2(m[k], mr[k]) <= tol, (early, k, rel_l2(m[k], mr[k]))
     assert rel_l2(s.f_planes()[:16], f) <= tol
+    s.step(c["steps"] - early)
+    f, lam = ob.run(f, lam, c["steps"] - early)
+    eps, mult = (1e-15, 20.0) if prec == lbkm.F64 else (1e-7, 4.0)
+    rng = np.random.default_rng(li.SEED_BASE + 17)
+    fp, _ = ob.run(f0 * (1.0 + eps * rng.standard_normal(f0.shape)), fl["lam"], c["steps"])
+    m, mr, mp = s.macros(), ob.macros(f), ob.macros(fp)
+    # FP32 arithmetic recomputes the equilibrium every step (S dt = 1 here); in the
+    # uniform regions its rounding repeats identically from step to step and so adds up
+    # linearly (Lax: 2.5e-4 in rho after 15000 steps), which no perturbation of the
+    # initial state reproduces. The FP32 end state is therefore held to 1e-3 and to the
+    # oracle's own distance from the exact Euler solution.
+    drift = 1e-3 if prec == lbkm.F32 else 0.0
+    for k in ("rho", "ux", "T", "p"):
+        bound = max(tol, drift, mult * rel_l2(mp[k], mr[k]))
+        assert rel_l2(m[k], mr[k]) <= bound, (k, rel_l2(m[k], mr[k]), bound)
+    bound = max(tol, drift, mult * rel_l2(fp, f))
+    assert rel_l2(s.f_planes()[:16], f) <= bound, (rel_l2(s.f_planes()[:16], f), bound)
+    p = c["params"]
+    x = (np.arange(p["nx"]) + 0.5) * p["dx"] - 0.5 * p["nx"] * p["dx"]
+    (rl, tl, ul), (rr, tr, ur) = c["left"], c["right"]
+    r, u, pe = er.sample((rl, ul, rl * tl), (rr, ur, rr * tr), p["gamma"],
+                         x / (c["steps"] * p["dt"]))
+    for k, ex in (("rho", r), ("ux", u), ("p", pe)):
+        d_gpu, d_orc = np.abs(m[k][0] - ex).mean(), np.abs(mr[k][0] - ex).mean()
+        assert d_gpu <= 1.02 * d_orc, (k, d_gpu, d_orc)
 
 
 @pytest.fixture(scope="module")

@@ -339,7 +339,7 @@ def test_lax_and_sjogreen_against_exact_riemann_solutions(oracle_mod, which):
     r, u, pe = er.sample((rl, ul, rl * tl), (rr, ur, rr * tr), p["gamma"], x / t_end)
     err = (np.abs(m["rho"][0] - r).mean(), np.abs(m["ux"][0] - u).mean(),
            np.abs(m["p"][0] - pe).mean())
-    bound = {"lax": (4.5e-3, 3.5e-3, 4.5e-3), "sjogreen": (4.7e-3, 5.4e-3, 1.95e-3)}[which]
+    bound = {"lax": (3.7e-3, 3.1e-3, 4.0e-3), "sjogreen": (4.7e-3, 5.4e-3, 1.95e-3)}[which]
     assert all(e < b for e, b in zip(err, bound)), err
 
 
