@@ -44,6 +44,19 @@ def _env_rank():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def max_over_ranks(ms, device, world):
+    """The slowest rank's time: barrier, then an all-reduce (MAX) of the per-rank
+    milliseconds; the replicas share no data, so this is the only collective."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -458,11 +471,7 @@ def main():
         with ClockSampler(local) as clk:
             ms = time_steps(solver, stream, args.steps)
         solver.sync()
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.barrier()
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, "cuda", world)
     value = world * n * args.steps / (ms_max * 1e-3) / 1e6
     per_launch_ms = ms / args.steps
     tag = "f32" if prec == lbkm.F32 else "f64"

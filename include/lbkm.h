@@ -85,7 +85,12 @@ typedef enum {
                               the FP32 pipes */
 } lbkm_recovery;
 
-typedef enum { LBKM_BC_PERIODIC = 0, LBKM_BC_ZERO_GRADIENT = 1 } lbkm_bc;
+/* LBKM_BC_WALL (bc_y only, ny >= 2, 2-D grids): walls below row 0 and above row ny-1
+ * by non-equilibrium extrapolation (Sec. IV.D): each ghost cell takes the f of the
+ * adjacent fluid cell plus M^-1 [f_hat^eq(rho, u_w, T_w) - f_hat^eq(rho, u, T)], with
+ * rho, u, T those of the fluid cell and u_w, T_w the wall's (wall_ux/uy/T below);
+ * lambda is copied from the fluid cell. */
+typedef enum { LBKM_BC_PERIODIC = 0, LBKM_BC_ZERO_GRADIENT = 1, LBKM_BC_WALL = 2 } lbkm_bc;
 
 typedef struct {
     int32_t nx, ny;        /* grid; ny = 1 for one-dimensional runs */
@@ -107,6 +112,9 @@ typedef struct {
     int32_t tne_every;     /* 0: no on-the-fly TNE; k > 0: reduce the TNE of the
                               input state of every k-th step into the history */
     int32_t tne_capacity;  /* records kept in the device history ring (>= 1) */
+    double wall_ux[2], wall_uy[2], wall_T[2]; /* bc_y = LBKM_BC_WALL: velocity and
+                              temperature of the wall below row 0 ([0]) and above
+                              row ny-1 ([1]); T_w > 0 */
 } lbkm_params;
 
 /* Grid-wide TNE measures of one state (Sec. VI). Sums are weighted by dx*dy;

@@ -11,6 +11,7 @@ analytic initial-value problem of the kind the paper runs in Sec. IV:
 * ``batched``    -- many 1-D detonations of uneven length and differing S, Q.
 * ``adjoint``    -- 1-D detonation whose target is a run with perturbed S, Q.
 * ``lax``, ``sjogreen`` -- the other two shock tubes of Sec. IV.B.
+* ``couette``    -- Couette flow between walls (Sec. IV.D).
 
 Default velocity set: a 16-velocity model of four orbits (axis, diagonal, axis,
 diagonal) with speeds (2.7, 2.2, 1.2, 1.0) and eta (5, 0, 3, 0). The paper's
@@ -112,6 +113,22 @@ def sjogreen(nx=500, steps=1500):
     S[7:9] = 2e4
     return _shock_tube(nx, steps, 2e-3, 2e-5, 4.0 / 3.0, S, (1.0, 0.5, -1.2),
                        (1.0, 0.5, 1.2), "sjogreen_nx%d" % nx)
+
+
+def couette(ny=200, steps=50000, u0=0.1, nx=1):
+    """Couette flow (Sec. IV.D): walls at y = 0 (at rest) and y = H = ny dy (moving at
+    u0), non-equilibrium extrapolation at both, periodic x; rho = 1, T = 1, u = 0 at
+    t = 0; dy = 1e-3, dt = 1e-5, I = 2 (gamma = 1.5), R_5..R_7 = 2e3, R_8 = R_9 = 1e4,
+    other R = 5e4. 50000 steps reach t = 0.5 (nu t / H^2 = 0.00625)."""
+    S = np.full(16, 5e4)
+    S[4:7] = 2e3
+    S[7:9] = 1e4
+    p = _base(nx=nx, ny=ny, S=S, dx=1e-3, dt=1e-5, gamma=1.5, bc_x=0, bc_y=2)
+    p["walls"] = ((0.0, 0.0, 1.0), (u0, 0.0, 1.0))
+    one, zero = np.ones((ny, nx)), np.zeros((ny, nx))
+    return dict(params=p, steps=steps, u0=u0,
+                fields=dict(rho=one, ux=zero, uy=zero.copy(), T=one.copy(), lam=zero.copy()),
+                name="couette_ny%d" % ny)
 
 
 def detonation(nx=16384, steps=20000, driver=50, Q=1.0, S=None, dx=1e-4, dt=2e-6,

@@ -10,7 +10,11 @@
  * and must never sit on the product path.
  *
  * What one step computes, in the paper's order (Sec. II):
- *   1. ghost cells (2 per side) from the boundary condition;
+ *   1. ghost cells (2 per side) from the boundary condition: periodic, zero
+ *      gradient, or a wall in y by non-equilibrium extrapolation (Sec. IV.D:
+ *      ghost f = f of the adjacent fluid cell + M^-1 [f_hat^eq(rho, u_w, T_w) -
+ *      f_hat^eq(rho, u, T)], rho, u, T those of the fluid cell, u_w and T_w the
+ *      wall's; lambda copied);
  *   2. moments f_hat = M f and macros rho, u, T, p for every cell and ghost
  *      (Eqs. (5)-(7), the rows m_1..m_16 listed after Eq. (16));
  *   3. grad u by second-order central differences (needed by Eqs. (3)-(4));
@@ -46,12 +50,13 @@
 
 typedef struct {
     int32_t nx, ny;
-    int32_t bc_x, bc_y; /* 0 = periodic, 1 = zero gradient (copy edge cell) */
+    int32_t bc_x, bc_y; /* 0 = periodic, 1 = zero gradient (copy edge cell), 2 = wall (y) */
     double vx[NV], vy[NV], eta[NV];
     double I;     /* extra (internal) degrees of freedom */
     double S[NV]; /* relaxation rates R_1..R_16 */
     double Q, omega1, omega2, T_ig;
     double dx, dy, dt;
+    double wall_ux[2], wall_uy[2], wall_T[2]; /* bc_y = 2: [0] wall below y = 0, [1] above */
 } orc_params;
 
 /* number of doubles in one TNE global record */
@@ -375,6 +380,32 @@ int orc_step(const orc_params* p, const double* M, const double* Minv, const dou
             for (int i = 0; i < NV; i++) fg[(size_t)i * ng + dst] = f[(size_t)i * n + src];
             lg[dst] = lam[src];
         }
+
+    /* walls in y: non-equilibrium extrapolation into both ghost rows of each side */
+    if (p->bc_y == 2) {
+        for (int side = 0; side < 2; side++) {
+            const int jsrc = side == 0 ? GH : GH + ny - 1;
+            for (int jx = 0; jx < gx; jx++) {
+                const size_t src = (size_t)jsrc * gx + jx;
+                double fh[NV], r, ux, uy, T, fw[NV], fs[NV], d[NV];
+                orc_moments_cell(M, fg, ng, src, fh);
+                macros_of(fh, I, &r, &ux, &uy, &T);
+                orc_feq_moments(r, p->wall_ux[side], p->wall_uy[side], p->wall_T[side], I, fw);
+                orc_feq_moments(r, ux, uy, T, I, fs);
+                for (int i = 0; i < NV; i++) {
+                    double s = 0.0;
+                    for (int k = 0; k < NV; k++) s += Minv[i * NV + k] * (fw[k] - fs[k]);
+                    d[i] = s;
+                }
+                for (int g = 0; g < GH; g++) {
+                    const int jg = side == 0 ? g : GH + ny + g;
+                    const size_t dst = (size_t)jg * gx + jx;
+                    for (int i = 0; i < NV; i++)
+                        fg[(size_t)i * ng + dst] = fg[(size_t)i * ng + src] + d[i];
+                }
+            }
+        }
+    }
 
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < (long)ng; c++) {

@@ -53,6 +53,8 @@ class Params(ctypes.Structure):
         ("Q", ctypes.c_double), ("omega1", ctypes.c_double), ("omega2", ctypes.c_double),
         ("T_ig", ctypes.c_double),
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dt", ctypes.c_double),
+        ("wall_ux", ctypes.c_double * 2), ("wall_uy", ctypes.c_double * 2),
+        ("wall_T", ctypes.c_double * 2),
     ]
 
 
@@ -112,7 +114,7 @@ class Oracle:
 
     def __init__(self, nx, ny, *, gamma, orbit_kind, orbit_speed, orbit_eta, S, Q=0.0,
                  omega1=0.0, omega2=0.0, T_ig=1.1, dx=1e-3, dy=None, dt=1e-5,
-                 bc_x=1, bc_y=0):
+                 bc_x=1, bc_y=0, walls=None):
         lib = _load()
         p = Params()
         p.nx, p.ny, p.bc_x, p.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
@@ -123,6 +125,9 @@ class Oracle:
         p.S[:] = list(S)
         p.Q, p.omega1, p.omega2, p.T_ig = float(Q), float(omega1), float(omega2), float(T_ig)
         p.dx, p.dy, p.dt = float(dx), float(dx if dy is None else dy), float(dt)
+        if walls is not None:  # ((ux, uy, T) below y = 0, (ux, uy, T) above y = ny)
+            for side in (0, 1):
+                p.wall_ux[side], p.wall_uy[side], p.wall_T[side] = map(float, walls[side])
         self.p = p
         self.nx, self.ny = int(nx), int(ny)
         self.n = self.nx * self.ny

@@ -218,8 +218,16 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
     }
     if (!(p.dx > 0 && p.dy > 0 && p.dt > 0))
         return fail(nullptr, LBKM_EINVAL, "dx, dy, dt must be > 0");
-    if (p.bc_x < 0 || p.bc_x > 1 || p.bc_y < 0 || p.bc_y > 1)
-        return fail(nullptr, LBKM_EINVAL, "bc_x, bc_y must be LBKM_BC_PERIODIC or _ZERO_GRADIENT");
+    if (p.bc_x < 0 || p.bc_x > 1 || p.bc_y < 0 || p.bc_y > 2)
+        return fail(nullptr, LBKM_EINVAL,
+                    "bc_x must be LBKM_BC_PERIODIC or _ZERO_GRADIENT, bc_y one of those or _WALL");
+    if (p.bc_y == LBKM_BC_WALL) {
+        if (p.ny < 2) return fail(nullptr, LBKM_EINVAL, "LBKM_BC_WALL needs ny >= 2");
+        for (int s = 0; s < 2; s++)
+            if (!(p.wall_T[s] > 0.0 && p.wall_T[s] < 1e300) || !(fabs(p.wall_ux[s]) < 1e300) ||
+                !(fabs(p.wall_uy[s]) < 1e300))
+                return fail(nullptr, LBKM_EINVAL, "wall velocities must be finite, wall_T > 0");
+    }
     if (p.Pr > 0) p.S[7] = p.S[8] = p.Pr * p.S[4];
     double smax = 0;
     for (int k = 4; k < 16; k++) {
@@ -263,6 +271,14 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
                              p.ny, h->pitch, p.bc_x, p.bc_y, &h->Kd);
     fill_model_const<float>(h->hm, p.S, p.Q, p.omega1, p.omega2, p.T_ig, p.dx, p.dy, p.dt, p.nx,
                             p.ny, h->pitch, p.bc_x, p.bc_y, &h->Kf);
+    for (int side = 0; side < 2; side++) {
+        h->Kd.wux[side] = p.wall_ux[side];
+        h->Kd.wuy[side] = p.wall_uy[side];
+        h->Kd.wT[side] = p.wall_T[side];
+        h->Kf.wux[side] = (float)p.wall_ux[side];
+        h->Kf.wuy[side] = (float)p.wall_uy[side];
+        h->Kf.wT[side] = (float)p.wall_T[side];
+    }
     h->stream = (cudaStream_t)cuda_stream;
 
     auto bail = [&](cudaError_t e, const char* what) {
@@ -582,6 +598,7 @@ lbkm_status lbkm_create_batched(const lbkm_params* pin, int32_t n_instances,
     q.nx = (int32_t)total;
     q.ny = 1;
     q.bc_x = LBKM_BC_ZERO_GRADIENT;
+    q.bc_y = LBKM_BC_PERIODIC;
     std::vector<InstParam> ip(n_instances);
     const double DI = 2.0 + (2.0 / (pin->gamma - 1.0) - 2.0);
     int64_t off = 0;

@@ -318,6 +318,29 @@ __device__ __forceinline__ R reaction_increment(R lam, R a, R b, R dt)
     return mu0 - mu;
 }
 
+__device__ __forceinline__ float lane_recip(float x) { return 1.0f / x; }
+__device__ __forceinline__ double lane_recip(double x) { return 1.0 / x; }
+
+// Non-equilibrium extrapolation at a wall (Sec. IV.D): the ghost cell next to a wall
+// is the adjacent fluid cell f plus d = M^-1 [f_hat^eq(rho, u_w, T_w) - f_hat^eq(rho,
+// u, T)], with rho, u, T those of f (plain sums in the lane type) and u_w, T_w the
+// wall's (side 0 below row 0, side 1 above row ny-1).
+template <typename R, typename L>
+__device__ __forceinline__ void wall_correction(const ModelConst<R>& K, const L* f, int side, L* d)
+{
+    L m[16], qw[16], qs[16], dm[16];
+    forward_moments(K, f, m);
+    const L rho = m[0];
+    const L ir = lane_recip(rho);
+    const L ux = m[1] * ir, uy = m[2] * ir;
+    const L T = (m[3] * ir - ux * ux - uy * uy) * K.inv_DI;
+    feq_moments(L(K.DI), rho, L(K.wux[side]), L(K.wuy[side]), L(K.wT[side]), qw);
+    feq_moments(L(K.DI), rho, ux, uy, T, qs);
+#pragma unroll
+    for (int k = 0; k < 16; k++) dm[k] = qw[k] - qs[k];
+    inverse_moments(K, dm, d);
+}
+
 __device__ __forceinline__ int map_index(int j, int n, int bc)
 {
     if (bc == 0) {

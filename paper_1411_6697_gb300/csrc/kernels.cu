@@ -87,6 +87,28 @@ __global__ void __launch_bounds__(TX * TY)
             sf[idx] = in[p * plane + (int64_t)gy * pitch + gx];
         }
         __syncthreads();
+        if constexpr (TWO_D) {
+            // walls: the staged ghost rows hold copies of the edge fluid row (the
+            // index map clamps); add the non-equilibrium-extrapolation correction
+            if (K.bc_y == 2 && (y0 - C::H < 0 || y0 + TY + C::H > ny)) {
+                for (int idx = tid; idx < 2 * C::SW; idx += C::NT) {
+                    const int side = idx / C::SW, c = idx - side * C::SW;
+                    const int rs = (side == 0 ? 0 : ny - 1) - (y0 - C::H); // fluid row
+                    if (rs < 0 || rs >= C::SH) continue;
+                    R fl[16], d[16];
+#pragma unroll
+                    for (int i = 0; i < 16; i++) fl[i] = sf[i * C::PS + rs * C::SW + c];
+                    wall_correction(K, fl, side, d);
+                    for (int r = 0; r < C::SH; r++) {
+                        const int gy = y0 - C::H + r;
+                        if (side == 0 ? gy >= 0 : gy < ny) continue;
+#pragma unroll
+                        for (int i = 0; i < 16; i++) sf[i * C::PS + r * C::SW + c] += d[i];
+                    }
+                }
+                __syncthreads();
+            }
+        }
         // 2. macros of the tile and its ring
         for (int idx = tid; idx < C::RS; idx += C::NT) {
             const int r = idx / C::RW, c = idx - r * C::RW;

@@ -166,6 +166,27 @@ __device__ __forceinline__ void issue_row(const float* __restrict__ in, float* r
 }
 constexpr unsigned ALL_CLASSES = 0xfu;
 
+// Walls (Sec. IV.D): the staged ghost row r_ghost holds a copy of the fluid row r_src
+// (the index map clamps); add the non-equilibrium-extrapolation correction to the
+// thread's own two columns of the f planes that keep that row (only the v_y > 0
+// class keeps row y0-2). Ghost rows are read only at the own columns of the thread
+// that corrects them (y-stencils and macros), so no barrier follows.
+__device__ __forceinline__ void wall_fix_row(float* ring, int r_ghost, int r_src, int side,
+                                             const ModelConst<float>& K, bool up_only)
+{
+    const int lx = 2 * threadIdx.x + 2;
+    V2 f[16], d[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) f[i] = ldv(plane_row(ring, i, r_src) + lx);
+    wall_correction(K, f, side, d);
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        if (up_only && pclass(i) != C_UP) continue;
+        float* q = plane_row(ring, i, r_ghost) + lx;
+        *reinterpret_cast<float2*>(q) = (ldv(q) + d[i]).v;
+    }
+}
+
 struct MacRow {
     V2 rho, ux, uy, T;
     bool ig0, ig1;
@@ -274,6 +295,10 @@ __global__ void __launch_bounds__(MT, 4)
         }
         cp_wait<PF>(); // rows y0-2 .. y0+1 have landed
         __syncthreads();
+        if (K.bc_y == 2 && y0 == 0) {
+            wall_fix_row(ring, -1, 0, 0, K, false);
+            wall_fix_row(ring, -2, 0, 0, K, true);
+        }
         for (int r = y0 - 1; r <= y0 + 1; r++)
             store_macros(mac, ign, r, row_macros<REC>(ring, r, K, C, bad, act0, act1));
 
@@ -282,6 +307,7 @@ __global__ void __launch_bounds__(MT, 4)
             __syncthreads();
             if (y + 2 + PF <= yend + 1) issue_row(in, ring, y + 2 + PF, x0, K, ALL_CLASSES);
             cp_commit();
+            if (K.bc_y == 2 && y + 2 >= ny) wall_fix_row(ring, y + 2, ny - 1, 1, K, false);
             // macros of row y+2 (read from the next iteration on)
             store_macros(mac, ign, y + 2, row_macros<REC>(ring, y + 2, K, C, bad, act0, act1));
 

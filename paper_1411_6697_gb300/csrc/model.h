@@ -43,7 +43,8 @@ struct ModelConst {
     double inv_DId, T_igd;
     // the same four FP64 quantities split as hi + lo FP32 pairs (double-float recovery)
     float cdh[4], cdl[4], wdh[4], wdl[4], idh, idl, tigh, tigl;
-    int32_t nx, ny, pitch, bc_x, bc_y;
+    R wux[2], wuy[2], wT[2];             // walls below row 0 [0] and above row ny-1 [1]
+    int32_t nx, ny, pitch, bc_x, bc_y;   // bc_y = 2: walls (non-equilibrium extrapolation)
     int32_t pad_;
     int64_t plane;                       // elements per plane = ny * pitch
 };

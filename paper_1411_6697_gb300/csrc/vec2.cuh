@@ -40,6 +40,7 @@ __device__ __forceinline__ V2 fma(float a, V2 b, V2 c)
 }
 __device__ __forceinline__ V2 vmin(V2 a, V2 b) { return V2(fminf(a.v.x, b.v.x), fminf(a.v.y, b.v.y)); }
 __device__ __forceinline__ V2 vmax(V2 a, V2 b) { return V2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
+__device__ __forceinline__ V2 lane_recip(V2 a) { return V2(1.0f / a.v.x, 1.0f / a.v.y); }
 __device__ __forceinline__ V2 vabs(V2 a) { return V2(fabsf(a.v.x), fabsf(a.v.y)); }
 
 // minmod(a, b) is the median of a, b and 0: four min/max operations, no arithmetic

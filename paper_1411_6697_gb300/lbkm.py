@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpaper_lbkm.so")
 
 F64, F32 = 0, 1
 RECOVER_F64, RECOVER_DF32 = 0, 1
-BC_PERIODIC, BC_ZERO_GRADIENT = 0, 1
+BC_PERIODIC, BC_ZERO_GRADIENT, BC_WALL = 0, 1, 2
 
 STATUS = {0: "LBKM_OK", 1: "LBKM_EINVAL", 2: "LBKM_ENOMEM", 3: "LBKM_ECUDA",
           4: "LBKM_ESINGULAR", 5: "LBKM_EUNSTABLE", 6: "LBKM_ETIMEOUT", 7: "LBKM_ESTATE"}
@@ -49,6 +49,8 @@ class Params(ctypes.Structure):
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dt", ctypes.c_double),
         ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
         ("tne_every", ctypes.c_int32), ("tne_capacity", ctypes.c_int32),
+        ("wall_ux", ctypes.c_double * 2), ("wall_uy", ctypes.c_double * 2),
+        ("wall_T", ctypes.c_double * 2),
     ]
 
 
@@ -148,6 +150,9 @@ def default_params(**kw) -> Params:
                 arr[i] = vals[i].item()
         elif k == "bc":
             p.bc_x, p.bc_y = v
+        elif k == "walls":  # ((ux, uy, T) below row 0, (ux, uy, T) above row ny-1)
+            for side in (0, 1):
+                p.wall_ux[side], p.wall_uy[side], p.wall_T[side] = map(float, v[side])
         else:
             setattr(p, k, v)
     return p

@@ -28,7 +28,11 @@ def create(**kw):
     (dict(dx=1e-5), 1),                        # CFL 2.7 > 1
     (dict(orbit_kind=(0, 0, 1, 1)), 1),        # order must be axis, diag, axis, diag
     (dict(orbit_speed=(2.7, -1.0, 1.2, 1.0)), 1),
-    (dict(bc=(2, 0)), 1),
+    (dict(bc=(2, 0)), 1),                      # walls only in y
+    (dict(bc=(0, 3)), 1),
+    (dict(bc=(0, 2), walls=((0, 0, 1), (0.1, 0, 1))), 1),            # walls need ny >= 2
+    (dict(ny=8, bc=(0, 2), walls=((0, 0, 1), (0.1, 0, 0.0))), 1),    # wall T must be > 0
+    (dict(ny=8, bc=(0, 2), walls=((float("nan"), 0, 1), (0, 0, 1))), 1),
     (dict(tne_every=-1), 1),
     (dict(tne_capacity=0), 1),
     (dict(omega1=-1.0), 1),
