@@ -12,6 +12,7 @@ analytic initial-value problem of the kind the paper runs in Sec. IV:
 * ``adjoint``    -- 1-D detonation whose target is a run with perturbed S, Q.
 * ``lax``, ``sjogreen`` -- the other two shock tubes of Sec. IV.B.
 * ``couette``    -- Couette flow between walls (Sec. IV.D).
+* ``shock_reflection`` -- regular reflection of an oblique shock on a wall (Sec. IV.C).
 
 Default velocity set: a 16-velocity model of four orbits (axis, diagonal, axis,
 diagonal) with speeds (2.7, 2.2, 1.2, 1.0) and eta (5, 0, 3, 0). The paper's
@@ -129,6 +130,27 @@ def couette(ny=200, steps=50000, u0=0.1, nx=1):
     return dict(params=p, steps=steps, u0=u0,
                 fields=dict(rho=one, ux=zero, uy=zero.copy(), T=one.copy(), lam=zero.copy()),
                 name="couette_ny%d" % ny)
+
+
+def shock_reflection(nx=300, ny=100, steps=100000, speed_scale=1.0):
+    """Regular shock reflection (Sec. IV.C): a 0.3 x 0.1 box of 300 x 100 cells, dx = dy
+    = 1e-3, dt = 5e-6 (100000 steps reach t = 0.5), I = 2 (gamma = 1.5); R_5..R_7 =
+    1.8e5, R_8 = R_9 = 2e5, other R = 1e5. Dirichlet inflow (rho, T, u_x, u_y) =
+    (1, 0.5, 2, 0) at x = 0 and the post-shock state (1.25, 0.56, 1.9, -0.173205) on the
+    top, supersonic outflow (zero gradient) at x = 0.3, a specular wall at y = 0. The
+    box starts filled with the inflow state."""
+    S = np.full(16, 1e5)
+    S[4:7] = 1.8e5
+    S[7:9] = 2e5
+    p = _base(nx=nx, ny=ny, S=S, dx=1e-3, dt=5e-6, gamma=1.5, bc_x=5, bc_y=5)
+    p["orbit_speed"] = [speed_scale * v for v in p["orbit_speed"]]
+    # (code, rho, ux, uy, T, lambda) of the sides x = 0, x = nx, y = 0, y = ny
+    p["sides"] = ((3, 1.0, 2.0, 0.0, 0.5, 0.0), (1, 1.0, 0.0, 0.0, 1.0, 0.0),
+                  (4, 1.0, 0.0, 0.0, 1.0, 0.0), (3, 1.25, 1.9, -0.173205, 0.56, 0.0))
+    one, zero = np.ones((ny, nx)), np.zeros((ny, nx))
+    return dict(params=p, steps=steps,
+                fields=dict(rho=one, ux=2.0 * one, uy=zero, T=0.5 * one, lam=zero.copy()),
+                name="shock_reflection_%dx%d" % (nx, ny))
 
 
 def detonation(nx=16384, steps=20000, driver=50, Q=1.0, S=None, dx=1e-4, dt=2e-6,

@@ -11,7 +11,9 @@
  *
  * What one step computes, in the paper's order (Sec. II):
  *   1. ghost cells (2 per side) from the boundary condition: periodic, zero
- *      gradient, or a wall in y by non-equilibrium extrapolation (Sec. IV.D:
+ *      gradient, Dirichlet (the equilibrium of a given state, Sec. IV.C), specular
+ *      reflection (Sec. IV.C, the mirror cell with v_y reversed), or a wall in y
+ *      by non-equilibrium extrapolation (Sec. IV.D:
  *      ghost f = f of the adjacent fluid cell + M^-1 [f_hat^eq(rho, u_w, T_w) -
  *      f_hat^eq(rho, u, T)], rho, u, T those of the fluid cell, u_w and T_w the
  *      wall's; lambda copied);
@@ -57,6 +59,13 @@ typedef struct {
     double Q, omega1, omega2, T_ig;
     double dx, dy, dt;
     double wall_ux[2], wall_uy[2], wall_T[2]; /* bc_y = 2: [0] wall below y = 0, [1] above */
+    /* bc_x or bc_y = 5: each side of that direction has its own condition, side_bc[s]
+     * for the sides x = 0, x = nx, y = 0, y = ny: 1 zero gradient, 2 wall by
+     * non-equilibrium extrapolation (y sides, wall_* [s - 2]), 3 Dirichlet (the
+     * equilibrium of side_rho/ux/uy/T, lambda side_lam), 4 specular reflection (y sides:
+     * the mirror cell with v_y reversed) */
+    int32_t side_bc[4];
+    double side_rho[4], side_ux[4], side_uy[4], side_T[4], side_lam[4];
 } orc_params;
 
 /* number of doubles in one TNE global record */
@@ -372,18 +381,54 @@ int orc_step(const orc_params* p, const double* M, const double* Minv, const dou
         free(fg); free(lg); free(fhg); free(rg); free(uxg); free(uyg); free(Tg);
         return -1;
     }
+    /* Dirichlet ghost values of each side: f = M^-1 f_hat^eq(side state) */
+    double fd[4][NV];
+    for (int s = 0; s < 4; s++) {
+        double fe[NV];
+        orc_feq_moments(p->side_rho[s], p->side_ux[s], p->side_uy[s], p->side_T[s], I, fe);
+        for (int i = 0; i < NV; i++) {
+            double acc = 0.0;
+            for (int k = 0; k < NV; k++) acc += Minv[i * NV + k] * fe[k];
+            fd[s][i] = acc;
+        }
+    }
+    /* the velocity with v_y reversed, for specular reflection */
+    int mirror[NV];
+    for (int i = 0; i < NV; i++) {
+        mirror[i] = i;
+        for (int j = 0; j < NV; j++)
+            if (p->vx[j] == p->vx[i] && p->vy[j] == -p->vy[i] && p->eta[j] == p->eta[i]) mirror[i] = j;
+    }
     for (int jy = 0; jy < gy; jy++)
         for (int jx = 0; jx < gx; jx++) {
-            int sx = map_index(jx - GH, nx, p->bc_x);
-            int sy = map_index(jy - GH, ny, p->bc_y);
-            size_t src = (size_t)sy * nx + sx, dst = (size_t)jy * gx + jx;
-            for (int i = 0; i < NV; i++) fg[(size_t)i * ng + dst] = f[(size_t)i * n + src];
+            const int x = jx - GH, y = jy - GH;
+            const size_t dst = (size_t)jy * gx + jx;
+            const int ys = y < 0 ? 2 : 3, xs = x < 0 ? 0 : 1;
+            const int cy = (y >= 0 && y < ny) ? -1 : (p->bc_y == 5 ? p->side_bc[ys] : p->bc_y);
+            const int cx = (x >= 0 && x < nx) ? -1 : (p->bc_x == 5 ? p->side_bc[xs] : p->bc_x);
+            if (cy == 3 || cx == 3) { /* Dirichlet (a y side first; corners are never read) */
+                const int s = cy == 3 ? ys : xs;
+                for (int i = 0; i < NV; i++) fg[(size_t)i * ng + dst] = fd[s][i];
+                lg[dst] = p->side_lam[s];
+                continue;
+            }
+            int sx = cx == -1 ? x : map_index(x, nx, cx == 0 ? 0 : 1);
+            int sy = cy == -1 ? y : map_index(y, ny, cy == 0 ? 0 : 1);
+            int mir = 0;
+            if (cy == 4) { /* specular: the mirror row across the wall face */
+                sy = y < 0 ? -y - 1 : 2 * ny - 1 - y;
+                mir = 1;
+            }
+            const size_t src = (size_t)sy * nx + sx;
+            for (int i = 0; i < NV; i++)
+                fg[(size_t)i * ng + dst] = f[(size_t)(mir ? mirror[i] : i) * n + src];
             lg[dst] = lam[src];
         }
 
     /* walls in y: non-equilibrium extrapolation into both ghost rows of each side */
-    if (p->bc_y == 2) {
+    if (p->bc_y == 2 || p->bc_y == 5) {
         for (int side = 0; side < 2; side++) {
+            if (p->bc_y == 5 && p->side_bc[2 + side] != 2) continue;
             const int jsrc = side == 0 ? GH : GH + ny - 1;
             for (int jx = 0; jx < gx; jx++) {
                 const size_t src = (size_t)jsrc * gx + jx;

@@ -55,6 +55,9 @@ class Params(ctypes.Structure):
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dt", ctypes.c_double),
         ("wall_ux", ctypes.c_double * 2), ("wall_uy", ctypes.c_double * 2),
         ("wall_T", ctypes.c_double * 2),
+        ("side_bc", ctypes.c_int32 * 4), ("side_rho", ctypes.c_double * 4),
+        ("side_ux", ctypes.c_double * 4), ("side_uy", ctypes.c_double * 4),
+        ("side_T", ctypes.c_double * 4), ("side_lam", ctypes.c_double * 4),
     ]
 
 
@@ -114,7 +117,7 @@ class Oracle:
 
     def __init__(self, nx, ny, *, gamma, orbit_kind, orbit_speed, orbit_eta, S, Q=0.0,
                  omega1=0.0, omega2=0.0, T_ig=1.1, dx=1e-3, dy=None, dt=1e-5,
-                 bc_x=1, bc_y=0, walls=None):
+                 bc_x=1, bc_y=0, walls=None, sides=None):
         lib = _load()
         p = Params()
         p.nx, p.ny, p.bc_x, p.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
@@ -128,6 +131,11 @@ class Oracle:
         if walls is not None:  # ((ux, uy, T) below y = 0, (ux, uy, T) above y = ny)
             for side in (0, 1):
                 p.wall_ux[side], p.wall_uy[side], p.wall_T[side] = map(float, walls[side])
+        if sides is not None:  # 4 x (code, rho, ux, uy, T, lam): x = 0, x = nx, y = 0, y = ny
+            for k, (code, r, u, v, T, lam) in enumerate(sides):
+                p.side_bc[k] = int(code)
+                p.side_rho[k], p.side_ux[k], p.side_uy[k], p.side_T[k], p.side_lam[k] = (
+                    float(r), float(u), float(v), float(T), float(lam))
         self.p = p
         self.nx, self.ny = int(nx), int(ny)
         self.n = self.nx * self.ny

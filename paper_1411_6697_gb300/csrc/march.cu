@@ -295,9 +295,10 @@ __global__ void __launch_bounds__(MT, 4)
         }
         cp_wait<PF>(); // rows y0-2 .. y0+1 have landed
         __syncthreads();
-        if (K.bc_y == 2 && y0 == 0) {
-            wall_fix_row(ring, -1, 0, 0, K, false);
-            wall_fix_row(ring, -2, 0, 0, K, true);
+        if (K.bc_y == 2) { // ghost rows among those landed; row y0+2 is fixed in the loop
+            if (y0 - 1 < 0) wall_fix_row(ring, y0 - 1, 0, 0, K, false);
+            if (y0 - 2 < 0) wall_fix_row(ring, y0 - 2, 0, 0, K, true); // kept by v_y > 0 only
+            if (y0 + 1 >= ny) wall_fix_row(ring, y0 + 1, ny - 1, 1, K, false);
         }
         for (int r = y0 - 1; r <= y0 + 1; r++)
             store_macros(mac, ign, r, row_macros<REC>(ring, r, K, C, bad, act0, act1));
