@@ -90,7 +90,20 @@ typedef enum {
  * adjacent fluid cell plus M^-1 [f_hat^eq(rho, u_w, T_w) - f_hat^eq(rho, u, T)], with
  * rho, u, T those of the fluid cell and u_w, T_w the wall's (wall_ux/uy/T below);
  * lambda is copied from the fluid cell. */
-typedef enum { LBKM_BC_PERIODIC = 0, LBKM_BC_ZERO_GRADIENT = 1, LBKM_BC_WALL = 2 } lbkm_bc;
+/* LBKM_BC_SIDES (bc_x or bc_y): the two sides of that direction take their own
+ * conditions from side_bc[] (x = 0, x = nx, y = 0, y = ny): LBKM_BC_ZERO_GRADIENT,
+ * LBKM_BC_WALL (y sides), LBKM_BC_DIRICHLET (ghost cells hold the equilibrium of
+ * side_rho/ux/uy/T and lambda side_lam: the fixed inflow states of Sec. IV.C) or
+ * LBKM_BC_SPECULAR (y sides: the ghost cell mirrors the fluid cell across the face with
+ * v_y reversed, the reflecting surface of Sec. IV.C). */
+typedef enum {
+    LBKM_BC_PERIODIC = 0,
+    LBKM_BC_ZERO_GRADIENT = 1,
+    LBKM_BC_WALL = 2,
+    LBKM_BC_DIRICHLET = 3,
+    LBKM_BC_SPECULAR = 4,
+    LBKM_BC_SIDES = 5
+} lbkm_bc;
 
 typedef struct {
     int32_t nx, ny;        /* grid; ny = 1 for one-dimensional runs */
@@ -115,6 +128,10 @@ typedef struct {
     double wall_ux[2], wall_uy[2], wall_T[2]; /* bc_y = LBKM_BC_WALL: velocity and
                               temperature of the wall below row 0 ([0]) and above
                               row ny-1 ([1]); T_w > 0 */
+    int32_t side_bc[4];    /* with LBKM_BC_SIDES: conditions of the sides x = 0, x = nx,
+                              y = 0, y = ny (see lbkm_bc) */
+    double side_rho[4], side_ux[4], side_uy[4], side_T[4], side_lam[4]; /* Dirichlet
+                              states of those sides; rho > 0, T > 0 */
 } lbkm_params;
 
 /* Grid-wide TNE measures of one state (Sec. VI). Sums are weighted by dx*dy;

@@ -197,6 +197,29 @@ void lbkm_default_params(lbkm_params* p)
     p->tne_capacity = 1;
 }
 
+// f_hat^eq_1..16 of (rho, u, T) (list after Eq. (16), entries 14 and 16 per Eq. (11)),
+// for the fixed ghost values of Dirichlet sides
+static void host_feq_moments(double DI, double rho, double ux, double uy, double T, double* q)
+{
+    const double u2 = ux * ux + uy * uy, A = (DI + 2) * T + u2, B = (DI + 4) * T + u2;
+    q[0] = rho;
+    q[1] = rho * ux;
+    q[2] = rho * uy;
+    q[3] = rho * (DI * T + u2);
+    q[4] = rho * (T + ux * ux);
+    q[5] = rho * ux * uy;
+    q[6] = rho * (T + uy * uy);
+    q[7] = rho * ux * A;
+    q[8] = rho * uy * A;
+    q[9] = 3 * rho * ux * T + rho * ux * ux * ux;
+    q[10] = rho * uy * T + rho * ux * ux * uy;
+    q[11] = rho * ux * T + rho * ux * uy * uy;
+    q[12] = 3 * rho * uy * T + rho * uy * uy * uy;
+    q[13] = rho * A * T + rho * ux * ux * B;
+    q[14] = rho * ux * uy * B;
+    q[15] = rho * A * T + rho * uy * uy * B;
+}
+
 lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
 {
     if (!out) return fail(nullptr, LBKM_EINVAL, "out is NULL");
@@ -218,15 +241,38 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
     }
     if (!(p.dx > 0 && p.dy > 0 && p.dt > 0))
         return fail(nullptr, LBKM_EINVAL, "dx, dy, dt must be > 0");
-    if (p.bc_x < 0 || p.bc_x > 1 || p.bc_y < 0 || p.bc_y > 2)
+    if (!(p.bc_x == LBKM_BC_PERIODIC || p.bc_x == LBKM_BC_ZERO_GRADIENT || p.bc_x == LBKM_BC_SIDES) ||
+        !(p.bc_y == LBKM_BC_PERIODIC || p.bc_y == LBKM_BC_ZERO_GRADIENT || p.bc_y == LBKM_BC_WALL ||
+          p.bc_y == LBKM_BC_SIDES))
         return fail(nullptr, LBKM_EINVAL,
-                    "bc_x must be LBKM_BC_PERIODIC or _ZERO_GRADIENT, bc_y one of those or _WALL");
-    if (p.bc_y == LBKM_BC_WALL) {
-        if (p.ny < 2) return fail(nullptr, LBKM_EINVAL, "LBKM_BC_WALL needs ny >= 2");
-        for (int s = 0; s < 2; s++)
-            if (!(p.wall_T[s] > 0.0 && p.wall_T[s] < 1e300) || !(fabs(p.wall_ux[s]) < 1e300) ||
-                !(fabs(p.wall_uy[s]) < 1e300))
+                    "bc_x must be LBKM_BC_PERIODIC, _ZERO_GRADIENT or _SIDES; bc_y one of those "
+                    "or _WALL");
+    int sbc[4];
+    for (int s = 0; s < 4; s++) {
+        const int dir = s < 2 ? p.bc_x : p.bc_y;
+        sbc[s] = dir == LBKM_BC_SIDES ? p.side_bc[s] : dir;
+        const bool x_side = s < 2;
+        const bool ok = sbc[s] == LBKM_BC_PERIODIC ? dir != LBKM_BC_SIDES
+                        : sbc[s] == LBKM_BC_ZERO_GRADIENT || sbc[s] == LBKM_BC_DIRICHLET
+                            ? true
+                            : (sbc[s] == LBKM_BC_WALL || sbc[s] == LBKM_BC_SPECULAR) && !x_side;
+        if (!ok)
+            return fail(nullptr, LBKM_EINVAL,
+                        "side %d: periodic only for both sides, walls and specular only in y", s);
+        if (!x_side && p.ny < 2 && sbc[s] >= LBKM_BC_WALL)
+            return fail(nullptr, LBKM_EINVAL, "walls, Dirichlet or specular y sides need ny >= 2");
+        if (sbc[s] == LBKM_BC_WALL) {
+            const int w = s - 2;
+            if (!(p.wall_T[w] > 0.0 && p.wall_T[w] < 1e300) || !(fabs(p.wall_ux[w]) < 1e300) ||
+                !(fabs(p.wall_uy[w]) < 1e300))
                 return fail(nullptr, LBKM_EINVAL, "wall velocities must be finite, wall_T > 0");
+        }
+        if (sbc[s] == LBKM_BC_DIRICHLET &&
+            (!(p.side_rho[s] > 0.0 && p.side_rho[s] < 1e300) ||
+             !(p.side_T[s] > 0.0 && p.side_T[s] < 1e300) || !(fabs(p.side_ux[s]) < 1e300) ||
+             !(fabs(p.side_uy[s]) < 1e300) || !(p.side_lam[s] >= 0.0 && p.side_lam[s] <= 1.0)))
+            return fail(nullptr, LBKM_EINVAL,
+                        "Dirichlet side %d: rho, T > 0 and finite u, lambda in [0, 1]", s);
     }
     if (p.Pr > 0) p.S[7] = p.S[8] = p.Pr * p.S[4];
     double smax = 0;
@@ -271,6 +317,22 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
                              p.ny, h->pitch, p.bc_x, p.bc_y, &h->Kd);
     fill_model_const<float>(h->hm, p.S, p.Q, p.omega1, p.omega2, p.T_ig, p.dx, p.dy, p.dt, p.nx,
                             p.ny, h->pitch, p.bc_x, p.bc_y, &h->Kf);
+    // per-side conditions; Dirichlet ghost values f = M^-1 f_hat^eq(state), lambda
+    for (int sd = 0; sd < 4; sd++) {
+        h->Kd.sbc[sd] = h->Kf.sbc[sd] = sbc[sd];
+        if (sbc[sd] != LBKM_BC_DIRICHLET) continue;
+        double fe[16];
+        host_feq_moments(2.0 + h->hm.I, p.side_rho[sd], p.side_ux[sd], p.side_uy[sd], p.side_T[sd],
+                         fe);
+        for (int i = 0; i < 16; i++) {
+            double acc = 0.0;
+            for (int k = 0; k < 16; k++) acc += h->hm.Minv[i * 16 + k] * fe[k];
+            h->Kd.sfeq[sd][i] = acc;
+            h->Kf.sfeq[sd][i] = (float)acc;
+        }
+        h->Kd.sfeq[sd][16] = p.side_lam[sd];
+        h->Kf.sfeq[sd][16] = (float)p.side_lam[sd];
+    }
     for (int side = 0; side < 2; side++) {
         h->Kd.wux[side] = p.wall_ux[side];
         h->Kd.wuy[side] = p.wall_uy[side];
@@ -780,6 +842,8 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     if (h->precision != LBKM_F64 || h->ny != 1 || h->batched)
         return fail(h, LBKM_EINVAL, "lbkm_grad needs a single LBKM_F64 grid with ny = 1");
     if (h->p.omega2 != 0.0) return fail(h, LBKM_EINVAL, "lbkm_grad needs omega2 = 0");
+    if (h->p.bc_x == LBKM_BC_SIDES)
+        return fail(h, LBKM_EINVAL, "lbkm_grad needs periodic or zero-gradient ends");
     if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_grad before lbkm_init_fields");
     if (!ob->rho_target || ob->steps < 1 || ob->checkpoint_every < 1)
         return fail(h, LBKM_EINVAL, "rho_target, steps >= 1 and checkpoint_every >= 1 needed");

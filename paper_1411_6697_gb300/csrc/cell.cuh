@@ -318,6 +318,51 @@ __device__ __forceinline__ R reaction_increment(R lam, R a, R b, R dt)
     return mu0 - mu;
 }
 
+__device__ __forceinline__ int map_index(int j, int n, int bc)
+{
+    if (bc == 0) {
+        if (j < 0) j += n;
+        if (j >= n) j -= n;
+    }
+    return j < 0 ? 0 : (j >= n ? n - 1 : j);
+}
+
+// plane of the velocity with v_y reversed (orbits axis, diagonal, axis, diagonal:
+// (c,0) (0,c) (-c,0) (0,-c) and (+,+) (-,+) (-,-) (+,-)); lambda maps to itself
+__host__ __device__ __forceinline__ int mirror_plane(int p)
+{
+    return p == 16 ? 16 : (((p >> 2) & 1) ? ((p & ~3) | (3 - (p & 3))) : ((p & 1) ? (p ^ 2) : p));
+}
+
+// Value of plane p at (x, y) of the ghost-extended grid: inside the grid the stored
+// value; outside it the side's condition: periodic wrap, zero gradient (and walls,
+// corrected afterwards) copy the edge cell, Dirichlet gives the side's equilibrium,
+// specular mirrors the cell across the face with v_y reversed. A Dirichlet y side
+// wins in a corner (corner ghosts are never read by the cross-shaped stencils).
+template <typename R>
+__device__ __forceinline__ R ghost_value(const ModelConst<R>& K, const R* __restrict__ in, int p,
+                                         int x, int y)
+{
+    int sp = p;
+    if (y < 0 || y >= K.ny) {
+        const int s = y < 0 ? 2 : 3, code = K.sbc[s];
+        if (code == 3) return K.sfeq[s][p];
+        if (code == 4) {
+            y = y < 0 ? -y - 1 : 2 * K.ny - 1 - y;
+            y = y < 0 ? 0 : (y >= K.ny ? K.ny - 1 : y);
+            sp = mirror_plane(p);
+        } else {
+            y = map_index(y, K.ny, code == 0 ? 0 : 1);
+        }
+    }
+    if (x < 0 || x >= K.nx) {
+        const int s = x < 0 ? 0 : 1, code = K.sbc[s];
+        if (code == 3) return K.sfeq[s][p];
+        x = map_index(x, K.nx, code == 0 ? 0 : 1);
+    }
+    return in[sp * K.plane + (int64_t)y * K.pitch + x];
+}
+
 __device__ __forceinline__ float lane_recip(float x) { return 1.0f / x; }
 __device__ __forceinline__ double lane_recip(double x) { return 1.0 / x; }
 
@@ -341,13 +386,6 @@ __device__ __forceinline__ void wall_correction(const ModelConst<R>& K, const L*
     inverse_moments(K, dm, d);
 }
 
-__device__ __forceinline__ int map_index(int j, int n, int bc)
-{
-    if (bc == 0) {
-        if (j < 0) j += n;
-        if (j >= n) j -= n;
-    }
-    return j < 0 ? 0 : (j >= n ? n - 1 : j);
-}
+
 
 } // namespace lbk

@@ -82,17 +82,16 @@ __global__ void __launch_bounds__(TX * TY)
             const int p = idx / C::PS;
             const int rem = idx - p * C::PS;
             const int r = rem / C::SW, c = rem - r * C::SW;
-            const int gx = map_index(x0 - 2 + c, nx, K.bc_x);
-            const int gy = TWO_D ? map_index(y0 - C::H + r, ny, K.bc_y) : y0;
-            sf[idx] = in[p * plane + (int64_t)gy * pitch + gx];
+            sf[idx] = ghost_value(K, in, p, x0 - 2 + c, TWO_D ? y0 - C::H + r : y0);
         }
         __syncthreads();
         if constexpr (TWO_D) {
             // walls: the staged ghost rows hold copies of the edge fluid row (the
             // index map clamps); add the non-equilibrium-extrapolation correction
-            if (K.bc_y == 2 && (y0 - C::H < 0 || y0 + TY + C::H > ny)) {
+            if ((K.sbc[2] == 2 || K.sbc[3] == 2) && (y0 - C::H < 0 || y0 + TY + C::H > ny)) {
                 for (int idx = tid; idx < 2 * C::SW; idx += C::NT) {
                     const int side = idx / C::SW, c = idx - side * C::SW;
+                    if (K.sbc[2 + side] != 2) continue;
                     const int rs = (side == 0 ? 0 : ny - 1) - (y0 - C::H); // fluid row
                     if (rs < 0 || rs >= C::SH) continue;
                     R fl[16], d[16];

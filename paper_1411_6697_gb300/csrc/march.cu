@@ -124,42 +124,63 @@ __device__ __forceinline__ void cp8(void* dst, const void* src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
 }
 
-// Stage row r (boundary-mapped) of the planes whose class is in `mask`, columns
-// x0-2 .. x0+BW+1: the 32 16-byte chunks of columns x0 .. x0+BW-1 of a plane by
-// one warp (lane = chunk), the two 8-byte edges (x0-2, x0-1 and x0+BW, x0+BW+1)
-// of all planes by the first 34 threads. Chunks that leave the grid are gathered
-// element by element through the boundary map.
+// Stage row r of the planes whose class is in `mask`, columns x0-2 .. x0+BW+1: the
+// 32 16-byte chunks of columns x0 .. x0+BW-1 of a plane by one warp (lane = chunk),
+// the two 8-byte edges (x0-2, x0-1 and x0+BW, x0+BW+1) of all planes by the first 34
+// threads. Rows outside the grid follow the side's condition: a Dirichlet side fills
+// the row with its equilibrium, a specular side copies the mirror row with the planes
+// of reversed v_y, the others copy the wrapped or edge row (walls are corrected after
+// the row lands). Columns outside the grid go element by element through the same
+// rules (ghost_value).
 __device__ __forceinline__ void issue_row(const float* __restrict__ in, float* ring, int r,
                                           int x0, const ModelConst<float>& K, unsigned mask)
 {
     static_assert(BW == 128 && NWM == 2, "staging layout assumes 32 chunks per row and 2 warps");
-    const int gy = map_index(r, K.ny, K.bc_y);
-    const float* rowp = in + (int64_t)gy * K.pitch;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int gy = r, dir_side = -1;
+    bool mir = false;
+    if (r < 0 || r >= K.ny) {
+        const int s = r < 0 ? 2 : 3, code = K.sbc[s];
+        if (code == 3) {
+            dir_side = s;
+        } else if (code == 4) {
+            gy = r < 0 ? -r - 1 : 2 * K.ny - 1 - r;
+            gy = gy < 0 ? 0 : (gy >= K.ny ? K.ny - 1 : gy);
+            mir = true;
+        } else {
+            gy = map_index(r, K.ny, code == 0 ? 0 : 1);
+        }
+    }
+    const float* rowp = in + (int64_t)gy * K.pitch;
 #pragma unroll
     for (int p = 0; p < NPLANE; p++) {
         if ((p & 1) != w || !((mask >> pclass(p)) & 1u)) continue;
         float* dst = plane_row(ring, p, r) + 2 + 4 * lane;
-        const float* src = rowp + p * K.plane;
         const int x = x0 + 4 * lane;
+        if (dir_side >= 0) {
+            const float v = K.sfeq[dir_side][p];
+            *reinterpret_cast<float4*>(dst) = make_float4(v, v, v, v);
+            continue;
+        }
+        const int sp = mir ? mirror_plane(p) : p;
+        const float* src = rowp + sp * K.plane;
         if (x + 4 <= K.nx) {
             cp16(dst, src + x);
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; e++) dst[e] = src[map_index(x + e, K.nx, K.bc_x)];
+            for (int e = 0; e < 4; e++) dst[e] = ghost_value(K, in, p, x + e, r);
         }
     }
     if (threadIdx.x < 2 * NPLANE) {
         const int p = threadIdx.x >> 1, side = threadIdx.x & 1;
         if ((mask >> pclass(p)) & 1u) {
             float* dst = plane_row(ring, p, r) + (side ? BW + 2 : 0);
-            const float* src = rowp + p * K.plane;
             const int x = side ? x0 + BW : x0 - 2;
-            if (x >= 0 && x + 2 <= K.nx) {
-                cp8(dst, src + x);
+            if (dir_side < 0 && x >= 0 && x + 2 <= K.nx) {
+                cp8(dst, rowp + (mir ? mirror_plane(p) : p) * K.plane + x);
             } else {
-                dst[0] = src[map_index(x, K.nx, K.bc_x)];
-                dst[1] = src[map_index(x + 1, K.nx, K.bc_x)];
+                dst[0] = ghost_value(K, in, p, x, r);
+                dst[1] = ghost_value(K, in, p, x + 1, r);
             }
         }
     }
@@ -295,11 +316,12 @@ __global__ void __launch_bounds__(MT, 4)
         }
         cp_wait<PF>(); // rows y0-2 .. y0+1 have landed
         __syncthreads();
-        if (K.bc_y == 2) { // ghost rows among those landed; row y0+2 is fixed in the loop
+        // walls: ghost rows among those landed (row y0+2 is fixed in the loop)
+        if (K.sbc[2] == 2) {
             if (y0 - 1 < 0) wall_fix_row(ring, y0 - 1, 0, 0, K, false);
             if (y0 - 2 < 0) wall_fix_row(ring, y0 - 2, 0, 0, K, true); // kept by v_y > 0 only
-            if (y0 + 1 >= ny) wall_fix_row(ring, y0 + 1, ny - 1, 1, K, false);
         }
+        if (K.sbc[3] == 2 && y0 + 1 >= ny) wall_fix_row(ring, y0 + 1, ny - 1, 1, K, false);
         for (int r = y0 - 1; r <= y0 + 1; r++)
             store_macros(mac, ign, r, row_macros<REC>(ring, r, K, C, bad, act0, act1));
 
@@ -308,7 +330,7 @@ __global__ void __launch_bounds__(MT, 4)
             __syncthreads();
             if (y + 2 + PF <= yend + 1) issue_row(in, ring, y + 2 + PF, x0, K, ALL_CLASSES);
             cp_commit();
-            if (K.bc_y == 2 && y + 2 >= ny) wall_fix_row(ring, y + 2, ny - 1, 1, K, false);
+            if (K.sbc[3] == 2 && y + 2 >= ny) wall_fix_row(ring, y + 2, ny - 1, 1, K, false);
             // macros of row y+2 (read from the next iteration on)
             store_macros(mac, ign, y + 2, row_macros<REC>(ring, y + 2, K, C, bad, act0, act1));
 

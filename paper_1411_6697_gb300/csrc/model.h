@@ -44,6 +44,10 @@ struct ModelConst {
     // the same four FP64 quantities split as hi + lo FP32 pairs (double-float recovery)
     float cdh[4], cdl[4], wdh[4], wdl[4], idh, idl, tigh, tigl;
     R wux[2], wuy[2], wT[2];             // walls below row 0 [0] and above row ny-1 [1]
+    int32_t sbc[4];                      // condition of the sides x=0, x=nx, y=0, y=ny:
+                                         // 0 periodic, 1 zero gradient, 2 wall (y),
+                                         // 3 Dirichlet, 4 specular (y)
+    R sfeq[4][17];                       // Dirichlet ghost values (f_1..f_16, lambda)
     int32_t nx, ny, pitch, bc_x, bc_y;   // bc_y = 2: walls (non-equilibrium extrapolation)
     int32_t pad_;
     int64_t plane;                       // elements per plane = ny * pitch

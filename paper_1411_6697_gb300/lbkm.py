@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpaper_lbkm.so")
 
 F64, F32 = 0, 1
 RECOVER_F64, RECOVER_DF32 = 0, 1
-BC_PERIODIC, BC_ZERO_GRADIENT, BC_WALL = 0, 1, 2
+BC_PERIODIC, BC_ZERO_GRADIENT, BC_WALL, BC_DIRICHLET, BC_SPECULAR, BC_SIDES = 0, 1, 2, 3, 4, 5
 
 STATUS = {0: "LBKM_OK", 1: "LBKM_EINVAL", 2: "LBKM_ENOMEM", 3: "LBKM_ECUDA",
           4: "LBKM_ESINGULAR", 5: "LBKM_EUNSTABLE", 6: "LBKM_ETIMEOUT", 7: "LBKM_ESTATE"}
@@ -51,6 +51,9 @@ class Params(ctypes.Structure):
         ("tne_every", ctypes.c_int32), ("tne_capacity", ctypes.c_int32),
         ("wall_ux", ctypes.c_double * 2), ("wall_uy", ctypes.c_double * 2),
         ("wall_T", ctypes.c_double * 2),
+        ("side_bc", ctypes.c_int32 * 4), ("side_rho", ctypes.c_double * 4),
+        ("side_ux", ctypes.c_double * 4), ("side_uy", ctypes.c_double * 4),
+        ("side_T", ctypes.c_double * 4), ("side_lam", ctypes.c_double * 4),
     ]
 
 
@@ -153,6 +156,11 @@ def default_params(**kw) -> Params:
         elif k == "walls":  # ((ux, uy, T) below row 0, (ux, uy, T) above row ny-1)
             for side in (0, 1):
                 p.wall_ux[side], p.wall_uy[side], p.wall_T[side] = map(float, v[side])
+        elif k == "sides":  # 4 x (code, rho, ux, uy, T, lambda): x = 0, x = nx, y = 0, y = ny
+            for j, (code, r, u, w, T, lam) in enumerate(v):
+                p.side_bc[j] = int(code)
+                p.side_rho[j], p.side_ux[j], p.side_uy[j], p.side_T[j], p.side_lam[j] = (
+                    float(r), float(u), float(w), float(T), float(lam))
         else:
             setattr(p, k, v)
     return p

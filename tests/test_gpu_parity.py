@@ -129,6 +129,86 @@ def test_step_2d_walls_parity(prec, rec, nx, ny, bcx):
         assert rel_l2(m[k], mr[k]) <= TOL[prec], (k, rel_l2(m[k], mr[k]))
 
 
+SIDES = {
+    # Dirichlet inflow at x = 0, outflow at x = nx, specular floor, Dirichlet lid
+    "inflow": ((3, 1.05, 0.15, 0.0, 1.1, 0.2), (1, 1, 0, 0, 1, 0),
+               (4, 1, 0, 0, 1, 0), (3, 0.95, 0.1, -0.05, 1.15, 0.3)),
+    # outflow at x = 0, Dirichlet at x = nx, a moving heated wall below, specular above
+    "mixed": ((1, 1, 0, 0, 1, 0), (3, 0.9, -0.1, 0.02, 1.2, 0.1),
+              (2, 1, 0, 0, 1, 0), (4, 1, 0, 0, 1, 0)),
+}
+
+
+@pytest.mark.parametrize("prec,rec", PRECS, ids=PID)
+@pytest.mark.parametrize("kind", ["inflow", "mixed"])
+@pytest.mark.parametrize("nx,ny", [(70, 37), (262, 40), (33, 9), (130, 3)])
+def test_step_2d_per_side_parity(prec, rec, kind, nx, ny):
+    """Per-side conditions (Sec. IV.C): Dirichlet equilibria, specular reflection,
+    zero-gradient outflow and a non-equilibrium-extrapolation wall, on a sheared
+    reactive non-equilibrium state."""
+    params, fields = mixed_2d(nx, ny, bc=(5, 5), seed=nx + 2)
+    params["sides"] = SIDES[kind]
+    params["walls"] = WALLS
+    s, ob, f, lam = start(params, fields, prec, rec, noise_seed=ny + 2)
+    steps = 25
+    s.step(steps)
+    f_ref, lam_ref = ob.run(f, lam, steps)
+    got = s.f_planes()
+    for i in range(16):
+        assert rel_l2(got[i], f_ref[i]) <= TOL[prec], ("f", i + 1, rel_l2(got[i], f_ref[i]))
+    assert rel_l2(got[16], lam_ref) <= TOL[prec]
+    m, mr = s.macros(), ob.macros(f_ref)
+    for k in ("rho", "ux", "uy", "T", "p"):
+        assert rel_l2(m[k], mr[k]) <= TOL[prec], (k, rel_l2(m[k], mr[k]))
+
+
+def reflected_state(gamma=1.5):
+    """State 3 of the regular reflection (Sec. IV.C, Eq. (RR4) family): the flow of
+    state 2 (the lid's state) turned back parallel to the wall by the reflected shock,
+    from the oblique-shock relations (weak solution of the theta-beta-M relation)."""
+    r2, T2, u2, v2 = 1.25, 0.56, 1.9, -0.173205
+    p2 = r2 * T2
+    M2 = np.hypot(u2, v2) / np.sqrt(gamma * p2 / r2)
+    theta = np.arctan2(-v2, u2)
+    from scipy.optimize import brentq
+
+    def f(b):
+        return (2 / np.tan(b) * (M2 ** 2 * np.sin(b) ** 2 - 1) /
+                (M2 ** 2 * (gamma + np.cos(2 * b)) + 2) - np.tan(theta))
+    beta = brentq(f, np.arcsin(1 / M2) + 1e-9, np.deg2rad(60))
+    Mn2 = (M2 * np.sin(beta)) ** 2
+    r3 = r2 * (gamma + 1) * Mn2 / ((gamma - 1) * Mn2 + 2)
+    p3 = p2 * (1 + 2 * gamma / (gamma + 1) * (Mn2 - 1))
+    return r3, p3 / r3
+
+
+def test_shock_reflection_parity_and_reflected_state():
+    """Regular shock reflection (Sec. IV.C) on the paper's 300 x 100 grid: the CUDA FP64
+    and FP32 runs against the oracle after 2000 steps, then to t = 0.25 on the GPU, where
+    the gas between the wall and the reflected shock (x in [0.22, 0.28], the first 6
+    rows) must carry the density and temperature of the oblique-shock solution."""
+    c = li.shock_reflection(steps=2000)
+    p, fl = c["params"], c["fields"]
+    ob = make_oracle(p)
+    f0 = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
+    f_ref, lam_ref = ob.run(f0, fl["lam"], c["steps"])
+    mr = ob.macros(f_ref)
+    r3, T3 = reflected_state()
+    for prec in (lbkm.F64, lbkm.F32):
+        s = solver(p, prec)
+        s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+        s.step(c["steps"])
+        m = s.macros()
+        tol = 1e-11 if prec == lbkm.F64 else 1e-4
+        for k in ("rho", "ux", "uy", "T"):
+            assert rel_l2(m[k], mr[k]) <= tol, (prec, k, rel_l2(m[k], mr[k]))
+        s.step(50000 - c["steps"])
+        m = s.macros()
+        region = (slice(0, 6), slice(220, 280))
+        rho3, t3 = m["rho"][region].mean(), m["T"][region].mean()
+        assert abs(rho3 / r3 - 1) < 0.03 and abs(t3 / T3 - 1) < 0.03, (prec, rho3, r3, t3, T3)
+
+
 @pytest.mark.parametrize("prec", [lbkm.F64, lbkm.F32], ids=["f64", "f32"])
 def test_couette_full_run(prec):
     """Couette start-up (Sec. IV.D, 200 rows, t = 0.5): every field against the oracle

@@ -33,6 +33,13 @@ def create(**kw):
     (dict(bc=(0, 2), walls=((0, 0, 1), (0.1, 0, 1))), 1),            # walls need ny >= 2
     (dict(ny=8, bc=(0, 2), walls=((0, 0, 1), (0.1, 0, 0.0))), 1),    # wall T must be > 0
     (dict(ny=8, bc=(0, 2), walls=((float("nan"), 0, 1), (0, 0, 1))), 1),
+    # per-side conditions: specular and walls only on y sides, periodic only for both
+    # sides of a direction, Dirichlet states physical
+    (dict(ny=8, bc=(5, 0), sides=[(4, 1, 0, 0, 1, 0), (1, 1, 0, 0, 1, 0)] + [(1, 1, 0, 0, 1, 0)] * 2), 1),
+    (dict(ny=8, bc=(0, 5), sides=[(1, 1, 0, 0, 1, 0)] * 2 + [(0, 1, 0, 0, 1, 0), (1, 1, 0, 0, 1, 0)]), 1),
+    (dict(ny=8, bc=(5, 0), sides=[(3, 0.0, 0, 0, 1, 0), (1, 1, 0, 0, 1, 0)] + [(1, 1, 0, 0, 1, 0)] * 2), 1),
+    (dict(ny=8, bc=(5, 0), sides=[(3, 1.0, 0, 0, 1, 1.5), (1, 1, 0, 0, 1, 0)] + [(1, 1, 0, 0, 1, 0)] * 2), 1),
+    (dict(ny=1, bc=(0, 5), sides=[(1, 1, 0, 0, 1, 0)] * 2 + [(4, 1, 0, 0, 1, 0)] * 2), 1),
     (dict(tne_every=-1), 1),
     (dict(tne_capacity=0), 1),
     (dict(omega1=-1.0), 1),
