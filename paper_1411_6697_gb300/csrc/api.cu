@@ -355,7 +355,7 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
     if ((e = cudaMalloc(&h->buf[1], h->state_bytes_dev)) != cudaSuccess) return bail(e, "state B");
     if ((e = cudaMemset(h->buf[0], 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemset(h->buf[1], 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
-    h->grid = step_grid(h->precision, h->recovery, h->two_d, h->nx, h->ny);
+    h->grid = step_grid(h->precision, h->recovery, h->two_d, h->nx, h->ny, sbc);
     if (h->grid < 1) return bail(cudaGetLastError(), "step grid");
     h->tgrid = tne_grid(h->nx, h->ny);
     int pg = h->grid > h->tgrid ? h->grid : h->tgrid;

@@ -1,6 +1,7 @@
 // kernels.cu -- CUDA kernels of the MRT-LBKM step for sm_103a.
 //
-// step_kernel: one fused forward-Euler stage. Each block walks tiles of
+// step_kernel: one fused forward-Euler stage of the FP64 form and of FP32 1-D grids
+// (FP32 2-D grids run march_kernel, march.cu). Each block walks tiles of
 // TX x TY cells (grid-stride loop, grid = SMs x resident blocks). Per tile it
 //   1. stages the 17 planes (f_1..f_16, lambda) of the tile plus a 2-cell halo
 //      in shared memory (coalesced row loads, boundary condition applied by
@@ -488,11 +489,16 @@ int elementwise_grid(int64_t n, int threads)
 
 } // namespace
 
-int step_grid(int precision, int recovery, bool two_d, int nx, int ny)
+static bool general_sides(const int sbc[4])
+{
+    return sbc[0] >= 2 || sbc[1] >= 2 || sbc[2] >= 2 || sbc[3] >= 2;
+}
+
+int step_grid(int precision, int recovery, bool two_d, int nx, int ny, const int sbc[4])
 {
     if (precision == 0)
         return two_d ? K2D<double, 0>::grid(nx, ny) : K1D<double, 0>::grid(nx, ny);
-    if (two_d) return march_grid(recovery, nx, ny);
+    if (two_d) return march_grid(recovery | (general_sides(sbc) ? 2 : 0), nx, ny);
     return recovery == 1 ? K1D<float, 1>::grid(nx, ny) : K1D<float, 0>::grid(nx, ny);
 }
 
@@ -501,7 +507,10 @@ cudaError_t launch_step(int precision, int recovery, bool two_d, const void* K,
 {
     if (precision == 0)
         return two_d ? K2D<double, 0>::launch(K, a, s) : K1D<double, 0>::launch(K, a, s);
-    if (two_d) return launch_march(recovery, *static_cast<const ModelConst<float>*>(K), a, s);
+    if (two_d) {
+        const ModelConst<float>& Kf = *static_cast<const ModelConst<float>*>(K);
+        return launch_march(recovery | (general_sides(Kf.sbc) ? 2 : 0), Kf, a, s);
+    }
     return recovery == 1 ? K1D<float, 1>::launch(K, a, s) : K1D<float, 0>::launch(K, a, s);
 }
 

@@ -40,7 +40,9 @@ cudaError_t launch_step(int precision, int recovery, bool two_d, const void* K,
                         const StepLaunch& a, cudaStream_t s);
 // Blocks to launch for a step on this grid (multiple of the SM count times the
 // resident blocks per SM, capped by the number of tiles).
-int step_grid(int precision, int recovery, bool two_d, int nx, int ny);
+// sbc: the side conditions (walls, Dirichlet or specular sides select the general
+// variant of the FP32 marching kernel)
+int step_grid(int precision, int recovery, bool two_d, int nx, int ny, const int sbc[4]);
 
 cudaError_t launch_init(int precision, const ModelConst<double>& Kd, const double* rho,
                         const double* ux, const double* uy, const double* T, const double* lam,
@@ -115,8 +117,9 @@ cudaError_t launch_adj_rho0(const ModelConst<double>& K, const AdjArgs& a, doubl
                             int grid, cudaStream_t s);
 
 // FP32 2-D step: y-marching strips, two cells per thread (march.cu)
-int march_grid(int recovery, int nx, int ny);
-cudaError_t launch_march(int recovery, const ModelConst<float>& K, const StepLaunch& a,
+// mode = recovery | (general side conditions << 1)
+int march_grid(int mode, int nx, int ny);
+cudaError_t launch_march(int mode, const ModelConst<float>& K, const StepLaunch& a,
                          cudaStream_t s);
 
 } // namespace lbk

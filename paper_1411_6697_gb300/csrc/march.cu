@@ -124,6 +124,14 @@ __device__ __forceinline__ void cp8(void* dst, const void* src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
 }
 
+// n staged values of plane p, row r, columns x .. x+n-1 through the boundary rules
+// (the rare path of the staging)
+__device__ __forceinline__ void stage_elements(const ModelConst<float>& K, const float* in, float* dst,
+                                            int p, int x, int r, int n)
+{
+    for (int e = 0; e < n; e++) dst[e] = ghost_value(K, in, p, x + e, r);
+}
+
 // Stage row r of the planes whose class is in `mask`, columns x0-2 .. x0+BW+1: the
 // 32 16-byte chunks of columns x0 .. x0+BW-1 of a plane by one warp (lane = chunk),
 // the two 8-byte edges (x0-2, x0-1 and x0+BW, x0+BW+1) of all planes by the first 34
@@ -132,11 +140,43 @@ __device__ __forceinline__ void cp8(void* dst, const void* src)
 // of reversed v_y, the others copy the wrapped or edge row (walls are corrected after
 // the row lands). Columns outside the grid go element by element through the same
 // rules (ghost_value).
+template <bool GEN>
 __device__ __forceinline__ void issue_row(const float* __restrict__ in, float* ring, int r,
                                           int x0, const ModelConst<float>& K, unsigned mask)
 {
     static_assert(BW == 128 && NWM == 2, "staging layout assumes 32 chunks per row and 2 warps");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if constexpr (!GEN) { // periodic or zero-gradient sides only: index maps, no ghost rules
+        const float* rowp = in + (int64_t)map_index(r, K.ny, K.bc_y) * K.pitch;
+#pragma unroll
+        for (int p = 0; p < NPLANE; p++) {
+            if ((p & 1) != w || !((mask >> pclass(p)) & 1u)) continue;
+            float* dst = plane_row(ring, p, r) + 2 + 4 * lane;
+            const float* src = rowp + p * K.plane;
+            const int x = x0 + 4 * lane;
+            if (x + 4 <= K.nx) {
+                cp16(dst, src + x);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; e++) dst[e] = src[map_index(x + e, K.nx, K.bc_x)];
+            }
+        }
+        if (threadIdx.x < 2 * NPLANE) {
+            const int p = threadIdx.x >> 1, side = threadIdx.x & 1;
+            if ((mask >> pclass(p)) & 1u) {
+                float* dst = plane_row(ring, p, r) + (side ? BW + 2 : 0);
+                const float* src = rowp + p * K.plane;
+                const int x = side ? x0 + BW : x0 - 2;
+                if (x >= 0 && x + 2 <= K.nx) {
+                    cp8(dst, src + x);
+                } else {
+                    dst[0] = src[map_index(x, K.nx, K.bc_x)];
+                    dst[1] = src[map_index(x + 1, K.nx, K.bc_x)];
+                }
+            }
+        }
+        return;
+    }
     int gy = r, dir_side = -1;
     bool mir = false;
     if (r < 0 || r >= K.ny) {
@@ -164,24 +204,20 @@ __device__ __forceinline__ void issue_row(const float* __restrict__ in, float* r
         }
         const int sp = mir ? mirror_plane(p) : p;
         const float* src = rowp + sp * K.plane;
-        if (x + 4 <= K.nx) {
+        if (x + 4 <= K.nx)
             cp16(dst, src + x);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; e++) dst[e] = ghost_value(K, in, p, x + e, r);
-        }
+        else
+            stage_elements(K, in, dst, p, x, r, 4);
     }
     if (threadIdx.x < 2 * NPLANE) {
         const int p = threadIdx.x >> 1, side = threadIdx.x & 1;
         if ((mask >> pclass(p)) & 1u) {
             float* dst = plane_row(ring, p, r) + (side ? BW + 2 : 0);
             const int x = side ? x0 + BW : x0 - 2;
-            if (dir_side < 0 && x >= 0 && x + 2 <= K.nx) {
+            if (dir_side < 0 && x >= 0 && x + 2 <= K.nx)
                 cp8(dst, rowp + (mir ? mirror_plane(p) : p) * K.plane + x);
-            } else {
-                dst[0] = ghost_value(K, in, p, x, r);
-                dst[1] = ghost_value(K, in, p, x + 1, r);
-            }
+            else
+                stage_elements(K, in, dst, p, x, r, 2);
         }
     }
 }
@@ -259,7 +295,7 @@ __device__ __forceinline__ void store_macros(float* mac, unsigned char* ign, int
     }
 }
 
-template <int REC>
+template <int REC, bool GEN>
 __global__ void __launch_bounds__(MT, 4)
     march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows)
 {
@@ -310,27 +346,30 @@ __global__ void __launch_bounds__(MT, 4)
         // rows y0-2 .. y0+2: row y0-2 only for the classes whose stencil reaches it
         for (int r = y0 - 2; r <= y0 + 1 + PF; r++) {
             if (r <= yend + 1)
-                issue_row(in, ring, r, x0, K,
-                          r == y0 - 2 ? ((1u << C_UP) | (1u << C_LAM)) : ALL_CLASSES);
+                issue_row<GEN>(in, ring, r, x0, K,
+                               r == y0 - 2 ? ((1u << C_UP) | (1u << C_LAM)) : ALL_CLASSES);
             cp_commit();
         }
         cp_wait<PF>(); // rows y0-2 .. y0+1 have landed
         __syncthreads();
         // walls: ghost rows among those landed (row y0+2 is fixed in the loop)
-        if (K.sbc[2] == 2) {
-            if (y0 - 1 < 0) wall_fix_row(ring, y0 - 1, 0, 0, K, false);
-            if (y0 - 2 < 0) wall_fix_row(ring, y0 - 2, 0, 0, K, true); // kept by v_y > 0 only
+        if constexpr (GEN) {
+            if (K.sbc[2] == 2) {
+                if (y0 - 1 < 0) wall_fix_row(ring, y0 - 1, 0, 0, K, false);
+                if (y0 - 2 < 0) wall_fix_row(ring, y0 - 2, 0, 0, K, true); // v_y > 0 only
+            }
+            if (K.sbc[3] == 2 && y0 + 1 >= ny) wall_fix_row(ring, y0 + 1, ny - 1, 1, K, false);
         }
-        if (K.sbc[3] == 2 && y0 + 1 >= ny) wall_fix_row(ring, y0 + 1, ny - 1, 1, K, false);
         for (int r = y0 - 1; r <= y0 + 1; r++)
             store_macros(mac, ign, r, row_macros<REC>(ring, r, K, C, bad, act0, act1));
 
         for (int y = y0; y < yend; y++) {
             cp_wait<PF - 1>(); // row y+2 has landed
             __syncthreads();
-            if (y + 2 + PF <= yend + 1) issue_row(in, ring, y + 2 + PF, x0, K, ALL_CLASSES);
+            if (y + 2 + PF <= yend + 1) issue_row<GEN>(in, ring, y + 2 + PF, x0, K, ALL_CLASSES);
             cp_commit();
-            if (K.sbc[3] == 2 && y + 2 >= ny) wall_fix_row(ring, y + 2, ny - 1, 1, K, false);
+            if constexpr (GEN)
+                if (K.sbc[3] == 2 && y + 2 >= ny) wall_fix_row(ring, y + 2, ny - 1, 1, K, false);
             // macros of row y+2 (read from the next iteration on)
             store_macros(mac, ign, y + 2, row_macros<REC>(ring, y + 2, K, C, bad, act0, act1));
 
@@ -548,12 +587,26 @@ __global__ void __launch_bounds__(MT, 4)
     }
 }
 
-template <int REC>
+template <int REC, bool GEN>
 cudaError_t march_prepare()
 {
     static cudaError_t done = cudaFuncSetAttribute(
-        march_kernel<REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MARCH_SMEM);
+        march_kernel<REC, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MARCH_SMEM);
     return done;
+}
+
+template <int REC, bool GEN>
+int resident_of()
+{
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        if (march_prepare<REC, GEN>() != cudaSuccess) return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<REC, GEN>, MT,
+                                                          MARCH_SMEM) != cudaSuccess)
+            return -1;
+        if (per_sm < 1) per_sm = 1;
+    }
+    return per_sm;
 }
 
 } // namespace
@@ -562,31 +615,27 @@ cudaError_t march_prepare()
 // per column of the grid is chosen so that the strips fill whole waves of the
 // resident blocks while each strip stays long compared with its 3-row
 // prologue (rows staged and macros recovered before the first update).
+// mode = recovery | (general boundaries << 1): the general variant carries walls,
+// Dirichlet and specular sides; the plain one only index maps.
 namespace {
-int resident_blocks(int recovery)
+int resident_blocks(int mode)
 {
-    static int cache[2] = {-1, -1};
-    int& c = cache[recovery & 1];
-    if (c < 0) {
-        cudaError_t e = recovery == 1 ? march_prepare<1>() : march_prepare<0>();
-        if (e != cudaSuccess) return -1;
-        int dev = 0, sms = 0, per_sm = 0;
+    static int sms = -1;
+    if (sms < 0) {
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = recovery == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                &per_sm, march_kernel<1>, MT, MARCH_SMEM)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                &per_sm, march_kernel<0>, MT, MARCH_SMEM);
-        if (e != cudaSuccess) return -1;
-        c = (per_sm < 1 ? 1 : per_sm) * sms;
     }
-    return c;
+    const int per_sm = mode == 0 ? resident_of<0, false>()
+                       : mode == 1 ? resident_of<1, false>()
+                       : mode == 2 ? resident_of<0, true>() : resident_of<1, true>();
+    return per_sm < 0 ? -1 : per_sm * sms;
 }
 } // namespace
 
-void march_plan(int recovery, int nx, int ny, int* grid, int* strip_rows)
+void march_plan(int mode, int nx, int ny, int* grid, int* strip_rows)
 {
-    const int G = resident_blocks(recovery);
+    const int G = resident_blocks(mode);
     const int nsx = (nx + BW - 1) / BW;
     // 32-row strips measured best at 4096^2 (16: -12 %, 64: -11 %, one wave of
     // 293-row strips: -36 %); smaller grids use shorter strips so that every
@@ -603,25 +652,27 @@ void march_plan(int recovery, int nx, int ny, int* grid, int* strip_rows)
     *strip_rows = rows;
 }
 
-int march_grid(int recovery, int nx, int ny)
+int march_grid(int mode, int nx, int ny)
 {
     int g, r;
-    march_plan(recovery, nx, ny, &g, &r);
+    march_plan(mode, nx, ny, &g, &r);
     return g;
 }
 
-cudaError_t launch_march(int recovery, const ModelConst<float>& K, const StepLaunch& a,
-                         cudaStream_t s)
+cudaError_t launch_march(int mode, const ModelConst<float>& K, const StepLaunch& a, cudaStream_t s)
 {
-    cudaError_t e = recovery == 1 ? march_prepare<1>() : march_prepare<0>();
-    if (e != cudaSuccess) return e;
     int g, rows;
-    march_plan(recovery, K.nx, K.ny, &g, &rows);
+    march_plan(mode, K.nx, K.ny, &g, &rows);
+    if (g < 0) return cudaErrorInvalidConfiguration;
     if (g != a.grid) return cudaErrorInvalidConfiguration; // partial buffers sized for a.grid
-    if (recovery == 1)
-        march_kernel<1><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+    if (mode == 0)
+        march_kernel<0, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+    else if (mode == 1)
+        march_kernel<1, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+    else if (mode == 2)
+        march_kernel<0, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
     else
-        march_kernel<0><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+        march_kernel<1, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
     return cudaGetLastError();
 }
 
