@@ -132,6 +132,10 @@ typedef struct {
                               y = 0, y = ny (see lbkm_bc) */
     double side_rho[4], side_ux[4], side_uy[4], side_T[4], side_lam[4]; /* Dirichlet
                               states of those sides; rho > 0, T > 0 */
+    int32_t time_scheme;   /* 0: forward Euler (the paper's single stage); 1: two-stage
+                              SSP Runge-Kutta from that step E, u^{n+1} = (u^n +
+                              E(E(u^n)))/2 (second order in time; two launches per
+                              step; TNE of u^n; not for batched instances or lbkm_grad) */
 } lbkm_params;
 
 /* Grid-wide TNE measures of one state (Sec. VI). Sums are weighted by dx*dy;

@@ -31,7 +31,9 @@
  *   8. NND flux differences of v_i f_i (Sec. II, NND scheme of Zhang 1988);
  *   9. u . grad(lambda) with NND interface values of lambda (Eq. (28));
  *  10. forward Euler: f^{n+1} = f^n + dt (-div(v f) + Omega),
- *      lambda^{n+1} = clamp(lambda^n - dt u.grad(lambda) + dlambda_chem, 0, 1).
+ *      lambda^{n+1} = clamp(lambda^n - dt u.grad(lambda) + dlambda_chem, 0, 1);
+ *      optionally (time_scheme 1) two such steps E averaged with the state at t_n,
+ *      u^{n+1} = (u^n + E(E(u^n))) / 2, the two-stage SSP Runge-Kutta scheme.
  * TNE measures (Sec. VI, Eqs. (90)-(91)) are evaluated on a given state.
  *
  * Every reading taken where the paper is silent or inconsistent (sign of A,
@@ -66,6 +68,9 @@ typedef struct {
      * the mirror cell with v_y reversed) */
     int32_t side_bc[4];
     double side_rho[4], side_ux[4], side_uy[4], side_T[4], side_lam[4];
+    /* 0: forward Euler; 1: the two-stage strong-stability-preserving Runge-Kutta
+     * scheme built from that step E: u1 = E(u), u^{n+1} = (u + E(u1)) / 2 */
+    int32_t time_scheme;
 } orc_params;
 
 /* number of doubles in one TNE global record */
@@ -559,15 +564,33 @@ int orc_run(const orc_params* p, const double* M, const double* Minv, double* f,
         return -1;
     }
     double *fa = f, *la = lam, *fb = f2, *lb = l2;
+    double *f3 = NULL, *l3 = NULL;
+    if (p->time_scheme == 1) {
+        f3 = malloc(sizeof(double) * NV * n);
+        l3 = malloc(sizeof(double) * n);
+        if (!f3 || !l3) {
+            free(f2); free(l2); free(f3); free(l3);
+            return -1;
+        }
+    }
     for (int64_t s = 0; s < nsteps; s++) {
         if (tne) orc_tne(p, M, fa, NULL, tne + (size_t)s * ORC_TNE_LEN);
         if (orc_step(p, M, Minv, fa, la, fb, lb) != 0) {
-            free(f2); free(l2);
+            free(f2); free(l2); free(f3); free(l3);
             return -1;
+        }
+        if (p->time_scheme == 1) { /* second stage from u1, then the average with u^n */
+            if (orc_step(p, M, Minv, fb, lb, f3, l3) != 0) {
+                free(f2); free(l2); free(f3); free(l3);
+                return -1;
+            }
+            for (size_t i = 0; i < NV * n; i++) fb[i] = 0.5 * (fa[i] + f3[i]);
+            for (size_t i = 0; i < n; i++) lb[i] = 0.5 * (la[i] + l3[i]);
         }
         double* t = fa; fa = fb; fb = t;
         t = la; la = lb; lb = t;
     }
+    free(f3); free(l3);
     if (fa != f) {
         memcpy(f, fa, sizeof(double) * NV * n);
         memcpy(lam, la, sizeof(double) * n);

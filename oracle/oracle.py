@@ -58,6 +58,7 @@ class Params(ctypes.Structure):
         ("side_bc", ctypes.c_int32 * 4), ("side_rho", ctypes.c_double * 4),
         ("side_ux", ctypes.c_double * 4), ("side_uy", ctypes.c_double * 4),
         ("side_T", ctypes.c_double * 4), ("side_lam", ctypes.c_double * 4),
+        ("time_scheme", ctypes.c_int32),
     ]
 
 
@@ -117,7 +118,7 @@ class Oracle:
 
     def __init__(self, nx, ny, *, gamma, orbit_kind, orbit_speed, orbit_eta, S, Q=0.0,
                  omega1=0.0, omega2=0.0, T_ig=1.1, dx=1e-3, dy=None, dt=1e-5,
-                 bc_x=1, bc_y=0, walls=None, sides=None):
+                 bc_x=1, bc_y=0, walls=None, sides=None, time_scheme=0):
         lib = _load()
         p = Params()
         p.nx, p.ny, p.bc_x, p.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
@@ -136,6 +137,7 @@ class Oracle:
                 p.side_bc[k] = int(code)
                 p.side_rho[k], p.side_ux[k], p.side_uy[k], p.side_T[k], p.side_lam[k] = (
                     float(r), float(u), float(v), float(T), float(lam))
+        p.time_scheme = int(time_scheme)
         self.p = p
         self.nx, self.ny = int(nx), int(ny)
         self.n = self.nx * self.ny

@@ -92,11 +92,15 @@ const void* model_ptr(const lbkm* h)
     return h->precision == 0 ? (const void*)&h->Kd : (const void*)&h->Kf;
 }
 
-StepLaunch step_args(const lbkm* h, int from)
+// stage 0: Euler step buf[from] -> buf[1-from]; stage 1: first RK2 stage, same
+// buffers; stage 2: second RK2 stage from buf[1-from] back into buf[from]
+StepLaunch step_args(const lbkm* h, int from, int stage = 0)
 {
     StepLaunch a;
-    a.in = h->buf[from];
-    a.out = h->buf[1 - from];
+    a.in = stage == 2 ? h->buf[1 - from] : h->buf[from];
+    a.out = stage == 2 ? h->buf[from] : h->buf[1 - from];
+    a.prev = h->buf[from];
+    a.stage = stage;
     a.partials = h->partials;
     a.ctr = h->ctr;
     a.hist = h->hist;
@@ -292,6 +296,8 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
         return fail(nullptr, LBKM_EINVAL, "omega1, omega2 must be >= 0");
     if (!(p.T_ig >= 0.0 && p.T_ig <= 1e300))
         return fail(nullptr, LBKM_EINVAL, "T_ig must be finite and >= 0");
+    if (p.time_scheme != 0 && p.time_scheme != 1)
+        return fail(nullptr, LBKM_EINVAL, "time_scheme must be 0 (Euler) or 1 (SSP-RK2)");
     if (p.tne_every < 0 || p.tne_capacity < 1)
         return fail(nullptr, LBKM_EINVAL, "tne_every must be >= 0 and tne_capacity >= 1");
 
@@ -419,6 +425,22 @@ lbkm_status lbkm_init_fields(lbkm_t h, const double* rho, const double* ux, cons
     return LBKM_OK;
 }
 
+// One time step from buf[c]: forward Euler (one launch, the state moves to the other
+// buffer), or the two-stage SSP Runge-Kutta scheme (E(u^n) into the other buffer, then
+// (u^n + E(E(u^n))) / 2 back into buf[c]). c is updated to the buffer holding u^{n+1}.
+static cudaError_t launch_full_step(const lbkm* h, const void* K, int& c, cudaStream_t st)
+{
+    if (h->p.time_scheme == 0) {
+        cudaError_t e = launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, c), st);
+        if (e == cudaSuccess) c = 1 - c;
+        return e;
+    }
+    cudaError_t e = launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, c, 1), st);
+    if (e == cudaSuccess)
+        e = launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, c, 2), st);
+    return e;
+}
+
 lbkm_status lbkm_step(lbkm_t h, int64_t n)
 {
     if (!h) return LBKM_EINVAL;
@@ -469,11 +491,8 @@ lbkm_status lbkm_step(lbkm_t h, int64_t n)
             CUDA_TRY(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
             int c = h->cur;
             cudaError_t le = cudaSuccess;
-            for (int s = 0; s < GRAPH_CHUNK && le == cudaSuccess; s++) {
-                le = launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, c),
-                                 h->capture_stream);
-                c = 1 - c;
-            }
+            for (int s = 0; s < GRAPH_CHUNK && le == cudaSuccess; s++)
+                le = launch_full_step(h, K, c, h->capture_stream);
             cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &g);
             if (le != cudaSuccess || ce != cudaSuccess) {
                 if (ce == cudaSuccess) cudaGraphDestroy(g);
@@ -490,9 +509,7 @@ lbkm_status lbkm_step(lbkm_t h, int64_t n)
         h->host_steps += GRAPH_CHUNK;
     }
     for (; n > 0; n--) {
-        CUDA_TRY(h, launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, h->cur),
-                                h->stream));
-        h->cur = 1 - h->cur;
+        CUDA_TRY(h, launch_full_step(h, K, h->cur, h->stream));
         h->host_steps++;
     }
     return LBKM_OK;
@@ -645,6 +662,8 @@ lbkm_status lbkm_create_batched(const lbkm_params* pin, int32_t n_instances,
         return fail(nullptr, LBKM_EINVAL, "params, inst_nx and n_instances >= 1 are required");
     if (pin->precision != LBKM_F32)
         return fail(nullptr, LBKM_EINVAL, "batched instances run in LBKM_F32");
+    if (pin->time_scheme != 0)
+        return fail(nullptr, LBKM_EINVAL, "batched instances step with forward Euler");
     if (pin->tne_every != 0)
         return fail(nullptr, LBKM_EINVAL,
                     "tne_every must be 0 for batched instances (use lbkm_tne_instances)");
@@ -844,6 +863,7 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     if (h->p.omega2 != 0.0) return fail(h, LBKM_EINVAL, "lbkm_grad needs omega2 = 0");
     if (h->p.bc_x == LBKM_BC_SIDES)
         return fail(h, LBKM_EINVAL, "lbkm_grad needs periodic or zero-gradient ends");
+    if (h->p.time_scheme != 0) return fail(h, LBKM_EINVAL, "lbkm_grad needs forward Euler");
     if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_grad before lbkm_init_fields");
     if (!ob->rho_target || ob->steps < 1 || ob->checkpoint_every < 1)
         return fail(h, LBKM_EINVAL, "rho_target, steps >= 1 and checkpoint_every >= 1 needed");

@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(TX * TY)
     R* __restrict__ out = static_cast<R*>(a.out);
 
     const int64_t step = a.ctr->step;
-    const bool do_tne = a.tne_every > 0 && (step % a.tne_every) == 0;
+    const bool do_tne = a.tne_every > 0 && (step % a.tne_every) == 0 && a.stage != 2;
+    const bool avg = a.stage == 2; // second SSP-RK2 stage: average with u^n (= out)
     if (do_tne) {
         for (int i = tid; i < C::NW * NSUM; i += C::NT) tsum[i] = 0.0;
         for (int i = tid; i < C::NW * NMM; i += C::NT)
@@ -222,7 +223,10 @@ __global__ void __launch_bounds__(TX * TY)
             }
             const int64_t g = (int64_t)gy * pitch + gx;
 #pragma unroll
-            for (int i = 0; i < 16; i++) out[i * plane + g] = f[i] + K.dt * (W[i] - adv[i]);
+            for (int i = 0; i < 16; i++) {
+                const R v = f[i] + K.dt * (W[i] - adv[i]);
+                out[i * plane + g] = avg ? R(0.5) * (out[i * plane + g] + v) : v;
+            }
 
             // lambda: u . grad(lambda) with NND interface values, reaction, clamp
             R la = ux > R(0) ? ux * PX(16) : (ux < R(0) ? ux * NX(16) : R(0));
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(TX * TY)
 #undef NY
             R ln = lam0 - K.dt * la + dlam;
             ln = ln < R(0) ? R(0) : (ln > R(1) ? R(1) : ln);
-            out[16 * plane + g] = ln;
+            out[16 * plane + g] = avg ? R(0.5) * (out[16 * plane + g] + ln) : ln;
         }
 
         // 4. TNE statistics of this tile (all lanes take part in the shuffles)
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(TX * TY)
         __syncthreads();
         if (tid == 0) {
             if (do_tne) a.ctr->hist_count += 1;
-            a.ctr->step = step + 1;
+            if (a.stage != 1) a.ctr->step = step + 1;
             a.ctr->arrivals = 0u;
         }
     }

@@ -26,6 +26,11 @@ struct TneRecord {
 struct StepLaunch {
     const void* in;      // state at t_n  [17][ny][pitch]
     void* out;           // state at t_n+1
+    // stage: 0 forward Euler step; 1 first stage of the SSP-RK2 step (writes E(u^n),
+    // reduces the TNE of u^n, does not advance the step counter); 2 second stage
+    // (writes (prev + E(in)) / 2 with prev = u^n, no TNE, advances the counter)
+    const void* prev;
+    int stage;
     double* partials;    // [grid][TNE_PART]
     DevCounters* ctr;
     TneRecord* hist;     // ring of hist_cap records

@@ -295,7 +295,7 @@ __device__ __forceinline__ void store_macros(float* mac, unsigned char* ign, int
     }
 }
 
-template <int REC, bool GEN>
+template <int REC, bool GEN, bool AVG>
 __global__ void __launch_bounds__(MT, 4)
     march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows)
 {
@@ -314,7 +314,8 @@ __global__ void __launch_bounds__(MT, 4)
     const DfConst C = df_constants(K);
 
     const int64_t step = a.ctr->step;
-    const bool do_tne = a.tne_every > 0 && (step % a.tne_every) == 0;
+    // AVG: second SSP-RK2 stage (average with u^n, which out still holds; no TNE)
+    const bool do_tne = !AVG && a.tne_every > 0 && (step % a.tne_every) == 0;
     if (do_tne) {
         for (int i = tid; i < NWM * NSUM; i += MT) tsum[i] = 0.0;
         for (int i = tid; i < NWM * NMM; i += MT) tmm[i] = (i % NMM) < TNE_K ? FLT_MAX : -FLT_MAX;
@@ -457,11 +458,15 @@ __global__ void __launch_bounds__(MT, 4)
             // NND flux differences (upwind side fixed per velocity), Euler update, store
             const int64_t g = (int64_t)y * K.pitch + cx;
             auto put = [&](int i, V2 adv) {
-                const V2 v = fma(V2(dt), W[i] - adv, f[i]);
-                if (act1)
-                    *reinterpret_cast<float2*>(out + i * K.plane + g) = v.v;
-                else if (act0)
-                    out[i * K.plane + g] = v.x();
+                V2 v = fma(V2(dt), W[i] - adv, f[i]);
+                if (act1) {
+                    float2* q = reinterpret_cast<float2*>(out + i * K.plane + g);
+                    if constexpr (AVG) v = V2(0.5f) * (V2(*q) + v);
+                    *q = v.v;
+                } else if (act0) {
+                    float* q = out + i * K.plane + g;
+                    *q = AVG ? 0.5f * (*q + v.x()) : v.x();
+                }
             };
 #define PX(i) nnd_pos_x(load6(plane_row(ring, (i), y), lx))
 #define NX(i) nnd_neg_x(load6(plane_row(ring, (i), y), lx))
@@ -491,10 +496,14 @@ __global__ void __launch_bounds__(MT, 4)
 #undef NX
 #undef PY
 #undef NY
-            if (act1)
-                *reinterpret_cast<float2*>(out + 16 * K.plane + g) = ln.v;
-            else if (act0)
-                out[16 * K.plane + g] = ln.x();
+            if (act1) {
+                float2* q = reinterpret_cast<float2*>(out + 16 * K.plane + g);
+                if constexpr (AVG) ln = V2(0.5f) * (V2(*q) + ln);
+                *q = ln.v;
+            } else if (act0) {
+                float* q = out + 16 * K.plane + g;
+                *q = AVG ? 0.5f * (*q + ln.x()) : ln.x();
+            }
 
             // TNE statistics of the state being stepped (Eqs. (90)-(91)); sums of Delta_k
             // and d^2 accumulate as packed pairs, folded at the end of the strip
@@ -581,32 +590,42 @@ __global__ void __launch_bounds__(MT, 4)
         __syncthreads();
         if (tid == 0) {
             if (do_tne) a.ctr->hist_count += 1;
-            a.ctr->step = step + 1;
+            if (a.stage != 1) a.ctr->step = step + 1;
             a.ctr->arrivals = 0u;
         }
     }
 }
 
-template <int REC, bool GEN>
+template <int REC, bool GEN, bool AVG>
 cudaError_t march_prepare()
 {
-    static cudaError_t done = cudaFuncSetAttribute(
-        march_kernel<REC, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MARCH_SMEM);
+    static cudaError_t done = cudaFuncSetAttribute(march_kernel<REC, GEN, AVG>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)MARCH_SMEM);
     return done;
 }
 
-template <int REC, bool GEN>
+// resident blocks per SM of a variant; the averaging stage of a step shares the grid
+// of its first stage, so both must fit that many blocks (checked at launch)
+template <int REC, bool GEN, bool AVG>
 int resident_of()
 {
     static int per_sm = -1;
     if (per_sm < 0) {
-        if (march_prepare<REC, GEN>() != cudaSuccess) return -1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<REC, GEN>, MT,
-                                                          MARCH_SMEM) != cudaSuccess)
+        if (march_prepare<REC, GEN, AVG>() != cudaSuccess) return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<REC, GEN, AVG>,
+                                                          MT, MARCH_SMEM) != cudaSuccess)
             return -1;
         if (per_sm < 1) per_sm = 1;
     }
     return per_sm;
+}
+
+template <int REC, bool GEN>
+int resident_min()
+{
+    const int a = resident_of<REC, GEN, false>(), b = resident_of<REC, GEN, true>();
+    return a < 0 || b < 0 ? -1 : (a < b ? a : b);
 }
 
 } // namespace
@@ -626,9 +645,10 @@ int resident_blocks(int mode)
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    const int per_sm = mode == 0 ? resident_of<0, false>()
-                       : mode == 1 ? resident_of<1, false>()
-                       : mode == 2 ? resident_of<0, true>() : resident_of<1, true>();
+    const int m = mode & 3;
+    const int per_sm = m == 0 ? resident_min<0, false>()
+                       : m == 1 ? resident_min<1, false>()
+                       : m == 2 ? resident_min<0, true>() : resident_min<1, true>();
     return per_sm < 0 ? -1 : per_sm * sms;
 }
 } // namespace
@@ -659,20 +679,31 @@ int march_grid(int mode, int nx, int ny)
     return g;
 }
 
+namespace {
+template <int REC, bool GEN>
+void launch_variant(bool avg, const ModelConst<float>& K, const StepLaunch& a, int rows,
+                    cudaStream_t s)
+{
+    if (avg)
+        march_kernel<REC, GEN, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+    else
+        march_kernel<REC, GEN, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+}
+} // namespace
+
 cudaError_t launch_march(int mode, const ModelConst<float>& K, const StepLaunch& a, cudaStream_t s)
 {
     int g, rows;
     march_plan(mode, K.nx, K.ny, &g, &rows);
     if (g < 0) return cudaErrorInvalidConfiguration;
     if (g != a.grid) return cudaErrorInvalidConfiguration; // partial buffers sized for a.grid
-    if (mode == 0)
-        march_kernel<0, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
-    else if (mode == 1)
-        march_kernel<1, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
-    else if (mode == 2)
-        march_kernel<0, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
-    else
-        march_kernel<1, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+    const bool avg = a.stage == 2;
+    switch (mode & 3) {
+    case 0: launch_variant<0, false>(avg, K, a, rows, s); break;
+    case 1: launch_variant<1, false>(avg, K, a, rows, s); break;
+    case 2: launch_variant<0, true>(avg, K, a, rows, s); break;
+    default: launch_variant<1, true>(avg, K, a, rows, s); break;
+    }
     return cudaGetLastError();
 }
 

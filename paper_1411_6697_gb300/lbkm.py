@@ -54,6 +54,7 @@ class Params(ctypes.Structure):
         ("side_bc", ctypes.c_int32 * 4), ("side_rho", ctypes.c_double * 4),
         ("side_ux", ctypes.c_double * 4), ("side_uy", ctypes.c_double * 4),
         ("side_T", ctypes.c_double * 4), ("side_lam", ctypes.c_double * 4),
+        ("time_scheme", ctypes.c_int32),
     ]
 
 

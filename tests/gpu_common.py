@@ -6,7 +6,7 @@ from oracle import oracle
 from paper_1411_6697_gb300 import lbkm
 
 KEYS = ("gamma", "orbit_kind", "orbit_speed", "orbit_eta", "S", "Q", "omega1", "omega2",
-        "T_ig", "dx", "dt", "walls", "sides")
+        "T_ig", "dx", "dt", "walls", "sides", "time_scheme")
 
 
 def solver(params, precision, recovery=0, tne_every=0, tne_capacity=1, **over):

@@ -104,6 +104,37 @@ def test_step_2d_nonequilibrium_parity(prec, rec, nx, ny, bc):
     assert lam_ref.max() > lam.max() - 1e-12  # the reaction ran
 
 
+# ------------------------------------------------------------------ SSP-RK2 steps
+@pytest.mark.parametrize("prec,rec", PRECS, ids=PID)
+@pytest.mark.parametrize("nx,ny,bc", [(70, 37, (0, 0)), (262, 40, (1, 1)), (33, 9, (1, 0)),
+                                      (300, 1, (1, 0))])
+def test_rk2_steps_parity(prec, rec, nx, ny, bc):
+    """The two-stage SSP Runge-Kutta scheme (two fused Euler launches, the second
+    averaged with u^n): 40 steps (one graph-captured chunk of 32 and 8 direct steps),
+    every plane against the oracle's scheme, the step count and the per-step TNE of u^n."""
+    params, fields = mixed_2d(nx, ny, bc=bc, seed=nx + 3)
+    params["time_scheme"] = 1
+    s, ob, f, lam = start(params, fields, prec, rec, noise_seed=ny + 3, tne_every=1,
+                          tne_capacity=64)
+    steps = 40
+    s.step(steps)
+    f_ref, lam_ref, tne_ref = ob.run(f, lam, steps, tne=True)
+    got = s.f_planes()
+    for i in range(16):
+        assert rel_l2(got[i], f_ref[i]) <= TOL[prec], ("f", i + 1, rel_l2(got[i], f_ref[i]))
+    assert rel_l2(got[16], lam_ref) <= TOL[prec]
+    assert s.steps_taken == steps
+    hist = s.tne_history(max_records=steps)
+    assert len(hist) == steps
+    from oracle.oracle import unpack_tne
+    for n in (0, steps // 2, steps - 1):
+        ref = unpack_tne(tne_ref[n])
+        scale = np.abs(ref["abs_sum"]).max()
+        tol = 1e-10 if prec == lbkm.F64 else 1e-3
+        assert np.abs(hist[n]["abs_sum"] - ref["abs_sum"]).max() <= tol * scale, n
+        assert hist[n]["step"] == n
+
+
 # ------------------------------------------------------------------ walls (Sec. IV.D)
 WALLS = ((-0.03, 0.0, 1.05), (0.08, 0.0, 0.97))
 

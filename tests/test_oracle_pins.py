@@ -365,6 +365,33 @@ def test_couette_start_up_against_series_solution(oracle_mod):
     assert np.abs(m["uy"]).max() < 1e-3 * u0 and abs(m["rho"].mean() - 1.0) < 1e-3
 
 
+def test_time_schemes_converge_at_their_order(oracle_mod):
+    """Forward Euler and the two-stage SSP Runge-Kutta scheme built from it, on a smooth
+    periodic flow at fixed grid: the difference to a run at dt/16 halves (Euler) or
+    quarters (SSP-RK2) when dt halves."""
+    nx = 64
+    x = (np.arange(nx) + 0.5) / nx
+    rho = (1 + 0.05 * np.sin(2 * np.pi * x))[None]
+    T = (1 + 0.05 * np.cos(2 * np.pi * x))[None]
+    ux = (0.1 * np.sin(4 * np.pi * x))[None]
+    z = np.zeros((1, nx))
+    S = np.full(16, 200.0)
+    S[7:9] = 300.0
+    ratios = {}
+    for scheme in (0, 1):
+        sol = {}
+        for k in (1, 2, 4, 16):
+            dt = 2e-4 / k
+            ob = make(oracle_mod, nx, 1, S=S, dx=1.0 / nx, dt=dt, bc_x=0, time_scheme=scheme)
+            f, _ = ob.run(ob.init(rho, ux, z, T), z, int(round(0.05 / dt)))
+            sol[k] = f
+        e = {k: np.linalg.norm(sol[k] - sol[16]) for k in (1, 2, 4)}
+        ratios[scheme] = (e[1] / e[2], e[2] / e[4], e[1])
+    assert 1.8 < ratios[0][0] < 2.6 and 1.8 < ratios[0][1] < 2.6, ratios
+    assert 3.5 < ratios[1][0] < 4.6 and 3.5 < ratios[1][1] < 4.6, ratios
+    assert ratios[1][2] < 1e-2 * ratios[0][2]
+
+
 def test_exact_riemann_solver_satisfies_jump_conditions():
     """The reference solver itself: Rankine-Hugoniot across the Sod shock and the
     isentropic relation across the rarefaction."""
