@@ -255,7 +255,7 @@ def _shared_params(p0):
 
 
 def run_batched(args):
-    """Config 4: 512 1-D detonations of uneven length in one persistent launch per chunk
+    """512 1-D detonations of uneven length in one persistent launch per chunk
     of steps, FP32; compared with the plain single-instance FP64 form on a sample of the
     same instances, run one after another."""
     import torch
@@ -321,7 +321,7 @@ def run_batched(args):
 
 
 def run_detonation(args):
-    """Config 2: one 1-D detonation of 16384 cells (L2-resident, latency-bound)."""
+    """One 1-D detonation of 16384 cells, 20000 steps (L2-resident, latency-bound)."""
     import torch
     from paper_1411_6697_gb300 import lbkm
     rank, local, world = _env_rank()
@@ -351,7 +351,7 @@ def run_detonation(args):
 
 
 def run_adjoint(args):
-    """Config 5: dJ/d(S, Q, omega1, rho0) of a 4000-step 1-D detonation of 8192 cells
+    """dJ/d(S, Q, omega1, rho0) of a 4000-step 1-D detonation of 8192 cells
     (profile mismatch + integrated TNE), checkpoints every 64 steps, through lbkm_grad;
     compared with the plain single-instance FP64 forward run that central differences
     would repeat twice per gradient entry."""

@@ -98,7 +98,8 @@ def bumps(nx, width=64.0, every=256):
 
 @pytest.mark.slow
 def test_adjoint_full_config_size():
-    """8192 cells, 4000 steps, checkpoints every 64, config-2 parameters (k = 2e4).
+    """8192 cells, 4000 steps, checkpoints every 64, with the parameters of the
+    16384-cell detonation (k = 2e4).
 
     J and the parameter gradients are compared directly. Single entries of drho0 are
     not well conditioned at this length: minmod arguments pass through zero at every

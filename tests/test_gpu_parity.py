@@ -277,7 +277,7 @@ def test_couette_full_run(prec):
     assert d_gpu <= (1.10 if prec == lbkm.F32 else 1.0 + 1e-6) * d_orc, (d_gpu, d_orc)
 
 
-# ------------------------------------------------------------------ configs 1 and 2
+# ------------------------------------------------------------------ Sod tube and detonation
 @pytest.mark.parametrize("run", ["A", "B"])
 def test_riemann_full_config_fp64(run):
     c = li.riemann(nx=400, steps=1000, run=run, interface=200)
