@@ -517,12 +517,15 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "kernel": ("march_kernel<%d> (f32)" % rec) if kernel == "march"
                      else "step_kernel (%s)" % tag,
-                     "algorithmic_bytes_per_launch": alg_bytes},
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "duration": "CUDA events over the timed steps, each the step kernel "
+                                 "and the few-microsecond TNE finish kernel"},
         "e2e": {"value": e2e_value, "unit": "Mcell-updates/s",
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
                 "note": "init_fields from pinned host + %d steps + macros to pinned host + "
                         "TNE history" % e2e_steps},
-        "gpu_launches": args.steps,
+        # per step: the fused step kernel and the TNE record finish
+        "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
     }
 

@@ -428,16 +428,15 @@ lbkm_status lbkm_init_fields(lbkm_t h, const double* rho, const double* ux, cons
 // One time step from buf[c]: forward Euler (one launch, the state moves to the other
 // buffer), or the two-stage SSP Runge-Kutta scheme (E(u^n) into the other buffer, then
 // (u^n + E(E(u^n))) / 2 back into buf[c]). c is updated to the buffer holding u^{n+1}.
+// With TNE on, a small kernel then turns the step's per-block partials into the record.
 static cudaError_t launch_full_step(const lbkm* h, const void* K, int& c, cudaStream_t st)
 {
-    if (h->p.time_scheme == 0) {
-        cudaError_t e = launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, c), st);
-        if (e == cudaSuccess) c = 1 - c;
-        return e;
-    }
-    cudaError_t e = launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, c, 1), st);
-    if (e == cudaSuccess)
+    const StepLaunch a0 = step_args(h, c, h->p.time_scheme == 0 ? 0 : 1);
+    cudaError_t e = launch_step(h->precision, h->recovery, h->two_d, K, a0, st);
+    if (e == cudaSuccess && h->p.time_scheme != 0)
         e = launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, c, 2), st);
+    if (e == cudaSuccess && a0.tne_every > 0) e = launch_tne_finish(a0, st);
+    if (e == cudaSuccess && h->p.time_scheme == 0) c = 1 - c;
     return e;
 }
 

@@ -296,18 +296,14 @@ __global__ void __launch_bounds__(TX * TY)
     __shared__ unsigned int s_last;
     if (tid == 0) s_last = (atomicAdd(&a.ctr->arrivals, 1u) == gridDim.x - 1) ? 1u : 0u;
     __syncthreads();
-    if (s_last) {
-        __threadfence();
+    if (s_last && tid == 0) { // the grid-wide TNE record is finished by launch_tne_finish
         if (do_tne) {
-            const int64_t slot = a.ctr->hist_count % a.hist_cap;
-            finish_tne(a.partials, gridDim.x, a.hist + slot, step, a.cell_area);
+            a.ctr->hist_count += 1;
+            a.ctr->tne_step = step;
         }
-        __syncthreads();
-        if (tid == 0) {
-            if (do_tne) a.ctr->hist_count += 1;
-            if (a.stage != 1) a.ctr->step = step + 1;
-            a.ctr->arrivals = 0u;
-        }
+        if (a.stage != 2) a.ctr->tne_pending = do_tne ? 1 : 0;
+        if (a.stage != 1) a.ctr->step = step + 1;
+        a.ctr->arrivals = 0u;
     }
 }
 
@@ -496,6 +492,50 @@ int elementwise_grid(int64_t n, int threads)
 static bool general_sides(const int sbc[4])
 {
     return sbc[0] >= 2 || sbc[1] >= 2 || sbc[2] >= 2 || sbc[3] >= 2;
+}
+
+namespace {
+constexpr int FIN_THREADS = 256;
+
+// Block q reduces quantity q of the step's partials (quantity-major: partials[q *
+// nblocks + b]) in a fixed order -- thread t takes blocks t, t + 256, ..., then the
+// lanes in a shuffle tree and the warps in order -- and writes it into the record.
+__global__ void __launch_bounds__(FIN_THREADS)
+    tne_finish_kernel(const double* __restrict__ partials, int nblocks, TneRecord* hist,
+                      int hist_cap, const DevCounters* ctr, double area)
+{
+    if (!ctr->tne_pending) return;
+    __shared__ double wsum[FIN_THREADS / 32];
+    const int q = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int kind = tne_kind(q);
+    double acc = kind == 0 ? 0.0 : (kind == 1 ? DBL_MAX : -DBL_MAX);
+    const double* pq = partials + (size_t)q * nblocks;
+    for (int b = t; b < nblocks; b += FIN_THREADS) acc = tne_comb(kind, acc, __ldcg(pq + b));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = tne_comb(kind, acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (lane == 0) wsum[w] = acc;
+    __syncthreads();
+    if (t != 0) return;
+    for (int k = 1; k < FIN_THREADS / 32; k++) acc = tne_comb(kind, acc, wsum[k]);
+    TneRecord* rec = hist + (ctr->hist_count - 1) % hist_cap;
+    if (q < TNE_K) rec->sum[q + 4] = acc * area;
+    else if (q < 2 * TNE_K) rec->abs_sum[q - TNE_K + 4] = acc * area;
+    else if (q < 3 * TNE_K) rec->min[q - 2 * TNE_K + 4] = acc;
+    else if (q < 4 * TNE_K) rec->max[q - 3 * TNE_K + 4] = acc;
+    else if (q == 4 * TNE_K) rec->d_sum = acc * area;
+    else rec->d2_sum = acc * area;
+    if (q == 0) {
+        for (int k = 0; k < 4; k++) rec->sum[k] = rec->abs_sum[k] = rec->min[k] = rec->max[k] = 0.0;
+        rec->step = ctr->tne_step;
+    }
+}
+} // namespace
+
+cudaError_t launch_tne_finish(const StepLaunch& a, cudaStream_t s)
+{
+    tne_finish_kernel<<<TNE_PART, FIN_THREADS, 0, s>>>(a.partials, a.grid, a.hist, a.hist_cap,
+                                                       a.ctr, a.cell_area);
+    return cudaGetLastError();
 }
 
 int step_grid(int precision, int recovery, bool two_d, int nx, int ny, const int sbc[4])

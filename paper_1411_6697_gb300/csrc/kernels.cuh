@@ -13,7 +13,9 @@ struct DevCounters {
     int64_t hist_count;    // TNE records written so far
     unsigned int arrivals; // blocks of the current launch that finished (reset by the last)
     int status;            // bit 0: non-finite or non-positive rho or T seen
+    int tne_pending;       // the launch just finished left TNE partials (set every step)
     int pad;
+    int64_t tne_step;      // step index of those partials
 };
 
 // One on-the-fly TNE record, laid out like lbkm_tne_global.
@@ -39,6 +41,11 @@ struct StepLaunch {
     int grid;            // blocks launched
     double cell_area;    // dx * dy
 };
+
+// Grid-wide TNE record of the partials a step left (if its schedule reduced TNE): one
+// block per quantity, each a fixed-order reduction over the step's blocks, written into
+// history slot (hist_count - 1) % hist_cap. Launched after every full step.
+cudaError_t launch_tne_finish(const StepLaunch& a, cudaStream_t s);
 
 // precision: 0 = FP64, 1 = FP32; recovery: 0 = FP64, 1 = double-float (FP32 only)
 cudaError_t launch_step(int precision, int recovery, bool two_d, const void* K,

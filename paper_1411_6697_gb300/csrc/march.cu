@@ -581,18 +581,14 @@ __global__ void __launch_bounds__(MT, 4)
     __shared__ unsigned int s_last;
     if (tid == 0) s_last = (atomicAdd(&a.ctr->arrivals, 1u) == gridDim.x - 1) ? 1u : 0u;
     __syncthreads();
-    if (s_last) {
-        __threadfence();
+    if (s_last && tid == 0) { // the grid-wide TNE record is finished by launch_tne_finish
         if (do_tne) {
-            const int64_t slot = a.ctr->hist_count % a.hist_cap;
-            finish_tne(a.partials, gridDim.x, a.hist + slot, step, a.cell_area);
+            a.ctr->hist_count += 1;
+            a.ctr->tne_step = step;
         }
-        __syncthreads();
-        if (tid == 0) {
-            if (do_tne) a.ctr->hist_count += 1;
-            if (a.stage != 1) a.ctr->step = step + 1;
-            a.ctr->arrivals = 0u;
-        }
+        if (a.stage != 2) a.ctr->tne_pending = do_tne ? 1 : 0;
+        if (a.stage != 1) a.ctr->step = step + 1;
+        a.ctr->arrivals = 0u;
     }
 }
 
