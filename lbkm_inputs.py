@@ -13,6 +13,9 @@ analytic initial-value problem of the kind the paper runs in Sec. IV:
 * ``lax``, ``sjogreen`` -- the other two shock tubes of Sec. IV.B.
 * ``couette``    -- Couette flow between walls (Sec. IV.D).
 * ``shock_reflection`` -- regular reflection of an oblique shock on a wall (Sec. IV.C).
+* ``d2v24_detonation``, ``d2v24_reactive2d`` -- the same kinds of problem for the
+  paper's own 24-velocity model D2V24 (Sec. II, Eqs. (25)-(27)), with the paper's
+  velocity parameters (v_a, v_b, v_c; eta_a, eta_b, eta_c).
 
 Default velocity set: a 16-velocity model of four orbits (axis, diagonal, axis,
 diagonal) with speeds (2.7, 2.2, 1.2, 1.0) and eta (5, 0, 3, 0). The paper's
@@ -29,6 +32,19 @@ SEED_BASE = 14116697
 
 DEFAULT_ORBITS = dict(orbit_kind=(0, 1, 0, 1), orbit_speed=(2.7, 2.2, 1.2, 1.0),
                       orbit_eta=(5.0, 0.0, 3.0, 0.0))
+
+
+# (v_a, v_b, v_c), (eta_a, eta_b, eta_c) of the paper's D2V24 runs
+D2V24_DETONATION_V = ((2.7, 2.2, 1.2), (5.0, 3.0, 1.1))    # steady detonation, Sec. IV.A
+D2V24_TNE_V = ((2.7, 2.2, 1.2), (1.5, 0.5, 5.0))           # TNE study, Sec. VI (R_i = 100)
+D2V24_TNE_V2 = ((2.7, 2.6, 1.9), (5.0, 0.0, 1.7))          # Sec. VI, R_i = 1e3 and 1e4
+
+
+def d2v24_orbits(v, eta):
+    """Six-orbit table (axis and diagonal at each of v_a, v_b, v_c) of a D2V24 set."""
+    return dict(orbit_kind=(0, 1, 0, 1, 0, 1),
+                orbit_speed=(v[0], v[0], v[1], v[1], v[2], v[2]),
+                orbit_eta=(eta[0], eta[0], eta[1], eta[1], eta[2], eta[2]))
 
 
 def cj_state(Q: float, gamma: float, rho0: float = 1.0, p0: float = 1.0):
@@ -189,6 +205,49 @@ def detonation(nx=16384, steps=20000, driver=50, Q=1.0, S=None, dx=1e-4, dt=2e-6
     return dict(params=_base(nx=nx, S=np.asarray(S, float), Q=Q, omega1=omega1, T_ig=1.1,
                              dx=dx, dt=dt, gamma=gamma),
                 steps=steps, fields=f, name="detonation_nx%d" % nx)
+
+
+def d2v24_detonation(nx=5000, steps=78000, omega1=2e4, dx=2e-4, dt=5e-6, S=None,
+                     v=D2V24_DETONATION_V, x_driver=0.2, ripple=0.0):
+    """The steady-detonation run of Sec. IV.A with D2V24: x in [0, nx dx), the paper's
+    printed burnt state (rho, T, u_x, lambda) = (1.38837, 1.57856, 0.577350, 1) for
+    x <= x_driver and (1, 1, 0, 0) beyond, gamma = 1.4 (I = 3), Q = 1, T_ig = 1.1,
+    R_5..R_7 = 1e4 and the others 1e5, dx = 2e-4, dt = 5e-6 (t = 0.39 after 78000
+    steps). The paper leaves the rate constant unstated: omega1 = 2e4 here.
+    Returns params for the D2V24 oracle (six orbits) and for lbkm24 (v, eta, S[24])."""
+    if S is None:
+        S = np.full(24, 1e5)
+        S[4:7] = 1e4
+    burnt = (np.arange(nx) * dx) <= x_driver + 1e-12
+    f = dict(rho=np.where(burnt, 1.38837, 1.0)[None, :],
+             ux=np.where(burnt, 0.577350, 0.0)[None, :], uy=np.zeros((1, nx)),
+             T=np.where(burnt, 1.57856, 1.0)[None, :], lam=np.where(burnt, 1.0, 0.0)[None, :])
+    if ripple > 0.0:
+        rng = np.random.default_rng(SEED_BASE + 7)
+        x = np.arange(nx) / nx
+        for k in ("rho", "T"):
+            amp, ph = rng.uniform(0.5, 1.0, 4), rng.uniform(0, 2 * np.pi, 4)
+            r = sum(a * np.sin(2 * np.pi * (j + 1) * x + p) for j, (a, p) in enumerate(zip(amp, ph)))
+            f[k] = f[k] * (1.0 + ripple * r / np.abs(r).max())
+    common = dict(nx=nx, ny=1, gamma=1.4, Q=1.0, omega1=omega1, omega2=0.0, T_ig=1.1, dx=dx,
+                  dy=dx, dt=dt, bc_x=1, bc_y=0)
+    oracle_params = dict(common, S=np.asarray(S, float), **d2v24_orbits(*v))
+    lib_params = dict(common, S=np.asarray(S, float), v=v[0], eta=v[1])
+    return dict(params=oracle_params, lib_params=lib_params, steps=steps, fields=f,
+                name="d2v24_detonation_nx%d" % nx)
+
+
+def d2v24_reactive2d(n=64, steps=20, T_ig=1.0, seed_offset=8, v=D2V24_DETONATION_V):
+    """2-D periodic reactive field of random Fourier modes (the recipe of reactive2d)
+    for D2V24: S_1..S_24 ~ U[1e4, 1e5], Q = 1, k = 2e4, dx = dy = 1e-3, dt = 5e-6."""
+    base = reactive2d(n=n, steps=steps, T_ig=T_ig, seed_offset=seed_offset)
+    rng = np.random.default_rng(SEED_BASE + seed_offset + 100)
+    S = rng.uniform(1e4, 1e5, 24)
+    common = dict(nx=n, ny=n, gamma=1.4, Q=1.0, omega1=2e4, omega2=0.0, T_ig=T_ig, dx=1e-3,
+                  dy=1e-3, dt=5e-6, bc_x=0, bc_y=0)
+    return dict(params=dict(common, S=S, **d2v24_orbits(*v)),
+                lib_params=dict(common, S=S, v=v[0], eta=v[1]), steps=steps,
+                fields=base["fields"], name="d2v24_reactive2d_%dx%d" % (n, n))
 
 
 def _modes(rng, nmodes, kmax):

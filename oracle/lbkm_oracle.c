@@ -36,11 +36,20 @@
  *      u^{n+1} = (u^n + E(E(u^n))) / 2, the two-stage SSP Runge-Kutta scheme.
  * TNE measures (Sec. VI, Eqs. (90)-(91)) are evaluated on a given state.
  *
+ * The same source builds two oracles. NV = 16 (default): the 16-velocity model in
+ * four orbits, chemical term in moment space as above. NV = 24 (-DNV=24): the
+ * paper's own D2V24 model (Eqs. (25)-(27): three groups of an axis and a diagonal
+ * orbit with speeds v_a, v_b, v_c and eta_a, eta_b, eta_c), all 24 rows m_1..m_24 of
+ * M and f_hat^eq_1..24 as listed after Eq. (16), and the chemical term taken
+ * literally in velocity space, Eq. (24):
+ *   C_i = f_i^eq Q [-(1+D) I T + I (v_i - u)^2 + eta_i^2] / (I (D+I) T^2) lambda',
+ * with f^eq = M^-1 f_hat^eq; step 7 becomes Omega = M^-1(-R_hat Delta + A_hat) + C.
+ *
  * Every reading taken where the paper is silent or inconsistent (sign of A,
  * the factor T in f_hat^eq_14/16, the integrator, the NND formula, ghost cells,
  * minmod tie-break) is listed in the design notes of the repository.
  *
- * Arrays: f is [16][ny][nx] (plane per velocity, row-major), lambda and the
+ * Arrays: f is [NV][ny][nx] (plane per velocity, row-major), lambda and the
  * macro fields are [ny][nx]. All FP64.
  */
 #include <math.h>
@@ -48,7 +57,12 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define NV 16 /* number of discrete velocities and of moments */
+#ifndef NV
+#define NV 16 /* number of discrete velocities and of moments: 16 or 24 */
+#endif
+#if NV != 16 && NV != 24
+#error "NV must be 16 or 24"
+#endif
 #define DIM 2 /* D, the spatial dimension */
 #define GH 2  /* ghost cells per side */
 
@@ -77,13 +91,16 @@ typedef struct {
 #define ORC_TNE_LEN (4 * NV + 2)
 
 /* ------------------------------------------------------------------ */
-/* Matrix M: rows m_1..m_16 of Sec. II (list after Eq. (16)).         */
+/* Matrix M: rows m_1..m_NV of Sec. II (list after Eq. (16)).         */
 /* ------------------------------------------------------------------ */
-void orc_build_M(const orc_params* p, double* M /* [16][16] */)
+void orc_build_M(const orc_params* p, double* M /* [NV][NV] */)
 {
     for (int i = 0; i < NV; i++) {
         double vx = p->vx[i], vy = p->vy[i];
         double w = vx * vx + vy * vy + p->eta[i] * p->eta[i]; /* v^2 + eta^2 */
+#if NV == 24
+        double e2 = p->eta[i] * p->eta[i], v2 = vx * vx + vy * vy;
+#endif
         double col[NV] = {
             1.0,             /* m1  */
             vx,              /* m2  */
@@ -101,6 +118,16 @@ void orc_build_M(const orc_params* p, double* M /* [16][16] */)
             w * vx * vx,     /* m14 */
             w * vx * vy,     /* m15 */
             w * vy * vy,     /* m16 */
+#if NV == 24
+            e2 * vx * vx,    /* m17 */
+            e2 * vx * vy,    /* m18 */
+            e2 * vy * vy,    /* m19 */
+            w * e2,          /* m20 */
+            w * v2 * vx,     /* m21 */
+            w * v2 * vy,     /* m22 */
+            w * e2 * vx,     /* m23 */
+            w * e2 * vy,     /* m24 */
+#endif
         };
         for (int k = 0; k < NV; k++) M[k * NV + i] = col[k];
     }
@@ -172,6 +199,19 @@ void orc_feq_moments(double rho, double ux, double uy, double T, double I, doubl
     out[13] = rho * A * T + rho * ux * ux * B;
     out[14] = rho * ux * uy * B;
     out[15] = rho * A * T + rho * uy * uy * B;
+#if NV == 24
+    /* f_hat^eq_17..24, the same list (moment relations Eqs. (12)-(15)) */
+    const double IT = I * T;
+    const double C = u2 * u2 + (D + 2.0) * (D + I + 4.0) * T * T + (2.0 * D + I + 8.0) * u2 * T;
+    out[16] = rho * IT * T + rho * ux * ux * IT;
+    out[17] = rho * ux * uy * IT;
+    out[18] = rho * IT * T + rho * uy * uy * IT;
+    out[19] = rho * IT * (u2 + (D + 3.0 * I) * T);
+    out[20] = rho * ux * C;
+    out[21] = rho * uy * C;
+    out[22] = rho * ux * IT * (u2 + (D + 3.0 * I + 2.0) * T);
+    out[23] = rho * uy * IT * (u2 + (D + 3.0 * I + 2.0) * T);
+#endif
 }
 
 /* d f_hat^eq_k / dT at fixed rho and u (the chemical term keeps rho and u
@@ -197,6 +237,17 @@ void orc_dfeq_dT(double rho, double ux, double uy, double T, double I, double* o
     out[13] = rho * dAT + rho * ux * ux * (D + I + 4.0);
     out[14] = rho * ux * uy * (D + I + 4.0);
     out[15] = rho * dAT + rho * uy * uy * (D + I + 4.0);
+#if NV == 24
+    const double dC = 2.0 * (D + 2.0) * (D + I + 4.0) * T + (2.0 * D + I + 8.0) * u2;
+    out[16] = 2.0 * rho * I * T + rho * ux * ux * I;
+    out[17] = rho * ux * uy * I;
+    out[18] = 2.0 * rho * I * T + rho * uy * uy * I;
+    out[19] = rho * I * (u2 + 2.0 * (D + 3.0 * I) * T);
+    out[20] = rho * ux * dC;
+    out[21] = rho * uy * dC;
+    out[22] = rho * ux * I * (u2 + 2.0 * (D + 3.0 * I + 2.0) * T);
+    out[23] = rho * uy * I * (u2 + 2.0 * (D + 3.0 * I + 2.0) * T);
+#endif
 }
 
 /* ------------------------------------------------------------------ */
@@ -316,8 +367,8 @@ void orc_macros(const orc_params* p, const double* M, const double* f, double* r
 
 /* TNE measures of a state (Sec. VI): Delta_k = f_hat_k - f_hat^eq_k (Eq. (90)),
  * Delta_1..4 = 0 exactly by conservation, d = sqrt(sum_k Delta_k^2) (Eq. (91)).
- * delta: [16][ny][nx] or NULL. rec: ORC_TNE_LEN doubles or NULL, laid out as
- * sum[16], abs_sum[16], min[16], max[16], d_sum, d2_sum with sums weighted by
+ * delta: [NV][ny][nx] or NULL. rec: ORC_TNE_LEN doubles or NULL, laid out as
+ * sum[NV], abs_sum[NV], min[NV], max[NV], d_sum, d2_sum with sums weighted by
  * dx*dy (min and max unweighted). */
 void orc_tne(const orc_params* p, const double* M, const double* f, double* delta, double* rec)
 {
@@ -502,12 +553,29 @@ int orc_step(const orc_params* p, const double* M, const double* Minv, const dou
                 dlam_chem = orc_reaction_increment(lam0, p->omega1 * pr, p->omega2 * pr, p->dt);
             double lam_rate = dlam_chem / p->dt; /* lambda' */
 
+            double Om_hat[NV], Om[NV];
+#if NV == 24
+            /* 6-7. collision in moment space, back to velocity space, plus the
+             * chemical term of Eq. (24) in velocity space on f^eq = M^-1 f_hat^eq */
+            (void)dfe;
+            for (int k = 0; k < NV; k++) Om_hat[k] = -p->S[k] * Delta[k] + Ahat[k];
+            for (int i = 0; i < NV; i++) {
+                double s = 0.0, fq = 0.0;
+                for (int k = 0; k < NV; k++) {
+                    s += Minv[i * NV + k] * Om_hat[k];
+                    fq += Minv[i * NV + k] * fe[k];
+                }
+                const double cx = p->vx[i] - ux, cy = p->vy[i] - uy;
+                const double shape = -(1.0 + D) * I * T + I * (cx * cx + cy * cy) +
+                                     p->eta[i] * p->eta[i];
+                Om[i] = s + fq * p->Q * shape / (I * (D + I) * T * T) * lam_rate;
+            }
+#else
             /* 6. chemical term in moment space */
             orc_dfeq_dT(rho, ux, uy, T, I, dfe);
             double dTdt = 2.0 * p->Q * lam_rate / (D + I);
 
             /* 7. collision in moment space, back to velocity space */
-            double Om_hat[NV], Om[NV];
             for (int k = 0; k < NV; k++)
                 Om_hat[k] = -p->S[k] * Delta[k] + Ahat[k] + dfe[k] * dTdt;
             for (int i = 0; i < NV; i++) {
@@ -515,6 +583,7 @@ int orc_step(const orc_params* p, const double* M, const double* Minv, const dou
                 for (int k = 0; k < NV; k++) s += Minv[i * NV + k] * Om_hat[k];
                 Om[i] = s;
             }
+#endif
 
             /* 8. NND flux differences and 10. forward Euler for each f_i */
             for (int i = 0; i < NV; i++) {

@@ -1,0 +1,1024 @@
+// d2v24.cu -- the paper's own 24-velocity model (D2V24, Sec. II Eqs. (25)-(27)):
+// kernels and the C ABI of include/lbkm24.h.
+//
+// The step is one fused kernel per time step, one thread per cell: the 24 f_i of
+// the cell and of its NND stencil (radius 2 in x and y) are read through the
+// read-only data cache, the conserved sums and rho, u, T are formed in FP64, the
+// 20 non-conserved moments, the relaxation, the back-transform and the chemical
+// term of Eq. (24) run in the storage type R (FP64 or FP32) with M and M^-1 as
+// kernel-parameter (constant-bank) operands, and the TNE partials of the state
+// being read are reduced per block in FP64 when due. A 82-block kernel then turns
+// the partials into one history record. The dense 24x24 transforms make this form
+// FP64- (or FP32-) arithmetic-bound; it is the paper-faithful model, not the
+// throughput path of the 16-velocity marching kernel.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "cell.cuh"
+#include "kernels.cuh"
+#include "lbkm24.h"
+
+namespace v24 {
+
+using lbk::DevCounters;
+using lbk::map_index;
+using lbk::nnd_neg;
+using lbk::nnd_pos;
+using lbk::reaction_increment;
+
+constexpr int NV = 24;
+constexpr int NP = NV + 1;       // planes: f_1..f_24, lambda
+constexpr int TK = NV - 4;       // non-conserved moments Delta_5..Delta_24
+constexpr int NQ = 4 * TK + 2;   // TNE quantities: sum, |sum|, min, max of each, d, d^2
+constexpr int BT = 128;          // threads per block
+constexpr int GRAPH_CHUNK = 32;  // even: a replay leaves the ping-pong index unchanged
+
+struct Record {
+    double sum[NV], abs_sum[NV], min[NV], max[NV];
+    double d_sum, d2_sum;
+    int64_t step;
+};
+static_assert(sizeof(Record) == sizeof(lbkm24_tne_global), "record layout");
+
+// Model constants, passed by value (constant bank). M is row-major [k][i]
+// (moment k of velocity i), Minv row-major [i][k].
+template <typename R>
+struct Model {
+    R M[NV * NV];
+    R Minv[NV * NV];
+    R vx[NV], vy[NV], eta2[NV], S[NV];
+    double vxd[NV], vyd[NV], wd[NV]; // FP64 copies for the conserved sums
+    double Minvd[NV * NV];           // FP64 M^-1 for the equilibrium start
+    double I, DI, Q, omega1, omega2, T_ig, A8c, A9c;
+    double dt, inv_dx, inv_dy;
+    int nx, ny, pitch, bc_x, bc_y, pad_;
+    int64_t plane;
+};
+
+struct Args {
+    const void* in;
+    void* out;
+    double* partials;  // [NQ][grid blocks]
+    DevCounters* ctr;
+    Record* hist;
+    int hist_cap;
+    int tne_every;
+    double area;       // dx * dy
+};
+
+__device__ __forceinline__ double tcomb(int kind, double a, double b)
+{
+    return kind == 0 ? a + b : (kind == 1 ? fmin(a, b) : fmax(a, b));
+}
+// quantity q: [0, TK) sum, [TK, 2TK) |.| sum, [2TK, 3TK) min, [3TK, 4TK) max, 4TK d, 4TK+1 d^2
+__host__ __device__ __forceinline__ int tkind(int q)
+{
+    return (q < 2 * TK || q >= 4 * TK) ? 0 : (q < 3 * TK ? 1 : 2);
+}
+
+// rho, u_x, u_y (FP64) at cell (x, y) of state `in`, boundary conditions applied
+template <typename R>
+__device__ __forceinline__ void conserved_at(const Model<R>& K, const R* __restrict__ in, int x,
+                                             int y, double& rho, double& ux, double& uy,
+                                             double* E = nullptr)
+{
+    x = map_index(x, K.nx, K.bc_x == 0 ? 0 : 1);
+    y = map_index(y, K.ny, K.bc_y == 0 ? 0 : 1);
+    const R* p = in + (size_t)y * K.pitch + x;
+    double r = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
+#pragma unroll
+    for (int i = 0; i < NV; i++) {
+        const double f = (double)__ldg(p + (size_t)i * K.plane);
+        r += f;
+        jx = fma(K.vxd[i], f, jx);
+        jy = fma(K.vyd[i], f, jy);
+        if (E) e = fma(K.wd[i], f, e);
+    }
+    rho = r;
+    ux = jx / r;
+    uy = jy / r;
+    if (E) *E = e;
+}
+
+// f_hat^eq_1..24 (list after Eq. (16); entries 14 and 16 with the factor T of Eq. (11))
+__device__ __forceinline__ void feq24(double I, double DI, double rho, double ux, double uy,
+                                      double T, double* q)
+{
+    const double u2 = ux * ux + uy * uy;
+    const double A = (DI + 2.0) * T + u2, B = (DI + 4.0) * T + u2;
+    const double rx = rho * ux, ry = rho * uy, IT = I * T;
+    const double C = u2 * u2 + 4.0 * (DI + 4.0) * T * T + (DI + 10.0) * u2 * T; // D = 2
+    q[0] = rho;
+    q[1] = rx;
+    q[2] = ry;
+    q[3] = rho * (DI * T + u2);
+    q[4] = rho * (T + ux * ux);
+    q[5] = rx * uy;
+    q[6] = rho * (T + uy * uy);
+    q[7] = rx * A;
+    q[8] = ry * A;
+    q[9] = rx * (3.0 * T + ux * ux);
+    q[10] = ry * (T + ux * ux);
+    q[11] = rx * (T + uy * uy);
+    q[12] = ry * (3.0 * T + uy * uy);
+    q[13] = rho * A * T + rx * ux * B;
+    q[14] = rx * uy * B;
+    q[15] = rho * A * T + ry * uy * B;
+    q[16] = rho * IT * (T + ux * ux);
+    q[17] = rx * uy * IT;
+    q[18] = rho * IT * (T + uy * uy);
+    q[19] = rho * IT * (u2 + (2.0 + 3.0 * I) * T);
+    q[20] = rx * C;
+    q[21] = ry * C;
+    q[22] = rx * IT * (u2 + (4.0 + 3.0 * I) * T);
+    q[23] = ry * IT * (u2 + (4.0 + 3.0 * I) * T);
+}
+
+// Block reduction of the TNE quantities of this thread's cell into partials
+// [q * nblocks + b] (warps by shuffle tree, then warps in order: deterministic).
+template <typename R>
+__device__ __forceinline__ void block_tne(const R* Dk, bool active, double* partials, int nblocks,
+                                          int b)
+{
+    __shared__ double red[BT / 32][NQ];
+    const int t = threadIdx.x + threadIdx.y * blockDim.x, lane = t & 31, w = t >> 5;
+    double d2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < TK; k++) d2 += active ? (double)Dk[k] * (double)Dk[k] : 0.0;
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        const int kind = tkind(q);
+        double v;
+        if (q < TK) v = active ? (double)Dk[q] : 0.0;
+        else if (q < 2 * TK) v = active ? fabs((double)Dk[q - TK]) : 0.0;
+        else if (q < 3 * TK) v = active ? (double)Dk[q - 2 * TK] : DBL_MAX;
+        else if (q < 4 * TK) v = active ? (double)Dk[q - 3 * TK] : -DBL_MAX;
+        else if (q == 4 * TK) v = active ? sqrt(d2) : 0.0;
+        else v = d2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = tcomb(kind, v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) red[w][q] = v;
+    }
+    __syncthreads();
+    for (int q = t; q < NQ; q += BT) {
+        double v = red[0][q];
+        for (int k = 1; k < BT / 32; k++) v = tcomb(tkind(q), v, red[k][q]);
+        partials[(size_t)q * nblocks + b] = v;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool active = x < K.nx && y < K.ny;
+    const int64_t step = a.ctr->step;
+    const bool do_tne = a.tne_every > 0 && (step % a.tne_every) == 0;
+    const R* __restrict__ in = static_cast<const R*>(a.in);
+    R* __restrict__ out = static_cast<R*>(a.out);
+    R Dk[TK];
+    bool bad = false;
+    if (active) {
+        const size_t g = (size_t)y * K.pitch + x;
+        R f[NV];
+#pragma unroll
+        for (int i = 0; i < NV; i++) f[i] = __ldg(in + (size_t)i * K.plane + g);
+        const R lam0 = __ldg(in + (size_t)NV * K.plane + g);
+
+        // 1. conserved sums and macros in FP64 (Eqs. (5)-(7))
+        double rho, ux, uy, E;
+        conserved_at(K, in, x, y, rho, ux, uy, &E);
+        const double T = (E / rho - (ux * ux + uy * uy)) / K.DI;
+        bad = !(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T);
+
+        // 2. velocity gradients, second-order central differences
+        double uxe, uye, uxw, uyw, r_;
+        conserved_at(K, in, x + 1, y, r_, uxe, uye);
+        conserved_at(K, in, x - 1, y, r_, uxw, uyw);
+        const double dux_dx = (uxe - uxw) * 0.5 * K.inv_dx, duy_dx = (uye - uyw) * 0.5 * K.inv_dx;
+        double dux_dy = 0.0, duy_dy = 0.0;
+        if (K.ny > 1) {
+            double uxn, uyn, uxs, uys;
+            conserved_at(K, in, x, y + 1, r_, uxn, uyn);
+            conserved_at(K, in, x, y - 1, r_, uxs, uys);
+            dux_dy = (uxn - uxs) * 0.5 * K.inv_dy;
+            duy_dy = (uyn - uys) * 0.5 * K.inv_dy;
+        }
+        const double th = (dux_dx + duy_dy) / K.DI;
+        const double pT = rho * T;
+
+        // 3. moments, equilibrium moments, non-equilibrium parts
+        double q[NV];
+        feq24(K.I, K.DI, rho, ux, uy, T, q);
+#pragma unroll
+        for (int k = 0; k < TK; k++) {
+            R m = R(0);
+#pragma unroll
+            for (int i = 0; i < NV; i++) m = fma(K.M[(k + 4) * NV + i], f[i], m);
+            Dk[k] = m - (R)q[k + 4];
+        }
+
+        // 4. relaxation with A_hat_8, A_hat_9 (Eqs. (3)-(4), sign as in Eq. (29))
+        R Om_hat[TK];
+#pragma unroll
+        for (int k = 0; k < TK; k++) Om_hat[k] = -K.S[k + 4] * Dk[k];
+        Om_hat[3] += (R)(pT * K.A8c * (4.0 * ux * (dux_dx - th) + 2.0 * uy * (duy_dx + dux_dy)));
+        Om_hat[4] += (R)(pT * K.A9c * (4.0 * uy * (duy_dy - th) + 2.0 * ux * (duy_dx + dux_dy)));
+
+        // 5. reaction over dt with p and T frozen at t_n (Eq. (28), m = n = 1)
+        double dlam = 0.0;
+        if (T > K.T_ig)
+            dlam = reaction_increment<double>((double)lam0, K.omega1 * pT, K.omega2 * pT, K.dt);
+        const double lrate = dlam / K.dt;
+
+        // 6. back-transform, chemical term of Eq. (24), NND advection, forward Euler
+        const bool react = lrate != 0.0;
+        R qr[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) qr[k] = (R)q[k];
+        const R chem = (R)(K.Q * lrate / (K.I * K.DI * T * T));
+        const R base = (R)(-(1.0 + 2.0) * K.I * T);
+        const R uxr = (R)ux, uyr = (R)uy, Ir = (R)K.I;
+        const int xm2 = map_index(x - 2, K.nx, K.bc_x == 0 ? 0 : 1);
+        const int xm1 = map_index(x - 1, K.nx, K.bc_x == 0 ? 0 : 1);
+        const int xp1 = map_index(x + 1, K.nx, K.bc_x == 0 ? 0 : 1);
+        const int xp2 = map_index(x + 2, K.nx, K.bc_x == 0 ? 0 : 1);
+        const int by = K.bc_y == 0 ? 0 : 1;
+        const size_t row = (size_t)y * K.pitch;
+        const size_t ym2 = (size_t)map_index(y - 2, K.ny, by) * K.pitch;
+        const size_t ym1 = (size_t)map_index(y - 1, K.ny, by) * K.pitch;
+        const size_t yp1 = (size_t)map_index(y + 1, K.ny, by) * K.pitch;
+        const size_t yp2 = (size_t)map_index(y + 2, K.ny, by) * K.pitch;
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+            R om = R(0);
+#pragma unroll
+            for (int k = 0; k < TK; k++) om = fma(K.Minv[i * NV + k + 4], Om_hat[k], om);
+            if (react) {
+                R fe = R(0);
+#pragma unroll
+                for (int k = 0; k < NV; k++) fe = fma(K.Minv[i * NV + k], qr[k], fe);
+                const R cx = K.vx[i] - uxr, cy = K.vy[i] - uyr;
+                om += fe * chem * (base + Ir * (cx * cx + cy * cy) + K.eta2[i]);
+            }
+            const R* pl = in + (size_t)i * K.plane;
+            R adv = R(0);
+            if (K.vx[i] > R(0))
+                adv = K.vx[i] * K.inv_dx *
+                      nnd_pos(__ldg(pl + row + xm2), __ldg(pl + row + xm1), f[i], __ldg(pl + row + xp1));
+            else if (K.vx[i] < R(0))
+                adv = K.vx[i] * K.inv_dx *
+                      nnd_neg(__ldg(pl + row + xm1), f[i], __ldg(pl + row + xp1), __ldg(pl + row + xp2));
+            if (K.ny > 1) {
+                if (K.vy[i] > R(0))
+                    adv += K.vy[i] * K.inv_dy *
+                           nnd_pos(__ldg(pl + ym2 + x), __ldg(pl + ym1 + x), f[i], __ldg(pl + yp1 + x));
+                else if (K.vy[i] < R(0))
+                    adv += K.vy[i] * K.inv_dy *
+                           nnd_neg(__ldg(pl + ym1 + x), f[i], __ldg(pl + yp1 + x), __ldg(pl + yp2 + x));
+            }
+            out[(size_t)i * K.plane + g] = f[i] + (R)K.dt * (om - adv);
+        }
+
+        // 7. lambda: u . grad(lambda) with NND interface values, then the update
+        const R* pl = in + (size_t)NV * K.plane;
+        R la = R(0);
+        if (uxr > R(0))
+            la = uxr * (R)K.inv_dx *
+                 nnd_pos(__ldg(pl + row + xm2), __ldg(pl + row + xm1), lam0, __ldg(pl + row + xp1));
+        else if (uxr < R(0))
+            la = uxr * (R)K.inv_dx *
+                 nnd_neg(__ldg(pl + row + xm1), lam0, __ldg(pl + row + xp1), __ldg(pl + row + xp2));
+        if (K.ny > 1) {
+            if (uyr > R(0))
+                la += uyr * (R)K.inv_dy *
+                      nnd_pos(__ldg(pl + ym2 + x), __ldg(pl + ym1 + x), lam0, __ldg(pl + yp1 + x));
+            else if (uyr < R(0))
+                la += uyr * (R)K.inv_dy *
+                      nnd_neg(__ldg(pl + ym1 + x), lam0, __ldg(pl + yp1 + x), __ldg(pl + yp2 + x));
+        }
+        R ln = lam0 - (R)K.dt * la + (R)dlam;
+        ln = ln < R(0) ? R(0) : (ln > R(1) ? R(1) : ln);
+        out[(size_t)NV * K.plane + g] = ln;
+    } else {
+#pragma unroll
+        for (int k = 0; k < TK; k++) Dk[k] = R(0);
+    }
+
+    // TNE partials of the state read (all threads take part), status, step counter
+    const int t = threadIdx.x + threadIdx.y * blockDim.x;
+    const int b = blockIdx.x + blockIdx.y * gridDim.x, nb = gridDim.x * gridDim.y;
+    if (do_tne) block_tne(Dk, active, a.partials, nb, b);
+    if (__syncthreads_or(bad) && t == 0) atomicOr(&a.ctr->status, 1);
+    __shared__ unsigned int s_last;
+    if (t == 0) s_last = (atomicAdd(&a.ctr->arrivals, 1u) == (unsigned)nb - 1) ? 1u : 0u;
+    __syncthreads();
+    if (s_last && t == 0) {
+        if (do_tne) {
+            a.ctr->hist_count += 1;
+            a.ctr->tne_step = step;
+        }
+        a.ctr->tne_pending = do_tne ? 1 : 0;
+        a.ctr->step = step + 1;
+        a.ctr->arrivals = 0u;
+    }
+}
+
+// TNE of a state on demand: Delta fields (optional) and block partials.
+template <typename R>
+__global__ void __launch_bounds__(BT) tne_kernel(const Model<R> K, const R* __restrict__ in,
+                                                 double* delta, double* partials)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool active = x < K.nx && y < K.ny;
+    R Dk[TK];
+#pragma unroll
+    for (int k = 0; k < TK; k++) Dk[k] = R(0);
+    if (active) {
+        const size_t g = (size_t)y * K.pitch + x;
+        double rho, ux, uy, E;
+        conserved_at(K, in, x, y, rho, ux, uy, &E);
+        const double T = (E / rho - (ux * ux + uy * uy)) / K.DI;
+        double q[NV];
+        feq24(K.I, K.DI, rho, ux, uy, T, q);
+        R f[NV];
+#pragma unroll
+        for (int i = 0; i < NV; i++) f[i] = __ldg(in + (size_t)i * K.plane + g);
+#pragma unroll
+        for (int k = 0; k < TK; k++) {
+            R m = R(0);
+#pragma unroll
+            for (int i = 0; i < NV; i++) m = fma(K.M[(k + 4) * NV + i], f[i], m);
+            Dk[k] = m - (R)q[k + 4];
+        }
+        if (delta) {
+            const size_t n = (size_t)K.nx * K.ny, c = (size_t)y * K.nx + x;
+#pragma unroll
+            for (int k = 0; k < NV; k++) delta[k * n + c] = k < 4 ? 0.0 : (double)Dk[k - 4];
+        }
+    }
+    block_tne(Dk, active, partials, gridDim.x * gridDim.y, blockIdx.x + blockIdx.y * gridDim.x);
+}
+
+// Record of a grid's partials: block q reduces quantity q in a fixed order.
+// rec == nullptr: the step's record, into history slot (hist_count - 1) % cap,
+// only when the step left partials (ctr->tne_pending).
+__global__ void __launch_bounds__(256)
+    finish_kernel(const double* __restrict__ partials, int nblocks, Record* hist, int hist_cap,
+                  const DevCounters* ctr, Record* rec_out, double area)
+{
+    if (!rec_out && !ctr->tne_pending) return;
+    __shared__ double wsum[8];
+    const int q = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int kind = tkind(q);
+    double acc = kind == 0 ? 0.0 : (kind == 1 ? DBL_MAX : -DBL_MAX);
+    const double* pq = partials + (size_t)q * nblocks;
+    for (int b = t; b < nblocks; b += 256) acc = tcomb(kind, acc, __ldcg(pq + b));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = tcomb(kind, acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (lane == 0) wsum[w] = acc;
+    __syncthreads();
+    if (t != 0) return;
+    for (int k = 1; k < 8; k++) acc = tcomb(kind, acc, wsum[k]);
+    Record* rec = rec_out ? rec_out : hist + (ctr->hist_count - 1) % hist_cap;
+    if (q < TK) rec->sum[q + 4] = acc * area;
+    else if (q < 2 * TK) rec->abs_sum[q - TK + 4] = acc * area;
+    else if (q < 3 * TK) rec->min[q - 2 * TK + 4] = acc;
+    else if (q < 4 * TK) rec->max[q - 3 * TK + 4] = acc;
+    else if (q == 4 * TK) rec->d_sum = acc * area;
+    else rec->d2_sum = acc * area;
+    if (q == 0) {
+        for (int k = 0; k < 4; k++) rec->sum[k] = rec->abs_sum[k] = rec->min[k] = rec->max[k] = 0.0;
+        rec->step = rec_out ? ctr->step : ctr->tne_step;
+    }
+}
+
+template <typename R>
+__global__ void init_kernel(const Model<R> K, const double* rho, const double* ux,
+                            const double* uy, const double* T, const double* lam, R* state)
+{
+    const int64_t n = (int64_t)K.nx * K.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(c % K.nx), y = (int)(c / K.nx);
+        double q[NV];
+        feq24(K.I, K.DI, rho[c], ux[c], uy[c], T[c], q);
+        const size_t g = (size_t)y * K.pitch + x;
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < NV; k++) s = fma(K.Minvd[i * NV + k], q[k], s);
+            state[(size_t)i * K.plane + g] = (R)s;
+        }
+        state[(size_t)NV * K.plane + g] = lam ? (R)lam[c] : R(0);
+    }
+}
+
+template <typename R>
+__global__ void macros_kernel(const Model<R> K, const R* __restrict__ in, double* rho,
+                              double* ux, double* uy, double* T, double* p, double* lam)
+{
+    const int64_t n = (int64_t)K.nx * K.ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(c % K.nx), y = (int)(c / K.nx);
+        double r, u, v, E;
+        conserved_at(K, in, x, y, r, u, v, &E);
+        const double t = (E / r - (u * u + v * v)) / K.DI;
+        if (rho) rho[c] = r;
+        if (ux) ux[c] = u;
+        if (uy) uy[c] = v;
+        if (T) T[c] = t;
+        if (p) p[c] = r * t;
+        if (lam) lam[c] = (double)in[(size_t)NV * K.plane + (size_t)y * K.pitch + x];
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+// velocities of the paper's D2V24 (Eqs. (25)-(27))
+void velocity_table(const double v[3], const double eta[3], double* vx, double* vy, double* e)
+{
+    static const int AX[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+    static const int DG[4][2] = {{1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+    for (int g = 0; g < 3; g++)
+        for (int o = 0; o < 2; o++)
+            for (int j = 0; j < 4; j++) {
+                const int i = 8 * g + 4 * o + j;
+                vx[i] = v[g] * (o == 0 ? AX[j][0] : DG[j][0]);
+                vy[i] = v[g] * (o == 0 ? AX[j][1] : DG[j][1]);
+                e[i] = eta[g];
+            }
+}
+
+// rows m_1..m_24 (list after Eq. (16)) at the discrete velocities
+void moment_rows(const double* vx, const double* vy, const double* e, double* M)
+{
+    for (int i = 0; i < NV; i++) {
+        const double a = vx[i], b = vy[i], e2 = e[i] * e[i], v2 = a * a + b * b, w = v2 + e2;
+        const double col[NV] = {1.0,       a,         b,         w,         a * a,
+                                a * b,     b * b,     w * a,     w * b,     a * a * a,
+                                a * a * b, a * b * b, b * b * b, w * a * a, w * a * b,
+                                w * b * b, e2 * a * a, e2 * a * b, e2 * b * b, w * e2,
+                                w * v2 * a, w * v2 * b, w * e2 * a, w * e2 * b};
+        for (int k = 0; k < NV; k++) M[k * NV + i] = col[k];
+    }
+}
+
+// M^-1 by LU factorisation with partial pivoting in long double, one step of
+// iterative refinement per column. Returns max |M Minv - 1|, or -1 if singular.
+double invert(const double* M, double* Minv)
+{
+    long double lu[NV][NV];
+    int perm[NV];
+    long double amax = 0;
+    for (int r = 0; r < NV; r++) {
+        perm[r] = r;
+        for (int c = 0; c < NV; c++) {
+            lu[r][c] = M[r * NV + c];
+            amax = fmaxl(amax, fabsl(lu[r][c]));
+        }
+    }
+    for (int k = 0; k < NV; k++) {
+        int p = k;
+        for (int r = k + 1; r < NV; r++)
+            if (fabsl(lu[r][k]) > fabsl(lu[p][k])) p = r;
+        if (fabsl(lu[p][k]) < 1e-13L * amax) return -1.0;
+        if (p != k) {
+            for (int c = 0; c < NV; c++) {
+                long double t = lu[k][c];
+                lu[k][c] = lu[p][c];
+                lu[p][c] = t;
+            }
+            int t = perm[k];
+            perm[k] = perm[p];
+            perm[p] = t;
+        }
+        for (int r = k + 1; r < NV; r++) {
+            lu[r][k] /= lu[k][k];
+            for (int c = k + 1; c < NV; c++) lu[r][c] -= lu[r][k] * lu[k][c];
+        }
+    }
+    auto solve = [&](const long double* rhs, long double* x) {
+        long double z[NV];
+        for (int r = 0; r < NV; r++) {
+            long double s = rhs[perm[r]];
+            for (int c = 0; c < r; c++) s -= lu[r][c] * z[c];
+            z[r] = s;
+        }
+        for (int r = NV - 1; r >= 0; r--) {
+            long double s = z[r];
+            for (int c = r + 1; c < NV; c++) s -= lu[r][c] * x[c];
+            x[r] = s / lu[r][r];
+        }
+    };
+    for (int col = 0; col < NV; col++) {
+        long double e[NV], x[NV], res[NV], dx[NV];
+        for (int r = 0; r < NV; r++) e[r] = r == col ? 1.0L : 0.0L;
+        solve(e, x);
+        for (int r = 0; r < NV; r++) {
+            long double s = e[r];
+            for (int c = 0; c < NV; c++) s -= (long double)M[r * NV + c] * x[c];
+            res[r] = s;
+        }
+        solve(res, dx);
+        for (int r = 0; r < NV; r++) Minv[r * NV + col] = (double)(x[r] + dx[r]);
+    }
+    double worst = 0.0;
+    for (int r = 0; r < NV; r++)
+        for (int c = 0; c < NV; c++) {
+            long double s = 0;
+            for (int k = 0; k < NV; k++) s += (long double)M[r * NV + k] * Minv[k * NV + c];
+            worst = fmax(worst, fabs((double)(s - (r == c ? 1.0L : 0.0L))));
+        }
+    return worst;
+}
+
+template <typename R>
+void fill_model(const lbkm24_params& p, const double* M, const double* Minv, const double* vx,
+                const double* vy, const double* e, int pitch, Model<R>* K)
+{
+    memset(K, 0, sizeof(*K));
+    for (int k = 0; k < NV * NV; k++) {
+        K->M[k] = (R)M[k];
+        K->Minv[k] = (R)Minv[k];
+        K->Minvd[k] = Minv[k];
+    }
+    for (int i = 0; i < NV; i++) {
+        K->vx[i] = (R)vx[i];
+        K->vy[i] = (R)vy[i];
+        K->eta2[i] = (R)(e[i] * e[i]);
+        K->S[i] = (R)p.S[i];
+        K->vxd[i] = vx[i];
+        K->vyd[i] = vy[i];
+        K->wd[i] = vx[i] * vx[i] + vy[i] * vy[i] + e[i] * e[i];
+    }
+    K->I = 2.0 / (p.gamma - 1.0) - 2.0;
+    K->DI = 2.0 + K->I;
+    K->Q = p.Q;
+    K->omega1 = p.omega1;
+    K->omega2 = p.omega2;
+    K->T_ig = p.T_ig;
+    K->A8c = (p.S[4] - p.S[7]) / p.S[4];
+    K->A9c = (p.S[6] - p.S[8]) / p.S[6];
+    K->dt = p.dt;
+    K->inv_dx = 1.0 / p.dx;
+    K->inv_dy = 1.0 / p.dy;
+    K->nx = p.nx;
+    K->ny = p.ny;
+    K->pitch = pitch;
+    K->bc_x = p.bc_x;
+    K->bc_y = p.bc_y;
+    K->plane = (int64_t)pitch * p.ny;
+}
+
+thread_local std::string g_create_error;
+
+} // namespace v24
+
+using namespace v24;
+
+struct lbkm24 {
+    lbkm24_params p;
+    Model<double> Kd;
+    Model<float> Kf;
+    int pitch;
+    size_t elem, plane_elems;
+    cudaStream_t stream, capture_stream;
+    void* buf[2];
+    int cur;
+    double* partials;
+    int nblocks;
+    dim3 grid, block;
+    DevCounters* ctr;
+    Record* hist;
+    Record* tne_out;
+    bool initialized;
+    int64_t host_steps;
+    cudaGraphExec_t graph[2];
+    std::string err;
+};
+
+namespace {
+
+lbkm_status fail(lbkm24_t h, lbkm_status st, const char* fmt, ...)
+{
+    char b[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b, sizeof(b), fmt, ap);
+    va_end(ap);
+    (h ? h->err : g_create_error) = b;
+    return st;
+}
+
+#define TRY24(h, call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? LBKM_ENOMEM : LBKM_ECUDA,      \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+cudaError_t launch_one_step(const lbkm24* h, int from, cudaStream_t st)
+{
+    Args a;
+    a.in = h->buf[from];
+    a.out = h->buf[1 - from];
+    a.partials = h->partials;
+    a.ctr = h->ctr;
+    a.hist = h->hist;
+    a.hist_cap = h->p.tne_capacity;
+    a.tne_every = h->p.tne_every;
+    a.area = h->p.dx * h->p.dy;
+    if (h->p.precision == LBKM_F64)
+        step_kernel<double><<<h->grid, h->block, 0, st>>>(h->Kd, a);
+    else
+        step_kernel<float><<<h->grid, h->block, 0, st>>>(h->Kf, a);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && h->p.tne_every > 0) {
+        finish_kernel<<<NQ, 256, 0, st>>>(h->partials, h->nblocks, h->hist, h->p.tne_capacity,
+                                          h->ctr, nullptr, a.area);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+int elementwise_blocks(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+lbkm_status check(lbkm24_t h)
+{
+    TRY24(h, cudaStreamSynchronize(h->stream));
+    int st = 0;
+    TRY24(h, cudaMemcpy(&st, &h->ctr->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & 1)
+        return fail(h, LBKM_EUNSTABLE,
+                    "a cell reached a non-finite or non-positive density or temperature");
+    return LBKM_OK;
+}
+
+void to_global(const Record& r, lbkm24_tne_global* g) { memcpy(g, &r, sizeof(r)); }
+
+} // namespace
+
+extern "C" {
+
+void lbkm24_default_params(lbkm24_params* p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->precision = LBKM_F64;
+    p->gamma = 1.4;
+    p->v[0] = 2.7;
+    p->v[1] = 2.2;
+    p->v[2] = 1.2;
+    p->eta[0] = 5.0;
+    p->eta[1] = 3.0;
+    p->eta[2] = 1.1;
+    for (int k = 0; k < NV; k++) p->S[k] = (k >= 4 && k <= 6) ? 1e4 : 1e5;
+    p->Q = 1.0;
+    p->T_ig = 1.1;
+    p->dx = p->dy = 2e-4;
+    p->dt = 5e-6;
+    p->bc_x = LBKM_BC_ZERO_GRADIENT;
+    p->bc_y = LBKM_BC_PERIODIC;
+    p->tne_capacity = 1;
+}
+
+const char* lbkm24_last_error(lbkm24_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t* out)
+{
+    if (!out) return fail(nullptr, LBKM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!pin) return fail(nullptr, LBKM_EINVAL, "params is NULL");
+    const lbkm24_params& p = *pin;
+    if (p.nx < 1 || p.ny < 1 || (int64_t)p.nx * p.ny > (int64_t)1 << 30)
+        return fail(nullptr, LBKM_EINVAL, "nx, ny must be >= 1 (at most 2^30 cells)");
+    if (p.precision != LBKM_F64 && p.precision != LBKM_F32)
+        return fail(nullptr, LBKM_EINVAL, "precision must be LBKM_F64 or LBKM_F32");
+    if (!(p.gamma > 1.0) || !(2.0 / (p.gamma - 1.0) - 2.0 > 0.0))
+        return fail(nullptr, LBKM_EINVAL, "gamma must give I = 2/(gamma-1) - 2 > 0");
+    for (int g = 0; g < 3; g++) {
+        if (!(p.v[g] > 0.0) || !isfinite(p.v[g]))
+            return fail(nullptr, LBKM_EINVAL, "v[%d] must be finite and > 0", g);
+        if (!(p.eta[g] >= 0.0) || !isfinite(p.eta[g]))
+            return fail(nullptr, LBKM_EINVAL, "eta[%d] must be finite and >= 0", g);
+    }
+    double smax = 0.0;
+    for (int k = 4; k < NV; k++) {
+        if (!(p.S[k] > 0.0) || !isfinite(p.S[k]))
+            return fail(nullptr, LBKM_EINVAL, "S[%d] must be finite and > 0", k);
+        smax = fmax(smax, p.S[k]);
+    }
+    if (!(p.dx > 0) || !(p.dy > 0) || !(p.dt > 0))
+        return fail(nullptr, LBKM_EINVAL, "dx, dy, dt must be > 0");
+    if (!(p.dt * smax < 2.0))
+        return fail(nullptr, LBKM_EINVAL, "dt * max S = %g must be < 2", p.dt * smax);
+    const double vmax = fmax(p.v[0], fmax(p.v[1], p.v[2])); // per-axis component of the diagonals
+    const double cfl = vmax * p.dt * (1.0 / p.dx + (p.ny > 1 ? 1.0 / p.dy : 0.0));
+    if (!(cfl <= 1.0))
+        return fail(nullptr, LBKM_EINVAL, "CFL number %g of the fastest velocity exceeds 1", cfl);
+    if (!(p.omega1 >= 0) || !(p.omega2 >= 0) || !isfinite(p.Q))
+        return fail(nullptr, LBKM_EINVAL, "omega1, omega2 must be >= 0 and Q finite");
+    if (!(p.T_ig >= 0) || !isfinite(p.T_ig))
+        return fail(nullptr, LBKM_EINVAL, "T_ig must be finite and >= 0");
+    for (int d = 0; d < 2; d++) {
+        const int bc = d == 0 ? p.bc_x : p.bc_y;
+        if (bc != LBKM_BC_PERIODIC && bc != LBKM_BC_ZERO_GRADIENT)
+            return fail(nullptr, LBKM_EINVAL, "%s must be periodic or zero gradient",
+                        d == 0 ? "bc_x" : "bc_y");
+    }
+    if (p.tne_every < 0 || (p.tne_every > 0 && p.tne_capacity < 1))
+        return fail(nullptr, LBKM_EINVAL, "tne_every >= 0 and tne_capacity >= 1");
+
+    double vx[NV], vy[NV], e[NV], M[NV * NV], Minv[NV * NV];
+    velocity_table(p.v, p.eta, vx, vy, e);
+    moment_rows(vx, vy, e, M);
+    const double res = invert(M, Minv);
+    if (res < 0.0 || res > 1e-9)
+        return fail(nullptr, LBKM_ESINGULAR, "the D2V24 velocity set gives a singular M");
+
+    lbkm24* h = new lbkm24();
+    h->p = p;
+    if (h->p.tne_capacity < 1) h->p.tne_capacity = 1;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->elem = p.precision == LBKM_F64 ? 8 : 4;
+    h->pitch = (p.nx + 31) / 32 * 32;
+    h->plane_elems = (size_t)h->pitch * p.ny;
+    fill_model(p, M, Minv, vx, vy, e, h->pitch, &h->Kd);
+    fill_model(p, M, Minv, vx, vy, e, h->pitch, &h->Kf);
+    h->block = p.ny > 1 ? dim3(32, BT / 32) : dim3(BT, 1);
+    h->grid = dim3((p.nx + h->block.x - 1) / h->block.x, (p.ny + h->block.y - 1) / h->block.y);
+    h->nblocks = (int)(h->grid.x * h->grid.y);
+    auto bail = [&](cudaError_t ce, const char* what) {
+        lbkm24_destroy(h);
+        return fail(nullptr, ce == cudaErrorMemoryAllocation ? LBKM_ENOMEM : LBKM_ECUDA, "%s: %s",
+                    what, cudaGetErrorString(ce));
+    };
+    cudaError_t ce;
+    const size_t sb = (size_t)NP * h->plane_elems * h->elem;
+    for (int k = 0; k < 2; k++)
+        if ((ce = cudaMalloc(&h->buf[k], sb)) != cudaSuccess) return bail(ce, "state");
+    if ((ce = cudaMalloc((void**)&h->partials, sizeof(double) * NQ * h->nblocks)) != cudaSuccess)
+        return bail(ce, "partials");
+    if ((ce = cudaMalloc((void**)&h->ctr, sizeof(DevCounters))) != cudaSuccess)
+        return bail(ce, "counters");
+    if ((ce = cudaMalloc((void**)&h->hist, sizeof(Record) * h->p.tne_capacity)) != cudaSuccess)
+        return bail(ce, "history");
+    if ((ce = cudaMalloc((void**)&h->tne_out, sizeof(Record))) != cudaSuccess)
+        return bail(ce, "record");
+    if ((ce = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(ce, "capture stream");
+    if ((ce = cudaMemset(h->buf[0], 0, sb)) != cudaSuccess ||
+        (ce = cudaMemset(h->buf[1], 0, sb)) != cudaSuccess ||
+        (ce = cudaMemset(h->ctr, 0, sizeof(DevCounters))) != cudaSuccess)
+        return bail(ce, "clear");
+    *out = h;
+    return LBKM_OK;
+}
+
+void lbkm24_destroy(lbkm24_t h)
+{
+    if (!h) return;
+    if (h->stream || h->buf[0]) cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < 2; i++) {
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+        if (h->buf[i]) cudaFree(h->buf[i]);
+    }
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    if (h->partials) cudaFree(h->partials);
+    if (h->ctr) cudaFree(h->ctr);
+    if (h->hist) cudaFree(h->hist);
+    if (h->tne_out) cudaFree(h->tne_out);
+    delete h;
+}
+
+lbkm_status lbkm24_init_fields(lbkm24_t h, const double* rho, const double* ux, const double* uy,
+                               const double* T, const double* lambda, int on_device)
+{
+    if (!h) return LBKM_EINVAL;
+    if (!rho || !ux || !uy || !T) return fail(h, LBKM_EINVAL, "rho, ux, uy and T are required");
+    const size_t n = (size_t)h->p.nx * h->p.ny, nb = n * sizeof(double);
+    const double* src[5] = {rho, ux, uy, T, lambda};
+    const double* dev[5] = {rho, ux, uy, T, lambda};
+    double* tmp = nullptr;
+    if (!on_device) {
+        TRY24(h, cudaMallocAsync((void**)&tmp, nb * 5, h->stream));
+        for (int k = 0; k < 5; k++) {
+            if (!src[k]) {
+                dev[k] = nullptr;
+                continue;
+            }
+            TRY24(h, cudaMemcpyAsync(tmp + k * n, src[k], nb, cudaMemcpyHostToDevice, h->stream));
+            dev[k] = tmp + k * n;
+        }
+    }
+    const int g = elementwise_blocks((int64_t)n);
+    if (h->p.precision == LBKM_F64)
+        init_kernel<double><<<g, 256, 0, h->stream>>>(h->Kd, dev[0], dev[1], dev[2], dev[3],
+                                                      dev[4], (double*)h->buf[0]);
+    else
+        init_kernel<float><<<g, 256, 0, h->stream>>>(h->Kf, dev[0], dev[1], dev[2], dev[3],
+                                                     dev[4], (float*)h->buf[0]);
+    TRY24(h, cudaGetLastError());
+    h->cur = 0;
+    TRY24(h, cudaMemsetAsync(h->ctr, 0, sizeof(DevCounters), h->stream));
+    if (tmp) TRY24(h, cudaFreeAsync(tmp, h->stream));
+    TRY24(h, cudaStreamSynchronize(h->stream));
+    h->initialized = true;
+    h->host_steps = 0;
+    return LBKM_OK;
+}
+
+lbkm_status lbkm24_step(lbkm24_t h, int64_t n)
+{
+    if (!h) return LBKM_EINVAL;
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm24_step before lbkm24_init_fields");
+    if (n < 0) return fail(h, LBKM_EINVAL, "n must be >= 0");
+    while (n >= GRAPH_CHUNK) {
+        cudaGraphExec_t& ex = h->graph[h->cur];
+        if (!ex) {
+            cudaGraph_t gr;
+            TRY24(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t le = cudaSuccess;
+            for (int s = 0; s < GRAPH_CHUNK && le == cudaSuccess; s++)
+                le = launch_one_step(h, (h->cur + s) & 1, h->capture_stream);
+            cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &gr);
+            if (le != cudaSuccess || ce != cudaSuccess) {
+                if (ce == cudaSuccess) cudaGraphDestroy(gr);
+                return fail(h, LBKM_ECUDA, "graph capture: %s",
+                            cudaGetErrorString(le != cudaSuccess ? le : ce));
+            }
+            cudaError_t ie = cudaGraphInstantiate(&ex, gr, 0);
+            cudaGraphDestroy(gr);
+            if (ie != cudaSuccess)
+                return fail(h, LBKM_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+        }
+        TRY24(h, cudaGraphLaunch(ex, h->stream));
+        n -= GRAPH_CHUNK;
+        h->host_steps += GRAPH_CHUNK;
+    }
+    for (; n > 0; n--) {
+        TRY24(h, launch_one_step(h, h->cur, h->stream));
+        h->cur = 1 - h->cur;
+        h->host_steps++;
+    }
+    return LBKM_OK;
+}
+
+lbkm_status lbkm24_sync(lbkm24_t h)
+{
+    if (!h) return LBKM_EINVAL;
+    return check(h);
+}
+
+int64_t lbkm24_steps_taken(lbkm24_t h) { return h ? h->host_steps : -1; }
+
+lbkm_status lbkm24_macros(lbkm24_t h, double* rho, double* ux, double* uy, double* T, double* p,
+                          double* lambda, int on_device)
+{
+    if (!h) return LBKM_EINVAL;
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm24_macros before lbkm24_init_fields");
+    const size_t n = (size_t)h->p.nx * h->p.ny, nb = n * sizeof(double);
+    double* outs[6] = {rho, ux, uy, T, p, lambda};
+    double* dev[6] = {rho, ux, uy, T, p, lambda};
+    double* tmp = nullptr;
+    if (!on_device) {
+        TRY24(h, cudaMallocAsync((void**)&tmp, nb * 6, h->stream));
+        for (int k = 0; k < 6; k++) dev[k] = outs[k] ? tmp + k * n : nullptr;
+    }
+    const int g = elementwise_blocks((int64_t)n);
+    if (h->p.precision == LBKM_F64)
+        macros_kernel<double><<<g, 256, 0, h->stream>>>(h->Kd, (const double*)h->buf[h->cur],
+                                                        dev[0], dev[1], dev[2], dev[3], dev[4],
+                                                        dev[5]);
+    else
+        macros_kernel<float><<<g, 256, 0, h->stream>>>(h->Kf, (const float*)h->buf[h->cur], dev[0],
+                                                       dev[1], dev[2], dev[3], dev[4], dev[5]);
+    TRY24(h, cudaGetLastError());
+    if (!on_device) {
+        for (int k = 0; k < 6; k++)
+            if (outs[k])
+                TRY24(h, cudaMemcpyAsync(outs[k], dev[k], nb, cudaMemcpyDeviceToHost, h->stream));
+        TRY24(h, cudaFreeAsync(tmp, h->stream));
+    }
+    return check(h);
+}
+
+lbkm_status lbkm24_tne(lbkm24_t h, double* delta, lbkm24_tne_global* g, int on_device)
+{
+    if (!h) return LBKM_EINVAL;
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm24_tne before lbkm24_init_fields");
+    const size_t n = (size_t)h->p.nx * h->p.ny, nb = (size_t)NV * n * sizeof(double);
+    double* dd = delta;
+    double* tmp = nullptr;
+    if (delta && !on_device) {
+        TRY24(h, cudaMallocAsync((void**)&tmp, nb, h->stream));
+        dd = tmp;
+    }
+    if (h->p.precision == LBKM_F64)
+        tne_kernel<double><<<h->grid, h->block, 0, h->stream>>>(
+            h->Kd, (const double*)h->buf[h->cur], dd, h->partials);
+    else
+        tne_kernel<float><<<h->grid, h->block, 0, h->stream>>>(
+            h->Kf, (const float*)h->buf[h->cur], dd, h->partials);
+    TRY24(h, cudaGetLastError());
+    finish_kernel<<<NQ, 256, 0, h->stream>>>(h->partials, h->nblocks, nullptr, 1, h->ctr,
+                                             h->tne_out, h->p.dx * h->p.dy);
+    TRY24(h, cudaGetLastError());
+    if (tmp) {
+        TRY24(h, cudaMemcpyAsync(delta, tmp, nb, cudaMemcpyDeviceToHost, h->stream));
+        TRY24(h, cudaFreeAsync(tmp, h->stream));
+    }
+    Record r;
+    TRY24(h, cudaMemcpyAsync(&r, h->tne_out, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+    lbkm_status st = check(h);
+    if (st != LBKM_OK) return st;
+    if (g) to_global(r, g);
+    return LBKM_OK;
+}
+
+lbkm_status lbkm24_tne_history(lbkm24_t h, lbkm24_tne_global* out, int32_t max_records,
+                               int32_t* n_out)
+{
+    if (!h || !n_out || (max_records > 0 && !out)) return LBKM_EINVAL;
+    *n_out = 0;
+    lbkm_status st = check(h);
+    if (st != LBKM_OK) return st;
+    DevCounters c;
+    TRY24(h, cudaMemcpy(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    const int cap = h->p.tne_capacity;
+    const int64_t have = c.hist_count < cap ? c.hist_count : cap;
+    const int64_t take = have < max_records ? have : max_records;
+    for (int64_t k = 0; k < take; k++) {
+        Record r;
+        TRY24(h, cudaMemcpy(&r, h->hist + (c.hist_count - have + k) % cap, sizeof(r),
+                            cudaMemcpyDeviceToHost));
+        to_global(r, out + k);
+    }
+    *n_out = (int32_t)take;
+    return LBKM_OK;
+}
+
+size_t lbkm24_state_bytes(lbkm24_t h)
+{
+    return h ? (size_t)NP * h->p.nx * h->p.ny * h->elem + sizeof(int64_t) : 0;
+}
+
+lbkm_status lbkm24_get_state(lbkm24_t h, void* dst, int on_device)
+{
+    if (!h || !dst) return LBKM_EINVAL;
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm24_get_state before init_fields");
+    const size_t row = (size_t)h->p.nx * h->elem, plane = row * h->p.ny;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int pl = 0; pl < NP; pl++)
+        TRY24(h, cudaMemcpy2DAsync((char*)dst + pl * plane, row,
+                                   (const char*)h->buf[h->cur] + pl * h->plane_elems * h->elem,
+                                   h->pitch * h->elem, row, h->p.ny, k, h->stream));
+    const int64_t s = h->host_steps;
+    TRY24(h, cudaMemcpyAsync((char*)dst + NP * plane, &s, sizeof(s),
+                             on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+                             h->stream));
+    return check(h);
+}
+
+lbkm_status lbkm24_set_state(lbkm24_t h, const void* src, int on_device)
+{
+    if (!h || !src) return LBKM_EINVAL;
+    const size_t row = (size_t)h->p.nx * h->elem, plane = row * h->p.ny;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    h->cur = 0;
+    for (int pl = 0; pl < NP; pl++)
+        TRY24(h, cudaMemcpy2DAsync((char*)h->buf[0] + pl * h->plane_elems * h->elem,
+                                   h->pitch * h->elem, (const char*)src + pl * plane, row, row,
+                                   h->p.ny, k, h->stream));
+    int64_t s = 0;
+    TRY24(h, cudaMemcpyAsync(&s, (const char*)src + NP * plane, sizeof(s),
+                             on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                             h->stream));
+    TRY24(h, cudaStreamSynchronize(h->stream));
+    DevCounters c;
+    memset(&c, 0, sizeof(c));
+    c.step = s;
+    TRY24(h, cudaMemcpy(h->ctr, &c, sizeof(c), cudaMemcpyHostToDevice));
+    h->host_steps = s;
+    h->initialized = true;
+    return LBKM_OK;
+}
+
+} // extern "C"

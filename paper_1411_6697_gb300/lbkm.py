@@ -29,6 +29,10 @@ EXPORTED = ["lbkm_default_params", "lbkm_create", "lbkm_destroy", "lbkm_set_stre
             "lbkm_set_state", "lbkm_last_error", "lbkm_version", "lbkm_tne_noalloc",
             "lbkm_create_batched", "lbkm_instances", "lbkm_tne_instances", "lbkm_autotune",
             "lbkm_set_wait_limit", "lbkm_grad"]
+EXPORTED24 = ["lbkm24_default_params", "lbkm24_create", "lbkm24_destroy", "lbkm24_init_fields",
+              "lbkm24_step", "lbkm24_sync", "lbkm24_steps_taken", "lbkm24_macros", "lbkm24_tne",
+              "lbkm24_tne_history", "lbkm24_state_bytes", "lbkm24_get_state", "lbkm24_set_state",
+              "lbkm24_last_error"]
 
 
 class LbkmError(RuntimeError):
@@ -71,16 +75,38 @@ class GradOut(ctypes.Structure):
                 ("drho0", ctypes.c_void_p), ("df0", ctypes.c_void_p)]
 
 
+class Params24(ctypes.Structure):
+    """lbkm24_params: the paper's D2V24 (include/lbkm24.h)."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("gamma", ctypes.c_double), ("v", ctypes.c_double * 3), ("eta", ctypes.c_double * 3),
+        ("S", ctypes.c_double * 24),
+        ("Q", ctypes.c_double), ("omega1", ctypes.c_double), ("omega2", ctypes.c_double),
+        ("T_ig", ctypes.c_double),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dt", ctypes.c_double),
+        ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+        ("tne_every", ctypes.c_int32), ("tne_capacity", ctypes.c_int32),
+    ]
+
+
+def _tne_fields(nv):
+    return [("sum", ctypes.c_double * nv), ("abs_sum", ctypes.c_double * nv),
+            ("min", ctypes.c_double * nv), ("max", ctypes.c_double * nv),
+            ("d_sum", ctypes.c_double), ("d2_sum", ctypes.c_double), ("step", ctypes.c_int64)]
+
+
 class TneGlobal(ctypes.Structure):
-    _fields_ = [("sum", ctypes.c_double * 16), ("abs_sum", ctypes.c_double * 16),
-                ("min", ctypes.c_double * 16), ("max", ctypes.c_double * 16),
-                ("d_sum", ctypes.c_double), ("d2_sum", ctypes.c_double),
-                ("step", ctypes.c_int64)]
+    _fields_ = _tne_fields(16)
 
     def as_dict(self):
         return {"sum": np.array(self.sum[:]), "abs_sum": np.array(self.abs_sum[:]),
                 "min": np.array(self.min[:]), "max": np.array(self.max[:]),
                 "d_sum": self.d_sum, "d2_sum": self.d2_sum, "step": int(self.step)}
+
+
+class TneGlobal24(ctypes.Structure):
+    _fields_ = _tne_fields(24)
+    as_dict = TneGlobal.as_dict
 
 
 _lib = None
@@ -139,6 +165,30 @@ def load():
                  "lbkm_macros", "lbkm_tne", "lbkm_tne_history", "lbkm_get_state",
                  "lbkm_set_state"):
         getattr(lib, name).restype = ctypes.c_int
+    P24 = ctypes.POINTER(Params24)
+    lib.lbkm24_default_params.argtypes = [P24]
+    lib.lbkm24_default_params.restype = None
+    lib.lbkm24_create.argtypes = [P24, _vp, ctypes.POINTER(H)]
+    lib.lbkm24_destroy.argtypes = [H]
+    lib.lbkm24_destroy.restype = None
+    lib.lbkm24_init_fields.argtypes = [H, _vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+    lib.lbkm24_step.argtypes = [H, ctypes.c_int64]
+    lib.lbkm24_sync.argtypes = [H]
+    lib.lbkm24_steps_taken.argtypes = [H]
+    lib.lbkm24_steps_taken.restype = ctypes.c_int64
+    lib.lbkm24_macros.argtypes = [H] + [_vp] * 6 + [ctypes.c_int]
+    lib.lbkm24_tne.argtypes = [H, _vp, ctypes.POINTER(TneGlobal24), ctypes.c_int]
+    lib.lbkm24_tne_history.argtypes = [H, ctypes.POINTER(TneGlobal24), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32)]
+    lib.lbkm24_state_bytes.argtypes = [H]
+    lib.lbkm24_state_bytes.restype = ctypes.c_size_t
+    lib.lbkm24_get_state.argtypes = [H, _vp, ctypes.c_int]
+    lib.lbkm24_set_state.argtypes = [H, _vp, ctypes.c_int]
+    lib.lbkm24_last_error.argtypes = [H]
+    lib.lbkm24_last_error.restype = ctypes.c_char_p
+    for name in ("create", "init_fields", "step", "sync", "macros", "tne", "tne_history",
+                 "get_state", "set_state"):
+        getattr(lib, "lbkm24_" + name).restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -167,6 +217,34 @@ def default_params(**kw) -> Params:
     return p
 
 
+def default_params24(**kw) -> Params24:
+    """lbkm24_params from the defaults (the steady-detonation set of Sec. IV.A) and
+    keyword overrides (v, eta: 3 values; S: 24 values or one; bc: (bc_x, bc_y))."""
+    p = Params24()
+    load().lbkm24_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k in ("v", "eta", "S"):
+            arr = getattr(p, k)
+            vals = np.broadcast_to(np.asarray(v, float), (len(arr),))
+            for i in range(len(arr)):
+                arr[i] = float(vals[i])
+        elif k == "bc":
+            p.bc_x, p.bc_y = v
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class _Api:
+    """The C functions of one handle type, by name without their prefix."""
+
+    def __init__(self, lib, prefix):
+        self._lib, self._prefix = lib, prefix
+
+    def __getattr__(self, name):
+        return getattr(self._lib, self._prefix + name)
+
+
 def _stream_ptr(stream):
     if stream is None:
         import torch
@@ -181,19 +259,28 @@ def _is_torch(a):
 
 
 class Solver:
-    """One MRT-LBKM grid on the GPU (a handle of the C ABI)."""
+    """One MRT-LBKM grid on the GPU (a handle of the C ABI), 16-velocity model."""
+
+    NV = 16
+    _PREFIX = "lbkm_"
+    _Tne = TneGlobal
 
     def __init__(self, params: Params = None, stream=None, **kw):
         lib = load()
         self._lib = lib
-        self.params = params if params is not None else default_params(**kw)
+        self._api = _Api(lib, self._PREFIX)
+        self.params = params if params is not None else self._default(**kw)
         self.nx, self.ny = int(self.params.nx), int(self.params.ny)
         h = ctypes.c_void_p()
-        rc = lib.lbkm_create(ctypes.byref(self.params), ctypes.c_void_p(_stream_ptr(stream)),
-                             ctypes.byref(h))
+        rc = self._api.create(ctypes.byref(self.params), ctypes.c_void_p(_stream_ptr(stream)),
+                              ctypes.byref(h))
         if rc != 0:
-            raise LbkmError(rc, lib.lbkm_last_error(None).decode())
+            raise LbkmError(rc, self._api.last_error(None).decode())
         self._h = h
+
+    @staticmethod
+    def _default(**kw):
+        return default_params(**kw)
 
     @classmethod
     def batched(cls, inst_nx, inst_S=None, inst_Q=None, inst_omega1=None, params=None,
@@ -267,11 +354,11 @@ class Solver:
     # ------------------------------------------------------------------
     def _check(self, rc):
         if rc != 0:
-            raise LbkmError(rc, self._lib.lbkm_last_error(self._h).decode())
+            raise LbkmError(rc, self._api.last_error(self._h).decode())
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.lbkm_destroy(self._h)
+            self._api.destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -310,18 +397,18 @@ class Solver:
                 dev.add(d)
         if len(dev) != 1:
             raise ValueError("fields must be all host arrays or all CUDA tensors")
-        self._check(self._lib.lbkm_init_fields(self._h, *[ctypes.c_void_p(p) for p in ptrs],
+        self._check(self._api.init_fields(self._h, *[ctypes.c_void_p(p) for p in ptrs],
                                                dev.pop()))
 
     def step(self, n=1):
-        self._check(self._lib.lbkm_step(self._h, int(n)))
+        self._check(self._api.step(self._h, int(n)))
 
     def sync(self):
-        self._check(self._lib.lbkm_sync(self._h))
+        self._check(self._api.sync(self._h))
 
     @property
     def steps_taken(self):
-        return int(self._lib.lbkm_steps_taken(self._h))
+        return int(self._api.steps_taken(self._h))
 
     def macros(self, device=False, out=None):
         """rho, ux, uy, T, p, lambda of the current state; with out (a dict of
@@ -330,7 +417,7 @@ class Solver:
         if out is not None:
             ptrs = [(out[k].data_ptr() if _is_torch(out[k]) else out[k].ctypes.data)
                     if k in out else None for k in names]
-            self._check(self._lib.lbkm_macros(self._h, *[ctypes.c_void_p(p) for p in ptrs],
+            self._check(self._api.macros(self._h, *[ctypes.c_void_p(p) for p in ptrs],
                                               1 if device else 0))
             return out
         if device:
@@ -341,74 +428,96 @@ class Solver:
         else:
             out = {k: np.empty((self.ny, self.nx)) for k in names}
             ptrs = [out[k].ctypes.data for k in names]
-        self._check(self._lib.lbkm_macros(self._h, *[ctypes.c_void_p(p) for p in ptrs],
+        self._check(self._api.macros(self._h, *[ctypes.c_void_p(p) for p in ptrs],
                                           1 if device else 0))
         return out
 
     def tne(self, fields=True, device=False):
-        g = TneGlobal()
+        g = self._Tne()
         delta = None
         ptr = None
         if fields:
             if device:
                 import torch
-                delta = torch.empty((16, self.ny, self.nx), dtype=torch.float64, device="cuda")
+                delta = torch.empty((self.NV, self.ny, self.nx), dtype=torch.float64,
+                                    device="cuda")
                 ptr = delta.data_ptr()
             else:
-                delta = np.empty((16, self.ny, self.nx))
+                delta = np.empty((self.NV, self.ny, self.nx))
                 ptr = delta.ctypes.data
-        self._check(self._lib.lbkm_tne(self._h, ctypes.c_void_p(ptr), ctypes.byref(g),
+        self._check(self._api.tne(self._h, ctypes.c_void_p(ptr), ctypes.byref(g),
                                        1 if device else 0))
         return delta, g.as_dict()
 
     def tne_history(self, max_records=None):
         cap = int(self.params.tne_capacity) if max_records is None else int(max_records)
-        buf = (TneGlobal * max(cap, 1))()
+        buf = (self._Tne * max(cap, 1))()
         n = ctypes.c_int32()
-        self._check(self._lib.lbkm_tne_history(self._h, buf, cap, ctypes.byref(n)))
+        self._check(self._api.tne_history(self._h, buf, cap, ctypes.byref(n)))
         return [buf[i].as_dict() for i in range(n.value)]
 
     def state_bytes(self):
-        return int(self._lib.lbkm_state_bytes(self._h))
+        return int(self._api.state_bytes(self._h))
 
     def get_state(self, device=False):
         """State snapshot as bytes: a NumPy uint8 array, or a CUDA uint8 tensor."""
         if device:
             import torch
             buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device="cuda")
-            self._check(self._lib.lbkm_get_state(self._h, ctypes.c_void_p(buf.data_ptr()), 1))
+            self._check(self._api.get_state(self._h, ctypes.c_void_p(buf.data_ptr()), 1))
             return buf
         buf = np.empty(self.state_bytes(), np.uint8)
-        self._check(self._lib.lbkm_get_state(self._h, ctypes.c_void_p(buf.ctypes.data), 0))
+        self._check(self._api.get_state(self._h, ctypes.c_void_p(buf.ctypes.data), 0))
         return buf
 
     def set_state(self, buf):
         if _is_torch(buf):
             if buf.numel() != self.state_bytes():
                 raise ValueError("state buffer has the wrong size")
-            self._check(self._lib.lbkm_set_state(self._h, ctypes.c_void_p(buf.data_ptr()), 1))
+            self._check(self._api.set_state(self._h, ctypes.c_void_p(buf.data_ptr()), 1))
             return
         buf = np.ascontiguousarray(buf, np.uint8)
         if buf.size != self.state_bytes():
             raise ValueError("state buffer has %d bytes, expected %d" % (buf.size,
                                                                         self.state_bytes()))
-        self._check(self._lib.lbkm_set_state(self._h, ctypes.c_void_p(buf.ctypes.data), 0))
+        self._check(self._api.set_state(self._h, ctypes.c_void_p(buf.ctypes.data), 0))
 
     def planes_device(self):
-        """Current f_1..f_16 and lambda as a CUDA tensor [17, ny, nx] in the state's dtype."""
+        """Current f_1..f_NV and lambda as a CUDA tensor [NV+1, ny, nx] in the state's dtype."""
         import torch
         raw = self.get_state(device=True)
         dt = torch.float64 if self.params.precision == F64 else torch.float32
-        n = 17 * self.ny * self.nx * (8 if dt == torch.float64 else 4)
-        return raw[:n].view(dt).view(17, self.ny, self.nx)
+        npl = self.NV + 1
+        n = npl * self.ny * self.nx * (8 if dt == torch.float64 else 4)
+        return raw[:n].view(dt).view(npl, self.ny, self.nx)
 
     def f_planes(self):
-        """Current f_1..f_16 and lambda as FP64 NumPy arrays [17, ny, nx] (from a state copy)."""
+        """Current f_1..f_NV and lambda as FP64 NumPy arrays [NV+1, ny, nx] (state copy)."""
         raw = self.get_state()
         dt = np.float64 if self.params.precision == F64 else np.float32
-        n = 17 * self.ny * self.nx
+        npl = self.NV + 1
+        n = npl * self.ny * self.nx
         return np.frombuffer(raw[: n * np.dtype(dt).itemsize].tobytes(), dt).reshape(
-            17, self.ny, self.nx).astype(np.float64)
+            npl, self.ny, self.nx).astype(np.float64)
+
+
+class Solver24(Solver):
+    """One grid of the paper's D2V24 model on the GPU (a handle of include/lbkm24.h):
+    the same calls as Solver (init_fields, step, sync, macros, tne, tne_history,
+    get_state, set_state), with 24 velocities; no batched instances or gradients."""
+
+    NV = 24
+    _PREFIX = "lbkm24_"
+    _Tne = TneGlobal24
+
+    @staticmethod
+    def _default(**kw):
+        return default_params24(**kw)
+
+    def _not_here(self, *a, **k):
+        raise NotImplementedError("the D2V24 handle has no batched instances or gradients")
+
+    batched = autotune = grad = set_wait_limit = tne_instances = instances = _not_here
 
 
 def tne_noalloc(params: Params, state_ptr: int, pitch: int, delta_ptr, out_ptr: int, stream=None):

@@ -7,6 +7,8 @@ It shares nothing with ``oracle/lbkm_oracle.c`` beyond the paper:
     continuous Maxwellian Eq. (21) and of its T-derivative Eq. (22);
   * collision is the full velocity-space product -M^-1 R_hat M (f - f^eq)
     plus M^-1 A_hat and M^-1 C_hat (Eq. (1) with the sign of A from Eq. (29));
+    with 24 velocities (the paper's D2V24, moments m_1..m_24) the chemical term is
+    Eq. (24) in velocity space on the quadrature-built f^eq instead;
   * the reaction step integrates Eq. (28) with a library ODE solver;
   * NND is written in its upwind form: for v > 0 the interface value is
     v (f_j + mm(f_j - f_{j-1}, f_{j+1} - f_j)/2), for v < 0
@@ -38,10 +40,25 @@ MOMENTS = [
     lambda vx, vy, e: (vx**2 + vy**2 + e**2) * vx * vy,
     lambda vx, vy, e: (vx**2 + vy**2 + e**2) * vy**2,
 ]
+# rows m_17..m_24 of the paper's D2V24 (list after Eq. (16))
+MOMENTS24 = MOMENTS + [
+    lambda vx, vy, e: e**2 * vx**2,
+    lambda vx, vy, e: e**2 * vx * vy,
+    lambda vx, vy, e: e**2 * vy**2,
+    lambda vx, vy, e: (vx**2 + vy**2 + e**2) * e**2,
+    lambda vx, vy, e: (vx**2 + vy**2 + e**2) * (vx**2 + vy**2) * vx,
+    lambda vx, vy, e: (vx**2 + vy**2 + e**2) * (vx**2 + vy**2) * vy,
+    lambda vx, vy, e: (vx**2 + vy**2 + e**2) * e**2 * vx,
+    lambda vx, vy, e: (vx**2 + vy**2 + e**2) * e**2 * vy,
+]
 
 
-def maxwellian_moments(rho, ux, uy, T, I, nodes=8, dT=False):
-    """Moments m_1..m_16 of the continuous f^eq of Eq. (21) (or of df^eq/dT, Eq. (22))."""
+def _moments(nv):
+    return MOMENTS if nv == 16 else MOMENTS24
+
+
+def maxwellian_moments(rho, ux, uy, T, I, nodes=8, dT=False, nv=16):
+    """Moments m_1..m_nv of the continuous f^eq of Eq. (21) (or of df^eq/dT, Eq. (22))."""
     x, w = np.polynomial.hermite_e.hermegauss(nodes)
     w = w / np.sqrt(2.0 * np.pi)
     X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
@@ -51,7 +68,7 @@ def maxwellian_moments(rho, ux, uy, T, I, nodes=8, dT=False):
     if dT:
         c2 = (vx - ux) ** 2 + (vy - uy) ** 2
         weight = weight * (-(1 + D) * I * T + I * c2 + eta**2) / (2.0 * I * T * T)
-    return np.array([np.sum(weight * m(vx, vy, eta)) for m in MOMENTS])
+    return np.array([np.sum(weight * m(vx, vy, eta)) for m in _moments(nv)])
 
 
 def velocity_set(orbit_kind, orbit_speed, orbit_eta):
@@ -66,7 +83,7 @@ def velocity_set(orbit_kind, orbit_speed, orbit_eta):
 
 
 def moment_matrix(vx, vy, eta):
-    return np.array([m(vx, vy, eta) for m in MOMENTS])
+    return np.array([m(vx, vy, eta) for m in _moments(len(vx))])
 
 
 def _mm(a, b):
@@ -78,12 +95,13 @@ def _idx(j, n, bc):
 
 
 def step(cfg, f, lam):
-    """cfg: dict with orbit table, gamma, S[16], Q, omega1, omega2, T_ig, dx, dy, dt,
-    bc_x, bc_y. f: [16, ny, nx], lam: [ny, nx]."""
+    """cfg: dict with orbit table (4 or 6 orbits), gamma, S[nv], Q, omega1, omega2, T_ig,
+    dx, dy, dt, bc_x, bc_y. f: [nv, ny, nx], lam: [ny, nx]."""
     vx, vy, eta = velocity_set(cfg["orbit_kind"], cfg["orbit_speed"], cfg["orbit_eta"])
+    nv = len(vx)
     I = 2.0 / (cfg["gamma"] - 1.0) - D
     M = moment_matrix(vx, vy, eta)
-    S = np.asarray(cfg["S"], float)
+    S = np.broadcast_to(np.asarray(cfg["S"], float), (nv,))
     ny, nx = lam.shape
     dx, dy, dt = cfg["dx"], cfg["dy"], cfg["dt"]
     bx, by = cfg["bc_x"], cfg["bc_y"]
@@ -108,9 +126,9 @@ def step(cfg, f, lam):
             duy_dy = (at(uy, x, y + 1) - at(uy, x, y - 1)) / (2 * dy)
             div = dux_dx + duy_dy
             fc = f[:, y, x]
-            feq = np.linalg.solve(M, maxwellian_moments(r, u, v, t, I))
+            feq = np.linalg.solve(M, maxwellian_moments(r, u, v, t, I, nv=nv))
             coll = -np.linalg.solve(M, S * (M @ (fc - feq)))
-            A = np.zeros(16)
+            A = np.zeros(nv)
             A[7] = r * t * (S[4] - S[7]) / S[4] * (4 * u * (dux_dx - div / (D + I))
                                                    + 2 * v * (duy_dx + dux_dy))
             A[8] = r * t * (S[6] - S[8]) / S[6] * (4 * v * (duy_dy - div / (D + I))
@@ -122,11 +140,17 @@ def step(cfg, f, lam):
                 sol = solve_ivp(lambda _, z: (1 - z) * (a + b * z), (0, dt), [l0],
                                 method="DOP853", rtol=1e-13, atol=1e-16)
                 dl = sol.y[0, -1] - l0
-            Chat = maxwellian_moments(r, u, v, t, I, dT=True) * 2 * cfg["Q"] * (dl / dt) / (D + I)
-            Om = coll + np.linalg.solve(M, A) + np.linalg.solve(M, Chat)
+            if nv == 16:
+                Chat = (maxwellian_moments(r, u, v, t, I, dT=True) * 2 * cfg["Q"] * (dl / dt)
+                        / (D + I))
+                C = np.linalg.solve(M, Chat)
+            else:
+                shape = -(1 + D) * I * t + I * ((vx - u) ** 2 + (vy - v) ** 2) + eta**2
+                C = feq * cfg["Q"] * shape / (I * (D + I) * t * t) * (dl / dt)
+            Om = coll + np.linalg.solve(M, A) + C
 
-            adv = np.zeros(16)
-            for i in range(16):
+            adv = np.zeros(nv)
+            for i in range(nv):
                 for vel, ax, h in ((vx[i], 0, dx), (vy[i], 1, dy)):
                     if vel == 0:
                         continue
@@ -160,10 +184,11 @@ def equilibrium(cfg, rho, ux, uy, T):
     vx, vy, eta = velocity_set(cfg["orbit_kind"], cfg["orbit_speed"], cfg["orbit_eta"])
     I = 2.0 / (cfg["gamma"] - 1.0) - D
     M = moment_matrix(vx, vy, eta)
+    nv = len(vx)
     ny, nx = rho.shape
-    f = np.empty((16, ny, nx))
+    f = np.empty((nv, ny, nx))
     for y in range(ny):
         for x in range(nx):
             f[:, y, x] = np.linalg.solve(M, maxwellian_moments(rho[y, x], ux[y, x], uy[y, x],
-                                                               T[y, x], I))
+                                                               T[y, x], I, nv=nv))
     return f

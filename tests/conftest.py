@@ -18,4 +18,5 @@ def pytest_configure(config):
 def oracle_mod():
     from oracle import oracle
     oracle.build()
+    oracle.build(nv=24)
     return oracle

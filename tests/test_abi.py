@@ -82,3 +82,46 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(lbkm, "LIB_PATH", "/nonexistent/libpaper_lbkm.so")
     with pytest.raises(ImportError):
         lbkm.load()
+
+
+HEADER24 = os.path.join(ROOT, "include", "lbkm24.h")
+
+
+def test_d2v24_symbols_and_layout(lib):
+    """include/lbkm24.h (the paper's D2V24): every declared call is exported and listed by
+    the binding, and lbkm24_params / lbkm24_tne_global have the ctypes layout."""
+    from paper_1411_6697_gb300 import lbkm
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER24).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(lbkm24_[a-z_]+)\s*\(", src)))
+    assert len(names) == 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(lbkm.EXPORTED24) == names
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "lbkm24.h"
+#define F(s, m) printf(#m " %zu\n", offsetof(s, m));
+int main(void) {
+  printf("params %zu\n", sizeof(lbkm24_params));
+  printf("tne %zu\n", sizeof(lbkm24_tne_global));
+  F(lbkm24_params, gamma) F(lbkm24_params, v) F(lbkm24_params, eta) F(lbkm24_params, S)
+  F(lbkm24_params, Q) F(lbkm24_params, dt) F(lbkm24_params, bc_x) F(lbkm24_params, tne_capacity)
+  F(lbkm24_tne_global, d_sum) F(lbkm24_tne_global, step)
+  return 0; }
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "l")
+        subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER24), c, "-o", exe])
+        out = dict(line.split() for line in subprocess.check_output([exe]).decode().splitlines())
+    assert int(out["params"]) == ctypes.sizeof(lbkm.Params24)
+    assert int(out["tne"]) == ctypes.sizeof(lbkm.TneGlobal24)
+    for m in ("gamma", "v", "eta", "S", "Q", "dt", "bc_x", "tne_capacity"):
+        assert int(out[m]) == getattr(lbkm.Params24, m).offset, m
+    assert int(out["d_sum"]) == lbkm.TneGlobal24.d_sum.offset
+    assert int(out["step"]) == lbkm.TneGlobal24.step.offset
+    p = lbkm.default_params24(nx=8, ny=1)
+    assert list(p.v) == [2.7, 2.2, 1.2] and list(p.eta) == [5.0, 3.0, 1.1]
+    assert p.S[4] == 1e4 and p.S[7] == 1e5 and p.dx == 2e-4 and p.dt == 5e-6

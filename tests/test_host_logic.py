@@ -58,3 +58,19 @@ def test_pr_sets_heat_conduction_rates():
     p = lbkm.default_params(nx=4, ny=1, Pr=0.5, S=[1e4] * 16)
     # the override happens inside lbkm_create; the stored copy keeps the caller's values
     assert p.Pr == 0.5 and p.S[7] == 1e4
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=0), dict(precision=3), dict(gamma=1.0), dict(gamma=2.5),
+    dict(v=(2.7, 0.0, 1.2)), dict(eta=(5.0, -1.0, 1.1)), dict(dt=5e-4),
+    dict(dx=1e-6), dict(bc=(2, 0)), dict(bc=(0, 5)), dict(T_ig=float("nan")),
+    dict(omega1=-1.0), dict(tne_every=-1),
+    dict(v=(1.0, 1.0, 1.0), eta=(1.0, 1.0, 1.0)),  # three equal groups: singular M
+])
+def test_d2v24_invalid_parameters_are_rejected(kw):
+    """lbkm24_create validates on the host before any CUDA call."""
+    base = dict(nx=16, ny=1)
+    base.update(kw)
+    with pytest.raises(lbkm.LbkmError) as e:
+        lbkm.Solver24(stream=0, **base)
+    assert e.value.code in (1, 4)

@@ -1,0 +1,216 @@
+"""Pins of the D2V24 oracle (the paper's own 24-velocity model, Sec. II) against what
+the paper and the mathematics fix: the moment matrix from the listed rows m_1..m_24 and
+a library inverse, the 24 equilibrium moments against quadrature of the continuous
+Maxwellian, the velocity-space chemical term of Eq. (24) against the mass, momentum and
+energy it must carry, a uniform equilibrium that stays put, an independent brute-force
+formulation on tiny grids, and a detonation that runs at the Chapman-Jouguet speed with
+the paper's D2V24 parameters."""
+import numpy as np
+import pytest
+
+import brute_force as bf
+import lbkm_inputs as li
+
+SETS = {  # (v_a, v_b, v_c), (eta_a, eta_b, eta_c), gamma -- the paper's runs
+    "detonation": (li.D2V24_DETONATION_V[0], li.D2V24_DETONATION_V[1], 1.4),   # Sec. IV.A
+    "lax": ((2.5, 2.2, 1.2), (6.5, 3.0, 0.0), 1.4),                            # Sec. IV.B
+    "sjogreen": ((4.7, 3.3, 1.0), (6.0, 2.5, 0.9), 5.0 / 3.0),                 # Sec. IV.B
+    "couette": ((0.8, 1.2, 1.3), (1.0, 2.7, 0.8), 1.5),                        # Sec. IV.D
+    "tne": (li.D2V24_TNE_V[0], li.D2V24_TNE_V[1], 1.4),                        # Sec. VI
+    "tne2": (li.D2V24_TNE_V2[0], li.D2V24_TNE_V2[1], 1.4),                     # Sec. VI
+}
+
+
+def make(oracle_mod, nx, ny, which="detonation", **kw):
+    v, eta, gamma = SETS[which]
+    base = dict(gamma=gamma, **li.d2v24_orbits(v, eta), S=1e5)
+    base.update(kw)
+    return oracle_mod.Oracle(nx, ny, **base)
+
+
+@pytest.mark.parametrize("which", sorted(SETS))
+def test_moment_matrix_and_inverse(oracle_mod, which):
+    ob = make(oracle_mod, 4, 1, which)
+    assert ob.nv == 24 and ob.M.shape == (24, 24)
+    vx, vy, eta = bf.velocity_set(**{k: li.d2v24_orbits(*SETS[which][:2])[k] for k in
+                                     ("orbit_kind", "orbit_speed", "orbit_eta")})
+    M2 = bf.moment_matrix(vx, vy, eta)
+    assert np.allclose(M2, ob.M, rtol=1e-14, atol=0)
+    Minv2 = np.linalg.inv(M2)
+    assert np.abs(Minv2 - ob.Minv).max() < 1e-10 * np.abs(Minv2).max()
+    assert np.abs(ob.M @ ob.Minv - np.eye(24)).max() < 1e-11
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_feq_1_to_24_match_maxwellian_quadrature(oracle_mod, seed):
+    """All 24 closed forms listed after Eq. (16) (17..24 are new with D2V24) equal the
+    moments of the continuous Maxwellian Eq. (21) by Gauss-Hermite quadrature."""
+    rng = np.random.default_rng(300 + seed)
+    rho, ux, uy, T = rng.uniform(0.2, 3), rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.3, 3)
+    which = sorted(SETS)[seed % len(SETS)]
+    ob = make(oracle_mod, 4, 1, which)
+    q = bf.maxwellian_moments(rho, ux, uy, T, ob.p.I, nv=24)
+    got = ob.feq_moments(rho, ux, uy, T)
+    assert np.allclose(got, q, rtol=1e-12, atol=1e-12 * np.abs(q).max())
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_dfeq_dT_matches_eq22_quadrature(oracle_mod, seed):
+    rng = np.random.default_rng(400 + seed)
+    rho, ux, uy, T = rng.uniform(0.2, 3), rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.3, 3)
+    ob = make(oracle_mod, 4, 1)
+    q = bf.maxwellian_moments(rho, ux, uy, T, ob.p.I, dT=True, nv=24)
+    assert np.allclose(ob.dfeq_dT(rho, ux, uy, T), q, rtol=1e-11, atol=1e-11 * np.abs(q).max())
+
+
+def test_velocity_space_chemical_term_carries_mass_momentum_energy(oracle_mod):
+    """On a uniform non-equilibrium state (no advection) with equal rates S: rows 1-3 of
+    M (f_new - f) vanish and row 4 gains 2 rho Q dlambda -- Eq. (24) in velocity space
+    is exact for these moments with 24 velocities (it needs rows m_14, m_16, m_20)."""
+    rng = np.random.default_rng(17)
+    for which in ("detonation", "tne"):
+        ob = make(oracle_mod, 3, 2, which, Q=1.0, omega1=2e4, omega2=3e3, T_ig=1.1, bc_x=0,
+                  bc_y=0, S=rng.uniform(1e3, 1e5, 24), dt=2e-6)
+        feq = ob.init(1.1, 0.2, 0.1, 1.5)
+        f = feq + 1e-3 * rng.standard_normal(24)[:, None, None] * np.abs(feq)
+        f1, lam1 = ob.step(f, 0.4)
+        dm = np.einsum("ki,iyx->kyx", ob.M, f1 - f)
+        rho = ob.macros(f)["rho"]
+        scale = np.abs(np.einsum("ki,iyx->kyx", np.abs(ob.M), np.abs(f))).max()
+        assert np.abs(dm[:3]).max() < 1e-12 * scale
+        assert lam1[0, 0] > 0.4
+        assert np.allclose(dm[3], 2 * rho * ob.p.Q * (lam1 - 0.4), rtol=1e-9)
+
+
+def test_chemical_term_differs_from_moment_space_form(oracle_mod):
+    """A planted moment-space chemical term (C_hat = d f_hat^eq/dT dT/dt, the 16-velocity
+    reading) would change the non-conserved moments: the D2V24 oracle does take Eq. (24)
+    in velocity space, whose moments 5..24 differ from C_hat beyond rounding."""
+    ob = make(oracle_mod, 1, 1, "tne", Q=1.0, omega1=2e4, T_ig=1.1, bc_x=0, bc_y=0, dt=1e-6,
+              S=np.full(24, 1e3))
+    rho, ux, uy, T, lam = 1.1, 0.3, -0.2, 1.5, 0.3
+    feq = ob.init(rho, ux, uy, T)
+    f1, lam1 = ob.step(feq, lam)
+    # uniform equilibrium: the whole change is dt * C
+    C = (f1 - feq)[:, 0, 0] / ob.p.dt
+    lrate = (lam1[0, 0] - lam) / ob.p.dt
+    I, DI = ob.p.I, 2 + ob.p.I
+    v = ob.M[1:3, :]
+    shape = -(3.0) * I * T + I * ((v[0] - ux) ** 2 + (v[1] - uy) ** 2) + (ob.M[3] - ob.M[4] - ob.M[6])
+    want = feq[:, 0, 0] * ob.p.Q * shape / (I * DI * T * T) * lrate
+    assert np.allclose(C, want, rtol=1e-8, atol=1e-10 * np.abs(want).max())
+    Chat = ob.dfeq_dT(rho, ux, uy, T) * 2 * ob.p.Q * lrate / DI
+    assert np.abs(ob.M @ C - Chat)[4:].max() > 1e-3 * np.abs(Chat).max()
+
+
+def test_uniform_equilibrium_is_fixed(oracle_mod):
+    for T0, Q in ((1.0, 1.0), (1.3, 0.0)):
+        ob = make(oracle_mod, 6, 5, Q=Q, omega1=2e4, bc_x=0, bc_y=0, S=np.linspace(1e4, 1e5, 24))
+        f0 = ob.init(1.2, 0.3, -0.2, T0)
+        f, lam = ob.run(f0, 0.25, 50)
+        assert np.abs(f - f0).max() < 1e-13 * np.abs(f0).max()
+        assert np.all(lam == 0.25) if T0 < 1.1 else np.all(lam > 0.25)
+
+
+def test_conservation_periodic_2d(oracle_mod):
+    rng = np.random.default_rng(19)
+    nx, ny = 12, 10
+    x = np.arange(nx) / nx
+    y = np.arange(ny)[:, None] / ny
+    ob = make(oracle_mod, nx, ny, "tne", bc_x=0, bc_y=0, S=rng.uniform(1e3, 1e4, 24), dx=1e-2,
+              dt=1e-4)
+    f0 = ob.init(1 + 0.2 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y),
+                 0.3 * np.cos(2 * np.pi * y) + 0 * x, 0.2 * np.sin(2 * np.pi * x) + 0 * y,
+                 1 + 0.1 * np.cos(2 * np.pi * (x + y)))
+    f, _ = ob.run(f0, 0.0, 30)
+    tot0 = np.einsum("ki,iyx->k", ob.M[:4], f0)
+    tot = np.einsum("ki,iyx->k", ob.M[:4], f)
+    scale = np.einsum("ki,iyx->k", np.abs(ob.M[:4]), np.abs(f0))
+    assert np.all(np.abs(tot - tot0) < 1e-12 * scale)
+    assert np.abs(f - f0).max() > 1e-4
+
+
+@pytest.mark.parametrize("nx,ny,bc_x,bc_y", [(8, 1, 1, 0), (4, 2, 0, 0), (5, 3, 1, 1)])
+def test_brute_force_small_grids(oracle_mod, nx, ny, bc_x, bc_y):
+    """Oracle vs the naive independent formulation (quadrature f^eq, full velocity-space
+    collision, ODE-solver reaction, Eq. (24) on the quadrature f^eq) for 6 steps."""
+    rng = np.random.default_rng(nx * 100 + ny + 7)
+    v, eta, gamma = SETS["detonation"]
+    cfg = dict(li.d2v24_orbits(v, eta), gamma=gamma, S=rng.uniform(2e3, 1e5, 24), Q=1.0,
+               omega1=2e3, omega2=500.0, T_ig=1.1, dx=1e-3, dy=1e-3, dt=1e-5, bc_x=bc_x,
+               bc_y=bc_y)
+    ob = oracle_mod.Oracle(nx, ny, **cfg)
+    x = np.arange(nx) / nx
+    y = np.arange(ny)[:, None] / ny
+    rho = 1 + 0.1 * np.sin(2 * np.pi * x) + 0.05 * np.cos(2 * np.pi * y)
+    ux = 0.2 * np.cos(2 * np.pi * x) + 0.05 * np.sin(2 * np.pi * y)
+    uy = -0.1 + 0.05 * np.sin(2 * np.pi * (x + y))
+    T = np.where(x < 0.5, 1.35, 0.95) + 0.02 * np.cos(2 * np.pi * y)
+    f = bf.equilibrium(cfg, rho, ux, uy, T)
+    f = f * (1 + 2e-3 * rng.standard_normal(f.shape))
+    lam = rng.uniform(0, 0.8, (ny, nx))
+    fo, lo, fb, lb = f, lam, f, lam
+    for _ in range(6):
+        fo, lo = ob.step(fo, lo)
+        fb, lb = bf.step(cfg, fb, lb)
+    assert np.abs(fo - fb).max() < 1e-10 * np.abs(f).max()
+    assert np.abs(lo - lb).max() < 1e-12
+    delta, rec = ob.tne(fo)
+    m = ob.macros(fo)
+    for (yy, xx) in [(0, 0), (ny - 1, nx - 1)]:
+        fh = ob.M @ fo[:, yy, xx]
+        q = bf.maxwellian_moments(m["rho"][yy, xx], m["ux"][yy, xx], m["uy"][yy, xx],
+                                  m["T"][yy, xx], ob.p.I, nv=24)
+        assert np.allclose(delta[4:, yy, xx], (fh - q)[4:], atol=1e-11 * np.abs(fh).max())
+        assert np.all(delta[:4, yy, xx] == 0)
+    assert rec["sum"].shape == (24,)
+
+
+def test_one_dimensional_symmetry_zeros(oracle_mod):
+    """Uniform in y: the shear and y-flux non-equilibria vanish (Sec. VI, Fig. 10 (g), (k),
+    (m), (o)), and Delta_5 + Delta_7 + Delta_eta2 = 0, Delta_eta2 = Delta_4 - Delta_5 -
+    Delta_7 being the eta^2 part (Sec. VI, item 4); here Delta_4 = 0 by conservation."""
+    c = li.d2v24_detonation(nx=300, steps=1, omega1=1e3, x_driver=0.02)
+    p = dict(c["params"])
+    p.pop("nx"), p.pop("ny")
+    ob = oracle_mod.Oracle(300, 1, **p)
+    fl = c["fields"]
+    f = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
+    f, lam = ob.run(f, fl["lam"], 200)
+    delta, _ = ob.tne(f)
+    scale = np.abs(delta).max()
+    assert scale > 1e-4
+    for k in (6, 9, 11, 13, 15, 18, 22, 24):  # 1-based: odd in v_y
+        assert np.abs(delta[k - 1]).max() < 1e-12 * scale, k
+
+
+@pytest.mark.slow
+def test_detonation_runs_at_cj_speed_with_paper_d2v24(oracle_mod):
+    """The paper's D2V24 steady-detonation parameters (Sec. IV.A: v = (2.7, 2.2, 1.2),
+    eta = (5, 3, 1.1), dx = 2e-4, dt = 5e-6, R_5..7 = 1e4, others 1e5) with a rate
+    constant that resolves the reaction zone over a few cells: the front runs at the CJ
+    speed (the paper finds 2.06 against 2.06395) and leaves the CJ state behind it."""
+    nx, steps = 700, 8000
+    c = li.d2v24_detonation(nx=nx, steps=steps, omega1=1e3, x_driver=0.02)
+    p = dict(c["params"])
+    p.pop("nx"), p.pop("ny")
+    dx, dt = p["dx"], p["dt"]
+    ob = oracle_mod.Oracle(nx, 1, **p)
+    fl = c["fields"]
+    f = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
+    lam = fl["lam"]
+    ts, xs = [], []
+    for k in range(steps // 1000):
+        f, lam = ob.run(f, lam, 1000)
+        pr = ob.macros(f)["p"][0]
+        jp = int(np.argmax(pr))
+        ts.append((k + 1) * 1000 * dt)
+        xs.append((jp + np.argmax(pr[jp:] < 1.5)) * dx)
+    Dcj, rcj, ucj, pcj, Tcj = li.cj_state(1.0, 1.4)
+    speed = np.polyfit(ts[3:], xs[3:], 1)[0]
+    assert abs(speed / Dcj - 1) < 0.01
+    m = ob.macros(f)
+    j = int(xs[-1] / dx)
+    seg = slice(j // 2 - 20, j // 2 + 20)
+    for k, ref in (("rho", rcj), ("ux", ucj), ("T", Tcj), ("p", pcj)):
+        assert abs(m[k][0][seg].mean() / ref - 1) < 0.006, k
