@@ -350,6 +350,57 @@ def run_detonation(args):
     return 0
 
 
+def run_d2v24(args):
+    """The paper's own D2V24 model: the steady-detonation run of Sec. IV.A (5000 cells,
+    1 MB of state, L2-resident and latency-bound) and a 2-D reactive field of 2048^2
+    cells (state > L2), each in FP64 and FP32, through lbkm24."""
+    import torch
+    from paper_1411_6697_gb300 import lbkm
+    rank, local, world = _env_rank()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    out = {}
+    cases = (("detonation", li.d2v24_detonation(), args.steps),
+             ("reactive2d", li.d2v24_reactive2d(n=2048, steps=args.steps), max(args.steps // 10, 5)))
+    with ClockSampler(local) as clk:
+        for name, cfg, steps in cases:
+            fl = cfg["fields"]
+            for tag, prec in (("f64", lbkm.F64), ("f32", lbkm.F32)):
+                p = dict(cfg["lib_params"])
+                bc = (p.pop("bc_x"), p.pop("bc_y"))
+                s = lbkm.Solver24(precision=prec, bc=bc, stream=stream, **p)
+                s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+                with torch.cuda.stream(stream):
+                    s.step(args.warmup)
+                    ms = time_steps(s, stream, steps)
+                s.sync()
+                n = p["nx"] * p["ny"]
+                out["%s_%s" % (name, tag)] = dict(
+                    mcell_per_s=n * steps / (ms * 1e-3) / 1e6, ms_per_step=ms / steps,
+                    cells=n, steps=steps)
+                s.close()
+    peak, peak_kind = measured_peak()
+    big = out["reactive2d_f32"]
+    alg = 200 * big["cells"]  # 25 FP32 planes read and written per cell update
+    achieved = alg / (big["ms_per_step"] * 1e-3) / 1e9
+    line = {"metric": METRIC.replace("16 f_i", "24 f_i"), "value": out["detonation_f32"]["mcell_per_s"],
+            "unit": "Mcell-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "d2v24_detonation_5000x1",
+                       "note": "the paper's D2V24 steady-detonation set (Sec. IV.A); 1 MB "
+                               "state, L2-resident"},
+            "cases": out,
+            "roofline_reactive2d_f32": {"bound": "alu", "achieved": achieved, "peak": peak,
+                                        "unit": "GB/s", "frac": achieved / peak,
+                                        "peak_kind": peak_kind,
+                                        "note": "HBM fraction of the 2048^2 FP32 step; the "
+                                                "dense 24x24 transforms bound it"},
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def run_adjoint(args):
     """dJ/d(S, Q, omega1, rho0) of a 4000-step 1-D detonation of 8192 cells
     (profile mismatch + integrated TNE), checkpoints every 64 steps, through lbkm_grad;
@@ -433,7 +484,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--side", type=int, default=N_CELLS_SIDE)
     ap.add_argument("--workload", default="reactive2d",
-                    choices=["reactive2d", "batched", "detonation", "adjoint"])
+                    choices=["reactive2d", "batched", "detonation", "adjoint", "d2v24"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -443,6 +494,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "detonation":
         return run_detonation(args)
+    if args.workload == "d2v24":
+        return run_d2v24(args)
 
     import torch
     import torch.distributed as dist

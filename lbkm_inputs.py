@@ -207,13 +207,16 @@ def detonation(nx=16384, steps=20000, driver=50, Q=1.0, S=None, dx=1e-4, dt=2e-6
                 steps=steps, fields=f, name="detonation_nx%d" % nx)
 
 
-def d2v24_detonation(nx=5000, steps=78000, omega1=2e4, dx=2e-4, dt=5e-6, S=None,
+def d2v24_detonation(nx=5000, steps=78000, omega1=1e3, dx=2e-4, dt=5e-6, S=None,
                      v=D2V24_DETONATION_V, x_driver=0.2, ripple=0.0):
     """The steady-detonation run of Sec. IV.A with D2V24: x in [0, nx dx), the paper's
     printed burnt state (rho, T, u_x, lambda) = (1.38837, 1.57856, 0.577350, 1) for
     x <= x_driver and (1, 1, 0, 0) beyond, gamma = 1.4 (I = 3), Q = 1, T_ig = 1.1,
     R_5..R_7 = 1e4 and the others 1e5, dx = 2e-4, dt = 5e-6 (t = 0.39 after 78000
-    steps). The paper leaves the rate constant unstated: omega1 = 2e4 here.
+    steps). The paper leaves the rate constant unstated: omega1 = 1e3 here. With 2e4 at
+    this dx the premix ahead of the shock, heated past T_ig by the fastest particles,
+    burns first and the burn front outruns the shock (about 2.47 against 2.06), which
+    the paper's printed speed rules out.
     Returns params for the D2V24 oracle (six orbits) and for lbkm24 (v, eta, S[24])."""
     if S is None:
         S = np.full(24, 1e5)
