@@ -394,8 +394,9 @@ def run_d2v24(args):
             "roofline_reactive2d_f32": {"bound": "alu", "achieved": achieved, "peak": peak,
                                         "unit": "GB/s", "frac": achieved / peak,
                                         "peak_kind": peak_kind,
-                                        "note": "HBM fraction of the 2048^2 FP32 step; the "
-                                                "dense 24x24 transforms bound it"},
+                                        "note": "HBM fraction of the 2048^2 FP32 step; its "
+                                                "FP64 conserved sums and recovery (1:58 FP64 "
+                                                "rate) and the block transforms bound it"},
             "clocks": clk.summary()}
     print(json.dumps(line))
     return 0

@@ -5,12 +5,19 @@
 // the cell and of its NND stencil (radius 2 in x and y) are read through the
 // read-only data cache, the conserved sums and rho, u, T are formed in FP64, the
 // 20 non-conserved moments, the relaxation, the back-transform and the chemical
-// term of Eq. (24) run in the storage type R (FP64 or FP32) with M and M^-1 as
-// kernel-parameter (constant-bank) operands, and the TNE partials of the state
-// being read are reduced per block in FP64 when due. A 82-block kernel then turns
-// the partials into one history record. The dense 24x24 transforms make this form
-// FP64- (or FP32-) arithmetic-bound; it is the paper-faithful model, not the
-// throughput path of the 16-velocity marching kernel.
+// term of Eq. (24) run in the storage type R (FP64 or FP32), and the TNE partials of
+// the state being read are reduced per block in FP64 when due. A 82-block kernel then
+// turns the partials into one history record.
+//
+// M and M^-1 act in block form: butterflies inside each orbit of four velocities
+// (axis: f1+f3, f2+f4, f1-f3, f2-f4; diagonal: the sum and the three sign patterns)
+// split the 24 components by parity in (v_x, v_y), and the moments of each parity
+// sector depend on that sector's components only. The sectors are 9 (even, even:
+// m1 m4 m5 m7 m14 m16 m17 m19 m20), 6 (odd, even: m2 m8 m10 m12 m21 m23), 6 (even,
+// odd: m3 m9 m11 m13 m22 m24) and 3 (odd, odd: m6 m15 m18), so one transform costs
+// 162 multiply-adds instead of 576. The blocks and their inverses are built on the
+// host from M itself (checking that everything outside the blocks vanishes) and
+// reach the kernel as kernel-parameter (constant-bank) operands.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -37,8 +44,23 @@ constexpr int NV = 24;
 constexpr int NP = NV + 1;       // planes: f_1..f_24, lambda
 constexpr int TK = NV - 4;       // non-conserved moments Delta_5..Delta_24
 constexpr int NQ = 4 * TK + 2;   // TNE quantities: sum, |sum|, min, max of each, d, d^2
-constexpr int BT = 128;          // threads per block
+constexpr int BT = 128;          // threads per block: 128 x 1 (1-D grids) or 32 x 4
+constexpr int MAC_CELLS = 390;   // macros staged per block: (128 + 2) x 3 >= (32 + 2) x 6
 constexpr int GRAPH_CHUNK = 32;  // even: a replay leaves the ping-pong index unchanged
+
+// parity sectors: sizes, offsets of their blocks, and the moment (0-based) at each
+// sector-ordered position p = 0..23 (ee 0..8, oe 9..14, eo 15..20, oo 21..23)
+constexpr int NSEC = 4;
+constexpr int NB = 162; // 81 + 36 + 36 + 9 block entries
+__host__ __device__ constexpr int sec_n(int s) { return s == 0 ? 9 : (s == 3 ? 3 : 6); }
+__host__ __device__ constexpr int sec_p(int s) { return s == 0 ? 0 : (s == 1 ? 9 : (s == 2 ? 15 : 21)); }
+__host__ __device__ constexpr int sec_b(int s) { return s == 0 ? 0 : (s == 1 ? 81 : (s == 2 ? 117 : 153)); }
+__host__ __device__ constexpr int mom_of(int p)
+{
+    constexpr int t[NV] = {0, 3, 4, 6, 13, 15, 16, 18, 19, 1, 7, 9, 11, 20, 22,
+                           2, 8, 10, 12, 21, 23, 5, 14, 17};
+    return t[p];
+}
 
 struct Record {
     double sum[NV], abs_sum[NV], min[NV], max[NV];
@@ -51,8 +73,8 @@ static_assert(sizeof(Record) == sizeof(lbkm24_tne_global), "record layout");
 // (moment k of velocity i), Minv row-major [i][k].
 template <typename R>
 struct Model {
-    R M[NV * NV];
-    R Minv[NV * NV];
+    R Bf[NB];  // forward blocks, row-major [moment][component] per sector
+    R Bi[NB];  // their inverses, row-major [component][moment]
     R vx[NV], vy[NV], eta2[NV], S[NV];
     double vxd[NV], vyd[NV], wd[NV]; // FP64 copies for the conserved sums
     double Minvd[NV * NV];           // FP64 M^-1 for the equilibrium start
@@ -105,6 +127,68 @@ __device__ __forceinline__ void conserved_at(const Model<R>& K, const R* __restr
     ux = jx / r;
     uy = jy / r;
     if (E) *E = e;
+}
+
+// orbit butterflies: f (velocity order) -> g (sector order)
+template <typename R>
+__host__ __device__ __forceinline__ void butterfly(const R* f, R* g)
+{
+#pragma unroll
+    for (int o = 0; o < 6; o++) {
+        const R a = f[4 * o], b = f[4 * o + 1], c = f[4 * o + 2], d = f[4 * o + 3];
+        const int e0 = (o / 2) * 3;
+        if ((o & 1) == 0) { // axis orbit: (1,0) (0,1) (-1,0) (0,-1)
+            g[e0] = a + c;
+            g[e0 + 1] = b + d;
+            g[9 + o] = a - c;
+            g[15 + o] = b - d;
+        } else {            // diagonal orbit: (1,1) (-1,1) (-1,-1) (1,-1)
+            g[e0 + 2] = (a + c) + (b + d);
+            g[9 + o] = (a - c) - (b - d);
+            g[15 + o] = (a - c) + (b - d);
+            g[21 + o / 2] = (a + c) - (b + d);
+        }
+    }
+}
+
+// inverse butterflies: g (sector order) -> f (velocity order)
+template <typename R>
+__host__ __device__ __forceinline__ void unbutterfly(const R* g, R* f)
+{
+#pragma unroll
+    for (int o = 0; o < 6; o++) {
+        const int e0 = (o / 2) * 3;
+        if ((o & 1) == 0) {
+            const R sx = g[e0], sy = g[e0 + 1], ax = g[9 + o], ay = g[15 + o];
+            f[4 * o] = R(0.5) * (sx + ax);
+            f[4 * o + 1] = R(0.5) * (sy + ay);
+            f[4 * o + 2] = R(0.5) * (sx - ax);
+            f[4 * o + 3] = R(0.5) * (sy - ay);
+        } else {
+            const R e = g[e0 + 2], ax = g[9 + o], ay = g[15 + o], od = g[21 + o / 2];
+            f[4 * o] = R(0.25) * ((e + od) + (ax + ay));
+            f[4 * o + 1] = R(0.25) * ((e - od) - (ax - ay));
+            f[4 * o + 2] = R(0.25) * ((e + od) - (ax + ay));
+            f[4 * o + 3] = R(0.25) * ((e - od) + (ax - ay));
+        }
+    }
+}
+
+// y = blockdiag(B) x over the four sectors (x, y in sector order)
+template <typename R>
+__device__ __forceinline__ void block_apply(const R* B, const R* x, R* y)
+{
+#pragma unroll
+    for (int sct = 0; sct < NSEC; sct++) {
+        const int n = sec_n(sct), p0 = sec_p(sct), b0 = sec_b(sct);
+#pragma unroll
+        for (int r = 0; r < n; r++) {
+            R acc = R(0);
+#pragma unroll
+            for (int j = 0; j < n; j++) acc = fma(B[b0 + r * n + j], x[p0 + j], acc);
+            y[p0 + r] = acc;
+        }
+    }
 }
 
 // f_hat^eq_1..24 (list after Eq. (16); entries 14 and 16 with the factor T of Eq. (11))
@@ -186,6 +270,21 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
     R* __restrict__ out = static_cast<R*>(a.out);
     R Dk[TK];
     bool bad = false;
+
+    // 1. conserved sums and macros in FP64 (Eqs. (5)-(7)) of the block's cells and a
+    //    one-cell rim (the central differences of u need them), each computed once
+    __shared__ double s_rho[MAC_CELLS], s_ux[MAC_CELLS], s_uy[MAC_CELLS], s_E[MAC_CELLS];
+    {
+        const int bw = blockDim.x + 2, bh = K.ny > 1 ? blockDim.y + 2 : 1;
+        const int x0 = blockIdx.x * blockDim.x - 1, y0 = blockIdx.y * blockDim.y - (K.ny > 1);
+        for (int c = threadIdx.x + threadIdx.y * blockDim.x; c < bw * bh; c += BT) {
+            const int hx = c % bw, hy = c / bw;
+            double E;
+            conserved_at(K, in, x0 + hx, y0 + hy, s_rho[c], s_ux[c], s_uy[c], &E);
+            s_E[c] = E;
+        }
+        __syncthreads();
+    }
     if (active) {
         const size_t g = (size_t)y * K.pitch + x;
         R f[NV];
@@ -193,37 +292,33 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
         for (int i = 0; i < NV; i++) f[i] = __ldg(in + (size_t)i * K.plane + g);
         const R lam0 = __ldg(in + (size_t)NV * K.plane + g);
 
-        // 1. conserved sums and macros in FP64 (Eqs. (5)-(7))
-        double rho, ux, uy, E;
-        conserved_at(K, in, x, y, rho, ux, uy, &E);
-        const double T = (E / rho - (ux * ux + uy * uy)) / K.DI;
+        const int bw = blockDim.x + 2, two = K.ny > 1;
+        const int c0 = (threadIdx.y + two) * bw + threadIdx.x + 1;
+        const double rho = s_rho[c0], ux = s_ux[c0], uy = s_uy[c0];
+        const double T = (s_E[c0] / rho - (ux * ux + uy * uy)) / K.DI;
         bad = !(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T);
 
         // 2. velocity gradients, second-order central differences
-        double uxe, uye, uxw, uyw, r_;
-        conserved_at(K, in, x + 1, y, r_, uxe, uye);
-        conserved_at(K, in, x - 1, y, r_, uxw, uyw);
-        const double dux_dx = (uxe - uxw) * 0.5 * K.inv_dx, duy_dx = (uye - uyw) * 0.5 * K.inv_dx;
+        const double dux_dx = (s_ux[c0 + 1] - s_ux[c0 - 1]) * 0.5 * K.inv_dx;
+        const double duy_dx = (s_uy[c0 + 1] - s_uy[c0 - 1]) * 0.5 * K.inv_dx;
         double dux_dy = 0.0, duy_dy = 0.0;
-        if (K.ny > 1) {
-            double uxn, uyn, uxs, uys;
-            conserved_at(K, in, x, y + 1, r_, uxn, uyn);
-            conserved_at(K, in, x, y - 1, r_, uxs, uys);
-            dux_dy = (uxn - uxs) * 0.5 * K.inv_dy;
-            duy_dy = (uyn - uys) * 0.5 * K.inv_dy;
+        if (two) {
+            dux_dy = (s_ux[c0 + bw] - s_ux[c0 - bw]) * 0.5 * K.inv_dy;
+            duy_dy = (s_uy[c0 + bw] - s_uy[c0 - bw]) * 0.5 * K.inv_dy;
         }
         const double th = (dux_dx + duy_dy) / K.DI;
         const double pT = rho * T;
 
-        // 3. moments, equilibrium moments, non-equilibrium parts
+        // 3. moments (block form), equilibrium moments, non-equilibrium parts
         double q[NV];
         feq24(K.I, K.DI, rho, ux, uy, T, q);
+        {
+            R gv[NV], h[NV];
+            butterfly(f, gv);
+            block_apply(K.Bf, gv, h);
 #pragma unroll
-        for (int k = 0; k < TK; k++) {
-            R m = R(0);
-#pragma unroll
-            for (int i = 0; i < NV; i++) m = fma(K.M[(k + 4) * NV + i], f[i], m);
-            Dk[k] = m - (R)q[k + 4];
+            for (int p = 0; p < NV; p++)
+                if (mom_of(p) >= 4) Dk[mom_of(p) - 4] = h[p] - (R)q[mom_of(p)];
         }
 
         // 4. relaxation with A_hat_8, A_hat_9 (Eqs. (3)-(4), sign as in Eq. (29))
@@ -239,11 +334,23 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
             dlam = reaction_increment<double>((double)lam0, K.omega1 * pT, K.omega2 * pT, K.dt);
         const double lrate = dlam / K.dt;
 
-        // 6. back-transform, chemical term of Eq. (24), NND advection, forward Euler
+        // 6. back-transform (block form), chemical term of Eq. (24) on f^eq = M^-1 f_hat^eq,
+        //    NND advection, forward Euler
         const bool react = lrate != 0.0;
-        R qr[NV];
+        R Om[NV], fe[NV];
+        {
+            R w[NV], gv[NV];
 #pragma unroll
-        for (int k = 0; k < NV; k++) qr[k] = (R)q[k];
+            for (int p = 0; p < NV; p++) w[p] = mom_of(p) >= 4 ? Om_hat[mom_of(p) - 4] : R(0);
+            block_apply(K.Bi, w, gv);
+            unbutterfly(gv, Om);
+            if (react) {
+#pragma unroll
+                for (int p = 0; p < NV; p++) w[p] = (R)q[mom_of(p)];
+                block_apply(K.Bi, w, gv);
+                unbutterfly(gv, fe);
+            }
+        }
         const R chem = (R)(K.Q * lrate / (K.I * K.DI * T * T));
         const R base = (R)(-(1.0 + 2.0) * K.I * T);
         const R uxr = (R)ux, uyr = (R)uy, Ir = (R)K.I;
@@ -259,15 +366,10 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
         const size_t yp2 = (size_t)map_index(y + 2, K.ny, by) * K.pitch;
 #pragma unroll
         for (int i = 0; i < NV; i++) {
-            R om = R(0);
-#pragma unroll
-            for (int k = 0; k < TK; k++) om = fma(K.Minv[i * NV + k + 4], Om_hat[k], om);
+            R om = Om[i];
             if (react) {
-                R fe = R(0);
-#pragma unroll
-                for (int k = 0; k < NV; k++) fe = fma(K.Minv[i * NV + k], qr[k], fe);
                 const R cx = K.vx[i] - uxr, cy = K.vy[i] - uyr;
-                om += fe * chem * (base + Ir * (cx * cx + cy * cy) + K.eta2[i]);
+                om += fe[i] * chem * (base + Ir * (cx * cx + cy * cy) + K.eta2[i]);
             }
             const R* pl = in + (size_t)i * K.plane;
             R adv = R(0);
@@ -350,16 +452,14 @@ __global__ void __launch_bounds__(BT) tne_kernel(const Model<R> K, const R* __re
         const double T = (E / rho - (ux * ux + uy * uy)) / K.DI;
         double q[NV];
         feq24(K.I, K.DI, rho, ux, uy, T, q);
-        R f[NV];
+        R f[NV], gv[NV], h[NV];
 #pragma unroll
         for (int i = 0; i < NV; i++) f[i] = __ldg(in + (size_t)i * K.plane + g);
+        butterfly(f, gv);
+        block_apply(K.Bf, gv, h);
 #pragma unroll
-        for (int k = 0; k < TK; k++) {
-            R m = R(0);
-#pragma unroll
-            for (int i = 0; i < NV; i++) m = fma(K.M[(k + 4) * NV + i], f[i], m);
-            Dk[k] = m - (R)q[k + 4];
-        }
+        for (int p = 0; p < NV; p++)
+            if (mom_of(p) >= 4) Dk[mom_of(p) - 4] = h[p] - (R)q[mom_of(p)];
         if (delta) {
             const size_t n = (size_t)K.nx * K.ny, c = (size_t)y * K.nx + x;
 #pragma unroll
@@ -475,27 +575,28 @@ void moment_rows(const double* vx, const double* vy, const double* e, double* M)
     }
 }
 
-// M^-1 by LU factorisation with partial pivoting in long double, one step of
-// iterative refinement per column. Returns max |M Minv - 1|, or -1 if singular.
-double invert(const double* M, double* Minv)
+// The inverse of an n x n matrix (n <= 24) by LU factorisation with partial pivoting
+// in long double, one step of iterative refinement per column. Returns max |A Ainv - 1|,
+// or -1 if singular.
+double invert(const double* M, double* Minv, int n = NV)
 {
     long double lu[NV][NV];
     int perm[NV];
     long double amax = 0;
-    for (int r = 0; r < NV; r++) {
+    for (int r = 0; r < n; r++) {
         perm[r] = r;
-        for (int c = 0; c < NV; c++) {
-            lu[r][c] = M[r * NV + c];
+        for (int c = 0; c < n; c++) {
+            lu[r][c] = M[r * n + c];
             amax = fmaxl(amax, fabsl(lu[r][c]));
         }
     }
-    for (int k = 0; k < NV; k++) {
+    for (int k = 0; k < n; k++) {
         int p = k;
-        for (int r = k + 1; r < NV; r++)
+        for (int r = k + 1; r < n; r++)
             if (fabsl(lu[r][k]) > fabsl(lu[p][k])) p = r;
         if (fabsl(lu[p][k]) < 1e-13L * amax) return -1.0;
         if (p != k) {
-            for (int c = 0; c < NV; c++) {
+            for (int c = 0; c < n; c++) {
                 long double t = lu[k][c];
                 lu[k][c] = lu[p][c];
                 lu[p][c] = t;
@@ -504,56 +605,94 @@ double invert(const double* M, double* Minv)
             perm[k] = perm[p];
             perm[p] = t;
         }
-        for (int r = k + 1; r < NV; r++) {
+        for (int r = k + 1; r < n; r++) {
             lu[r][k] /= lu[k][k];
-            for (int c = k + 1; c < NV; c++) lu[r][c] -= lu[r][k] * lu[k][c];
+            for (int c = k + 1; c < n; c++) lu[r][c] -= lu[r][k] * lu[k][c];
         }
     }
     auto solve = [&](const long double* rhs, long double* x) {
         long double z[NV];
-        for (int r = 0; r < NV; r++) {
+        for (int r = 0; r < n; r++) {
             long double s = rhs[perm[r]];
             for (int c = 0; c < r; c++) s -= lu[r][c] * z[c];
             z[r] = s;
         }
-        for (int r = NV - 1; r >= 0; r--) {
+        for (int r = n - 1; r >= 0; r--) {
             long double s = z[r];
-            for (int c = r + 1; c < NV; c++) s -= lu[r][c] * x[c];
+            for (int c = r + 1; c < n; c++) s -= lu[r][c] * x[c];
             x[r] = s / lu[r][r];
         }
     };
-    for (int col = 0; col < NV; col++) {
+    for (int col = 0; col < n; col++) {
         long double e[NV], x[NV], res[NV], dx[NV];
-        for (int r = 0; r < NV; r++) e[r] = r == col ? 1.0L : 0.0L;
+        for (int r = 0; r < n; r++) e[r] = r == col ? 1.0L : 0.0L;
         solve(e, x);
-        for (int r = 0; r < NV; r++) {
+        for (int r = 0; r < n; r++) {
             long double s = e[r];
-            for (int c = 0; c < NV; c++) s -= (long double)M[r * NV + c] * x[c];
+            for (int c = 0; c < n; c++) s -= (long double)M[r * n + c] * x[c];
             res[r] = s;
         }
         solve(res, dx);
-        for (int r = 0; r < NV; r++) Minv[r * NV + col] = (double)(x[r] + dx[r]);
+        for (int r = 0; r < n; r++) Minv[r * n + col] = (double)(x[r] + dx[r]);
     }
     double worst = 0.0;
-    for (int r = 0; r < NV; r++)
-        for (int c = 0; c < NV; c++) {
+    for (int r = 0; r < n; r++)
+        for (int c = 0; c < n; c++) {
             long double s = 0;
-            for (int k = 0; k < NV; k++) s += (long double)M[r * NV + k] * Minv[k * NV + c];
+            for (int k = 0; k < n; k++) s += (long double)M[r * n + k] * Minv[k * n + c];
             worst = fmax(worst, fabs((double)(s - (r == c ? 1.0L : 0.0L))));
         }
     return worst;
 }
 
+// The sector blocks of M (column j of a sector = M applied to the inverse butterfly of
+// that sector's j-th unit component, restricted to the sector's moments) and their
+// inverses. Returns the largest |entry| M produces outside the blocks relative to the
+// largest inside, or -1 if a block is singular.
+double build_blocks(const double* M, double* Bf, double* Bi)
+{
+    double leak = 0.0, big = 0.0;
+    for (int sct = 0; sct < NSEC; sct++) {
+        const int n = sec_n(sct), p0 = sec_p(sct);
+        double blk[NV * NV], inv[NV * NV];
+        for (int j = 0; j < n; j++) {
+            double gv[NV] = {0}, f[NV], col[NV];
+            gv[p0 + j] = 1.0;
+            unbutterfly(gv, f);
+            for (int k = 0; k < NV; k++) {
+                col[k] = 0.0;
+                for (int i = 0; i < NV; i++) col[k] += M[k * NV + i] * f[i];
+            }
+            for (int p = 0; p < NV; p++) {
+                const bool inside = p >= p0 && p < p0 + n;
+                if (inside) {
+                    blk[(p - p0) * n + j] = col[mom_of(p)];
+                    big = fmax(big, fabs(col[mom_of(p)]));
+                } else {
+                    leak = fmax(leak, fabs(col[mom_of(p)]));
+                }
+            }
+        }
+        const double res = invert(blk, inv, n);
+        if (res < 0.0 || res > 1e-9) return -1.0;
+        for (int k = 0; k < n * n; k++) {
+            Bf[sec_b(sct) + k] = blk[k];
+            Bi[sec_b(sct) + k] = inv[k];
+        }
+    }
+    return leak / big;
+}
+
 template <typename R>
-void fill_model(const lbkm24_params& p, const double* M, const double* Minv, const double* vx,
-                const double* vy, const double* e, int pitch, Model<R>* K)
+void fill_model(const lbkm24_params& p, const double* Bf, const double* Bi, const double* Minv,
+                const double* vx, const double* vy, const double* e, int pitch, Model<R>* K)
 {
     memset(K, 0, sizeof(*K));
-    for (int k = 0; k < NV * NV; k++) {
-        K->M[k] = (R)M[k];
-        K->Minv[k] = (R)Minv[k];
-        K->Minvd[k] = Minv[k];
+    for (int k = 0; k < NB; k++) {
+        K->Bf[k] = (R)Bf[k];
+        K->Bi[k] = (R)Bi[k];
     }
+    for (int k = 0; k < NV * NV; k++) K->Minvd[k] = Minv[k];
     for (int i = 0; i < NV; i++) {
         K->vx[i] = (R)vx[i];
         K->vy[i] = (R)vy[i];
@@ -746,12 +885,15 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
     if (p.tne_every < 0 || (p.tne_every > 0 && p.tne_capacity < 1))
         return fail(nullptr, LBKM_EINVAL, "tne_every >= 0 and tne_capacity >= 1");
 
-    double vx[NV], vy[NV], e[NV], M[NV * NV], Minv[NV * NV];
+    double vx[NV], vy[NV], e[NV], M[NV * NV], Minv[NV * NV], Bf[NB], Bi[NB];
     velocity_table(p.v, p.eta, vx, vy, e);
     moment_rows(vx, vy, e, M);
     const double res = invert(M, Minv);
-    if (res < 0.0 || res > 1e-9)
+    const double leak = res < 0.0 ? -1.0 : build_blocks(M, Bf, Bi);
+    if (res < 0.0 || res > 1e-9 || leak < 0.0)
         return fail(nullptr, LBKM_ESINGULAR, "the D2V24 velocity set gives a singular M");
+    if (leak > 1e-12)
+        return fail(nullptr, LBKM_ESINGULAR, "M is not block-diagonal under the butterflies");
 
     lbkm24* h = new lbkm24();
     h->p = p;
@@ -760,8 +902,8 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
     h->elem = p.precision == LBKM_F64 ? 8 : 4;
     h->pitch = (p.nx + 31) / 32 * 32;
     h->plane_elems = (size_t)h->pitch * p.ny;
-    fill_model(p, M, Minv, vx, vy, e, h->pitch, &h->Kd);
-    fill_model(p, M, Minv, vx, vy, e, h->pitch, &h->Kf);
+    fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, &h->Kd);
+    fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, &h->Kf);
     h->block = p.ny > 1 ? dim3(32, BT / 32) : dim3(BT, 1);
     h->grid = dim3((p.nx + h->block.x - 1) / h->block.x, (p.ny + h->block.y - 1) / h->block.y);
     h->nblocks = (int)(h->grid.x * h->grid.y);
