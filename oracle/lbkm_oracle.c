@@ -33,7 +33,9 @@
  *  10. forward Euler: f^{n+1} = f^n + dt (-div(v f) + Omega),
  *      lambda^{n+1} = clamp(lambda^n - dt u.grad(lambda) + dlambda_chem, 0, 1);
  *      optionally (time_scheme 1) two such steps E averaged with the state at t_n,
- *      u^{n+1} = (u^n + E(E(u^n))) / 2, the two-stage SSP Runge-Kutta scheme.
+ *      u^{n+1} = (u^n + E(E(u^n))) / 2, the two-stage SSP Runge-Kutta scheme, or
+ *      (time_scheme 2) the three-stage one, u1 = E(u^n), u2 = 3/4 u^n + 1/4 E(u1),
+ *      u^{n+1} = 1/3 u^n + 2/3 E(u2) (Shu and Osher's third-order form).
  * TNE measures (Sec. VI, Eqs. (90)-(91)) are evaluated on a given state.
  *
  * The same source builds two oracles. NV = 16 (default): the 16-velocity model in
@@ -83,7 +85,8 @@ typedef struct {
     int32_t side_bc[4];
     double side_rho[4], side_ux[4], side_uy[4], side_T[4], side_lam[4];
     /* 0: forward Euler; 1: the two-stage strong-stability-preserving Runge-Kutta
-     * scheme built from that step E: u1 = E(u), u^{n+1} = (u + E(u1)) / 2 */
+     * scheme built from that step E: u1 = E(u), u^{n+1} = (u + E(u1)) / 2; 2: the
+     * three-stage one, u2 = 3/4 u + 1/4 E(u1), u^{n+1} = 1/3 u + 2/3 E(u2) */
     int32_t time_scheme;
 } orc_params;
 
@@ -634,7 +637,7 @@ int orc_run(const orc_params* p, const double* M, const double* Minv, double* f,
     }
     double *fa = f, *la = lam, *fb = f2, *lb = l2;
     double *f3 = NULL, *l3 = NULL;
-    if (p->time_scheme == 1) {
+    if (p->time_scheme == 1 || p->time_scheme == 2) {
         f3 = malloc(sizeof(double) * NV * n);
         l3 = malloc(sizeof(double) * n);
         if (!f3 || !l3) {
@@ -655,6 +658,20 @@ int orc_run(const orc_params* p, const double* M, const double* Minv, double* f,
             }
             for (size_t i = 0; i < NV * n; i++) fb[i] = 0.5 * (fa[i] + f3[i]);
             for (size_t i = 0; i < n; i++) lb[i] = 0.5 * (la[i] + l3[i]);
+        } else if (p->time_scheme == 2) {
+            /* three stages: u2 = 3/4 u + 1/4 E(u1), u^{n+1} = 1/3 u + 2/3 E(u2) */
+            if (orc_step(p, M, Minv, fb, lb, f3, l3) != 0) {
+                free(f2); free(l2); free(f3); free(l3);
+                return -1;
+            }
+            for (size_t i = 0; i < NV * n; i++) f3[i] = 0.75 * fa[i] + 0.25 * f3[i];
+            for (size_t i = 0; i < n; i++) l3[i] = 0.75 * la[i] + 0.25 * l3[i];
+            if (orc_step(p, M, Minv, f3, l3, fb, lb) != 0) {
+                free(f2); free(l2); free(f3); free(l3);
+                return -1;
+            }
+            for (size_t i = 0; i < NV * n; i++) fb[i] = fa[i] / 3.0 + 2.0 * fb[i] / 3.0;
+            for (size_t i = 0; i < n; i++) lb[i] = la[i] / 3.0 + 2.0 * lb[i] / 3.0;
         }
         double* t = fa; fa = fb; fb = t;
         t = la; la = lb; lb = t;
