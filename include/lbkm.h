@@ -135,7 +135,10 @@ typedef struct {
     int32_t time_scheme;   /* 0: forward Euler (the paper's single stage); 1: two-stage
                               SSP Runge-Kutta from that step E, u^{n+1} = (u^n +
                               E(E(u^n)))/2 (second order in time; two launches per
-                              step; TNE of u^n; not for batched instances or lbkm_grad) */
+                              step); 2: three-stage SSP Runge-Kutta (Shu-Osher form),
+                              u2 = 3/4 u^n + 1/4 E(E(u^n)), u^{n+1} = 1/3 u^n + 2/3 E(u2)
+                              (third order; three launches per step, a third state
+                              copy); TNE of u^n; not for batched instances or lbkm_grad */
 } lbkm_params;
 
 /* Grid-wide TNE measures of one state (Sec. VI). Sums are weighted by dx*dy;

@@ -38,6 +38,7 @@ struct lbkm {
     cudaStream_t stream;
     cudaStream_t capture_stream;
     void* buf[2];
+    void* buf3;  // the middle-stage state of the three-stage scheme (time_scheme 2)
     int cur;
     double* partials;
     int grid, tgrid;
@@ -92,15 +93,20 @@ const void* model_ptr(const lbkm* h)
     return h->precision == 0 ? (const void*)&h->Kd : (const void*)&h->Kf;
 }
 
-// stage 0: Euler step buf[from] -> buf[1-from]; stage 1: first RK2 stage, same
-// buffers; stage 2: second RK2 stage from buf[1-from] back into buf[from]
-StepLaunch step_args(const lbkm* h, int from, int stage = 0)
+// stage 0: Euler step buf[from] -> buf[1-from]; stage 1: first Runge-Kutta stage, same
+// buffers (u1 = E(u^n) into buf[1-from]); stage 2: last stage from `src` (u1 for RK2, u2
+// for RK3) back into buf[from] with weights (wp, wn) on (u^n, E(src)); stage 3: the
+// middle RK3 stage, u2 = 3/4 u^n + 1/4 E(u1) into buf3
+StepLaunch step_args(const lbkm* h, int from, int stage = 0, const void* src = nullptr,
+                     double wp = 0.0, double wn = 1.0)
 {
     StepLaunch a;
-    a.in = stage == 2 ? h->buf[1 - from] : h->buf[from];
-    a.out = stage == 2 ? h->buf[from] : h->buf[1 - from];
+    a.in = stage >= 2 ? src : h->buf[from];
+    a.out = stage == 2 ? h->buf[from] : (stage == 3 ? h->buf3 : h->buf[1 - from]);
     a.prev = h->buf[from];
     a.stage = stage;
+    a.wprev = wp;
+    a.wnew = wn;
     a.partials = h->partials;
     a.ctr = h->ctr;
     a.hist = h->hist;
@@ -132,6 +138,7 @@ void release(lbkm* h)
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
+    cudaFree(h->buf3);
     cudaFree(h->partials);
     cudaFree(h->ctr);
     cudaFree(h->hist);
@@ -296,8 +303,9 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
         return fail(nullptr, LBKM_EINVAL, "omega1, omega2 must be >= 0");
     if (!(p.T_ig >= 0.0 && p.T_ig <= 1e300))
         return fail(nullptr, LBKM_EINVAL, "T_ig must be finite and >= 0");
-    if (p.time_scheme != 0 && p.time_scheme != 1)
-        return fail(nullptr, LBKM_EINVAL, "time_scheme must be 0 (Euler) or 1 (SSP-RK2)");
+    if (p.time_scheme < 0 || p.time_scheme > 2)
+        return fail(nullptr, LBKM_EINVAL,
+                    "time_scheme must be 0 (Euler), 1 (SSP-RK2) or 2 (SSP-RK3)");
     if (p.tne_every < 0 || p.tne_capacity < 1)
         return fail(nullptr, LBKM_EINVAL, "tne_every must be >= 0 and tne_capacity >= 1");
 
@@ -361,6 +369,10 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
     if ((e = cudaMalloc(&h->buf[1], h->state_bytes_dev)) != cudaSuccess) return bail(e, "state B");
     if ((e = cudaMemset(h->buf[0], 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemset(h->buf[1], 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
+    if (p.time_scheme == 2) {
+        if ((e = cudaMalloc(&h->buf3, h->state_bytes_dev)) != cudaSuccess) return bail(e, "state C");
+        if ((e = cudaMemset(h->buf3, 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
+    }
     h->grid = step_grid(h->precision, h->recovery, h->two_d, h->nx, h->ny, sbc);
     if (h->grid < 1) return bail(cudaGetLastError(), "step grid");
     h->tgrid = tne_grid(h->nx, h->ny);
@@ -429,14 +441,25 @@ lbkm_status lbkm_init_fields(lbkm_t h, const double* rho, const double* ux, cons
 // buffer), or the two-stage SSP Runge-Kutta scheme (E(u^n) into the other buffer, then
 // (u^n + E(E(u^n))) / 2 back into buf[c]). c is updated to the buffer holding u^{n+1}.
 // With TNE on, a small kernel then turns the step's per-block partials into the record.
+// The three-stage scheme (Shu and Osher's SSP-RK3): u1 = E(u^n) into buf[1-c],
+// u2 = 3/4 u^n + 1/4 E(u1) into buf3, u^{n+1} = 1/3 u^n + 2/3 E(u2) back into buf[c].
 static cudaError_t launch_full_step(const lbkm* h, const void* K, int& c, cudaStream_t st)
 {
-    const StepLaunch a0 = step_args(h, c, h->p.time_scheme == 0 ? 0 : 1);
+    const int ts = h->p.time_scheme;
+    const StepLaunch a0 = step_args(h, c, ts == 0 ? 0 : 1);
     cudaError_t e = launch_step(h->precision, h->recovery, h->two_d, K, a0, st);
-    if (e == cudaSuccess && h->p.time_scheme != 0)
-        e = launch_step(h->precision, h->recovery, h->two_d, K, step_args(h, c, 2), st);
+    if (e == cudaSuccess && ts == 1)
+        e = launch_step(h->precision, h->recovery, h->two_d, K,
+                        step_args(h, c, 2, h->buf[1 - c], 0.5, 0.5), st);
+    if (e == cudaSuccess && ts == 2) {
+        e = launch_step(h->precision, h->recovery, h->two_d, K,
+                        step_args(h, c, 3, h->buf[1 - c], 0.75, 0.25), st);
+        if (e == cudaSuccess)
+            e = launch_step(h->precision, h->recovery, h->two_d, K,
+                            step_args(h, c, 2, h->buf3, 1.0 / 3.0, 2.0 / 3.0), st);
+    }
     if (e == cudaSuccess && a0.tne_every > 0) e = launch_tne_finish(a0, st);
-    if (e == cudaSuccess && h->p.time_scheme == 0) c = 1 - c;
+    if (e == cudaSuccess && ts == 0) c = 1 - c;
     return e;
 }
 

@@ -60,11 +60,13 @@ __global__ void __launch_bounds__(TX * TY)
     const int nx = K.nx, ny = K.ny, pitch = K.pitch;
     const int64_t plane = K.plane;
     const R* __restrict__ in = static_cast<const R*>(a.in);
-    R* __restrict__ out = static_cast<R*>(a.out);
+    R* out = static_cast<R*>(a.out); // not restrict: prev may alias it
 
     const int64_t step = a.ctr->step;
-    const bool do_tne = a.tne_every > 0 && (step % a.tne_every) == 0 && a.stage != 2;
-    const bool avg = a.stage == 2; // second SSP-RK2 stage: average with u^n (= out)
+    const bool do_tne = a.tne_every > 0 && (step % a.tne_every) == 0 && a.stage < 2;
+    const bool avg = a.stage >= 2; // later SSP-RK stage: weighted with u^n (prev)
+    const R* prev = static_cast<const R*>(a.prev);
+    const R wp = (R)a.wprev, wn = (R)a.wnew;
     if (do_tne) {
         for (int i = tid; i < C::NW * NSUM; i += C::NT) tsum[i] = 0.0;
         for (int i = tid; i < C::NW * NMM; i += C::NT)
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(TX * TY)
 #pragma unroll
             for (int i = 0; i < 16; i++) {
                 const R v = f[i] + K.dt * (W[i] - adv[i]);
-                out[i * plane + g] = avg ? R(0.5) * (out[i * plane + g] + v) : v;
+                out[i * plane + g] = avg ? wp * prev[i * plane + g] + wn * v : v;
             }
 
             // lambda: u . grad(lambda) with NND interface values, reaction, clamp
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(TX * TY)
 #undef NY
             R ln = lam0 - K.dt * la + dlam;
             ln = ln < R(0) ? R(0) : (ln > R(1) ? R(1) : ln);
-            out[16 * plane + g] = avg ? R(0.5) * (out[16 * plane + g] + ln) : ln;
+            out[16 * plane + g] = avg ? wp * prev[16 * plane + g] + wn * ln : ln;
         }
 
         // 4. TNE statistics of this tile (all lanes take part in the shuffles)
@@ -301,8 +303,8 @@ __global__ void __launch_bounds__(TX * TY)
             a.ctr->hist_count += 1;
             a.ctr->tne_step = step;
         }
-        if (a.stage != 2) a.ctr->tne_pending = do_tne ? 1 : 0;
-        if (a.stage != 1) a.ctr->step = step + 1;
+        if (a.stage < 2) a.ctr->tne_pending = do_tne ? 1 : 0;
+        if (a.stage == 0 || a.stage == 2) a.ctr->step = step + 1;
         a.ctr->arrivals = 0u;
     }
 }

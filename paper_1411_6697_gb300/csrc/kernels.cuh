@@ -28,11 +28,13 @@ struct TneRecord {
 struct StepLaunch {
     const void* in;      // state at t_n  [17][ny][pitch]
     void* out;           // state at t_n+1
-    // stage: 0 forward Euler step; 1 first stage of the SSP-RK2 step (writes E(u^n),
-    // reduces the TNE of u^n, does not advance the step counter); 2 second stage
-    // (writes (prev + E(in)) / 2 with prev = u^n, no TNE, advances the counter)
+    // stage: 0 forward Euler step; 1 first stage of an SSP Runge-Kutta step (writes
+    // E(u^n), reduces the TNE of u^n, does not advance the step counter); 2 last stage
+    // (writes wprev * prev + wnew * E(in) with prev = u^n, no TNE, advances the
+    // counter); 3 a middle stage (the same weighted write, no TNE, no counter)
     const void* prev;
     int stage;
+    double wprev, wnew;
     double* partials;    // [grid][TNE_PART]
     DevCounters* ctr;
     TneRecord* hist;     // ring of hist_cap records

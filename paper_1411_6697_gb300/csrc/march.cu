@@ -309,12 +309,17 @@ __global__ void __launch_bounds__(MT, 4)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = K.nx, ny = K.ny;
     const float* __restrict__ in = static_cast<const float*>(a.in);
-    float* __restrict__ out = static_cast<float*>(a.out);
+    float* out = static_cast<float*>(a.out); // not restrict: prev may alias it
+    // AVG: a later SSP Runge-Kutta stage, out = wp * u^n + wn * E(in), u^n read from prev
+    // at the cell's own position (prev may be out itself: each value is read before it
+    // is written, by the same thread)
+    const float* pv = static_cast<const float*>(a.prev);
+    const float wp = (float)a.wprev, wn = (float)a.wnew;
 
     const DfConst C = df_constants(K);
 
     const int64_t step = a.ctr->step;
-    // AVG: second SSP-RK2 stage (average with u^n, which out still holds; no TNE)
+    // AVG stages reduce no TNE
     const bool do_tne = !AVG && a.tne_every > 0 && (step % a.tne_every) == 0;
     if (do_tne) {
         for (int i = tid; i < NWM * NSUM; i += MT) tsum[i] = 0.0;
@@ -461,11 +466,13 @@ __global__ void __launch_bounds__(MT, 4)
                 V2 v = fma(V2(dt), W[i] - adv, f[i]);
                 if (act1) {
                     float2* q = reinterpret_cast<float2*>(out + i * K.plane + g);
-                    if constexpr (AVG) v = V2(0.5f) * (V2(*q) + v);
+                    if constexpr (AVG)
+                        v = fma(V2(wp), V2(*reinterpret_cast<const float2*>(pv + i * K.plane + g)),
+                                V2(wn) * v);
                     *q = v.v;
                 } else if (act0) {
                     float* q = out + i * K.plane + g;
-                    *q = AVG ? 0.5f * (*q + v.x()) : v.x();
+                    *q = AVG ? fmaf(wp, pv[i * K.plane + g], wn * v.x()) : v.x();
                 }
             };
 #define PX(i) nnd_pos_x(load6(plane_row(ring, (i), y), lx))
@@ -498,11 +505,13 @@ __global__ void __launch_bounds__(MT, 4)
 #undef NY
             if (act1) {
                 float2* q = reinterpret_cast<float2*>(out + 16 * K.plane + g);
-                if constexpr (AVG) ln = V2(0.5f) * (V2(*q) + ln);
+                if constexpr (AVG)
+                    ln = fma(V2(wp), V2(*reinterpret_cast<const float2*>(pv + 16 * K.plane + g)),
+                             V2(wn) * ln);
                 *q = ln.v;
             } else if (act0) {
                 float* q = out + 16 * K.plane + g;
-                *q = AVG ? 0.5f * (*q + ln.x()) : ln.x();
+                *q = AVG ? fmaf(wp, pv[16 * K.plane + g], wn * ln.x()) : ln.x();
             }
 
             // TNE statistics of the state being stepped (Eqs. (90)-(91)); sums of Delta_k
@@ -586,8 +595,8 @@ __global__ void __launch_bounds__(MT, 4)
             a.ctr->hist_count += 1;
             a.ctr->tne_step = step;
         }
-        if (a.stage != 2) a.ctr->tne_pending = do_tne ? 1 : 0;
-        if (a.stage != 1) a.ctr->step = step + 1;
+        if (a.stage < 2) a.ctr->tne_pending = do_tne ? 1 : 0;
+        if (a.stage == 0 || a.stage == 2) a.ctr->step = step + 1;
         a.ctr->arrivals = 0u;
     }
 }
@@ -693,7 +702,7 @@ cudaError_t launch_march(int mode, const ModelConst<float>& K, const StepLaunch&
     march_plan(mode, K.nx, K.ny, &g, &rows);
     if (g < 0) return cudaErrorInvalidConfiguration;
     if (g != a.grid) return cudaErrorInvalidConfiguration; // partial buffers sized for a.grid
-    const bool avg = a.stage == 2;
+    const bool avg = a.stage >= 2;
     switch (mode & 3) {
     case 0: launch_variant<0, false>(avg, K, a, rows, s); break;
     case 1: launch_variant<1, false>(avg, K, a, rows, s); break;

@@ -290,6 +290,7 @@ class Solver:
         self = cls.__new__(cls)
         lib = load()
         self._lib = lib
+        self._api = _Api(lib, cls._PREFIX)
         kw.setdefault("precision", F32)
         self.params = params if params is not None else default_params(**kw)
         nxs = np.ascontiguousarray(inst_nx, dtype=np.int32)

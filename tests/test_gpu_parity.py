@@ -104,16 +104,17 @@ def test_step_2d_nonequilibrium_parity(prec, rec, nx, ny, bc):
     assert lam_ref.max() > lam.max() - 1e-12  # the reaction ran
 
 
-# ------------------------------------------------------------------ SSP-RK2 steps
+# ------------------------------------------------------------------ SSP-RK2 / RK3 steps
+@pytest.mark.parametrize("scheme", [1, 2], ids=["rk2", "rk3"])
 @pytest.mark.parametrize("prec,rec", PRECS, ids=PID)
 @pytest.mark.parametrize("nx,ny,bc", [(70, 37, (0, 0)), (262, 40, (1, 1)), (33, 9, (1, 0)),
                                       (300, 1, (1, 0))])
-def test_rk2_steps_parity(prec, rec, nx, ny, bc):
-    """The two-stage SSP Runge-Kutta scheme (two fused Euler launches, the second
-    averaged with u^n): 40 steps (one graph-captured chunk of 32 and 8 direct steps),
+def test_rk_steps_parity(prec, rec, nx, ny, bc, scheme):
+    """The two- and three-stage SSP Runge-Kutta schemes (fused Euler launches, the later
+    ones weighted with u^n): 40 steps (one graph-captured chunk of 32 and 8 direct steps),
     every plane against the oracle's scheme, the step count and the per-step TNE of u^n."""
     params, fields = mixed_2d(nx, ny, bc=bc, seed=nx + 3)
-    params["time_scheme"] = 1
+    params["time_scheme"] = scheme
     s, ob, f, lam = start(params, fields, prec, rec, noise_seed=ny + 3, tne_every=1,
                           tne_capacity=64)
     steps = 40

@@ -41,7 +41,7 @@ def create(**kw):
     (dict(ny=8, bc=(5, 0), sides=[(3, 1.0, 0, 0, 1, 1.5), (1, 1, 0, 0, 1, 0)] + [(1, 1, 0, 0, 1, 0)] * 2), 1),
     (dict(ny=1, bc=(0, 5), sides=[(1, 1, 0, 0, 1, 0)] * 2 + [(4, 1, 0, 0, 1, 0)] * 2), 1),
     (dict(tne_every=-1), 1),
-    (dict(time_scheme=2), 1),
+    (dict(time_scheme=3), 1),
     (dict(tne_capacity=0), 1),
     (dict(omega1=-1.0), 1),
     # the paper's first two rings (shared speed and eta): singular M
