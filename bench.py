@@ -379,6 +379,27 @@ def run_d2v24(args):
                     mcell_per_s=n * steps / (ms * 1e-3) / 1e6, ms_per_step=ms / steps,
                     cells=n, steps=steps)
                 s.close()
+        # single- against multiple-relaxation-time cost (Sec. V, Table I: the paper's MRT
+        # D2V24 takes 3 % longer than its SRT form on one CPU core): equal rates, no TNE,
+        # the fast path (collision = 0) against the general kernel (collision = 1)
+        cfg = cases[1][1]
+        fl = cfg["fields"]
+        steps = cases[1][2]
+        for tag, prec in (("f64", lbkm.F64), ("f32", lbkm.F32)):
+            for form, coll in (("srt", 0), ("mrt", 1)):
+                p = dict(cfg["lib_params"])
+                bc = (p.pop("bc_x"), p.pop("bc_y"))
+                p["S"] = np.full(24, 5e4)
+                s = lbkm.Solver24(precision=prec, bc=bc, stream=stream, collision=coll, **p)
+                s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+                with torch.cuda.stream(stream):
+                    s.step(args.warmup)
+                    ms = time_steps(s, stream, steps)
+                s.sync()
+                n = p["nx"] * p["ny"]
+                out["reactive2d_equal_rates_%s_%s" % (form, tag)] = dict(
+                    mcell_per_s=n * steps / (ms * 1e-3) / 1e6, ms_per_step=ms / steps)
+                s.close()
     peak, peak_kind = measured_peak()
     big = out["reactive2d_f32"]
     alg = 200 * big["cells"]  # 25 FP32 planes read and written per cell update

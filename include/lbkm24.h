@@ -65,6 +65,11 @@ typedef struct {
     int32_t bc_x, bc_y;   /* LBKM_BC_PERIODIC or LBKM_BC_ZERO_GRADIENT */
     int32_t tne_every;    /* 0: no on-the-fly TNE; k > 0: every k-th step */
     int32_t tne_capacity; /* records kept in the device history ring (>= 1) */
+    int32_t collision;    /* 0: when R_5..R_24 are all equal and tne_every = 0, step with
+                             the single-relaxation-time form of Sec. V, -R (f_i -
+                             [M^-1 f_hat^eq]_i) + C_i, which skips M f (the same update
+                             up to rounding: A_hat vanishes for equal rates); 1: always
+                             the general moment-space form */
 } lbkm24_params;
 
 /* Grid-wide TNE measures of one state (Sec. VI): index k-1 holds Delta_k;

@@ -258,17 +258,23 @@ __device__ __forceinline__ void block_tne(const R* Dk, bool active, double* part
     }
 }
 
-template <typename R>
+// SRT: the single-relaxation-time fast path (all R_5..R_24 equal, no TNE due): with one
+// rate the moment-space relaxation is -R (f - M^-1 f_hat^eq) in velocity space (the SRT
+// form of Sec. V) and A_hat vanishes, so the forward transform of f is skipped and only
+// f^eq = M^-1 f_hat^eq is formed (it also feeds the chemical term of Eq. (24)).
+template <typename R, bool SRT>
 __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const bool active = x < K.nx && y < K.ny;
     const int64_t step = a.ctr->step;
-    const bool do_tne = a.tne_every > 0 && (step % a.tne_every) == 0;
+    const bool do_tne = !SRT && a.tne_every > 0 && (step % a.tne_every) == 0;
     const R* __restrict__ in = static_cast<const R*>(a.in);
     R* __restrict__ out = static_cast<R*>(a.out);
     R Dk[TK];
+#pragma unroll
+    for (int k = 0; k < TK; k++) Dk[k] = R(0);
     bool bad = false;
 
     // 1. conserved sums and macros in FP64 (Eqs. (5)-(7)) of the block's cells and a
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
         // 3. moments (block form), equilibrium moments, non-equilibrium parts
         double q[NV];
         feq24(K.I, K.DI, rho, ux, uy, T, q);
-        {
+        if (!SRT) {
             R gv[NV], h[NV];
             butterfly(f, gv);
             block_apply(K.Bf, gv, h);
@@ -325,8 +331,10 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
         R Om_hat[TK];
 #pragma unroll
         for (int k = 0; k < TK; k++) Om_hat[k] = -K.S[k + 4] * Dk[k];
-        Om_hat[3] += (R)(pT * K.A8c * (4.0 * ux * (dux_dx - th) + 2.0 * uy * (duy_dx + dux_dy)));
-        Om_hat[4] += (R)(pT * K.A9c * (4.0 * uy * (duy_dy - th) + 2.0 * ux * (duy_dx + dux_dy)));
+        if (!SRT) {
+            Om_hat[3] += (R)(pT * K.A8c * (4.0 * ux * (dux_dx - th) + 2.0 * uy * (duy_dx + dux_dy)));
+            Om_hat[4] += (R)(pT * K.A9c * (4.0 * uy * (duy_dy - th) + 2.0 * ux * (duy_dx + dux_dy)));
+        }
 
         // 5. reaction over dt with p and T frozen at t_n (Eq. (28), m = n = 1)
         double dlam = 0.0;
@@ -340,15 +348,21 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
         R Om[NV], fe[NV];
         {
             R w[NV], gv[NV];
+            if (!SRT) {
 #pragma unroll
-            for (int p = 0; p < NV; p++) w[p] = mom_of(p) >= 4 ? Om_hat[mom_of(p) - 4] : R(0);
-            block_apply(K.Bi, w, gv);
-            unbutterfly(gv, Om);
-            if (react) {
+                for (int p = 0; p < NV; p++) w[p] = mom_of(p) >= 4 ? Om_hat[mom_of(p) - 4] : R(0);
+                block_apply(K.Bi, w, gv);
+                unbutterfly(gv, Om);
+            }
+            if (SRT || react) {
 #pragma unroll
                 for (int p = 0; p < NV; p++) w[p] = (R)q[mom_of(p)];
                 block_apply(K.Bi, w, gv);
                 unbutterfly(gv, fe);
+            }
+            if (SRT) {
+#pragma unroll
+                for (int i = 0; i < NV; i++) Om[i] = -K.S[4] * (f[i] - fe[i]);
             }
         }
         const R chem = (R)(K.Q * lrate / (K.I * K.DI * T * T));
@@ -410,9 +424,6 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
         R ln = lam0 - (R)K.dt * la + (R)dlam;
         ln = ln < R(0) ? R(0) : (ln > R(1) ? R(1) : ln);
         out[(size_t)NV * K.plane + g] = ln;
-    } else {
-#pragma unroll
-        for (int k = 0; k < TK; k++) Dk[k] = R(0);
     }
 
     // TNE partials of the state read (all threads take part), status, step counter
@@ -743,6 +754,7 @@ struct lbkm24 {
     Record* hist;
     Record* tne_out;
     bool initialized;
+    bool srt;  // the single-relaxation-time fast path runs the steps
     int64_t host_steps;
     cudaGraphExec_t graph[2];
     std::string err;
@@ -780,10 +792,17 @@ cudaError_t launch_one_step(const lbkm24* h, int from, cudaStream_t st)
     a.hist_cap = h->p.tne_capacity;
     a.tne_every = h->p.tne_every;
     a.area = h->p.dx * h->p.dy;
-    if (h->p.precision == LBKM_F64)
-        step_kernel<double><<<h->grid, h->block, 0, st>>>(h->Kd, a);
-    else
-        step_kernel<float><<<h->grid, h->block, 0, st>>>(h->Kf, a);
+    if (h->p.precision == LBKM_F64) {
+        if (h->srt)
+            step_kernel<double, true><<<h->grid, h->block, 0, st>>>(h->Kd, a);
+        else
+            step_kernel<double, false><<<h->grid, h->block, 0, st>>>(h->Kd, a);
+    } else {
+        if (h->srt)
+            step_kernel<float, true><<<h->grid, h->block, 0, st>>>(h->Kf, a);
+        else
+            step_kernel<float, false><<<h->grid, h->block, 0, st>>>(h->Kf, a);
+    }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && h->p.tne_every > 0) {
         finish_kernel<<<NQ, 256, 0, st>>>(h->partials, h->nblocks, h->hist, h->p.tne_capacity,
@@ -884,6 +903,8 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
     }
     if (p.tne_every < 0 || (p.tne_every > 0 && p.tne_capacity < 1))
         return fail(nullptr, LBKM_EINVAL, "tne_every >= 0 and tne_capacity >= 1");
+    if (p.collision != 0 && p.collision != 1)
+        return fail(nullptr, LBKM_EINVAL, "collision must be 0 (fast path allowed) or 1");
 
     double vx[NV], vy[NV], e[NV], M[NV * NV], Minv[NV * NV], Bf[NB], Bi[NB];
     velocity_table(p.v, p.eta, vx, vy, e);
@@ -902,6 +923,9 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
     h->elem = p.precision == LBKM_F64 ? 8 : 4;
     h->pitch = (p.nx + 31) / 32 * 32;
     h->plane_elems = (size_t)h->pitch * p.ny;
+    bool equal = true;
+    for (int k = 5; k < NV; k++) equal = equal && p.S[k] == p.S[4];
+    h->srt = equal && p.tne_every == 0 && p.collision == 0;
     fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, &h->Kd);
     fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, &h->Kf);
     h->block = p.ny > 1 ? dim3(32, BT / 32) : dim3(BT, 1);

@@ -86,6 +86,7 @@ class Params24(ctypes.Structure):
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dt", ctypes.c_double),
         ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
         ("tne_every", ctypes.c_int32), ("tne_capacity", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
     ]
 
 

@@ -107,6 +107,7 @@ int main(void) {
   printf("tne %zu\n", sizeof(lbkm24_tne_global));
   F(lbkm24_params, gamma) F(lbkm24_params, v) F(lbkm24_params, eta) F(lbkm24_params, S)
   F(lbkm24_params, Q) F(lbkm24_params, dt) F(lbkm24_params, bc_x) F(lbkm24_params, tne_capacity)
+  F(lbkm24_params, collision)
   F(lbkm24_tne_global, d_sum) F(lbkm24_tne_global, step)
   return 0; }
 """
@@ -118,7 +119,7 @@ int main(void) {
         out = dict(line.split() for line in subprocess.check_output([exe]).decode().splitlines())
     assert int(out["params"]) == ctypes.sizeof(lbkm.Params24)
     assert int(out["tne"]) == ctypes.sizeof(lbkm.TneGlobal24)
-    for m in ("gamma", "v", "eta", "S", "Q", "dt", "bc_x", "tne_capacity"):
+    for m in ("gamma", "v", "eta", "S", "Q", "dt", "bc_x", "tne_capacity", "collision"):
         assert int(out[m]) == getattr(lbkm.Params24, m).offset, m
     assert int(out["d_sum"]) == lbkm.TneGlobal24.d_sum.offset
     assert int(out["step"]) == lbkm.TneGlobal24.step.offset

@@ -297,3 +297,23 @@ def test_paper_steady_detonation_at_full_size(prec):
         # the paper's values sit 0.02 % from CJ; 0.5 % is the bound the 16-velocity
         # detonation pin holds against CJ, and what an unstated rate constant allows
         assert abs(v / gold[k] - 1) < 5e-3, (k, v, gold[k])
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PID)
+def test_srt_fast_path(prec):
+    """All R_5..R_24 equal and no TNE: the single-relaxation-time form of Sec. V, which
+    skips M f, against the oracle's moment-space step and against the general kernel
+    forced by collision = 1 (the same update up to rounding)."""
+    cfg = mixed_2d(70, 23, bc=(0, 1), seed=11)
+    S = np.full(24, 3e4)
+    cfg["params"]["S"] = S
+    cfg["lib_params"]["S"] = S
+    s, ob, f, lam = start(cfg, prec, noise_seed=3)
+    g = solver(cfg, prec, collision=1)
+    g.set_state(state_bytes(np.concatenate([f, lam[None]]), prec))
+    s.step(20)
+    g.step(20)
+    f_ref, lam_ref = ob.run(f, lam, 20)
+    check_state(s, ob, f_ref, lam_ref, prec)
+    a, b = s.f_planes(), g.f_planes()
+    assert rel_l2(a, b) <= (1e-13 if prec == lbkm.F64 else 1e-5)

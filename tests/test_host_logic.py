@@ -74,3 +74,9 @@ def test_d2v24_invalid_parameters_are_rejected(kw):
     with pytest.raises(lbkm.LbkmError) as e:
         lbkm.Solver24(stream=0, **base)
     assert e.value.code in (1, 4)
+
+
+def test_d2v24_collision_flag_is_checked():
+    with pytest.raises(lbkm.LbkmError) as e:
+        lbkm.Solver24(stream=0, nx=16, ny=1, collision=2)
+    assert e.value.code == 1
