@@ -44,7 +44,7 @@ constexpr int NV = 24;
 constexpr int NP = NV + 1;       // planes: f_1..f_24, lambda
 constexpr int TK = NV - 4;       // non-conserved moments Delta_5..Delta_24
 constexpr int NQ = 4 * TK + 2;   // TNE quantities: sum, |sum|, min, max of each, d, d^2
-constexpr int BT = 128;          // threads per block: 128 x 1 (1-D grids) or 32 x 4
+constexpr int BT = 128;          // threads per block: 128 x 1 or 32 x 1 (1-D grids), 32 x 4
 constexpr int MAC_CELLS = 390;   // macros staged per block: (128 + 2) x 3 >= (32 + 2) x 6
 constexpr int GRAPH_CHUNK = 32;  // even: a replay leaves the ping-pong index unchanged
 
@@ -251,9 +251,10 @@ __device__ __forceinline__ void block_tne(const R* Dk, bool active, double* part
         if (lane == 0) red[w][q] = v;
     }
     __syncthreads();
-    for (int q = t; q < NQ; q += BT) {
+    const int nt = blockDim.x * blockDim.y, nw = (nt + 31) / 32;
+    for (int q = t; q < NQ; q += nt) {
         double v = red[0][q];
-        for (int k = 1; k < BT / 32; k++) v = tcomb(tkind(q), v, red[k][q]);
+        for (int k = 1; k < nw; k++) v = tcomb(tkind(q), v, red[k][q]);
         partials[(size_t)q * nblocks + b] = v;
     }
 }
@@ -283,7 +284,8 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
     {
         const int bw = blockDim.x + 2, bh = K.ny > 1 ? blockDim.y + 2 : 1;
         const int x0 = blockIdx.x * blockDim.x - 1, y0 = blockIdx.y * blockDim.y - (K.ny > 1);
-        for (int c = threadIdx.x + threadIdx.y * blockDim.x; c < bw * bh; c += BT) {
+        for (int c = threadIdx.x + threadIdx.y * blockDim.x; c < bw * bh;
+             c += blockDim.x * blockDim.y) {
             const int hx = c % bw, hy = c / bw;
             double E;
             conserved_at(K, in, x0 + hx, y0 + hy, s_rho[c], s_ux[c], s_uy[c], &E);
@@ -928,7 +930,10 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
     h->srt = equal && p.tne_every == 0 && p.collision == 0;
     fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, &h->Kd);
     fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, &h->Kf);
-    h->block = p.ny > 1 ? dim3(32, BT / 32) : dim3(BT, 1);
+    // 1-D grids too short to give every SM a block of 128 cells run blocks of one warp:
+    // the step is latency-bound there, and more SMs each take fewer cells
+    const bool narrow = p.ny == 1 && (p.nx + BT - 1) / BT < 2 * 152;
+    h->block = p.ny > 1 ? dim3(32, BT / 32) : dim3(narrow ? 32 : BT, 1);
     h->grid = dim3((p.nx + h->block.x - 1) / h->block.x, (p.ny + h->block.y - 1) / h->block.y);
     h->nblocks = (int)(h->grid.x * h->grid.y);
     auto bail = [&](cudaError_t ce, const char* what) {

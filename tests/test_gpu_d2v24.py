@@ -317,3 +317,14 @@ def test_srt_fast_path(prec):
     check_state(s, ob, f_ref, lam_ref, prec)
     a, b = s.f_planes(), g.f_planes()
     assert rel_l2(a, b) <= (1e-13 if prec == lbkm.F64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PID)
+def test_long_1d_grid_uses_wide_blocks(prec):
+    """1-D grids long enough for 2 x 152 blocks of 128 cells run 128-thread blocks (short
+    ones run one-warp blocks): 40000 cells with a detonation driver, 10 steps."""
+    cfg = li.d2v24_detonation(nx=40000, steps=10, omega1=1e3, x_driver=1.0)
+    s, ob, f, lam = start(cfg, prec)
+    s.step(10)
+    f_ref, lam_ref = ob.run(f, lam, 10)
+    check_state(s, ob, f_ref, lam_ref, prec)
