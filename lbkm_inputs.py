@@ -240,6 +240,44 @@ def d2v24_detonation(nx=5000, steps=78000, omega1=1e3, dx=2e-4, dt=5e-6, S=None,
                 name="d2v24_detonation_nx%d" % nx)
 
 
+def d2v24_shock_tube(which, steps=None):
+    """The three shock tubes of Sec. IV.B with the paper's own D2V24 sets:
+    Sod: (1, 1, 0) | (0.125, 0.8, 0) on [0, 1], 1000 cells, dt = 1e-5, t = 0.2, I = 3,
+    (v; eta) = (2.5, 2.2, 1.2; 6.5, 3, 0), R_5..R_7 = 1.2e4, others 1e5;
+    Lax: (0.445, 7.928, 0.698) | (0.5, 1.142, 0) on [-1, 1], 2000 cells, dt = 1e-5,
+    t = 0.15, I = 1, (4.7, 3.3, 1; 6, 2.5, 0.9), R_5..R_7 = 2e4, R_8, R_9 = 8e4, others 1e5;
+    Sjogreen: (1, 0.5, -1.2) | (1, 0.5, 1.2) on [-0.5, 0.5], 500 cells, dt = 2e-5,
+    t = 0.03, I = 4, (0.4, 1.0, 1.8; 0.3, 1.9, 1.5), R_8, R_9 = 2e4, others 5e4.
+    States are (rho, T, u_x); steps defaults to the paper's end time."""
+    S = np.full(24, 1e5)
+    if which == "sod":
+        S[4:7] = 1.2e4
+        nx, dx, dt, t, gamma, v = 1000, 1e-3, 1e-5, 0.2, 1.4, ((2.5, 2.2, 1.2), (6.5, 3.0, 0.0))
+        left, right = (1.0, 1.0, 0.0), (0.125, 0.8, 0.0)
+    elif which == "lax":
+        S[4:7] = 2e4
+        S[7:9] = 8e4
+        nx, dx, dt, t, gamma, v = 2000, 1e-3, 1e-5, 0.15, 5.0 / 3.0, ((4.7, 3.3, 1.0), (6.0, 2.5, 0.9))
+        left, right = (0.445, 7.928, 0.698), (0.5, 1.142, 0.0)
+    else:
+        S[:] = 5e4
+        S[7:9] = 2e4
+        nx, dx, dt, t, gamma, v = 500, 2e-3, 2e-5, 0.03, 4.0 / 3.0, ((0.4, 1.0, 1.8), (0.3, 1.9, 1.5))
+        left, right = (1.0, 0.5, -1.2), (1.0, 0.5, 1.2)
+    x = np.arange(nx)
+    L = x < nx // 2
+    fields = dict(rho=np.where(L, left[0], right[0])[None, :],
+                  T=np.where(L, left[1], right[1])[None, :],
+                  ux=np.where(L, left[2], right[2])[None, :], uy=np.zeros((1, nx)),
+                  lam=np.zeros((1, nx)))
+    common = dict(nx=nx, ny=1, gamma=gamma, Q=0.0, omega1=0.0, omega2=0.0, T_ig=1.1, dx=dx,
+                  dy=dx, dt=dt, bc_x=1, bc_y=0)
+    n = int(round(t / dt)) if steps is None else steps
+    return dict(params=dict(common, S=S, **d2v24_orbits(*v)),
+                lib_params=dict(common, S=S, v=v[0], eta=v[1]), steps=n, fields=fields,
+                left=left, right=right, name="d2v24_%s_nx%d" % (which, nx))
+
+
 def d2v24_reactive2d(n=64, steps=20, T_ig=1.0, seed_offset=8, v=D2V24_DETONATION_V):
     """2-D periodic reactive field of random Fourier modes (the recipe of reactive2d)
     for D2V24: S_1..S_24 ~ U[1e4, 1e5], Q = 1, k = 2e4, dx = dy = 1e-3, dt = 5e-6."""
