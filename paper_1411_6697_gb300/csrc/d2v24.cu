@@ -31,10 +31,12 @@
 #include "cell.cuh"
 #include "kernels.cuh"
 #include "lbkm24.h"
+#include "pair.cuh"
 
 namespace v24 {
 
 using lbk::DevCounters;
+using lbk::f2d_exact;
 using lbk::map_index;
 using lbk::nnd_neg;
 using lbk::nnd_pos;
@@ -77,8 +79,9 @@ struct Model {
     R Bi[NB];  // their inverses, row-major [component][moment]
     R vx[NV], vy[NV], eta2[NV], S[NV];
     double vxd[NV], vyd[NV], wd[NV]; // FP64 copies for the conserved sums
+    double cd[6], wod[6];            // speed and v^2 + eta^2 of each orbit (FP64)
     double Minvd[NV * NV];           // FP64 M^-1 for the equilibrium start
-    double I, DI, Q, omega1, omega2, T_ig, A8c, A9c;
+    double I, DI, inv_DI, Q, omega1, omega2, T_ig, A8c, A9c;
     double dt, inv_dx, inv_dy;
     int nx, ny, pitch, bc_x, bc_y, pad_;
     int64_t plane;
@@ -105,28 +108,51 @@ __host__ __device__ __forceinline__ int tkind(int q)
     return (q < 2 * TK || q >= 4 * TK) ? 0 : (q < 3 * TK ? 1 : 2);
 }
 
-// rho, u_x, u_y (FP64) at cell (x, y) of state `in`, boundary conditions applied
+__device__ __forceinline__ double to_f64(double x) { return x; }
+// exact, on the integer pipe (the FP64 unit runs at 1/58 of the FP32 rate on GB300)
+__device__ __forceinline__ double to_f64(float x) { return f2d_exact(x); }
+
+// rho, u_x, u_y and, if asked, T (FP64) at cell (x, y) of state `in`, boundary conditions
+// applied (Eqs. (5)-(7)). The sums go orbit by orbit: an orbit of speed c adds its sum s
+// to rho, c times its x and y differences to rho u, and (c^2 or 2 c^2) + eta^2 times s to
+// the energy moment m_4; 1/rho comes from an FP32 seed and two Newton steps.
 template <typename R>
 __device__ __forceinline__ void conserved_at(const Model<R>& K, const R* __restrict__ in, int x,
                                              int y, double& rho, double& ux, double& uy,
-                                             double* E = nullptr)
+                                             double* T = nullptr)
 {
     x = map_index(x, K.nx, K.bc_x == 0 ? 0 : 1);
     y = map_index(y, K.ny, K.bc_y == 0 ? 0 : 1);
     const R* p = in + (size_t)y * K.pitch + x;
     double r = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
 #pragma unroll
-    for (int i = 0; i < NV; i++) {
-        const double f = (double)__ldg(p + (size_t)i * K.plane);
-        r += f;
-        jx = fma(K.vxd[i], f, jx);
-        jy = fma(K.vyd[i], f, jy);
-        if (E) e = fma(K.wd[i], f, e);
+    for (int o = 0; o < 6; o++) {
+        const double a = to_f64(__ldg(p + (size_t)(4 * o) * K.plane));
+        const double b = to_f64(__ldg(p + (size_t)(4 * o + 1) * K.plane));
+        const double c = to_f64(__ldg(p + (size_t)(4 * o + 2) * K.plane));
+        const double d = to_f64(__ldg(p + (size_t)(4 * o + 3) * K.plane));
+        const double sac = a + c, sbd = b + d, dac = a - c, dbd = b - d;
+        const double sum = sac + sbd;
+        double gx, gy;
+        if ((o & 1) == 0) { // axis: (1,0) (0,1) (-1,0) (0,-1)
+            gx = dac;
+            gy = dbd;
+        } else {            // diagonal: (1,1) (-1,1) (-1,-1) (1,-1)
+            gx = dac - dbd;
+            gy = dac + dbd;
+        }
+        r += sum;
+        jx = fma(K.cd[o], gx, jx);
+        jy = fma(K.cd[o], gy, jy);
+        if (T) e = fma(K.wod[o], sum, e);
     }
+    double q = f2d_exact(lbk::rcp_approx(lbk::d2f_rn(r)));
+    q = fma(q, fma(-r, q, 1.0), q);
+    q = fma(q, fma(-r, q, 1.0), q);
     rho = r;
-    ux = jx / r;
-    uy = jy / r;
-    if (E) *E = e;
+    ux = jx * q;
+    uy = jy * q;
+    if (T) *T = (e * q - (ux * ux + uy * uy)) * K.inv_DI;
 }
 
 // orbit butterflies: f (velocity order) -> g (sector order)
@@ -191,14 +217,15 @@ __device__ __forceinline__ void block_apply(const R* B, const R* x, R* y)
     }
 }
 
-// f_hat^eq_1..24 (list after Eq. (16); entries 14 and 16 with the factor T of Eq. (11))
-__device__ __forceinline__ void feq24(double I, double DI, double rho, double ux, double uy,
-                                      double T, double* q)
+// f_hat^eq_1..24 (list after Eq. (16); entries 14 and 16 with the factor T of Eq. (11)),
+// in the arithmetic type F
+template <typename F>
+__device__ __forceinline__ void feq24(F I, F DI, F rho, F ux, F uy, F T, F* q)
 {
-    const double u2 = ux * ux + uy * uy;
-    const double A = (DI + 2.0) * T + u2, B = (DI + 4.0) * T + u2;
-    const double rx = rho * ux, ry = rho * uy, IT = I * T;
-    const double C = u2 * u2 + 4.0 * (DI + 4.0) * T * T + (DI + 10.0) * u2 * T; // D = 2
+    const F u2 = ux * ux + uy * uy;
+    const F A = (DI + F(2)) * T + u2, B = (DI + F(4)) * T + u2;
+    const F rx = rho * ux, ry = rho * uy, IT = I * T;
+    const F C = u2 * u2 + F(4) * (DI + F(4)) * T * T + (DI + F(10)) * u2 * T; // D = 2
     q[0] = rho;
     q[1] = rx;
     q[2] = ry;
@@ -208,21 +235,21 @@ __device__ __forceinline__ void feq24(double I, double DI, double rho, double ux
     q[6] = rho * (T + uy * uy);
     q[7] = rx * A;
     q[8] = ry * A;
-    q[9] = rx * (3.0 * T + ux * ux);
+    q[9] = rx * (F(3) * T + ux * ux);
     q[10] = ry * (T + ux * ux);
     q[11] = rx * (T + uy * uy);
-    q[12] = ry * (3.0 * T + uy * uy);
+    q[12] = ry * (F(3) * T + uy * uy);
     q[13] = rho * A * T + rx * ux * B;
     q[14] = rx * uy * B;
     q[15] = rho * A * T + ry * uy * B;
     q[16] = rho * IT * (T + ux * ux);
     q[17] = rx * uy * IT;
     q[18] = rho * IT * (T + uy * uy);
-    q[19] = rho * IT * (u2 + (2.0 + 3.0 * I) * T);
+    q[19] = rho * IT * (u2 + (F(2) + F(3) * I) * T);
     q[20] = rx * C;
     q[21] = ry * C;
-    q[22] = rx * IT * (u2 + (4.0 + 3.0 * I) * T);
-    q[23] = ry * IT * (u2 + (4.0 + 3.0 * I) * T);
+    q[22] = rx * IT * (u2 + (F(4) + F(3) * I) * T);
+    q[23] = ry * IT * (u2 + (F(4) + F(3) * I) * T);
 }
 
 // Block reduction of the TNE quantities of this thread's cell into partials
@@ -280,16 +307,14 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
 
     // 1. conserved sums and macros in FP64 (Eqs. (5)-(7)) of the block's cells and a
     //    one-cell rim (the central differences of u need them), each computed once
-    __shared__ double s_rho[MAC_CELLS], s_ux[MAC_CELLS], s_uy[MAC_CELLS], s_E[MAC_CELLS];
+    __shared__ double s_rho[MAC_CELLS], s_ux[MAC_CELLS], s_uy[MAC_CELLS], s_T[MAC_CELLS];
     {
         const int bw = blockDim.x + 2, bh = K.ny > 1 ? blockDim.y + 2 : 1;
         const int x0 = blockIdx.x * blockDim.x - 1, y0 = blockIdx.y * blockDim.y - (K.ny > 1);
         for (int c = threadIdx.x + threadIdx.y * blockDim.x; c < bw * bh;
              c += blockDim.x * blockDim.y) {
             const int hx = c % bw, hy = c / bw;
-            double E;
-            conserved_at(K, in, x0 + hx, y0 + hy, s_rho[c], s_ux[c], s_uy[c], &E);
-            s_E[c] = E;
+            conserved_at(K, in, x0 + hx, y0 + hy, s_rho[c], s_ux[c], s_uy[c], &s_T[c]);
         }
         __syncthreads();
     }
@@ -303,7 +328,7 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
         const int bw = blockDim.x + 2, two = K.ny > 1;
         const int c0 = (threadIdx.y + two) * bw + threadIdx.x + 1;
         const double rho = s_rho[c0], ux = s_ux[c0], uy = s_uy[c0];
-        const double T = (s_E[c0] / rho - (ux * ux + uy * uy)) / K.DI;
+        const double T = s_T[c0];
         bad = !(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T);
 
         // 2. velocity gradients, second-order central differences
@@ -314,19 +339,20 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
             dux_dy = (s_ux[c0 + bw] - s_ux[c0 - bw]) * 0.5 * K.inv_dy;
             duy_dy = (s_uy[c0 + bw] - s_uy[c0 - bw]) * 0.5 * K.inv_dy;
         }
-        const double th = (dux_dx + duy_dy) / K.DI;
         const double pT = rho * T;
 
-        // 3. moments (block form), equilibrium moments, non-equilibrium parts
-        double q[NV];
-        feq24(K.I, K.DI, rho, ux, uy, T, q);
+        // 3. moments (block form), equilibrium moments, non-equilibrium parts; rho, u, T
+        //    were recovered in FP64, the bulk from here on runs in R
+        const R rr = (R)rho, uxr = (R)ux, uyr = (R)uy, Tr = (R)T, Ir = (R)K.I;
+        R q[NV];
+        feq24<R>(Ir, (R)K.DI, rr, uxr, uyr, Tr, q);
         if (!SRT) {
             R gv[NV], h[NV];
             butterfly(f, gv);
             block_apply(K.Bf, gv, h);
 #pragma unroll
             for (int p = 0; p < NV; p++)
-                if (mom_of(p) >= 4) Dk[mom_of(p) - 4] = h[p] - (R)q[mom_of(p)];
+                if (mom_of(p) >= 4) Dk[mom_of(p) - 4] = h[p] - q[mom_of(p)];
         }
 
         // 4. relaxation with A_hat_8, A_hat_9 (Eqs. (3)-(4), sign as in Eq. (29))
@@ -334,8 +360,10 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
 #pragma unroll
         for (int k = 0; k < TK; k++) Om_hat[k] = -K.S[k + 4] * Dk[k];
         if (!SRT) {
-            Om_hat[3] += (R)(pT * K.A8c * (4.0 * ux * (dux_dx - th) + 2.0 * uy * (duy_dx + dux_dy)));
-            Om_hat[4] += (R)(pT * K.A9c * (4.0 * uy * (duy_dy - th) + 2.0 * ux * (duy_dx + dux_dy)));
+            const R gxx = (R)dux_dx, gyx = (R)duy_dx, gxy = (R)dux_dy, gyy = (R)duy_dy;
+            const R th = (gxx + gyy) / (R)K.DI, pTr = rr * Tr, shear = gyx + gxy;
+            Om_hat[3] += pTr * (R)K.A8c * (R(4) * uxr * (gxx - th) + R(2) * uyr * shear);
+            Om_hat[4] += pTr * (R)K.A9c * (R(4) * uyr * (gyy - th) + R(2) * uxr * shear);
         }
 
         // 5. reaction over dt with p and T frozen at t_n (Eq. (28), m = n = 1)
@@ -358,7 +386,7 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
             }
             if (SRT || react) {
 #pragma unroll
-                for (int p = 0; p < NV; p++) w[p] = (R)q[mom_of(p)];
+                for (int p = 0; p < NV; p++) w[p] = q[mom_of(p)];
                 block_apply(K.Bi, w, gv);
                 unbutterfly(gv, fe);
             }
@@ -369,7 +397,6 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
         }
         const R chem = (R)(K.Q * lrate / (K.I * K.DI * T * T));
         const R base = (R)(-(1.0 + 2.0) * K.I * T);
-        const R uxr = (R)ux, uyr = (R)uy, Ir = (R)K.I;
         const int xm2 = map_index(x - 2, K.nx, K.bc_x == 0 ? 0 : 1);
         const int xm1 = map_index(x - 1, K.nx, K.bc_x == 0 ? 0 : 1);
         const int xp1 = map_index(x + 1, K.nx, K.bc_x == 0 ? 0 : 1);
@@ -460,11 +487,10 @@ __global__ void __launch_bounds__(BT) tne_kernel(const Model<R> K, const R* __re
     for (int k = 0; k < TK; k++) Dk[k] = R(0);
     if (active) {
         const size_t g = (size_t)y * K.pitch + x;
-        double rho, ux, uy, E;
-        conserved_at(K, in, x, y, rho, ux, uy, &E);
-        const double T = (E / rho - (ux * ux + uy * uy)) / K.DI;
-        double q[NV];
-        feq24(K.I, K.DI, rho, ux, uy, T, q);
+        double rho, ux, uy, T;
+        conserved_at(K, in, x, y, rho, ux, uy, &T);
+        R q[NV];
+        feq24<R>((R)K.I, (R)K.DI, (R)rho, (R)ux, (R)uy, (R)T, q);
         R f[NV], gv[NV], h[NV];
 #pragma unroll
         for (int i = 0; i < NV; i++) f[i] = __ldg(in + (size_t)i * K.plane + g);
@@ -472,7 +498,7 @@ __global__ void __launch_bounds__(BT) tne_kernel(const Model<R> K, const R* __re
         block_apply(K.Bf, gv, h);
 #pragma unroll
         for (int p = 0; p < NV; p++)
-            if (mom_of(p) >= 4) Dk[mom_of(p) - 4] = h[p] - (R)q[mom_of(p)];
+            if (mom_of(p) >= 4) Dk[mom_of(p) - 4] = h[p] - q[mom_of(p)];
         if (delta) {
             const size_t n = (size_t)K.nx * K.ny, c = (size_t)y * K.nx + x;
 #pragma unroll
@@ -524,7 +550,7 @@ __global__ void init_kernel(const Model<R> K, const double* rho, const double* u
          c += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(c % K.nx), y = (int)(c / K.nx);
         double q[NV];
-        feq24(K.I, K.DI, rho[c], ux[c], uy[c], T[c], q);
+        feq24<double>(K.I, K.DI, rho[c], ux[c], uy[c], T[c], q);
         const size_t g = (size_t)y * K.pitch + x;
 #pragma unroll
         for (int i = 0; i < NV; i++) {
@@ -545,9 +571,8 @@ __global__ void macros_kernel(const Model<R> K, const R* __restrict__ in, double
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(c % K.nx), y = (int)(c / K.nx);
-        double r, u, v, E;
-        conserved_at(K, in, x, y, r, u, v, &E);
-        const double t = (E / r - (u * u + v * v)) / K.DI;
+        double r, u, v, t;
+        conserved_at(K, in, x, y, r, u, v, &t);
         if (rho) rho[c] = r;
         if (ux) ux[c] = u;
         if (uy) uy[c] = v;
@@ -715,8 +740,14 @@ void fill_model(const lbkm24_params& p, const double* Bf, const double* Bi, cons
         K->vyd[i] = vy[i];
         K->wd[i] = vx[i] * vx[i] + vy[i] * vy[i] + e[i] * e[i];
     }
+    for (int o = 0; o < 6; o++) {
+        const double c = p.v[o / 2], et = p.eta[o / 2];
+        K->cd[o] = c;
+        K->wod[o] = c * c * ((o & 1) ? 2.0 : 1.0) + et * et;
+    }
     K->I = 2.0 / (p.gamma - 1.0) - 2.0;
     K->DI = 2.0 + K->I;
+    K->inv_DI = 1.0 / K->DI;
     K->Q = p.Q;
     K->omega1 = p.omega1;
     K->omega2 = p.omega2;
