@@ -78,8 +78,11 @@ struct Model {
     R Bf[NB];  // forward blocks, row-major [moment][component] per sector
     R Bi[NB];  // their inverses, row-major [component][moment]
     R vx[NV], vy[NV], eta2[NV], S[NV];
+    R vxs[NV], vys[NV];              // v_x / dx and v_y / dy in R
+    R dt_r, inv_dx_r, inv_dy_r, hdx_r, hdy_r, I_r, DI_r, A8c_r, A9c_r; // constants in R
     double vxd[NV], vyd[NV], wd[NV]; // FP64 copies for the conserved sums
     double cd[6], wod[6];            // speed and v^2 + eta^2 of each orbit (FP64)
+    float cdh[6], cdl[6], wdh[6], wdl[6]; // the same split into hi + lo FP32 pairs
     double Minvd[NV * NV];           // FP64 M^-1 for the equilibrium start
     double I, DI, inv_DI, Q, omega1, omega2, T_ig, A8c, A9c;
     double dt, inv_dx, inv_dy;
@@ -108,6 +111,14 @@ __host__ __device__ __forceinline__ int tkind(int q)
     return (q < 2 * TK || q >= 4 * TK) ? 0 : (q < 3 * TK ? 1 : 2);
 }
 
+// FP64 -> R: exact (double) or rounded to nearest on the integer pipe (float)
+template <typename R>
+__device__ __forceinline__ R to_r(double x);
+template <>
+__device__ __forceinline__ double to_r<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_r<float>(double x) { return lbk::d2f_rn(x); }
+
 __device__ __forceinline__ double to_f64(double x) { return x; }
 // exact, on the integer pipe (the FP64 unit runs at 1/58 of the FP32 rate on GB300)
 __device__ __forceinline__ double to_f64(float x) { return f2d_exact(x); }
@@ -125,6 +136,37 @@ __device__ __forceinline__ void conserved_at(const Model<R>& K, const R* __restr
     y = map_index(y, K.ny, K.bc_y == 0 ? 0 : 1);
     const R* p = in + (size_t)y * K.pitch + x;
     double r = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
+    if constexpr (sizeof(R) == 4) {
+        // FP32 state: the same sums as double-floats on the FP32 pipes (error-free
+        // TwoSum butterflies, products with split constants, ~48 significant bits),
+        // carried into FP64 once
+        using lbk::df;
+        df R0{0.f, 0.f}, R1{0.f, 0.f}, R2{0.f, 0.f}, R3{0.f, 0.f};
+#pragma unroll
+        for (int o = 0; o < 6; o++) {
+            const float a = __ldg(p + (size_t)(4 * o) * K.plane);
+            const float b = __ldg(p + (size_t)(4 * o + 1) * K.plane);
+            const float c = __ldg(p + (size_t)(4 * o + 2) * K.plane);
+            const float d = __ldg(p + (size_t)(4 * o + 3) * K.plane);
+            const df sac = lbk::two_sum(a, c), sbd = lbk::two_sum(b, d);
+            const df dac = lbk::two_sum(a, -c), dbd = lbk::two_sum(b, -d);
+            const df sum = lbk::df_add(sac, sbd);
+            df gx = dac, gy = dbd;
+            if (o & 1) {
+                gx = lbk::df_sub(dac, dbd);
+                gy = lbk::df_add(dac, dbd);
+            }
+            const df co{K.cdh[o], K.cdl[o]};
+            R0 = lbk::df_add(R0, sum);
+            R1 = lbk::df_add(R1, lbk::df_mul(co, gx));
+            R2 = lbk::df_add(R2, lbk::df_mul(co, gy));
+            if (T) R3 = lbk::df_add(R3, lbk::df_mul(df{K.wdh[o], K.wdl[o]}, sum));
+        }
+        r = f2d_exact(R0.hi) + f2d_exact(R0.lo);
+        jx = f2d_exact(R1.hi) + f2d_exact(R1.lo);
+        jy = f2d_exact(R2.hi) + f2d_exact(R2.lo);
+        if (T) e = f2d_exact(R3.hi) + f2d_exact(R3.lo);
+    } else {
 #pragma unroll
     for (int o = 0; o < 6; o++) {
         const double a = to_f64(__ldg(p + (size_t)(4 * o) * K.plane));
@@ -145,6 +187,7 @@ __device__ __forceinline__ void conserved_at(const Model<R>& K, const R* __restr
         jx = fma(K.cd[o], gx, jx);
         jy = fma(K.cd[o], gy, jy);
         if (T) e = fma(K.wod[o], sum, e);
+    }
     }
     double q = f2d_exact(lbk::rcp_approx(lbk::d2f_rn(r)));
     q = fma(q, fma(-r, q, 1.0), q);
@@ -291,7 +334,7 @@ __device__ __forceinline__ void block_tne(const R* Dk, bool active, double* part
 // form of Sec. V) and A_hat vanishes, so the forward transform of f is skipped and only
 // f^eq = M^-1 f_hat^eq is formed (it also feeds the chemical term of Eq. (24)).
 template <typename R, bool SRT>
-__global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a)
+__global__ void __launch_bounds__(BT, sizeof(R) == 4 ? 3 : 1) step_kernel(const Model<R> K, const Args a)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -331,21 +374,23 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
         const double T = s_T[c0];
         bad = !(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T);
 
-        // 2. velocity gradients, second-order central differences
-        const double dux_dx = (s_ux[c0 + 1] - s_ux[c0 - 1]) * 0.5 * K.inv_dx;
-        const double duy_dx = (s_uy[c0 + 1] - s_uy[c0 - 1]) * 0.5 * K.inv_dx;
-        double dux_dy = 0.0, duy_dy = 0.0;
-        if (two) {
-            dux_dy = (s_ux[c0 + bw] - s_ux[c0 - bw]) * 0.5 * K.inv_dy;
-            duy_dy = (s_uy[c0 + bw] - s_uy[c0 - bw]) * 0.5 * K.inv_dy;
-        }
         const double pT = rho * T;
 
-        // 3. moments (block form), equilibrium moments, non-equilibrium parts; rho, u, T
-        //    were recovered in FP64, the bulk from here on runs in R
-        const R rr = (R)rho, uxr = (R)ux, uyr = (R)uy, Tr = (R)T, Ir = (R)K.I;
+        // 2. rho, u, T were recovered in FP64; the bulk from here on runs in R, including
+        //    the velocity gradients (second-order central differences)
+        const R rr = to_r<R>(rho), uxr = to_r<R>(ux), uyr = to_r<R>(uy), Tr = to_r<R>(T);
+        const R Ir = K.I_r;
+        const R gxx = (to_r<R>(s_ux[c0 + 1]) - to_r<R>(s_ux[c0 - 1])) * K.hdx_r;
+        const R gyx = (to_r<R>(s_uy[c0 + 1]) - to_r<R>(s_uy[c0 - 1])) * K.hdx_r;
+        R gxy = R(0), gyy = R(0);
+        if (two) {
+            gxy = (to_r<R>(s_ux[c0 + bw]) - to_r<R>(s_ux[c0 - bw])) * K.hdy_r;
+            gyy = (to_r<R>(s_uy[c0 + bw]) - to_r<R>(s_uy[c0 - bw])) * K.hdy_r;
+        }
+
+        // 3. moments (block form), equilibrium moments, non-equilibrium parts
         R q[NV];
-        feq24<R>(Ir, (R)K.DI, rr, uxr, uyr, Tr, q);
+        feq24<R>(Ir, K.DI_r, rr, uxr, uyr, Tr, q);
         if (!SRT) {
             R gv[NV], h[NV];
             butterfly(f, gv);
@@ -360,10 +405,9 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
 #pragma unroll
         for (int k = 0; k < TK; k++) Om_hat[k] = -K.S[k + 4] * Dk[k];
         if (!SRT) {
-            const R gxx = (R)dux_dx, gyx = (R)duy_dx, gxy = (R)dux_dy, gyy = (R)duy_dy;
-            const R th = (gxx + gyy) / (R)K.DI, pTr = rr * Tr, shear = gyx + gxy;
-            Om_hat[3] += pTr * (R)K.A8c * (R(4) * uxr * (gxx - th) + R(2) * uyr * shear);
-            Om_hat[4] += pTr * (R)K.A9c * (R(4) * uyr * (gyy - th) + R(2) * uxr * shear);
+            const R th = (gxx + gyy) / K.DI_r, pTr = rr * Tr, shear = gyx + gxy;
+            Om_hat[3] += pTr * K.A8c_r * (R(4) * uxr * (gxx - th) + R(2) * uyr * shear);
+            Om_hat[4] += pTr * K.A9c_r * (R(4) * uyr * (gyy - th) + R(2) * uxr * shear);
         }
 
         // 5. reaction over dt with p and T frozen at t_n (Eq. (28), m = n = 1)
@@ -395,8 +439,8 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
                 for (int i = 0; i < NV; i++) Om[i] = -K.S[4] * (f[i] - fe[i]);
             }
         }
-        const R chem = (R)(K.Q * lrate / (K.I * K.DI * T * T));
-        const R base = (R)(-(1.0 + 2.0) * K.I * T);
+        const R chem = react ? to_r<R>(K.Q * lrate / (K.I * K.DI * T * T)) : R(0);
+        const R base = R(-3) * Ir * Tr; // -(1 + D) I T
         const int xm2 = map_index(x - 2, K.nx, K.bc_x == 0 ? 0 : 1);
         const int xm1 = map_index(x - 1, K.nx, K.bc_x == 0 ? 0 : 1);
         const int xp1 = map_index(x + 1, K.nx, K.bc_x == 0 ? 0 : 1);
@@ -417,40 +461,40 @@ __global__ void __launch_bounds__(BT) step_kernel(const Model<R> K, const Args a
             const R* pl = in + (size_t)i * K.plane;
             R adv = R(0);
             if (K.vx[i] > R(0))
-                adv = K.vx[i] * K.inv_dx *
+                adv = K.vxs[i] *
                       nnd_pos(__ldg(pl + row + xm2), __ldg(pl + row + xm1), f[i], __ldg(pl + row + xp1));
             else if (K.vx[i] < R(0))
-                adv = K.vx[i] * K.inv_dx *
+                adv = K.vxs[i] *
                       nnd_neg(__ldg(pl + row + xm1), f[i], __ldg(pl + row + xp1), __ldg(pl + row + xp2));
             if (K.ny > 1) {
                 if (K.vy[i] > R(0))
-                    adv += K.vy[i] * K.inv_dy *
+                    adv += K.vys[i] *
                            nnd_pos(__ldg(pl + ym2 + x), __ldg(pl + ym1 + x), f[i], __ldg(pl + yp1 + x));
                 else if (K.vy[i] < R(0))
-                    adv += K.vy[i] * K.inv_dy *
+                    adv += K.vys[i] *
                            nnd_neg(__ldg(pl + ym1 + x), f[i], __ldg(pl + yp1 + x), __ldg(pl + yp2 + x));
             }
-            out[(size_t)i * K.plane + g] = f[i] + (R)K.dt * (om - adv);
+            out[(size_t)i * K.plane + g] = f[i] + K.dt_r * (om - adv);
         }
 
         // 7. lambda: u . grad(lambda) with NND interface values, then the update
         const R* pl = in + (size_t)NV * K.plane;
         R la = R(0);
         if (uxr > R(0))
-            la = uxr * (R)K.inv_dx *
+            la = uxr * K.inv_dx_r *
                  nnd_pos(__ldg(pl + row + xm2), __ldg(pl + row + xm1), lam0, __ldg(pl + row + xp1));
         else if (uxr < R(0))
-            la = uxr * (R)K.inv_dx *
+            la = uxr * K.inv_dx_r *
                  nnd_neg(__ldg(pl + row + xm1), lam0, __ldg(pl + row + xp1), __ldg(pl + row + xp2));
         if (K.ny > 1) {
             if (uyr > R(0))
-                la += uyr * (R)K.inv_dy *
+                la += uyr * K.inv_dy_r *
                       nnd_pos(__ldg(pl + ym2 + x), __ldg(pl + ym1 + x), lam0, __ldg(pl + yp1 + x));
             else if (uyr < R(0))
-                la += uyr * (R)K.inv_dy *
+                la += uyr * K.inv_dy_r *
                       nnd_neg(__ldg(pl + ym1 + x), lam0, __ldg(pl + yp1 + x), __ldg(pl + yp2 + x));
         }
-        R ln = lam0 - (R)K.dt * la + (R)dlam;
+        R ln = lam0 - K.dt_r * la + to_r<R>(dlam);
         ln = ln < R(0) ? R(0) : (ln > R(1) ? R(1) : ln);
         out[(size_t)NV * K.plane + g] = ln;
     }
@@ -490,7 +534,7 @@ __global__ void __launch_bounds__(BT) tne_kernel(const Model<R> K, const R* __re
         double rho, ux, uy, T;
         conserved_at(K, in, x, y, rho, ux, uy, &T);
         R q[NV];
-        feq24<R>((R)K.I, (R)K.DI, (R)rho, (R)ux, (R)uy, (R)T, q);
+        feq24<R>(K.I_r, K.DI_r, to_r<R>(rho), to_r<R>(ux), to_r<R>(uy), to_r<R>(T), q);
         R f[NV], gv[NV], h[NV];
 #pragma unroll
         for (int i = 0; i < NV; i++) f[i] = __ldg(in + (size_t)i * K.plane + g);
@@ -744,6 +788,10 @@ void fill_model(const lbkm24_params& p, const double* Bf, const double* Bi, cons
         const double c = p.v[o / 2], et = p.eta[o / 2];
         K->cd[o] = c;
         K->wod[o] = c * c * ((o & 1) ? 2.0 : 1.0) + et * et;
+        K->cdh[o] = (float)c;
+        K->cdl[o] = (float)(c - (double)K->cdh[o]);
+        K->wdh[o] = (float)K->wod[o];
+        K->wdl[o] = (float)(K->wod[o] - (double)K->wdh[o]);
     }
     K->I = 2.0 / (p.gamma - 1.0) - 2.0;
     K->DI = 2.0 + K->I;
@@ -757,6 +805,19 @@ void fill_model(const lbkm24_params& p, const double* Bf, const double* Bi, cons
     K->dt = p.dt;
     K->inv_dx = 1.0 / p.dx;
     K->inv_dy = 1.0 / p.dy;
+    for (int i = 0; i < NV; i++) {
+        K->vxs[i] = (R)(vx[i] / p.dx);
+        K->vys[i] = (R)(vy[i] / p.dy);
+    }
+    K->dt_r = (R)p.dt;
+    K->inv_dx_r = (R)(1.0 / p.dx);
+    K->inv_dy_r = (R)(1.0 / p.dy);
+    K->hdx_r = (R)(0.5 / p.dx);
+    K->hdy_r = (R)(0.5 / p.dy);
+    K->I_r = (R)K->I;
+    K->DI_r = (R)K->DI;
+    K->A8c_r = (R)K->A8c;
+    K->A9c_r = (R)K->A9c;
     K->nx = p.nx;
     K->ny = p.ny;
     K->pitch = pitch;
