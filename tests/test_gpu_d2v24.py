@@ -354,3 +354,17 @@ def test_shock_tubes_paper_sets_full_time(which):
            np.abs(m["p"][0] - pe).mean())
     print("D2V24", which, "distance to the exact solution at the paper's end time", err)
     assert all(e < 1e-2 for e in err), err
+
+
+def test_zero_steps_and_tiny_grids():
+    """Degenerate grids (1 x 1, 3 x 1, 2 x 2, 5 x 3; periodic, so every neighbour wraps onto
+    the grid itself) and a zero-step call, FP64 against the oracle."""
+    for nx, ny in ((1, 1), (3, 1), (2, 2), (5, 3)):
+        cfg = mixed_2d(nx, ny, bc=(0, 0), seed=nx + ny)
+        s, ob, f, lam = start(cfg, lbkm.F64, noise_seed=1)
+        s.step(0)
+        assert np.array_equal(s.f_planes()[:24], f)
+        s.step(7)
+        f_ref, lam_ref = ob.run(f, lam, 7)
+        assert rel_l2(s.f_planes()[:24], f_ref) <= 1e-12, (nx, ny)
+        assert rel_l2(s.f_planes()[24], lam_ref) <= 1e-12, (nx, ny)
