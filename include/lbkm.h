@@ -179,8 +179,10 @@ lbkm_status lbkm_init_fields(lbkm_t h, const double* rho, const double* ux, cons
                              const double* T, const double* lambda, int on_device);
 
 /* Advance n >= 0 time steps, asynchronously on the handle's stream. Each step
- * is one fused kernel (stencil, collision, reaction, Euler update and, when due,
- * the TNE reduction). Repeated chunks are replayed from a CUDA graph.
+ * (each stage of a Runge-Kutta step) is one fused kernel (stencil, collision,
+ * reaction, Euler update and, when due, the per-block TNE partials); on steps that
+ * reduce TNE a small kernel then folds the partials into the history record.
+ * Repeated chunks are replayed from a CUDA graph.
  * Errors: LBKM_ESTATE (no init_fields yet), LBKM_EINVAL (n < 0), LBKM_ECUDA. */
 lbkm_status lbkm_step(lbkm_t h, int64_t n);
 
