@@ -3,11 +3,13 @@
 //
 // The step is one fused kernel per time step, one thread per cell: the 24 f_i of
 // the cell and of its NND stencil (radius 2 in x and y) are read through the
-// read-only data cache, the conserved sums and rho, u, T are formed in FP64, the
-// 20 non-conserved moments, the relaxation, the back-transform and the chemical
-// term of Eq. (24) run in the storage type R (FP64 or FP32), and the TNE partials of
-// the state being read are reduced per block in FP64 when due. A 82-block kernel then
-// turns the partials into one history record.
+// read-only data cache; rho, u, T of the block's cells and a one-cell rim are formed
+// once, in FP64 (an FP32 state sums its conserved moments as exact double-floats on
+// the FP32 pipes first), and kept in shared memory; the equilibrium moments, the 20
+// non-conserved moments, the relaxation, the back-transform, the chemical term of
+// Eq. (24) and the NND update run in the storage type R (FP64 or FP32); the TNE
+// partials of the state being read are reduced per block in FP64 when due, and an
+// 82-block kernel turns them into one history record.
 //
 // M and M^-1 act in block form: butterflies inside each orbit of four velocities
 // (axis: f1+f3, f2+f4, f1-f3, f2-f4; diagonal: the sum and the three sign patterns)
