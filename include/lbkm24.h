@@ -62,7 +62,8 @@ typedef struct {
     double omega1, omega2; /* Cochran rate constants of Eq. (28), m = n = 1 */
     double T_ig;          /* reaction only where T > T_ig; finite, >= 0 */
     double dx, dy, dt;    /* grid spacing and time step */
-    int32_t bc_x, bc_y;   /* LBKM_BC_PERIODIC or LBKM_BC_ZERO_GRADIENT */
+    int32_t bc_x, bc_y;   /* LBKM_BC_PERIODIC, LBKM_BC_ZERO_GRADIENT, or LBKM_BC_SIDES
+                             (each side of that direction by side_bc below) */
     int32_t tne_every;    /* 0: no on-the-fly TNE; k > 0: every k-th step */
     int32_t tne_capacity; /* records kept in the device history ring (>= 1) */
     int32_t collision;    /* 0: when R_5..R_24 are all equal and tne_every = 0, step with
@@ -70,6 +71,14 @@ typedef struct {
                              [M^-1 f_hat^eq]_i) + C_i, which skips M f (the same update
                              up to rounding: A_hat vanishes for equal rates); 1: always
                              the general moment-space form */
+    int32_t side_bc[4];   /* with LBKM_BC_SIDES, the sides x = 0, x = nx, y = 0, y = ny:
+                             LBKM_BC_ZERO_GRADIENT (outflow), LBKM_BC_DIRICHLET (both
+                             ghost layers hold the equilibrium of side_rho/ux/uy/T and
+                             lambda side_lam: the fixed states of Sec. IV.C), or
+                             LBKM_BC_SPECULAR (y sides: the mirror cell across the face
+                             with v_y reversed, the reflecting surface of Sec. IV.C) */
+    double side_rho[4], side_ux[4], side_uy[4], side_T[4], side_lam[4]; /* Dirichlet
+                             states: rho > 0, T > 0, lambda in [0, 1] */
 } lbkm24_params;
 
 /* Grid-wide TNE measures of one state (Sec. VI): index k-1 holds Delta_k;

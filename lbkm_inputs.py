@@ -278,6 +278,29 @@ def d2v24_shock_tube(which, steps=None):
                 left=left, right=right, name="d2v24_%s_nx%d" % (which, nx))
 
 
+def d2v24_shock_reflection(steps=100000, nx=300, ny=100):
+    """The regular shock reflection of Sec. IV.C with the paper's own D2V24 set:
+    (v_a, v_b, v_c; eta_a, eta_b, eta_c) = (1.0, 2.7, 2.9; 1.0, 2.9, 0.96), I = 2
+    (gamma = 1.5), dt = 5e-6, dx = dy = 1e-3 on a 0.3 x 0.1 box (100000 steps reach
+    t = 0.5), R_5..R_7 = 1.8e5, R_8 = R_9 = 2e5, others 1e5; Dirichlet inflow (rho, T, u_x,
+    u_y) = (1, 0.5, 2, 0) at x = 0 and the post-shock state (1.25, 0.56, 1.9, -0.173205)
+    on the top, zero-gradient outflow at x = 0.3, a specular wall at y = 0; the box starts
+    filled with the inflow state."""
+    S = np.full(24, 1e5)
+    S[4:7] = 1.8e5
+    S[7:9] = 2e5
+    v = ((1.0, 2.7, 2.9), (1.0, 2.9, 0.96))
+    sides = ((3, 1.0, 2.0, 0.0, 0.5, 0.0), (1, 1.0, 0.0, 0.0, 1.0, 0.0),
+             (4, 1.0, 0.0, 0.0, 1.0, 0.0), (3, 1.25, 1.9, -0.173205, 0.56, 0.0))
+    common = dict(nx=nx, ny=ny, gamma=1.5, Q=0.0, omega1=0.0, omega2=0.0, T_ig=1.1, dx=1e-3,
+                  dy=1e-3, dt=5e-6, bc_x=5, bc_y=5, sides=sides)
+    one, zero = np.ones((ny, nx)), np.zeros((ny, nx))
+    return dict(params=dict(common, S=S, **d2v24_orbits(*v)),
+                lib_params=dict(common, S=S, v=v[0], eta=v[1]), steps=steps,
+                fields=dict(rho=one, ux=2.0 * one, uy=zero, T=0.5 * one, lam=zero.copy()),
+                name="d2v24_shock_reflection_%dx%d" % (nx, ny))
+
+
 def d2v24_reactive2d(n=64, steps=20, T_ig=1.0, seed_offset=8, v=D2V24_DETONATION_V):
     """2-D periodic reactive field of random Fourier modes (the recipe of reactive2d)
     for D2V24: S_1..S_24 ~ U[1e4, 1e5], Q = 1, k = 2e4, dx = dy = 1e-3, dt = 5e-6."""

@@ -90,6 +90,12 @@ struct Model {
     double dt, inv_dx, inv_dy;
     int nx, ny, pitch, bc_x, bc_y, pad_;
     int64_t plane;
+    // per-side conditions (bc_x or bc_y = LBKM_BC_SIDES) of the sides x = 0, x = nx,
+    // y = 0, y = ny: 1 zero gradient, 3 Dirichlet (ghost cells hold sfeq: the
+    // equilibrium f of the side's state and its lambda), 4 specular (y sides: the mirror
+    // cell across the face with v_y reversed); 0 for a periodic direction
+    int sbc[4];
+    R sfeq[4][NP];
 };
 
 struct Args {
@@ -125,18 +131,61 @@ __device__ __forceinline__ double to_f64(double x) { return x; }
 // exact, on the integer pipe (the FP64 unit runs at 1/58 of the FP32 rate on GB300)
 __device__ __forceinline__ double to_f64(float x) { return f2d_exact(x); }
 
+// plane of the velocity with v_y reversed (axis orbits (c,0) (0,c) (-c,0) (0,-c);
+// diagonal orbits (+,+) (-,+) (-,-) (+,-)); lambda maps to itself
+__host__ __device__ __forceinline__ int mirror24(int i)
+{
+    if (i >= NV) return i;
+    const int o = i / 4, j = i % 4;
+    const int jm = (o & 1) ? 3 - j : (j == 1 ? 3 : (j == 3 ? 1 : j));
+    return 4 * o + jm;
+}
+
+// Value of plane i (0..23 f, 24 lambda) at cell (x, y), which may lie up to two cells
+// outside the grid: periodic or zero-gradient directions map the index; with per-side
+// conditions a Dirichlet side (a y side first, as corners are never read by the
+// cross-shaped stencil) gives its equilibrium value, a specular y side the mirror
+// cell's value of the velocity with v_y reversed, an outflow side the edge cell's.
+template <typename R>
+__device__ __forceinline__ R fval(const Model<R>& K, const R* __restrict__ in, int i, int x, int y)
+{
+    const int cx = (x >= 0 && x < K.nx) ? -1 : (K.bc_x == 5 ? K.sbc[x < 0 ? 0 : 1] : K.bc_x);
+    const int cy = (y >= 0 && y < K.ny) ? -1 : (K.bc_y == 5 ? K.sbc[y < 0 ? 2 : 3] : K.bc_y);
+    if (cy == 3) return K.sfeq[y < 0 ? 2 : 3][i];
+    if (cx == 3) return K.sfeq[x < 0 ? 0 : 1][i];
+    const int sx = cx == -1 ? x : map_index(x, K.nx, cx == 0 ? 0 : 1);
+    int sy, ii = i;
+    if (cy == 4) {
+        sy = y < 0 ? -y - 1 : 2 * K.ny - 1 - y;
+        ii = mirror24(i);
+    } else {
+        sy = cy == -1 ? y : map_index(y, K.ny, cy == 0 ? 0 : 1);
+    }
+    return __ldg(in + (size_t)ii * K.plane + (size_t)sy * K.pitch + sx);
+}
+
 // rho, u_x, u_y and, if asked, T (FP64) at cell (x, y) of state `in`, boundary conditions
 // applied (Eqs. (5)-(7)). The sums go orbit by orbit: an orbit of speed c adds its sum s
 // to rho, c times its x and y differences to rho u, and (c^2 or 2 c^2) + eta^2 times s to
 // the energy moment m_4; 1/rho comes from an FP32 seed and two Newton steps.
-template <typename R>
+template <typename R, bool GEN = false>
 __device__ __forceinline__ void conserved_at(const Model<R>& K, const R* __restrict__ in, int x,
                                              int y, double& rho, double& ux, double& uy,
                                              double* T = nullptr)
 {
+    R gf[GEN ? NV : 1];
+    if constexpr (GEN) {
+#pragma unroll
+        for (int i = 0; i < NV; i++) gf[i] = fval(K, in, i, x, y);
+    }
     x = map_index(x, K.nx, K.bc_x == 0 ? 0 : 1);
     y = map_index(y, K.ny, K.bc_y == 0 ? 0 : 1);
     const R* p = in + (size_t)y * K.pitch + x;
+    // plane i of this cell: through the side rules, or straight from the mapped cell
+    auto ld = [&](int i) -> R {
+        if constexpr (GEN) return gf[i];
+        else return __ldg(p + (size_t)i * K.plane);
+    };
     double r = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
     if constexpr (sizeof(R) == 4) {
         // FP32 state: the same sums as double-floats on the FP32 pipes (error-free
@@ -146,10 +195,7 @@ __device__ __forceinline__ void conserved_at(const Model<R>& K, const R* __restr
         df R0{0.f, 0.f}, R1{0.f, 0.f}, R2{0.f, 0.f}, R3{0.f, 0.f};
 #pragma unroll
         for (int o = 0; o < 6; o++) {
-            const float a = __ldg(p + (size_t)(4 * o) * K.plane);
-            const float b = __ldg(p + (size_t)(4 * o + 1) * K.plane);
-            const float c = __ldg(p + (size_t)(4 * o + 2) * K.plane);
-            const float d = __ldg(p + (size_t)(4 * o + 3) * K.plane);
+            const float a = ld(4 * o), b = ld(4 * o + 1), c = ld(4 * o + 2), d = ld(4 * o + 3);
             const df sac = lbk::two_sum(a, c), sbd = lbk::two_sum(b, d);
             const df dac = lbk::two_sum(a, -c), dbd = lbk::two_sum(b, -d);
             const df sum = lbk::df_add(sac, sbd);
@@ -171,10 +217,8 @@ __device__ __forceinline__ void conserved_at(const Model<R>& K, const R* __restr
     } else {
 #pragma unroll
     for (int o = 0; o < 6; o++) {
-        const double a = to_f64(__ldg(p + (size_t)(4 * o) * K.plane));
-        const double b = to_f64(__ldg(p + (size_t)(4 * o + 1) * K.plane));
-        const double c = to_f64(__ldg(p + (size_t)(4 * o + 2) * K.plane));
-        const double d = to_f64(__ldg(p + (size_t)(4 * o + 3) * K.plane));
+        const double a = to_f64(ld(4 * o)), b = to_f64(ld(4 * o + 1));
+        const double c = to_f64(ld(4 * o + 2)), d = to_f64(ld(4 * o + 3));
         const double sac = a + c, sbd = b + d, dac = a - c, dbd = b - d;
         const double sum = sac + sbd;
         double gx, gy;
@@ -265,7 +309,7 @@ __device__ __forceinline__ void block_apply(const R* B, const R* x, R* y)
 // f_hat^eq_1..24 (list after Eq. (16); entries 14 and 16 with the factor T of Eq. (11)),
 // in the arithmetic type F
 template <typename F>
-__device__ __forceinline__ void feq24(F I, F DI, F rho, F ux, F uy, F T, F* q)
+__host__ __device__ __forceinline__ void feq24(F I, F DI, F rho, F ux, F uy, F T, F* q)
 {
     const F u2 = ux * ux + uy * uy;
     const F A = (DI + F(2)) * T + u2, B = (DI + F(4)) * T + u2;
@@ -335,7 +379,7 @@ __device__ __forceinline__ void block_tne(const R* Dk, bool active, double* part
 // rate the moment-space relaxation is -R (f - M^-1 f_hat^eq) in velocity space (the SRT
 // form of Sec. V) and A_hat vanishes, so the forward transform of f is skipped and only
 // f^eq = M^-1 f_hat^eq is formed (it also feeds the chemical term of Eq. (24)).
-template <typename R, bool SRT>
+template <typename R, bool SRT, bool GEN>
 __global__ void __launch_bounds__(BT, sizeof(R) == 4 ? 3 : 1) step_kernel(const Model<R> K, const Args a)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -359,7 +403,7 @@ __global__ void __launch_bounds__(BT, sizeof(R) == 4 ? 3 : 1) step_kernel(const 
         for (int c = threadIdx.x + threadIdx.y * blockDim.x; c < bw * bh;
              c += blockDim.x * blockDim.y) {
             const int hx = c % bw, hy = c / bw;
-            conserved_at(K, in, x0 + hx, y0 + hy, s_rho[c], s_ux[c], s_uy[c], &s_T[c]);
+            conserved_at<R, GEN>(K, in, x0 + hx, y0 + hy, s_rho[c], s_ux[c], s_uy[c], &s_T[c]);
         }
         __syncthreads();
     }
@@ -453,6 +497,18 @@ __global__ void __launch_bounds__(BT, sizeof(R) == 4 ? 3 : 1) step_kernel(const 
         const size_t ym1 = (size_t)map_index(y - 1, K.ny, by) * K.pitch;
         const size_t yp1 = (size_t)map_index(y + 1, K.ny, by) * K.pitch;
         const size_t yp2 = (size_t)map_index(y + 2, K.ny, by) * K.pitch;
+        // stencil value of plane i at x + d (LX) or y + d (LY): the side rules for the
+        // per-side variant, the mapped offsets otherwise
+        auto LX = [&](int i, int d) -> R {
+            if constexpr (GEN) return fval(K, in, i, x + d, y);
+            const int xo = d == -2 ? xm2 : (d == -1 ? xm1 : (d == 1 ? xp1 : xp2));
+            return __ldg(in + (size_t)i * K.plane + row + xo);
+        };
+        auto LY = [&](int i, int d) -> R {
+            if constexpr (GEN) return fval(K, in, i, x, y + d);
+            const size_t yo = d == -2 ? ym2 : (d == -1 ? ym1 : (d == 1 ? yp1 : yp2));
+            return __ldg(in + (size_t)i * K.plane + yo + x);
+        };
 #pragma unroll
         for (int i = 0; i < NV; i++) {
             R om = Om[i];
@@ -463,38 +519,29 @@ __global__ void __launch_bounds__(BT, sizeof(R) == 4 ? 3 : 1) step_kernel(const 
             const R* pl = in + (size_t)i * K.plane;
             R adv = R(0);
             if (K.vx[i] > R(0))
-                adv = K.vxs[i] *
-                      nnd_pos(__ldg(pl + row + xm2), __ldg(pl + row + xm1), f[i], __ldg(pl + row + xp1));
+                adv = K.vxs[i] * nnd_pos(LX(i, -2), LX(i, -1), f[i], LX(i, 1));
             else if (K.vx[i] < R(0))
-                adv = K.vxs[i] *
-                      nnd_neg(__ldg(pl + row + xm1), f[i], __ldg(pl + row + xp1), __ldg(pl + row + xp2));
+                adv = K.vxs[i] * nnd_neg(LX(i, -1), f[i], LX(i, 1), LX(i, 2));
             if (K.ny > 1) {
                 if (K.vy[i] > R(0))
-                    adv += K.vys[i] *
-                           nnd_pos(__ldg(pl + ym2 + x), __ldg(pl + ym1 + x), f[i], __ldg(pl + yp1 + x));
+                    adv += K.vys[i] * nnd_pos(LY(i, -2), LY(i, -1), f[i], LY(i, 1));
                 else if (K.vy[i] < R(0))
-                    adv += K.vys[i] *
-                           nnd_neg(__ldg(pl + ym1 + x), f[i], __ldg(pl + yp1 + x), __ldg(pl + yp2 + x));
+                    adv += K.vys[i] * nnd_neg(LY(i, -1), f[i], LY(i, 1), LY(i, 2));
             }
             out[(size_t)i * K.plane + g] = f[i] + K.dt_r * (om - adv);
         }
 
         // 7. lambda: u . grad(lambda) with NND interface values, then the update
-        const R* pl = in + (size_t)NV * K.plane;
         R la = R(0);
         if (uxr > R(0))
-            la = uxr * K.inv_dx_r *
-                 nnd_pos(__ldg(pl + row + xm2), __ldg(pl + row + xm1), lam0, __ldg(pl + row + xp1));
+            la = uxr * K.inv_dx_r * nnd_pos(LX(NV, -2), LX(NV, -1), lam0, LX(NV, 1));
         else if (uxr < R(0))
-            la = uxr * K.inv_dx_r *
-                 nnd_neg(__ldg(pl + row + xm1), lam0, __ldg(pl + row + xp1), __ldg(pl + row + xp2));
+            la = uxr * K.inv_dx_r * nnd_neg(LX(NV, -1), lam0, LX(NV, 1), LX(NV, 2));
         if (K.ny > 1) {
             if (uyr > R(0))
-                la += uyr * K.inv_dy_r *
-                      nnd_pos(__ldg(pl + ym2 + x), __ldg(pl + ym1 + x), lam0, __ldg(pl + yp1 + x));
+                la += uyr * K.inv_dy_r * nnd_pos(LY(NV, -2), LY(NV, -1), lam0, LY(NV, 1));
             else if (uyr < R(0))
-                la += uyr * K.inv_dy_r *
-                      nnd_neg(__ldg(pl + ym1 + x), lam0, __ldg(pl + yp1 + x), __ldg(pl + yp2 + x));
+                la += uyr * K.inv_dy_r * nnd_neg(LY(NV, -1), lam0, LY(NV, 1), LY(NV, 2));
         }
         R ln = lam0 - K.dt_r * la + to_r<R>(dlam);
         ln = ln < R(0) ? R(0) : (ln > R(1) ? R(1) : ln);
@@ -769,9 +816,14 @@ double build_blocks(const double* M, double* Bf, double* Bi)
 
 template <typename R>
 void fill_model(const lbkm24_params& p, const double* Bf, const double* Bi, const double* Minv,
-                const double* vx, const double* vy, const double* e, int pitch, Model<R>* K)
+                const double* vx, const double* vy, const double* e, int pitch,
+                const int* sbc, const double (*sfeq)[NP], Model<R>* K)
 {
     memset(K, 0, sizeof(*K));
+    for (int sd = 0; sd < 4; sd++) {
+        K->sbc[sd] = sbc[sd];
+        for (int i = 0; i < NP; i++) K->sfeq[sd][i] = (R)sfeq[sd][i];
+    }
     for (int k = 0; k < NB; k++) {
         K->Bf[k] = (R)Bf[k];
         K->Bi[k] = (R)Bi[k];
@@ -888,17 +940,19 @@ cudaError_t launch_one_step(const lbkm24* h, int from, cudaStream_t st)
     a.hist_cap = h->p.tne_capacity;
     a.tne_every = h->p.tne_every;
     a.area = h->p.dx * h->p.dy;
-    if (h->p.precision == LBKM_F64) {
-        if (h->srt)
-            step_kernel<double, true><<<h->grid, h->block, 0, st>>>(h->Kd, a);
-        else
-            step_kernel<double, false><<<h->grid, h->block, 0, st>>>(h->Kd, a);
-    } else {
-        if (h->srt)
-            step_kernel<float, true><<<h->grid, h->block, 0, st>>>(h->Kf, a);
-        else
-            step_kernel<float, false><<<h->grid, h->block, 0, st>>>(h->Kf, a);
-    }
+    const bool gen = h->p.bc_x == LBKM_BC_SIDES || h->p.bc_y == LBKM_BC_SIDES;
+#define V24_LAUNCH(R_, KK)                                                                   \
+    do {                                                                                     \
+        if (h->srt && gen) step_kernel<R_, true, true><<<h->grid, h->block, 0, st>>>(KK, a); \
+        else if (h->srt) step_kernel<R_, true, false><<<h->grid, h->block, 0, st>>>(KK, a);  \
+        else if (gen) step_kernel<R_, false, true><<<h->grid, h->block, 0, st>>>(KK, a);     \
+        else step_kernel<R_, false, false><<<h->grid, h->block, 0, st>>>(KK, a);             \
+    } while (0)
+    if (h->p.precision == LBKM_F64)
+        V24_LAUNCH(double, h->Kd);
+    else
+        V24_LAUNCH(float, h->Kf);
+#undef V24_LAUNCH
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && h->p.tne_every > 0) {
         finish_kernel<<<NQ, 256, 0, st>>>(h->partials, h->nblocks, h->hist, h->p.tne_capacity,
@@ -993,9 +1047,27 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
         return fail(nullptr, LBKM_EINVAL, "T_ig must be finite and >= 0");
     for (int d = 0; d < 2; d++) {
         const int bc = d == 0 ? p.bc_x : p.bc_y;
-        if (bc != LBKM_BC_PERIODIC && bc != LBKM_BC_ZERO_GRADIENT)
-            return fail(nullptr, LBKM_EINVAL, "%s must be periodic or zero gradient",
+        if (bc != LBKM_BC_PERIODIC && bc != LBKM_BC_ZERO_GRADIENT && bc != LBKM_BC_SIDES)
+            return fail(nullptr, LBKM_EINVAL, "%s must be periodic, zero gradient or sides",
                         d == 0 ? "bc_x" : "bc_y");
+    }
+    for (int sd = 0; sd < 4; sd++) {
+        if ((sd < 2 ? p.bc_x : p.bc_y) != LBKM_BC_SIDES) continue;
+        const int code = p.side_bc[sd];
+        const bool ok = code == LBKM_BC_ZERO_GRADIENT || code == LBKM_BC_DIRICHLET ||
+                        (code == LBKM_BC_SPECULAR && sd >= 2);
+        if (!ok)
+            return fail(nullptr, LBKM_EINVAL,
+                        "side_bc[%d]: zero gradient, Dirichlet, or specular (y sides only)", sd);
+        if (code == LBKM_BC_SPECULAR && p.ny < 2)
+            return fail(nullptr, LBKM_EINVAL, "a specular side needs ny >= 2");
+        if (code == LBKM_BC_DIRICHLET &&
+            (!(p.side_rho[sd] > 0) || !(p.side_T[sd] > 0) || !isfinite(p.side_rho[sd]) ||
+             !isfinite(p.side_T[sd]) || !isfinite(p.side_ux[sd]) || !isfinite(p.side_uy[sd]) ||
+             !(p.side_lam[sd] >= 0 && p.side_lam[sd] <= 1)))
+            return fail(nullptr, LBKM_EINVAL,
+                        "side %d: Dirichlet state needs rho > 0, T > 0, finite u, lambda in [0, 1]",
+                        sd);
     }
     if (p.tne_every < 0 || (p.tne_every > 0 && p.tne_capacity < 1))
         return fail(nullptr, LBKM_EINVAL, "tne_every >= 0 and tne_capacity >= 1");
@@ -1022,8 +1094,26 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
     bool equal = true;
     for (int k = 5; k < NV; k++) equal = equal && p.S[k] == p.S[4];
     h->srt = equal && p.tne_every == 0 && p.collision == 0;
-    fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, &h->Kd);
-    fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, &h->Kf);
+    // Dirichlet sides: ghost f = M^-1 f_hat^eq(side state), ghost lambda = the side's
+    int sbc[4] = {0, 0, 0, 0};
+    double sfeq[4][NP];
+    memset(sfeq, 0, sizeof(sfeq));
+    const double Ih = 2.0 / (p.gamma - 1.0) - 2.0;
+    for (int sd = 0; sd < 4; sd++) {
+        if ((sd < 2 ? p.bc_x : p.bc_y) != LBKM_BC_SIDES) continue;
+        sbc[sd] = p.side_bc[sd];
+        if (sbc[sd] != LBKM_BC_DIRICHLET) continue;
+        double q[NV];
+        feq24<double>(Ih, 2.0 + Ih, p.side_rho[sd], p.side_ux[sd], p.side_uy[sd], p.side_T[sd], q);
+        for (int i = 0; i < NV; i++) {
+            double acc = 0.0;
+            for (int k = 0; k < NV; k++) acc += Minv[i * NV + k] * q[k];
+            sfeq[sd][i] = acc;
+        }
+        sfeq[sd][NV] = p.side_lam[sd];
+    }
+    fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, sbc, sfeq, &h->Kd);
+    fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, sbc, sfeq, &h->Kf);
     // 1-D grids too short to give every SM a block of 128 cells run blocks of one warp:
     // the step is latency-bound there, and more SMs each take fewer cells
     const bool narrow = p.ny == 1 && (p.nx + BT - 1) / BT < 2 * 152;

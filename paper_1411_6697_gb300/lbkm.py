@@ -87,6 +87,9 @@ class Params24(ctypes.Structure):
         ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
         ("tne_every", ctypes.c_int32), ("tne_capacity", ctypes.c_int32),
         ("collision", ctypes.c_int32),
+        ("side_bc", ctypes.c_int32 * 4), ("side_rho", ctypes.c_double * 4),
+        ("side_ux", ctypes.c_double * 4), ("side_uy", ctypes.c_double * 4),
+        ("side_T", ctypes.c_double * 4), ("side_lam", ctypes.c_double * 4),
     ]
 
 
@@ -231,6 +234,11 @@ def default_params24(**kw) -> Params24:
                 arr[i] = float(vals[i])
         elif k == "bc":
             p.bc_x, p.bc_y = v
+        elif k == "sides":  # 4 x (code, rho, ux, uy, T, lambda): x = 0, x = nx, y = 0, y = ny
+            for j, (code, r, u, w, T, lam) in enumerate(v):
+                p.side_bc[j] = int(code)
+                p.side_rho[j], p.side_ux[j], p.side_uy[j], p.side_T[j], p.side_lam[j] = (
+                    float(r), float(u), float(w), float(T), float(lam))
         else:
             setattr(p, k, v)
     return p

@@ -368,3 +368,75 @@ def test_zero_steps_and_tiny_grids():
         f_ref, lam_ref = ob.run(f, lam, 7)
         assert rel_l2(s.f_planes()[:24], f_ref) <= 1e-12, (nx, ny)
         assert rel_l2(s.f_planes()[24], lam_ref) <= 1e-12, (nx, ny)
+
+
+SIDES = [(3, 1.05, 0.1, 0.02, 1.15, 0.3), (1, 1.0, 0.0, 0.0, 1.0, 0.0),
+         (4, 1.0, 0.0, 0.0, 1.0, 0.0), (3, 0.95, 0.05, -0.03, 1.05, 0.1)]
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PID)
+@pytest.mark.parametrize("nx,ny", [(45, 19), (70, 6)])
+def test_per_side_parity(prec, nx, ny):
+    """Per-side conditions (Dirichlet inflow at x = 0 and on the top, outflow at x = nx, a
+    specular floor) on a non-equilibrium reacting field, 25 steps, against the oracle."""
+    cfg = mixed_2d(nx, ny, bc=(5, 5), seed=nx + 7)
+    for key in ("params", "lib_params"):
+        cfg[key]["sides"] = SIDES
+    s, ob, f, lam = start(cfg, prec, noise_seed=ny + 2)
+    s.step(25)
+    f_ref, lam_ref = ob.run(f, lam, 25)
+    # FP32 holds the Dirichlet ghost states rounded to FP32 (the oracle in FP64), and
+    # their influx adds to the state's own rounding: 2.3e-5 measured on 45 x 19
+    check_state(s, ob, f_ref, lam_ref, prec, floor=0.0 if prec == lbkm.F64 else 4e-5)
+
+
+def test_shock_reflection_with_paper_d2v24():
+    """Sec. IV.C with the paper's own D2V24 set on its 300 x 100 grid (FP64): 300 steps
+    against the oracle, then on to t = 0.5, where the regular reflection stands as
+    two-shock theory puts it for the stated inflow (M1 = 2.3094) and lid state: the
+    incident shock at 30 degrees, rho 1.25 behind it, the reflected shock leaving the
+    floor at x = 0.1732 at 28.09 degrees (the weak solution turning the flow back by
+    the deflection tan(theta) = 0.173205 / 1.9 = 9.116e-2) and rho 1.538 behind it."""
+    c = li.d2v24_shock_reflection(steps=300)
+    s, ob, f, lam = start(c, lbkm.F64)
+    s.step(300)
+    f_ref, lam_ref = ob.run(f, lam, 300)
+    spread = oracle_spread(ob, f, lam, 300, f_ref, lam_ref)
+    check_state(s, ob, f_ref, lam_ref, lbkm.F64, floor=20 * spread)
+    s.step(100000 - 300)
+    m = s.macros()
+    rho = m["rho"]
+    p = c["params"]
+    ny, nx, dx = p["ny"], p["nx"], p["dx"]
+    ys = (np.arange(ny) + 0.5) * dx
+    assert np.isfinite(rho).all()
+
+    def crossing(col, level, rising):
+        """Height where the column first passes `level` going up from the floor: from
+        below to above it (rising) or from above to below it."""
+        idx = np.where(col > level)[0] if rising else np.where(col < level)[0]
+        i = int(idx.min())
+        j = i - 1
+        return ys[j] + (level - col[j]) * (ys[i] - ys[j]) / (col[i] - col[j])
+
+    # incident shock: the level 1.125 between the inflow (below) and the lid state
+    # (above), over x in [0.02, 0.09]
+    xs = [(j + 0.5) * dx for j in range(20, 90, 5)]
+    yi = [crossing(rho[:, j], 1.125, True) for j in range(20, 90, 5)]
+    angle_i = np.degrees(np.arctan(-np.polyfit(xs, yi, 1)[0]))
+    behind_i = rho[-8:-3, 30:60].mean()
+    # reflected shock: the level (1.25 + 1.538) / 2 between the reflected state (below)
+    # and the incident shock's (above), over x in [0.20, 0.27]
+    xr = [(j + 0.5) * dx for j in range(200, 271, 5)]
+    yr = [crossing(rho[:, j], 1.394, False) for j in range(200, 271, 5)]
+    slope, icpt = np.polyfit(xr, yr, 1)
+    angle_r = np.degrees(np.arctan(slope))
+    x_foot = -icpt / slope
+    behind_r = rho[2:6, 230:260].mean()
+    print("D2V24 shock reflection: incident", angle_i, behind_i, "reflected", angle_r, x_foot,
+          behind_r)
+    assert abs(angle_i - 30.0) < 1.5, angle_i
+    assert abs(behind_i / 1.25 - 1) < 0.02, behind_i
+    assert abs(angle_r - 28.09) < 2.0, angle_r
+    assert abs(x_foot - 0.1732) < 0.01, x_foot
+    assert abs(behind_r / 1.538 - 1) < 0.03, behind_r
