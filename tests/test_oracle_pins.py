@@ -511,3 +511,30 @@ def test_one_dimensional_symmetry_zeros(oracle_mod):
     assert big > 1e-3
     for k in (5, 8, 10, 12, 14):
         assert np.abs(delta[k]).max() < 1e-12 * big
+
+
+@pytest.mark.slow
+def test_couette_viscous_heating_fixes_the_sign_of_A(oracle_mod):
+    """Steady Couette flow between walls at T1 = 1 and T2 = 1.01, the top one moving at
+    u0 = 0.3 (Sec. IV.D, non-equilibrium extrapolation walls), Pr = R_kappa/R_mu = 5:
+    viscous heating bends the temperature profile upward by (Pr u0^2 / (2 c_p)) eta(1-eta)
+    on top of the linear conduction profile (the Chapman-Enskog balance kappa T'' =
+    -mu u'^2 of Sec. III). With the sign of A_hat taken from the Chapman-Enskog form
+    Eq. (29) the fitted bump is positive and of that size (0.75x on this 20-cell channel);
+    with the sign of Eq. (1) it comes out negative (-0.61x): the profile cools in the
+    middle, which no heat-conducting flow does."""
+    ny, dy, dt, u0, T1, T2, Pr, Rmu = 20, 1e-3, 1e-5, 0.3, 1.0, 1.01, 5.0, 2e3
+    S = np.full(16, 5e4)
+    S[4:7] = Rmu
+    S[7:9] = Pr * Rmu
+    ob = make(oracle_mod, 1, ny, S=S, dx=dy, dy=dy, dt=dt, bc_x=0, bc_y=2,
+              walls=((0.0, 0.0, T1), (u0, 0.0, T2)))
+    eta = ((np.arange(ny) + 0.5) / ny)[:, None]
+    f = ob.init(1.0, u0 * eta, 0.0, T1 + (T2 - T1) * eta)
+    f, _ = ob.run(f, np.zeros((ny, 1)), 200000)  # t = 2: steady to 1e-4 of the bump
+    T = ob.macros(f)["T"][:, 0]
+    e = eta[:, 0]
+    coef = np.linalg.lstsq(np.stack([np.ones_like(e), e, e * (1 - e)], 1), T, rcond=None)[0]
+    cp = (2 + ob.p.I + 2) / 2
+    ratio = coef[2] / (Pr * u0 ** 2 / (2 * cp))
+    assert 0.6 < ratio < 1.2, ratio
