@@ -126,3 +126,17 @@ int main(void) {
     p = lbkm.default_params24(nx=8, ny=1)
     assert list(p.v) == [2.7, 2.2, 1.2] and list(p.eta) == [5.0, 3.0, 1.1]
     assert p.S[4] == 1e4 and p.S[7] == 1e5 and p.dx == 2e-4 and p.dt == 5e-6
+
+
+def test_d2v24_params_from_keywords(lib):
+    """default_params24 maps the keyword forms (v, eta, S broadcast, bc, sides) onto the
+    C structure; no GPU involved."""
+    from paper_1411_6697_gb300 import lbkm
+    sides = [(3, 1.0, 2.0, 0.0, 0.5, 0.0), (1, 1.0, 0.0, 0.0, 1.0, 0.0),
+             (4, 1.0, 0.0, 0.0, 1.0, 0.0), (3, 1.25, 1.9, -0.173205, 0.56, 0.2)]
+    p = lbkm.default_params24(nx=300, ny=100, v=(1.0, 2.7, 2.9), eta=(1.0, 2.9, 0.96),
+                              S=1e5, bc=(5, 5), sides=sides, collision=1)
+    assert list(p.v) == [1.0, 2.7, 2.9] and list(p.eta) == [1.0, 2.9, 0.96]
+    assert list(p.S) == [1e5] * 24 and (p.bc_x, p.bc_y) == (5, 5) and p.collision == 1
+    assert list(p.side_bc) == [3, 1, 4, 3]
+    assert p.side_uy[3] == -0.173205 and p.side_lam[3] == 0.2 and p.side_T[0] == 0.5
