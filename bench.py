@@ -13,8 +13,8 @@ the step kernel against the measured HBM copy bandwidth, an end-to-end figure
 through the C ABI with host buffers, the CPU oracle timed on the host cores,
 and SM clocks sampled during the timed region.
 
---impl reference times the FP64 CPU oracle (the reference arm of this build) on
-a bounded sample of the same workload.
+--impl reference times the FP64 CPU oracle (the method has no other reference
+implementation: the paper prints no code) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
