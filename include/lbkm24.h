@@ -76,7 +76,12 @@ typedef struct {
                              ghost layers hold the equilibrium of side_rho/ux/uy/T and
                              lambda side_lam: the fixed states of Sec. IV.C), or
                              LBKM_BC_SPECULAR (y sides: the mirror cell across the face
-                             with v_y reversed, the reflecting surface of Sec. IV.C) */
+                             with v_y reversed, the reflecting surface of Sec. IV.C), or
+                             LBKM_BC_WALL (y sides, ny >= 2: both ghost rows take the edge
+                             row's f plus M^-1 [f_hat^eq(rho, u_w, T_w) - f_hat^eq(rho, u,
+                             T)], rho, u, T of the edge cell, u_w = (side_ux, side_uy) and
+                             T_w = side_T the wall's: non-equilibrium extrapolation,
+                             Sec. IV.D; lambda copied) */
     double side_rho[4], side_ux[4], side_uy[4], side_T[4], side_lam[4]; /* Dirichlet
                              states: rho > 0, T > 0, lambda in [0, 1] */
 } lbkm24_params;

@@ -301,6 +301,32 @@ def d2v24_shock_reflection(steps=100000, nx=300, ny=100):
                 name="d2v24_shock_reflection_%dx%d" % (nx, ny))
 
 
+def d2v24_couette(ny=200, steps=100000, u0=0.1):
+    """Couette flow of Sec. IV.D with the paper's own D2V24 set: 1 x 200 cells, dy = 1e-3
+    (H = 0.2), dt = 1e-5, I = 2 (gamma = 1.5), (v; eta) = (0.8, 1.2, 1.3; 1.0, 2.7, 0.8),
+    R_5..R_7 = 2e3, R_8 = R_9 = 1e4, others 5e4; walls by non-equilibrium extrapolation,
+    the lower at rest, the upper moving at u0, both at T = 1; periodic in x; the fluid
+    starts at rest with rho = 1, T = 1. With this set the moving wall's non-equilibrium
+    extrapolation grows an instability next to it within a few hundred steps (u_x there
+    turns negative, then non-finite; a wall at rest and a periodic shear stay bounded),
+    in the oracle as on the GPU."""
+    S = np.full(24, 5e4)
+    S[4:7] = 2e3
+    S[7:9] = 1e4
+    v = ((0.8, 1.2, 1.3), (1.0, 2.7, 0.8))
+    sides = ((1, 1.0, 0.0, 0.0, 1.0, 0.0), (1, 1.0, 0.0, 0.0, 1.0, 0.0),
+             (2, 1.0, 0.0, 0.0, 1.0, 0.0), (2, 1.0, u0, 0.0, 1.0, 0.0))
+    common = dict(nx=1, ny=ny, gamma=1.5, Q=0.0, omega1=0.0, omega2=0.0, T_ig=1.1, dx=1e-3,
+                  dy=1e-3, dt=1e-5, bc_x=0, bc_y=5, sides=sides)
+    one, zero = np.ones((ny, 1)), np.zeros((ny, 1))
+    oracle_params = dict(common, S=S, walls=((0.0, 0.0, 1.0), (u0, 0.0, 1.0)),
+                         **d2v24_orbits(*v))
+    return dict(params=oracle_params, lib_params=dict(common, S=S, v=v[0], eta=v[1]),
+                steps=steps, u0=u0,
+                fields=dict(rho=one, ux=zero, uy=zero.copy(), T=one.copy(), lam=zero.copy()),
+                name="d2v24_couette_1x%d" % ny)
+
+
 def d2v24_reactive2d(n=64, steps=20, T_ig=1.0, seed_offset=8, v=D2V24_DETONATION_V):
     """2-D periodic reactive field of random Fourier modes (the recipe of reactive2d)
     for D2V24: S_1..S_24 ~ U[1e4, 1e5], Q = 1, k = 2e4, dx = dy = 1e-3, dt = 5e-6."""

@@ -96,6 +96,11 @@ struct Model {
     // cell across the face with v_y reversed); 0 for a periodic direction
     int sbc[4];
     R sfeq[4][NP];
+    // walls (code 2, y sides) by non-equilibrium extrapolation: the ghost rows take the
+    // edge row's f plus wall[side][i][x] = [M^-1 (f_hat^eq(rho, u_w, T_w) -
+    // f_hat^eq(rho, u, T))]_i, rho, u, T of the edge cell, refreshed before every step
+    const R* wall;
+    double wux[2], wuy[2], wT[2];
 };
 
 struct Args {
@@ -154,6 +159,11 @@ __device__ __forceinline__ R fval(const Model<R>& K, const R* __restrict__ in, i
     if (cy == 3) return K.sfeq[y < 0 ? 2 : 3][i];
     if (cx == 3) return K.sfeq[x < 0 ? 0 : 1][i];
     const int sx = cx == -1 ? x : map_index(x, K.nx, cx == 0 ? 0 : 1);
+    if (cy == 2) { // wall: the edge row plus its non-equilibrium correction (lambda copied)
+        const int side = y < 0 ? 0 : 1, sy = side ? K.ny - 1 : 0;
+        const R edge = __ldg(in + (size_t)i * K.plane + (size_t)sy * K.pitch + sx);
+        return i < NV ? edge + K.wall[((size_t)side * NV + i) * K.nx + sx] : edge;
+    }
     int sy, ii = i;
     if (cy == 4) {
         sy = y < 0 ? -y - 1 : 2 * K.ny - 1 - y;
@@ -634,6 +644,30 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// The wall corrections of the edge rows (non-equilibrium extrapolation, Sec. IV.D):
+// thread (side, x) forms rho, u, T of the edge cell in FP64 and
+// M^-1 [f_hat^eq(rho, u_w, T_w) - f_hat^eq(rho, u, T)] in FP64, stored in R.
+template <typename R>
+__global__ void wall_kernel(const Model<R> K, const R* __restrict__ in, R* wall)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * K.nx) return;
+    const int side = t / K.nx, x = t % K.nx;
+    if (K.sbc[2 + side] != 2) return;
+    double rho, ux, uy, T;
+    conserved_at<R, false>(K, in, x, side ? K.ny - 1 : 0, rho, ux, uy, &T);
+    double qw[NV], qf[NV];
+    feq24<double>(K.I, K.DI, rho, K.wux[side], K.wuy[side], K.wT[side], qw);
+    feq24<double>(K.I, K.DI, rho, ux, uy, T, qf);
+#pragma unroll 4
+    for (int i = 0; i < NV; i++) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < NV; k++) acc = fma(K.Minvd[i * NV + k], qw[k] - qf[k], acc);
+        wall[((size_t)side * NV + i) * K.nx + x] = (R)acc;
+    }
+}
+
 template <typename R>
 __global__ void init_kernel(const Model<R> K, const double* rho, const double* ux,
                             const double* uy, const double* T, const double* lam, R* state)
@@ -903,6 +937,8 @@ struct lbkm24 {
     Record* tne_out;
     bool initialized;
     bool srt;  // the single-relaxation-time fast path runs the steps
+    bool has_wall;
+    void* wallbuf;  // [2][24][nx] wall corrections in the state's precision
     int64_t host_steps;
     cudaGraphExec_t graph[2];
     std::string err;
@@ -941,6 +977,15 @@ cudaError_t launch_one_step(const lbkm24* h, int from, cudaStream_t st)
     a.tne_every = h->p.tne_every;
     a.area = h->p.dx * h->p.dy;
     const bool gen = h->p.bc_x == LBKM_BC_SIDES || h->p.bc_y == LBKM_BC_SIDES;
+    if (h->has_wall) {
+        const int g = (2 * h->p.nx + 127) / 128;
+        if (h->p.precision == LBKM_F64)
+            wall_kernel<double><<<g, 128, 0, st>>>(h->Kd, (const double*)a.in, (double*)h->wallbuf);
+        else
+            wall_kernel<float><<<g, 128, 0, st>>>(h->Kf, (const float*)a.in, (float*)h->wallbuf);
+        const cudaError_t we = cudaGetLastError();
+        if (we != cudaSuccess) return we;
+    }
 #define V24_LAUNCH(R_, KK)                                                                   \
     do {                                                                                     \
         if (h->srt && gen) step_kernel<R_, true, true><<<h->grid, h->block, 0, st>>>(KK, a); \
@@ -1055,12 +1100,18 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
         if ((sd < 2 ? p.bc_x : p.bc_y) != LBKM_BC_SIDES) continue;
         const int code = p.side_bc[sd];
         const bool ok = code == LBKM_BC_ZERO_GRADIENT || code == LBKM_BC_DIRICHLET ||
-                        (code == LBKM_BC_SPECULAR && sd >= 2);
+                        ((code == LBKM_BC_SPECULAR || code == LBKM_BC_WALL) && sd >= 2);
         if (!ok)
             return fail(nullptr, LBKM_EINVAL,
-                        "side_bc[%d]: zero gradient, Dirichlet, or specular (y sides only)", sd);
-        if (code == LBKM_BC_SPECULAR && p.ny < 2)
-            return fail(nullptr, LBKM_EINVAL, "a specular side needs ny >= 2");
+                        "side_bc[%d]: zero gradient, Dirichlet, or specular / wall (y sides only)",
+                        sd);
+        if ((code == LBKM_BC_SPECULAR || code == LBKM_BC_WALL) && p.ny < 2)
+            return fail(nullptr, LBKM_EINVAL, "a specular or wall side needs ny >= 2");
+        if (code == LBKM_BC_WALL &&
+            (!(p.side_T[sd] > 0) || !isfinite(p.side_T[sd]) || !isfinite(p.side_ux[sd]) ||
+             !isfinite(p.side_uy[sd])))
+            return fail(nullptr, LBKM_EINVAL, "side %d: a wall needs T > 0 and a finite velocity",
+                        sd);
         if (code == LBKM_BC_DIRICHLET &&
             (!(p.side_rho[sd] > 0) || !(p.side_T[sd] > 0) || !isfinite(p.side_rho[sd]) ||
              !isfinite(p.side_T[sd]) || !isfinite(p.side_ux[sd]) || !isfinite(p.side_uy[sd]) ||
@@ -1114,6 +1165,12 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
     }
     fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, sbc, sfeq, &h->Kd);
     fill_model(p, Bf, Bi, Minv, vx, vy, e, h->pitch, sbc, sfeq, &h->Kf);
+    h->has_wall = p.bc_y == LBKM_BC_SIDES && (sbc[2] == LBKM_BC_WALL || sbc[3] == LBKM_BC_WALL);
+    for (int w = 0; w < 2; w++) {
+        h->Kd.wux[w] = h->Kf.wux[w] = p.side_ux[2 + w];
+        h->Kd.wuy[w] = h->Kf.wuy[w] = p.side_uy[2 + w];
+        h->Kd.wT[w] = h->Kf.wT[w] = p.side_T[2 + w];
+    }
     // 1-D grids too short to give every SM a block of 128 cells run blocks of one warp:
     // the step is latency-bound there, and more SMs each take fewer cells
     const bool narrow = p.ny == 1 && (p.nx + BT - 1) / BT < 2 * 152;
@@ -1131,6 +1188,13 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
         if ((ce = cudaMalloc(&h->buf[k], sb)) != cudaSuccess) return bail(ce, "state");
     if ((ce = cudaMalloc((void**)&h->partials, sizeof(double) * NQ * h->nblocks)) != cudaSuccess)
         return bail(ce, "partials");
+    if (h->has_wall) {
+        const size_t wb = sizeof(double) * 2 * NV * (size_t)p.nx;
+        if ((ce = cudaMalloc(&h->wallbuf, wb)) != cudaSuccess) return bail(ce, "walls");
+        if ((ce = cudaMemset(h->wallbuf, 0, wb)) != cudaSuccess) return bail(ce, "walls");
+        h->Kd.wall = static_cast<const double*>(h->wallbuf);
+        h->Kf.wall = static_cast<const float*>(h->wallbuf);
+    }
     if ((ce = cudaMalloc((void**)&h->ctr, sizeof(DevCounters))) != cudaSuccess)
         return bail(ce, "counters");
     if ((ce = cudaMalloc((void**)&h->hist, sizeof(Record) * h->p.tne_capacity)) != cudaSuccess)
@@ -1160,6 +1224,7 @@ void lbkm24_destroy(lbkm24_t h)
     if (h->ctr) cudaFree(h->ctr);
     if (h->hist) cudaFree(h->hist);
     if (h->tne_out) cudaFree(h->tne_out);
+    if (h->wallbuf) cudaFree(h->wallbuf);
     delete h;
 }
 

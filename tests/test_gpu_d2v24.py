@@ -440,3 +440,23 @@ def test_shock_reflection_with_paper_d2v24():
     assert abs(angle_r - 28.09) < 2.0, angle_r
     assert abs(x_foot - 0.1732) < 0.01, x_foot
     assert abs(behind_r / 1.538 - 1) < 0.03, behind_r
+
+
+WALL_SIDES = [(1, 1.0, 0.0, 0.0, 1.0, 0.0), (1, 1.0, 0.0, 0.0, 1.0, 0.0),
+              (2, 1.0, -0.03, 0.0, 1.05, 0.0), (2, 1.0, 0.08, 0.0, 0.97, 0.0)]
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PID)
+@pytest.mark.parametrize("nx,ny", [(45, 19), (33, 3)])
+def test_walls_parity(prec, nx, ny):
+    """Moving heated walls in y (non-equilibrium extrapolation, Sec. IV.D) on a reacting
+    non-equilibrium field, 25 steps, against the oracle."""
+    cfg = mixed_2d(nx, ny, bc=(0, 5), seed=nx + 11)
+    for key in ("params", "lib_params"):
+        cfg[key]["sides"] = WALL_SIDES
+    cfg["params"]["walls"] = ((-0.03, 0.0, 1.05), (0.08, 0.0, 0.97))
+    s, ob, f, lam = start(cfg, prec, noise_seed=ny + 5)
+    s.step(25)
+    f_ref, lam_ref = ob.run(f, lam, 25)
+    # FP32 holds the wall corrections (formed in FP64) in FP32: 2.2e-5 measured
+    check_state(s, ob, f_ref, lam_ref, prec, floor=0.0 if prec == lbkm.F64 else 4e-5)

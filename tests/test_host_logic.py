@@ -84,13 +84,15 @@ def test_d2v24_collision_flag_is_checked():
 
 @pytest.mark.parametrize("kw", [
     dict(ny=8, bc=(5, 0), sides=[(4, 1, 0, 0, 1, 0), (1, 1, 0, 0, 1, 0)] + [(1, 1, 0, 0, 1, 0)] * 2),
-    dict(ny=8, bc=(0, 5), sides=[(1, 1, 0, 0, 1, 0)] * 2 + [(2, 1, 0, 0, 1, 0), (1, 1, 0, 0, 1, 0)]),
+    dict(ny=8, bc=(5, 0), sides=[(2, 1, 0, 0, 1, 0)] + [(1, 1, 0, 0, 1, 0)] * 3),
     dict(ny=8, bc=(5, 0), sides=[(3, 0.0, 0, 0, 1, 0), (1, 1, 0, 0, 1, 0)] + [(1, 1, 0, 0, 1, 0)] * 2),
     dict(ny=1, bc=(0, 5), sides=[(1, 1, 0, 0, 1, 0)] * 2 + [(4, 1, 0, 0, 1, 0)] * 2),
+    dict(ny=1, bc=(0, 5), sides=[(1, 1, 0, 0, 1, 0)] * 2 + [(2, 1, 0, 0, 1, 0)] * 2),
+    dict(ny=8, bc=(0, 5), sides=[(1, 1, 0, 0, 1, 0)] * 2 + [(2, 1, 0, 0, 0.0, 0)] * 2),
 ])
 def test_d2v24_side_conditions_are_checked(kw):
-    """D2V24 per-side conditions: specular only on y sides (and ny >= 2), no walls,
-    physical Dirichlet states."""
+    """D2V24 per-side conditions: specular and walls only on y sides (and ny >= 2), a
+    positive wall temperature, physical Dirichlet states."""
     base = dict(nx=16, ny=1, dx=1e-3, dy=1e-3, dt=1e-5)
     base.update(kw)
     with pytest.raises(lbkm.LbkmError) as e:
