@@ -538,3 +538,28 @@ def test_couette_viscous_heating_fixes_the_sign_of_A(oracle_mod):
     cp = (2 + ob.p.I + 2) / 2
     ratio = coef[2] / (Pr * u0 ** 2 / (2 * cp))
     assert 0.6 < ratio < 1.2, ratio
+
+
+def test_entropy_mode_decays_at_the_thermal_diffusivity(oracle_mod):
+    """A temperature ripple at uniform pressure (an entropy mode) decays at alpha k^2 with
+    alpha = kappa / (rho c_p) = T / R_kappa, R_kappa = R_8 = R_9 (the energy equation of
+    Sec. III; Pr = R_kappa / R_mu, Eq. (86)): independent of R_5..R_7 and halved when
+    R_kappa doubles. Measured within 3 % on 128 cells (the rest is the scheme's own
+    diffusion); the bound is 6 %."""
+    nx, A = 128, 0.01
+    x = (np.arange(nx) + 0.5) / nx
+    T0 = 1 + A * np.cos(2 * np.pi * x)
+    for Rmu, Rk in ((1000.0, 200.0), (200.0, 200.0), (1000.0, 400.0)):
+        S = np.full(16, 2e3)
+        S[4:7] = Rmu
+        S[7:9] = Rk
+        ob = make(oracle_mod, nx, 1, S=S, dx=1.0 / nx, dt=1e-4, bc_x=0)
+        f = ob.init((1.0 / T0)[None], 0.0, 0.0, T0[None])
+        lam = np.zeros((1, nx))
+        amps = []
+        for _ in range(4):
+            f, lam = ob.run(f, lam, 2500)
+            T = ob.macros(f)["T"][0]
+            amps.append(2 * np.mean((T - T.mean()) * np.cos(2 * np.pi * x)))
+        rate = -np.polyfit(0.25 * np.arange(1, 5), np.log(np.abs(amps)), 1)[0]
+        assert abs(rate / ((2 * np.pi) ** 2 / Rk) - 1) < 0.06, (Rmu, Rk, rate)
