@@ -210,6 +210,31 @@ def cpu_oracle_rate(budget_s=12.0, side=1024):
     return rate, desc, int(os.environ["OMP_NUM_THREADS"])
 
 
+def cpu_oracle_rate_d2v24(budget_s=10.0, side=256):
+    """The D2V24 FP64 oracle, as it stands, on a side x side window of the 2-D D2V24 field
+    recipe; steps chosen to fill about budget_s seconds. Returns (Mcell/s, desc, cores)."""
+    from oracle import oracle
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    cfg = li.d2v24_reactive2d(n=side, steps=1)
+    p = dict(cfg["params"])
+    nx, ny = p.pop("nx"), p.pop("ny")
+    ob = oracle.Oracle(nx, ny, **p)
+    fl = cfg["fields"]
+    f = ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"])
+    t0 = time.perf_counter()
+    f, lam = ob.run(f, fl["lam"], 1)
+    one = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    ob.run(f, lam, steps)
+    dt = time.perf_counter() - t0
+    rate = nx * ny * steps / dt / 1e6
+    desc = ("FP64 C oracle with 24 velocities (OpenMP, %d threads) on a %dx%d D2V24 field, "
+            "%d steps, %.1f s" % (int(os.environ["OMP_NUM_THREADS"]), side, side, steps, dt))
+    return rate, desc, int(os.environ["OMP_NUM_THREADS"])
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, a bounded window per step."""
     rank, _, world = _env_rank()
@@ -412,6 +437,8 @@ def run_d2v24(args):
                        "note": "the paper's D2V24 steady-detonation set (Sec. IV.A); 1 MB "
                                "state, L2-resident"},
             "cases": out,
+            "cpu_baseline": dict(zip(("value", "sample", "cores"), cpu_oracle_rate_d2v24()),
+                                 unit="Mcell-updates/s", kind="oracle"),
             "roofline_reactive2d_f32": {"bound": "alu", "achieved": achieved, "peak": peak,
                                         "unit": "GB/s", "frac": achieved / peak,
                                         "peak_kind": peak_kind,
