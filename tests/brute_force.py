@@ -192,3 +192,32 @@ def equilibrium(cfg, rho, ux, uy, T):
             f[:, y, x] = np.linalg.solve(M, maxwellian_moments(rho[y, x], ux[y, x], uy[y, x],
                                                                T[y, x], I, nv=nv))
     return f
+
+
+def tne_record(cfg, f):
+    """Grid-wide TNE record of a state, written from Sec. VI without the oracle: for every
+    cell Delta_k = (M f)_k - f_hat^eq_k (k >= 5) with f_hat^eq from quadrature of the
+    continuous Maxwellian at the cell's rho, u, T; Delta_1..4 vanish by conservation and are
+    taken as 0. d = sqrt(sum_k Delta_k^2) (Eq. (91)). Sums of Delta_k, |Delta_k|, d and d^2
+    are weighted by the cell area dx dy; min and max are per-cell values.
+    Returns (delta [nv, ny, nx], dict like the oracle's record)."""
+    vx, vy, eta = velocity_set(cfg["orbit_kind"], cfg["orbit_speed"], cfg["orbit_eta"])
+    nv = len(vx)
+    I = 2.0 / (cfg["gamma"] - 1.0) - D
+    M = moment_matrix(vx, vy, eta)
+    _, ny, nx = f.shape
+    rho = f.sum(axis=0)
+    ux = np.tensordot(vx, f, 1) / rho
+    uy = np.tensordot(vy, f, 1) / rho
+    T = (np.tensordot(vx**2 + vy**2 + eta**2, f, 1) / rho - ux**2 - uy**2) / (D + I)
+    delta = np.zeros((nv, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            q = maxwellian_moments(rho[y, x], ux[y, x], uy[y, x], T[y, x], I, nv=nv)
+            delta[4:, y, x] = (M @ f[:, y, x] - q)[4:]
+    area = cfg["dx"] * cfg["dy"]
+    d = np.sqrt((delta ** 2).sum(axis=0))
+    rec = {"sum": delta.sum(axis=(1, 2)) * area, "abs_sum": np.abs(delta).sum(axis=(1, 2)) * area,
+           "min": delta.min(axis=(1, 2)), "max": delta.max(axis=(1, 2)),
+           "d_sum": float(d.sum() * area), "d2_sum": float((d ** 2).sum() * area)}
+    return delta, rec

@@ -262,6 +262,48 @@ def test_brute_force_small_grids(oracle_mod, nx, ny, bc_x, bc_y):
         assert np.all(delta[:4, yy, xx] == 0)
 
 
+@pytest.mark.parametrize("nv", [16, 24])
+def test_tne_grid_record_matches_independent_sums(oracle_mod, nv):
+    """The oracle's grid-wide TNE record (Sec. VI, Eqs. (90)-(91)) against the same record
+    rebuilt by the brute-force formulation: Delta_k from its own moment functions and the
+    quadrature Maxwellian, sums of Delta_k, |Delta_k|, d and d^2 weighted by dx dy,
+    unweighted min and max. Unequal dx and dy, so a missing or squared cell area, an
+    unweighted sum or a weighted extremum all fail; a state driven off equilibrium by a few
+    reactive steps, so every Delta_k has both signs."""
+    nx, ny = 7, 5
+    rng = np.random.default_rng(90 + nv)
+    orbits = li.DEFAULT_ORBITS if nv == 16 else li.d2v24_orbits(*li.D2V24_DETONATION_V)
+    cfg = dict(orbits, gamma=1.4, S=rng.uniform(2e3, 1e5, nv), Q=1.0, omega1=2e3,
+               omega2=0.0, T_ig=1.0, dx=1e-3, dy=2.5e-3, dt=1e-5, bc_x=0, bc_y=0)
+    ob = oracle_mod.Oracle(nx, ny, **cfg)
+    x = np.arange(nx) / nx
+    y = np.arange(ny)[:, None] / ny
+    rho = 1 + 0.1 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    ux = 0.2 * np.cos(2 * np.pi * (x + y))
+    uy = 0.1 * np.sin(2 * np.pi * y) - 0.05
+    T = 1.1 + 0.1 * np.sin(2 * np.pi * (x - y))
+    rho, ux, uy, T = (np.broadcast_to(a, (ny, nx)) for a in (rho, ux, uy, T))
+    f = bf.equilibrium(cfg, rho, ux, uy, T) * (1 + 3e-3 * rng.standard_normal((nv, ny, nx)))
+    f, _ = ob.run(f, rng.uniform(0, 0.5, (ny, nx)), 3)
+    delta, rec = ob.tne(f)
+    bdelta, brec = bf.tne_record(cfg, f)
+    scale = np.abs(bdelta).max()
+    assert np.abs(delta - bdelta).max() < 1e-11 * scale
+    area = cfg["dx"] * cfg["dy"]
+    for key in ("sum", "abs_sum"):
+        assert np.allclose(rec[key], brec[key], rtol=0, atol=1e-11 * scale * nx * ny * area)
+    for key in ("min", "max"):
+        assert np.allclose(rec[key][4:], brec[key][4:], rtol=0, atol=1e-11 * scale)
+        assert np.all(rec[key][:4] == 0)
+    assert abs(rec["d_sum"] - brec["d_sum"]) < 1e-10 * brec["d_sum"]
+    assert abs(rec["d2_sum"] - brec["d2_sum"]) < 1e-10 * brec["d2_sum"]
+    # the record is not degenerate: most Delta_k change sign over the grid, extremes
+    # apart, d^2 not d
+    signs = (brec["min"][4:] < 0) & (brec["max"][4:] > 0)
+    assert signs.sum() >= (nv - 4) // 2 and (brec["min"][4:] < brec["max"][4:]).all()
+    assert abs(brec["d2_sum"] - brec["d_sum"]) > 0.1 * brec["d_sum"]
+
+
 # ---------------------------------------------------------------- NND scheme
 def test_nnd_conservative_and_non_oscillatory(oracle_mod):
     n = 64
