@@ -233,11 +233,14 @@ lbkm_status lbkm_set_state(lbkm_t h, const void* src, int on_device);
  * asynchronous on cuda_stream. Scratch: a fixed device array inside the library
  * (about 0.8 MB on every GPU that loads it, kept until the process exits),
  * shared by all calls: calls that overlap on the GPU race, so serialise them
- * (one stream, or events). The first call on a device looks up the scratch
- * address with that device current; make that first call before any stream
- * capture. Limit: nx * ny <= 16,777,216 cells; larger grids return
- * LBKM_EINVAL. Errors: LBKM_EINVAL, LBKM_ESINGULAR, LBKM_ECUDA, with the
- * message in lbkm_last_error(NULL). */
+ * (one stream, or events). Each call outside stream capture looks up the
+ * scratch address with the calling device current (so a device reset or a new
+ * primary context is followed); a call during capture uses the address the
+ * last such lookup on that device found, so the first call on a device must
+ * come before any stream capture (else LBKM_ESTATE). Limits: nx * ny <=
+ * 16,777,216 cells and nx <= pitch <= 2,147,483,647 elements; other values
+ * return LBKM_EINVAL. Errors: LBKM_EINVAL, LBKM_ESINGULAR, LBKM_ESTATE,
+ * LBKM_ECUDA, with the message in lbkm_last_error(NULL). */
 lbkm_status lbkm_tne_noalloc(const lbkm_params* p, const void* state, int64_t pitch,
                              double* delta, lbkm_tne_global* out, void* cuda_stream);
 

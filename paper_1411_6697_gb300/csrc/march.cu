@@ -1,25 +1,35 @@
-// march.cu -- the FP32 2-D step kernel: y-marching strips, two cells per thread.
+// march.cu -- the FP32 2-D step kernel: y-marching strips, two rows per iteration,
+// two cells per thread, rows staged by bulk asynchronous copies.
 //
-// A block of 64 threads owns a strip of 128 columns x `strip_rows` rows and
-// marches up it one row per iteration. Thread t updates the cells (x0+2t, y)
-// and (x0+2t+1, y) together, so most arithmetic runs as packed FP32 pairs
-// (FFMA2 / FADD2 / FMUL2, sm_100+).
+// A block of 128 threads (4 warps) owns a strip of 128 columns x `strip_rows` rows
+// and marches up it two rows per iteration: warps 0-1 (warp pair 0) update row y,
+// warps 2-3 (warp pair 1) row y + 1. Thread t of a warp pair updates the cells
+// (x0 + 2t, y + r) and (x0 + 2t + 1, y + r) together, so most arithmetic runs as
+// packed FP32 pairs.
 //
-// Shared memory keeps the staged rows (128 + 4 columns, filled by 16- and 8-byte
-// cp.async copies) of the 17 planes in rings sized by what each plane still
-// needs: the y-stencil of a plane with v_y > 0 reads rows y-2..y+1, with v_y < 0
-// rows y-1..y+2, with v_y = 0 only row y, lambda rows y-2..y+2; every plane also
-// holds row y+2 (recovered this iteration) and the prefetched row y+3. That is
-// 88 staged plane-rows instead of 17 x 7, which lets four blocks share an SM.
-// A ring of 4 macro rows holds rho, u, T of rows y-1..y+2 (with one halo column
-// on each side for grad u). Per iteration: wait for row y+2, one __syncthreads,
-// issue the copy of row y+3, recover rho, u, T of row y+2 from its conserved
-// moments, update row y. The
-// conserved moments are summed exactly (TwoSum butterflies, split constants);
-// rho, u, T are then formed in FP64 (REC = 0) or in double-float on the FP32
-// pipes (REC = 1), and the ignition test T > T_ig is taken in that precision.
-// The TNE statistics of the updated state's input (Delta_5..Delta_16, Sec. VI)
-// accumulate in registers and are reduced per strip into FP64.
+// Shared memory keeps the staged rows of the 17 planes in rings sized per plane
+// class (the upwind side of the NND y-stencil is fixed by the sign of v_y): a plane
+// with v_y > 0 keeps rows y-2..y+5, v_y < 0 rows y-1..y+5, v_y = 0 rows y..y+5, lambda
+// y-2..y+5. Rows y+2, y+3 are recovered (rho, u, T) in the iteration, rows y+4, y+5
+// are in flight. Each staged plane row holds columns x0-4 .. x0+131 and is filled by
+// one bulk asynchronous copy (the TMA unit's non-tensor mode: both addresses and the
+// size multiples of 16 bytes), completing on an mbarrier per pair of rows; columns
+// that no such copy can reach (the wrapped or clamped halo at the grid's x-edges,
+// the tail of a row whose length is not a multiple of 4, ghost rows of Dirichlet or
+// specular sides) are filled by per-element asynchronous copies that arrive on the
+// same mbarrier, or by stores of the side's equilibrium.
+//
+// Per iteration (rows y, y+1): wait for rows y+2, y+3; warp pair r recovers rho, u, T
+// of row y+2+r from its exact conserved sums (kept in registers: the same pair
+// updates that row in the next iteration; u, v also go to a shared ring of five rows
+// for the neighbours' gradients); one barrier; warp pair r updates row y+r; one
+// barrier; warp 0 and warps 2-3 issue the copies of rows y+6, y+7 into the slots of
+// rows y-2, y-1.
+// The conserved moments are summed exactly (double-float butterflies); rho, u, T are
+// then formed in FP64 (REC = 0) or in double-float on the FP32 pipes (REC = 1), and
+// the ignition test T > T_ig is taken in that precision. The TNE statistics of the
+// updated state's input (Delta_5..Delta_16, Sec. VI, Eqs. (90)-(91)) accumulate per
+// thread in FP32 over a strip (32 cells) and from there on in FP64.
 #include <float.h>
 #include <stdlib.h>
 
@@ -33,19 +43,16 @@ namespace lbk {
 
 namespace {
 
-constexpr int MT = 64;         // threads per block
-constexpr int NWM = MT / 32;   // warps per block
-constexpr int BW = 2 * MT;     // columns per strip
-constexpr int RW = BW + 4;     // staged row: x0-2 .. x0+BW+1
-constexpr int PF = 1;          // staged rows in flight beyond y+2
-constexpr int MRING = 4;       // macro rows kept
-constexpr int MW = BW + 4;     // macro row: x0-2 .. x0+BW+1, own cells at even offsets
+constexpr int MT = 128;          // threads per block
+constexpr int NWM = MT / 32;     // warps per block
+constexpr int BW = 128;          // columns per strip
+constexpr int XO = 4;            // column x0 sits at element XO of a staged row
+constexpr int RW = BW + 2 * XO;  // staged row: columns x0-4 .. x0+BW+3 (544 bytes)
+constexpr int UVR = 5;           // rows of (u, v) kept: y-1 .. y+3
 
-// plane classes by the sign of v_y (orbits 0 and 2 are axis orbits, 1 and 3
-// diagonal): rows kept = rows the y-stencil reads below y+2, plus y+2 and y+3
 enum { C_UP = 0, C_DN = 1, C_FLAT = 2, C_LAM = 3 };
-constexpr int NROWS[4] = {6, 5, 4, 6};   // y-2..y+3, y-1..y+3, y..y+3, y-2..y+3
-constexpr int NPL[4] = {6, 6, 4, 1};     // planes per class
+constexpr int NROWS[4] = {8, 7, 6, 8};  // y-2..y+5, y-1..y+5, y..y+5, y-2..y+5
+constexpr int NPL[4] = {6, 6, 4, 1};    // planes per class
 __host__ __device__ constexpr int pclass(int p)
 {
     return p == 16 ? C_LAM
@@ -74,39 +81,37 @@ __host__ __device__ constexpr bool class_layout_ok()
     return true;
 }
 static_assert(class_layout_ok(), "every plane has its own slot in its class");
-
-// ring base (floats) of each class; the whole ring starts 2 floats into shared
-// memory so that every row base is 2 mod 4 floats and column x0 (element 2 of a
-// staged row) sits on a 16-byte boundary
-constexpr int CBASE0 = 2;
-constexpr int CBASE1 = CBASE0 + NROWS[0] * NPL[0] * RW;
-constexpr int CBASE2 = CBASE1 + NROWS[1] * NPL[1] * RW;
-constexpr int CBASE3 = CBASE2 + NROWS[2] * NPL[2] * RW;
-constexpr int RING_FLOATS = CBASE3 + NROWS[3] * NPL[3] * RW;
-static_assert(RW % 4 == 0 && CBASE1 % 4 == 2 && CBASE2 % 4 == 2 && CBASE3 % 4 == 2,
-              "row bases must be 2 mod 4 floats");
 static_assert(pclass(1) == C_UP && pclass(3) == C_DN && pclass(0) == C_FLAT && pclass(2) == C_FLAT &&
                   pclass(4) == C_UP && pclass(5) == C_UP && pclass(6) == C_DN && pclass(7) == C_DN &&
                   pclass(8) == C_FLAT && pclass(9) == C_UP && pclass(11) == C_DN &&
                   pclass(13) == C_UP && pclass(14) == C_DN && pindex(15) == 5 && pindex(10) == 3,
               "plane classes follow the orbit layout axis, diagonal, axis, diagonal");
 
-constexpr size_t OFF_MAC = ((size_t)RING_FLOATS * 4 + 15) / 16 * 16;
-constexpr size_t OFF_IGN = OFF_MAC + (size_t)4 * MRING * MW * 4;
-constexpr size_t OFF_TSUM = (OFF_IGN + (size_t)MRING * BW + 15) / 16 * 16;
-constexpr size_t OFF_TMM = OFF_TSUM + (size_t)NWM * NSUM * 8;
-constexpr size_t MARCH_SMEM = OFF_TMM + (size_t)NWM * NMM * 4;
-static_assert(MARCH_SMEM <= 56 * 1024, "four blocks per SM need <= 56 KB each");
-
-__device__ __forceinline__ int mac_slot(int r) { return (r + MRING) & (MRING - 1); }
+// shared-memory layout (floats from the 16-byte aligned start)
+constexpr int CB0 = 0;
+constexpr int CB1 = CB0 + NROWS[0] * NPL[0] * RW;
+constexpr int CB2 = CB1 + NROWS[1] * NPL[1] * RW;
+constexpr int CB3 = CB2 + NROWS[2] * NPL[2] * RW;
+constexpr int RING_FLOATS = CB3 + NROWS[3] * NPL[3] * RW;
+constexpr int UVB = RING_FLOATS;                 // (u, v) ring: [UVR][2][RW]
+constexpr int SMEM_FLOATS = UVB + UVR * 2 * RW;
+static_assert(RW % 4 == 0 && CB1 % 4 == 0 && CB2 % 4 == 0 && CB3 % 4 == 0 && UVB % 4 == 0,
+              "every staged row starts on a 16-byte boundary");
+constexpr size_t OFF_TSUM = (size_t)SMEM_FLOATS * 4;            // double[NSUM]
+constexpr size_t OFF_TMM = OFF_TSUM + (size_t)NSUM * 8;           // float[NWM][NMM]
+constexpr size_t OFF_MBAR = (OFF_TMM + (size_t)NWM * NMM * 4 + 15) / 16 * 16;
+constexpr int NMB = 4;                                            // row pairs in flight or in use
+constexpr size_t MARCH_SMEM = OFF_MBAR + NMB * 8;
+static_assert(MARCH_SMEM <= 74 * 1024, "three blocks per SM need <= 74 KB each");
+static_assert(NSUM * MT <= RING_FLOATS && 4 * NSUM <= MT, "the strip's TNE partials fit in the idle ring, four threads per sum");
 
 // start of the staged row r of class c
 template <int CL>
 __device__ __forceinline__ float* class_row(float* ring, int r)
 {
     constexpr int N = NROWS[CL], np = NPL[CL];
-    constexpr int base = CL == 0 ? CBASE0 : CL == 1 ? CBASE1 : CL == 2 ? CBASE2 : CBASE3;
-    return ring + base + ((r + 8 * N) % N) * np * RW;
+    constexpr int base = CL == 0 ? CB0 : CL == 1 ? CB1 : CL == 2 ? CB2 : CB3;
+    return ring + base + ((r + 16 * N) % N) * np * RW;
 }
 // the staged row r of plane p (p a compile-time constant after unrolling)
 __device__ __forceinline__ float* plane_row(float* ring, int p, int r)
@@ -117,121 +122,195 @@ __device__ __forceinline__ float* plane_row(float* ring, int p, int r)
                                      : c == C_FLAT ? class_row<C_FLAT>(ring, r) : class_row<C_LAM>(ring, r);
     return b + pindex(p) * RW;
 }
-
-__device__ __forceinline__ void cp8(void* dst, const void* src)
+// the same for a plane index known only at run time
+__device__ __forceinline__ float* plane_row_rt(float* ring, int p, int r)
 {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+    float* b = ring;
+#pragma unroll
+    for (int q = 0; q < NPLANE; q++)
+        if (q == p) b = plane_row(ring, q, r);
+    return b;
+}
+__device__ __forceinline__ float* uv_row(float* smem_f, int r, int field)
+{
+    return smem_f + UVB + (((r + 16 * UVR) % UVR) * 2 + field) * RW;
 }
 
-// n staged values of plane p, row r, columns x .. x+n-1 through the boundary rules
-// (the rare path of the staging)
-__device__ __forceinline__ void stage_elements(const ModelConst<float>& K, const float* in, float* dst,
-                                            int p, int x, int r, int n)
+// ---------------- mbarriers and bulk copies -------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
-    for (int e = 0; e < n; e++) dst[e] = ghost_value(K, in, p, x + e, r);
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
+                 : "memory");
+}
+// one bounded wait for the phase with the given parity; false if it did not complete
+__device__ __forceinline__ bool mbar_try(uint32_t mb, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity), "r"(1000u)
+        : "memory");
+    return ok != 0;
+}
+// waits with a bound (about 20 ms of suspended polling); false if the bound ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity)
+{
+    for (int i = 0; i < 20000; i++)
+        if (mbar_try(mb, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mb)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(mb)
+        : "memory");
+}
+__device__ __forceinline__ void cp4(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_arrive_noinc(uint32_t mb)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
+}
+__device__ __forceinline__ void fence_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Stage row r of the planes whose class is in `mask`, columns x0-2 .. x0+BW+1: the
-// 32 16-byte chunks of columns x0 .. x0+BW-1 of a plane by one warp (lane = chunk),
-// the two 8-byte edges (x0-2, x0-1 and x0+BW, x0+BW+1) of all planes by the first 34
-// threads. Rows outside the grid follow the side's condition: a Dirichlet side fills
-// the row with its equilibrium, a specular side copies the mirror row with the planes
-// of reversed v_y, the others copy the wrapped or edge row (walls are corrected after
-// the row lands). Columns outside the grid go element by element through the same
-// rules (ghost_value).
+// Where plane p of staged row r comes from: the grid row gy and plane sp (specular
+// sides mirror the row and reverse v_y), or a Dirichlet side (dir >= 0) whose
+// equilibrium fills the row.
 template <bool GEN>
-__device__ __forceinline__ void issue_row(const float* __restrict__ in, float* ring, int r,
-                                          int x0, const ModelConst<float>& K, unsigned mask)
+__device__ __forceinline__ void row_source(const ModelConst<float>& K, int r, int p, int& gy, int& sp,
+                                           int& dir)
 {
-    static_assert(BW == 128 && NWM == 2, "staging layout assumes 32 chunks per row and 2 warps");
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if constexpr (!GEN) { // periodic or zero-gradient sides only: index maps, no ghost rules
-        const float* rowp = in + (int64_t)map_index(r, K.ny, K.bc_y) * K.pitch;
-#pragma unroll
-        for (int p = 0; p < NPLANE; p++) {
-            if ((p & 1) != w || !((mask >> pclass(p)) & 1u)) continue;
-            float* dst = plane_row(ring, p, r) + 2 + 4 * lane;
-            const float* src = rowp + p * K.plane;
-            const int x = x0 + 4 * lane;
-            if (x + 4 <= K.nx) {
-                cp16(dst, src + x);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; e++) dst[e] = src[map_index(x + e, K.nx, K.bc_x)];
-            }
-        }
-        if (threadIdx.x < 2 * NPLANE) {
-            const int p = threadIdx.x >> 1, side = threadIdx.x & 1;
-            if ((mask >> pclass(p)) & 1u) {
-                float* dst = plane_row(ring, p, r) + (side ? BW + 2 : 0);
-                const float* src = rowp + p * K.plane;
-                const int x = side ? x0 + BW : x0 - 2;
-                if (x >= 0 && x + 2 <= K.nx) {
-                    cp8(dst, src + x);
-                } else {
-                    dst[0] = src[map_index(x, K.nx, K.bc_x)];
-                    dst[1] = src[map_index(x + 1, K.nx, K.bc_x)];
-                }
-            }
-        }
-        return;
-    }
-    int gy = r, dir_side = -1;
-    bool mir = false;
-    if (r < 0 || r >= K.ny) {
+    gy = r;
+    sp = p;
+    dir = -1;
+    if (r >= 0 && r < K.ny) return;
+    if constexpr (!GEN) {
+        gy = map_index(r, K.ny, K.bc_y);
+    } else {
         const int s = r < 0 ? 2 : 3, code = K.sbc[s];
         if (code == 3) {
-            dir_side = s;
+            dir = s;
         } else if (code == 4) {
             gy = r < 0 ? -r - 1 : 2 * K.ny - 1 - r;
             gy = gy < 0 ? 0 : (gy >= K.ny ? K.ny - 1 : gy);
-            mir = true;
+            sp = mirror_plane(p);
         } else {
             gy = map_index(r, K.ny, code == 0 ? 0 : 1);
         }
     }
-    const float* rowp = in + (int64_t)gy * K.pitch;
+}
+
+// Issue the copies of staged rows ra, ra+1 (pair mbarrier mb) for the strip at x0;
+// rows above rmax are not needed. Warp 0: one bulk copy per plane row for the columns
+// [cs, ce) (16-byte aligned), after arming the mbarrier with their byte count.
+// Warps 2-3: the remaining columns x0-2 .. x0+BW+1 that active cells read (edges of
+// the grid, a row tail past the last multiple of 4, Dirichlet rows), element by
+// element, then one arrival each on the mbarrier once their copies have landed.
+template <bool GEN>
+__device__ __forceinline__ void issue_pair(const float* __restrict__ in, float* ring, uint32_t mb,
+                                           int ra, int rmax, int x0, const ModelConst<float>& K)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nx4 = K.nx & ~3;
+    const int cs = x0 - XO > 0 ? x0 - XO : 0;
+    const int ce = x0 + BW + XO < nx4 ? x0 + BW + XO : nx4;
+    if (warp == 0) {
+        const float* src[2];
+        uint32_t dst[2], nb[2];
+        uint32_t bytes = 0;
 #pragma unroll
-    for (int p = 0; p < NPLANE; p++) {
-        if ((p & 1) != w || !((mask >> pclass(p)) & 1u)) continue;
-        float* dst = plane_row(ring, p, r) + 2 + 4 * lane;
-        const int x = x0 + 4 * lane;
-        if (dir_side >= 0) {
-            const float v = K.sfeq[dir_side][p];
-            *reinterpret_cast<float4*>(dst) = make_float4(v, v, v, v);
-            continue;
+        for (int u = 0; u < 2; u++) {
+            const int task = lane + 32 * u;
+            nb[u] = 0;
+            if (task < 2 * NPLANE) {
+                const int r = ra + task / NPLANE, p = task % NPLANE;
+                int gy, sp, dir;
+                row_source<GEN>(K, r, p, gy, sp, dir);
+                if (r <= rmax && dir < 0 && ce > cs) {
+                    src[u] = in + sp * K.plane + (int64_t)gy * K.pitch + cs;
+                    dst[u] = smem_addr(plane_row_rt(ring, p, r) + (cs - (x0 - XO)));
+                    nb[u] = (uint32_t)(ce - cs) * 4u;
+                    bytes += nb[u];
+                }
+            }
         }
-        const int sp = mir ? mirror_plane(p) : p;
-        const float* src = rowp + sp * K.plane;
-        if (x + 4 <= K.nx)
-            cp16(dst, src + x);
-        else
-            stage_elements(K, in, dst, p, x, r, 4);
-    }
-    if (threadIdx.x < 2 * NPLANE) {
-        const int p = threadIdx.x >> 1, side = threadIdx.x & 1;
-        if ((mask >> pclass(p)) & 1u) {
-            float* dst = plane_row(ring, p, r) + (side ? BW + 2 : 0);
-            const int x = side ? x0 + BW : x0 - 2;
-            if (dir_side < 0 && x >= 0 && x + 2 <= K.nx)
-                cp8(dst, rowp + (mir ? mirror_plane(p) : p) * K.plane + x);
-            else
-                stage_elements(K, in, dst, p, x, r, 2);
+        bytes = __reduce_add_sync(0xffffffffu, bytes);
+        if (lane == 0) mbar_expect_tx(mb, bytes);
+        __syncwarp();
+        fence_async_shared();
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+            if (nb[u]) bulk_g2s(dst[u], src[u], nb[u], mb);
+    } else if (warp >= 2) {
+        const int ft = tid - 64; // 0..63
+        // tasks: (row, plane, side) with side 0 = columns [x0-2, cs), side 1 = columns
+        // [max(ce, x0-2), min(nx+4, x0+BW+2)) (the ghost columns active cells read, and
+        // two more that only an inactive neighbour reads); Dirichlet rows: every column
+        for (int task = ft; task < 4 * NPLANE; task += 64) {
+            const int side = task & 1, rp = task >> 1;
+            const int r = ra + rp / NPLANE, p = rp % NPLANE;
+            if (r > rmax) continue;
+            int gy, sp, dir;
+            row_source<GEN>(K, r, p, gy, sp, dir);
+            float* row = plane_row_rt(ring, p, r);
+            int c0, c1;
+            if (dir >= 0) { // the whole row holds the side's equilibrium (split between sides)
+                c0 = side ? x0 + BW / 2 : x0 - 2;
+                c1 = side ? x0 + BW + 2 : x0 + BW / 2;
+            } else {
+                c0 = side ? (ce > x0 - 2 ? ce : x0 - 2) : x0 - 2;
+                c1 = side ? (K.nx + 4 < x0 + BW + 2 ? K.nx + 4 : x0 + BW + 2) : cs;
+                if (!side && ce <= cs) c1 = x0 - 2; // no bulk copy: side 1 takes the row
+                if (side && ce <= cs) c0 = x0 - 2;
+            }
+            for (int x = c0; x < c1; x++) {
+                float* d = row + (x - (x0 - XO));
+                if (dir >= 0) {
+                    *d = K.sfeq[dir][p];
+                    continue;
+                }
+                int xx = x, psrc = sp;
+                if (x < 0 || x >= K.nx) {
+                    const int s = x < 0 ? 0 : 1;
+                    if constexpr (GEN) {
+                        if (K.sbc[s] == 3) {
+                            *d = K.sfeq[s][p];
+                            continue;
+                        }
+                        xx = map_index(x, K.nx, K.sbc[s] == 0 ? 0 : 1);
+                    } else {
+                        xx = map_index(x, K.nx, K.bc_x);
+                    }
+                }
+                cp4(smem_addr(d), in + psrc * K.plane + (int64_t)gy * K.pitch + xx);
+            }
         }
+        cp_arrive_noinc(mb);
     }
 }
-constexpr unsigned ALL_CLASSES = 0xfu;
 
-// Walls (Sec. IV.D): the staged ghost row r_ghost holds a copy of the fluid row r_src
-// (the index map clamps); add the non-equilibrium-extrapolation correction to the
-// thread's own two columns of the f planes that keep that row (only the v_y > 0
-// class keeps row y0-2). Ghost rows are read only at the own columns of the thread
-// that corrects them (y-stencils and macros), so no barrier follows.
+// Walls (Sec. IV.D): a staged ghost row r_ghost holds a copy of the fluid row r_src (the
+// index map clamps); add the non-equilibrium-extrapolation correction to the thread's
+// own two columns of its f planes (only the v_y > 0 class keeps row y0-2).
 __device__ __forceinline__ void wall_fix_row(float* ring, int r_ghost, int r_src, int side,
-                                             const ModelConst<float>& K, bool up_only)
+                                             const ModelConst<float>& K, bool up_only, int lx)
 {
-    const int lx = 2 * threadIdx.x + 2;
     V2 f[16], d[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) f[i] = ldv(plane_row(ring, i, r_src) + lx);
@@ -243,323 +322,373 @@ __device__ __forceinline__ void wall_fix_row(float* ring, int r_ghost, int r_src
         *reinterpret_cast<float2*>(q) = (ldv(q) + d[i]).v;
     }
 }
+// wall correction of staged row r if it is a wall ghost row
+template <bool GEN>
+__device__ __forceinline__ void wall_fix(float* ring, int r, const ModelConst<float>& K, int lx)
+{
+    if constexpr (GEN) {
+        if (r < 0 && K.sbc[2] == 2) wall_fix_row(ring, r, 0, 0, K, r < -1, lx);
+        if (r >= K.ny && K.sbc[3] == 2) wall_fix_row(ring, r, K.ny - 1, 1, K, false, lx);
+    }
+}
 
-struct MacRow {
+struct Mac {
     V2 rho, ux, uy, T;
     bool ig0, ig1;
-    float hu, hv; // velocity of the halo column (threads 0 and MT-1)
 };
 
-// rho, u, T of the thread's two cells of staged row r, kept in registers until
-// store_macros so that the update of an earlier row can run in between.
+// rho, u, T of the thread's two cells of staged row r (exact conserved sums, then FP64
+// or double-float); u, v also into the (u, v) ring, with the halo columns x0-1 and
+// x0+BW (plain FP32 velocity, used only in grad u) by the first and last thread.
 template <int REC>
-__device__ __forceinline__ MacRow row_macros(const float* ring, int r, const ModelConst<float>& K,
-                                             const DfConst& C, int& bad, bool act0, bool act1)
+__device__ __forceinline__ Mac recover_row(float* smem_f, float* ring, int r, int t,
+                                           const ModelConst<float>& K, const DfConst& C, int& bad,
+                                           bool act0, bool act1)
 {
-    const int tid = threadIdx.x;
-    float* rg = const_cast<float*>(ring);
-    const int lx = 2 * tid + 2;
+    const int lx = XO + 2 * t;
     V2 f[16];
 #pragma unroll
-    for (int i = 0; i < 16; i++) f[i] = V2(*reinterpret_cast<const float2*>(plane_row(rg, i, r) + lx));
-    MacRow o;
+    for (int i = 0; i < 16; i++) f[i] = ldv(plane_row(ring, i, r) + lx);
+    Mac o;
     bool ok0, ok1;
-    recover_pair<REC>(f, C, K, o.rho, o.ux, o.uy, o.T, o.ig0, o.ig1, ok0, ok1);
+    recover_pair_fast<REC>(f, C, K, o.rho, o.ux, o.uy, o.T, o.ig0, o.ig1, ok0, ok1);
     if ((act0 && !ok0) || (act1 && !ok1)) bad = 1;
-    o.hu = o.hv = 0.f;
-    if (tid == 0 || tid == MT - 1) { // halo columns x0-1 and x0+BW: velocity only
-        const int hx = tid == 0 ? 1 : BW + 2;
-        float g[16];
+    float* ur = uv_row(smem_f, r, 0);
+    float* vr = uv_row(smem_f, r, 1);
+    *reinterpret_cast<float2*>(ur + lx) = o.ux.v;
+    *reinterpret_cast<float2*>(vr + lx) = o.uy.v;
+    if (t == 0 || t == 63) {
+        const int hx = t == 0 ? XO - 1 : XO + BW;
+        float g[16], hu, hv;
 #pragma unroll
-        for (int i = 0; i < 16; i++) g[i] = plane_row(rg, i, r)[hx];
-        velocity_f32(g, K, o.hu, o.hv);
+        for (int i = 0; i < 16; i++) g[i] = plane_row(ring, i, r)[hx];
+        velocity_f32(g, K, hu, hv);
+        ur[hx] = hu;
+        vr[hx] = hv;
     }
     return o;
 }
 
-__device__ __forceinline__ void store_macros(float* mac, unsigned char* ign, int r, const MacRow& o)
-{
-    const int tid = threadIdx.x;
-    const int ms = mac_slot(r);
-    const int mi = 2 * tid + 2;
-    *reinterpret_cast<float2*>(mac + (0 * MRING + ms) * MW + mi) = o.rho.v;
-    *reinterpret_cast<float2*>(mac + (1 * MRING + ms) * MW + mi) = o.ux.v;
-    *reinterpret_cast<float2*>(mac + (2 * MRING + ms) * MW + mi) = o.uy.v;
-    *reinterpret_cast<float2*>(mac + (3 * MRING + ms) * MW + mi) = o.T.v;
-    ign[ms * BW + 2 * tid] = o.ig0;
-    ign[ms * BW + 2 * tid + 1] = o.ig1;
-    if (tid == 0 || tid == MT - 1) {
-        const int hm = tid == 0 ? 1 : BW + 2;
-        mac[(1 * MRING + ms) * MW + hm] = o.hu;
-        mac[(2 * MRING + ms) * MW + hm] = o.hv;
-    }
-}
+// per-thread TNE statistics of one strip (FP32) and of the whole launch (min, max)
+struct TneAcc {
+    float sum[TNE_K], abs[TNE_K], dsum, d2sum;
+};
 
-template <int REC, bool GEN, bool AVG>
-__global__ void __launch_bounds__(MT, 4)
-    march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows)
+// ---------------- the update of one row by one warp pair -------------------------
+// Row y, the thread's cells x0 + 2t and x0 + 2t + 1 (active when act0 / act1), macros
+// mc recovered in the previous iteration.
+template <int REC, bool AVG>
+__device__ __forceinline__ void update_row(float* smem_f, float* ring, int y, int x0, int t,
+                                           const ModelConst<float>& K, const StepLaunch& a,
+                                           const Mac& mc, bool act0, bool act1, bool do_tne,
+                                           TneAcc& acc, float* tmin, float* tmax)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    float* ring = reinterpret_cast<float*>(smem);  // class rings from float 2 on (see CBASE0)
-    float* mac = reinterpret_cast<float*>(smem + OFF_MAC);
-    unsigned char* ign = smem + OFF_IGN;
-    double* tsum = reinterpret_cast<double*>(smem + OFF_TSUM);
-    float* tmm = reinterpret_cast<float*>(smem + OFF_TMM);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nx = K.nx, ny = K.ny;
-    const float* __restrict__ in = static_cast<const float*>(a.in);
+    const int lx = XO + 2 * t;
+    const float dt = K.dt;
     float* out = static_cast<float*>(a.out); // not restrict: prev may alias it
     // AVG: a later SSP Runge-Kutta stage, out = wp * u^n + wn * E(in), u^n read from prev
     // at the cell's own position (prev may be out itself: each value is read before it
     // is written, by the same thread)
     const float* pv = static_cast<const float*>(a.prev);
     const float wp = (float)a.wprev, wn = (float)a.wnew;
+    const V2 rho = mc.rho, ux = mc.ux, uy = mc.uy, T = mc.T;
 
-    const DfConst C = df_constants(K);
-
-    const int64_t step = a.ctr->step;
-    // AVG stages reduce no TNE
-    const bool do_tne = !AVG && a.tne_every > 0 && (step % a.tne_every) == 0;
-    if (do_tne) {
-        for (int i = tid; i < NWM * NSUM; i += MT) tsum[i] = 0.0;
-        for (int i = tid; i < NWM * NMM; i += MT) tmm[i] = (i % NMM) < TNE_K ? FLT_MAX : -FLT_MAX;
+    // moments, equilibrium, non-equilibrium parts (Delta_1..4 vanish)
+    V2 m[16];
+    {
+        V2 f[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) f[i] = ldv(plane_row(ring, i, y) + lx);
+        forward_moments(K, f, m);
     }
-    float tmin[TNE_K], tmax[TNE_K];
+    {
+        V2 q[16];
+        feq_moments(V2(K.DI), rho, ux, uy, T, q);
 #pragma unroll
-    for (int k = 0; k < TNE_K; k++) tmin[k] = FLT_MAX, tmax[k] = -FLT_MAX;
-    int bad = 0;
-
-    const int nsx = (nx + BW - 1) / BW, nsy = (ny + strip_rows - 1) / strip_rows;
-    const int nstrips = nsx * nsy;
-    const int lx = 2 * tid + 2;  // own cells in a staged row
-    const int mi = 2 * tid + 2;  // own cells in a macro row
-    const float dt = K.dt;
-
-    for (int s = blockIdx.x; s < nstrips; s += gridDim.x) {
-        const int x0 = (s / nsy) * BW, y0 = (s % nsy) * strip_rows;
-        const int yend = y0 + strip_rows < ny ? y0 + strip_rows : ny;
-        const int cx = x0 + 2 * tid;
-        const bool act0 = cx < nx, act1 = cx + 1 < nx;
-        float tsm[NSUM];
-        V2 tsp[TNE_K], td2(0.f);
+        for (int k = 4; k < 16; k++) m[k] = m[k] - q[k];
+    }
+    // TNE statistics of the state being stepped (Eqs. (90)-(91))
+    if (do_tne && act0) {
+        V2 d2(0.f);
 #pragma unroll
-        for (int q = 0; q < NSUM; q++) tsm[q] = 0.f;
-#pragma unroll
-        for (int k = 0; k < TNE_K; k++) tsp[k] = V2(0.f);
-
-        __syncthreads(); // the previous strip is done with the rings
-        // rows y0-2 .. y0+2: row y0-2 only for the classes whose stencil reaches it
-        for (int r = y0 - 2; r <= y0 + 1 + PF; r++) {
-            if (r <= yend + 1)
-                issue_row<GEN>(in, ring, r, x0, K,
-                               r == y0 - 2 ? ((1u << C_UP) | (1u << C_LAM)) : ALL_CLASSES);
-            cp_commit();
+        for (int k = 0; k < TNE_K; k++) {
+            const V2 Dk = act1 ? m[k + 4] : V2(m[k + 4].x(), 0.f);
+            d2 = fma(Dk, Dk, d2);
+            acc.sum[k] += Dk.x() + Dk.y();
+            acc.abs[k] += fabsf(Dk.x()) + fabsf(Dk.y());
+            const float hi = act1 ? Dk.y() : Dk.x();
+            tmin[k] = fmin3(tmin[k], Dk.x(), hi);
+            tmax[k] = fmax3(tmax[k], Dk.x(), hi);
         }
-        cp_wait<PF>(); // rows y0-2 .. y0+1 have landed
-        __syncthreads();
-        // walls: ghost rows among those landed (row y0+2 is fixed in the loop)
-        if constexpr (GEN) {
-            if (K.sbc[2] == 2) {
-                if (y0 - 1 < 0) wall_fix_row(ring, y0 - 1, 0, 0, K, false);
-                if (y0 - 2 < 0) wall_fix_row(ring, y0 - 2, 0, 0, K, true); // v_y > 0 only
-            }
-            if (K.sbc[3] == 2 && y0 + 1 >= ny) wall_fix_row(ring, y0 + 1, ny - 1, 1, K, false);
+        acc.dsum += sqrt_approx(d2.x()) + sqrt_approx(d2.y());
+        acc.d2sum += d2.x() + d2.y();
+    }
+
+    // grad u: x from the (u, v) ring row y (halo columns included), y from rows y+-1
+    const float* uxr = uv_row(smem_f, y, 0);
+    const float* uyr = uv_row(smem_f, y, 1);
+    const float2 uxl = *reinterpret_cast<const float2*>(uxr + lx - 2);
+    const float2 uxh = *reinterpret_cast<const float2*>(uxr + lx + 2);
+    const float2 uyl = *reinterpret_cast<const float2*>(uyr + lx - 2);
+    const float2 uyh = *reinterpret_cast<const float2*>(uyr + lx + 2);
+    const V2 dux_dx = (V2(ux.y(), uxh.x) - V2(uxl.y, ux.x())) * K.half_inv_dx;
+    const V2 duy_dx = (V2(uy.y(), uyh.x) - V2(uyl.y, uy.x())) * K.half_inv_dx;
+    const V2 dux_dy = (ldv(uv_row(smem_f, y + 1, 0) + lx) - ldv(uv_row(smem_f, y - 1, 0) + lx)) *
+                      K.half_inv_dy;
+    const V2 duy_dy = (ldv(uv_row(smem_f, y + 1, 1) + lx) - ldv(uv_row(smem_f, y - 1, 1) + lx)) *
+                      K.half_inv_dy;
+    const V2 theta = (dux_dx + duy_dy) * K.inv_DI;
+    const V2 shear = duy_dx + dux_dy;
+    const V2 rT = rho * T;
+    const V2 A8 = (rT * K.A8c) * fma(V2(4.f) * ux, dux_dx - theta, V2(2.f) * uy * shear);
+    const V2 A9 = (rT * K.A9c) * fma(V2(4.f) * uy, duy_dy - theta, V2(2.f) * ux * shear);
+
+    // reaction over dt (Eq. (28)), decided by the recovered T
+    const float* lm = class_row<C_LAM>(ring, y);
+    const V2 lam0 = ldv(lm + lx);
+    const float ri0 = reaction_increment(lam0.x(), K.omega1 * rT.x(), K.omega2 * rT.x(), dt);
+    const float ri1 = reaction_increment(lam0.y(), K.omega1 * rT.y(), K.omega2 * rT.y(), dt);
+    const V2 dlam(mc.ig0 ? ri0 : 0.f, mc.ig1 ? ri1 : 0.f);
+    const V2 cr = dlam * K.chem;
+
+    // collision in moment space and back
+    V2 W[16];
+    {
+        V2 dq[16], Om[16];
+        dfeq_dT(V2(K.DI), rho, ux, uy, T, dq);
+        Om[0] = Om[1] = Om[2] = V2(0.f);
+        Om[3] = dq[3] * cr;
+#pragma unroll
+        for (int k = 4; k < 16; k++) Om[k] = fma(V2(-K.S[k]), m[k], dq[k] * cr);
+        Om[7] += A8;
+        Om[8] += A9;
+        inverse_moments(K, Om, W);
+    }
+
+    const int cx = x0 + 2 * t;
+    const int64_t g = (int64_t)y * K.pitch + cx;
+    auto store = [&](int i, V2 v) {
+        if (act1) {
+            float2* q = reinterpret_cast<float2*>(out + i * K.plane + g);
+            if constexpr (AVG)
+                v = fma(V2(wp), V2(*reinterpret_cast<const float2*>(pv + i * K.plane + g)), V2(wn) * v);
+            *q = v.v;
+        } else if (act0) {
+            float* q = out + i * K.plane + g;
+            *q = AVG ? fmaf(wp, pv[i * K.plane + g], wn * v.x()) : v.x();
         }
-        for (int r = y0 - 1; r <= y0 + 1; r++)
-            store_macros(mac, ign, r, row_macros<REC>(ring, r, K, C, bad, act0, act1));
+    };
 
-        for (int y = y0; y < yend; y++) {
-            cp_wait<PF - 1>(); // row y+2 has landed
-            __syncthreads();
-            if (y + 2 + PF <= yend + 1) issue_row<GEN>(in, ring, y + 2 + PF, x0, K, ALL_CLASSES);
-            cp_commit();
-            if constexpr (GEN)
-                if (K.sbc[3] == 2 && y + 2 >= ny) wall_fix_row(ring, y + 2, ny - 1, 1, K, false);
-            // macros of row y+2 (read from the next iteration on)
-            store_macros(mac, ign, y + 2, row_macros<REC>(ring, y + 2, K, C, bad, act0, act1));
+    // lambda: u . grad(lambda) with NND interface values
+    {
+        const Q6 lq = load6(lm, lx);
+        const V2 lpx = nnd_pos_x(lq), lnx = nnd_neg_x(lq);
+        const V2 lm1 = ldv(class_row<C_LAM>(ring, y - 1) + lx);
+        const V2 lp1 = ldv(class_row<C_LAM>(ring, y + 1) + lx);
+        const V2 lpy = nnd_pos_y(ldv(class_row<C_LAM>(ring, y - 2) + lx), lm1, lam0, lp1);
+        const V2 lny = nnd_neg_y(lm1, lam0, lp1, ldv(class_row<C_LAM>(ring, y + 2) + lx));
+        const V2 lax(ux.x() > 0.f ? lpx.x() : lnx.x(), ux.y() > 0.f ? lpx.y() : lnx.y());
+        const V2 lay(uy.x() > 0.f ? lpy.x() : lny.x(), uy.y() > 0.f ? lpy.y() : lny.y());
+        const V2 ladv = fma(ux * K.inv_dx, lax, uy * K.inv_dy * lay);
+        V2 ln = fma(V2(-dt), ladv, lam0) + dlam;
+        ln = vmin(vmax(ln, V2(0.f)), V2(1.f));
+        store(16, ln);
+    }
 
-            // ---------------- update of row y ----------------
-            // row y of every plane; rows y-2..y+1 of the v_y > 0 class, y-1..y+2 of the
-            // v_y < 0 class, y-2..y+2 of lambda
-            const float* up_m2 = class_row<C_UP>(ring, y - 2);
-            const float* up_m1 = class_row<C_UP>(ring, y - 1);
-            const float* up_p1 = class_row<C_UP>(ring, y + 1);
-            const float* dn_m1 = class_row<C_DN>(ring, y - 1);
-            const float* dn_p1 = class_row<C_DN>(ring, y + 1);
-            const float* dn_p2 = class_row<C_DN>(ring, y + 2);
-            const float* lm = class_row<C_LAM>(ring, y);
-            const int ms = mac_slot(y), msm = mac_slot(y - 1), msp = mac_slot(y + 1);
-            V2 f[16];
+    // NND flux differences (upwind side fixed per velocity), Euler update, store
+    const float* up_m2 = class_row<C_UP>(ring, y - 2);
+    const float* up_m1 = class_row<C_UP>(ring, y - 1);
+    const float* up_p1 = class_row<C_UP>(ring, y + 1);
+    const float* dn_m1 = class_row<C_DN>(ring, y - 1);
+    const float* dn_p1 = class_row<C_DN>(ring, y + 1);
+    const float* dn_p2 = class_row<C_DN>(ring, y + 2);
+    auto put = [&](int i, V2 f0, V2 adv) { store(i, fma(V2(dt), W[i] - adv, f0)); };
+#define ROW(i) plane_row(ring, (i), y)
+#define F0(i) ldv(ROW(i) + lx)
+#define PX(i) nnd_pos_x(load6(ROW(i), lx))
+#define NX(i) nnd_neg_x(load6(ROW(i), lx))
+#define PY(i, f0) nnd_pos_y(ldv(up_m2 + pindex(i) * RW + lx), ldv(up_m1 + pindex(i) * RW + lx), f0, \
+                            ldv(up_p1 + pindex(i) * RW + lx))
+#define NY(i, f0) nnd_neg_y(ldv(dn_m1 + pindex(i) * RW + lx), f0, ldv(dn_p1 + pindex(i) * RW + lx), \
+                            ldv(dn_p2 + pindex(i) * RW + lx))
 #pragma unroll
-            for (int i = 0; i < 16; i++) f[i] = ldv(plane_row(ring, i, y) + lx);
-            const V2 lam0 = ldv(lm + lx);
-            const V2 rho = ldv(mac + (0 * MRING + ms) * MW + mi);
-            const V2 ux = ldv(mac + (1 * MRING + ms) * MW + mi);
-            const V2 uy = ldv(mac + (2 * MRING + ms) * MW + mi);
-            const V2 T = ldv(mac + (3 * MRING + ms) * MW + mi);
-            const bool ig0 = ign[ms * BW + 2 * tid], ig1 = ign[ms * BW + 2 * tid + 1];
-
-            // moments, equilibrium, non-equilibrium parts
-            V2 m[16], q[16], D[TNE_K];
-            forward_moments(K, f, m);
-            feq_moments(V2(K.DI), rho, ux, uy, T, q);
+    for (int o = 0; o < 2; o++) { // axis orbits 0, 2
+        const int i0 = 8 * o;
+        const float cxs = K.c[2 * o] * K.inv_dx, cys = K.c[2 * o] * K.inv_dy;
+        V2 f0;
+        f0 = F0(i0 + 0);
+        put(i0 + 0, f0, cxs * PX(i0 + 0));
+        f0 = F0(i0 + 1);
+        put(i0 + 1, f0, cys * PY(i0 + 1, f0));
+        f0 = F0(i0 + 2);
+        put(i0 + 2, f0, -cxs * NX(i0 + 2));
+        f0 = F0(i0 + 3);
+        put(i0 + 3, f0, -cys * NY(i0 + 3, f0));
+    }
 #pragma unroll
-            for (int k = 0; k < TNE_K; k++) D[k] = m[k + 4] - q[k + 4];
-
-            // grad u: x from the macro row (halo columns included), y from rows y+-1
-            const float* uxr = mac + (1 * MRING + ms) * MW;
-            const float* uyr = mac + (2 * MRING + ms) * MW;
-            const float2 uxl = *reinterpret_cast<const float2*>(uxr + mi - 2);
-            const float2 uxh = *reinterpret_cast<const float2*>(uxr + mi + 2);
-            const float2 uyl = *reinterpret_cast<const float2*>(uyr + mi - 2);
-            const float2 uyh = *reinterpret_cast<const float2*>(uyr + mi + 2);
-            const V2 dux_dx = (V2(ux.y(), uxh.x) - V2(uxl.y, ux.x())) * K.half_inv_dx;
-            const V2 duy_dx = (V2(uy.y(), uyh.x) - V2(uyl.y, uy.x())) * K.half_inv_dx;
-            const V2 dux_dy = (ldv(mac + (1 * MRING + msp) * MW + mi) -
-                               ldv(mac + (1 * MRING + msm) * MW + mi)) * K.half_inv_dy;
-            const V2 duy_dy = (ldv(mac + (2 * MRING + msp) * MW + mi) -
-                               ldv(mac + (2 * MRING + msm) * MW + mi)) * K.half_inv_dy;
-            const V2 theta = (dux_dx + duy_dy) * K.inv_DI;
-            const V2 shear = duy_dx + dux_dy;
-            const V2 rT = rho * T;
-            const V2 A8 = (rT * K.A8c) * fma(V2(4.f) * ux, dux_dx - theta, V2(2.f) * uy * shear);
-            const V2 A9 = (rT * K.A9c) * fma(V2(4.f) * uy, duy_dy - theta, V2(2.f) * ux * shear);
-
-            // reaction over dt (Eq. (28)), decided by the recovered T
-            // (evaluated for both cells and selected: no divergent branch)
-            const float ri0 = reaction_increment(lam0.x(), K.omega1 * rT.x(), K.omega2 * rT.x(), dt);
-            const float ri1 = reaction_increment(lam0.y(), K.omega1 * rT.y(), K.omega2 * rT.y(), dt);
-            const float dl0 = ig0 ? ri0 : 0.f, dl1 = ig1 ? ri1 : 0.f;
-            const V2 dlam(dl0, dl1);
-            const V2 cr = dlam * K.chem;
-
-            // collision in moment space and back
-            V2 dq[16], Om[16], W[16];
-            dfeq_dT(V2(K.DI), rho, ux, uy, T, dq);
-            Om[0] = Om[1] = Om[2] = V2(0.f);
-            Om[3] = dq[3] * cr;
-#pragma unroll
-            for (int k = 4; k < 16; k++) Om[k] = fma(V2(-K.S[k]), D[k - 4], dq[k] * cr);
-            Om[7] += A8;
-            Om[8] += A9;
-            inverse_moments(K, Om, W);
-
-            // lambda: u . grad(lambda) with NND interface values
-            const Q6 lq = load6(lm, lx);
-            const float* lm_m2 = class_row<C_LAM>(ring, y - 2);
-            const float* lm_m1 = class_row<C_LAM>(ring, y - 1);
-            const float* lm_p1 = class_row<C_LAM>(ring, y + 1);
-            const float* lm_p2 = class_row<C_LAM>(ring, y + 2);
-            const V2 lpx = nnd_pos_x(lq), lnx = nnd_neg_x(lq);
-            const V2 lpy = nnd_pos_y(ldv(lm_m2 + lx), ldv(lm_m1 + lx), lam0, ldv(lm_p1 + lx));
-            const V2 lny = nnd_neg_y(ldv(lm_m1 + lx), lam0, ldv(lm_p1 + lx), ldv(lm_p2 + lx));
-            const V2 lax(ux.x() > 0.f ? lpx.x() : lnx.x(), ux.y() > 0.f ? lpx.y() : lnx.y());
-            const V2 lay(uy.x() > 0.f ? lpy.x() : lny.x(), uy.y() > 0.f ? lpy.y() : lny.y());
-            const V2 ladv = fma(ux * K.inv_dx, lax, uy * K.inv_dy * lay);
-            V2 ln = fma(V2(-dt), ladv, lam0) + dlam;
-            ln = vmin(vmax(ln, V2(0.f)), V2(1.f));
-
-            // NND flux differences (upwind side fixed per velocity), Euler update, store
-            const int64_t g = (int64_t)y * K.pitch + cx;
-            auto put = [&](int i, V2 adv) {
-                V2 v = fma(V2(dt), W[i] - adv, f[i]);
-                if (act1) {
-                    float2* q = reinterpret_cast<float2*>(out + i * K.plane + g);
-                    if constexpr (AVG)
-                        v = fma(V2(wp), V2(*reinterpret_cast<const float2*>(pv + i * K.plane + g)),
-                                V2(wn) * v);
-                    *q = v.v;
-                } else if (act0) {
-                    float* q = out + i * K.plane + g;
-                    *q = AVG ? fmaf(wp, pv[i * K.plane + g], wn * v.x()) : v.x();
-                }
-            };
-#define PX(i) nnd_pos_x(load6(plane_row(ring, (i), y), lx))
-#define NX(i) nnd_neg_x(load6(plane_row(ring, (i), y), lx))
-#define PY(i) nnd_pos_y(ldv(up_m2 + pindex(i) * RW + lx), ldv(up_m1 + pindex(i) * RW + lx), f[i], \
-                        ldv(up_p1 + pindex(i) * RW + lx))
-#define NY(i) nnd_neg_y(ldv(dn_m1 + pindex(i) * RW + lx), f[i], ldv(dn_p1 + pindex(i) * RW + lx), \
-                        ldv(dn_p2 + pindex(i) * RW + lx))
-#pragma unroll
-            for (int o = 0; o < 2; o++) { // axis orbits 0, 2
-                const int i0 = 8 * o;
-                const float cxs = K.c[2 * o] * K.inv_dx, cys = K.c[2 * o] * K.inv_dy;
-                put(i0 + 0, cxs * PX(i0 + 0));
-                put(i0 + 1, cys * PY(i0 + 1));
-                put(i0 + 2, -cxs * NX(i0 + 2));
-                put(i0 + 3, -cys * NY(i0 + 3));
-            }
-#pragma unroll
-            for (int o = 0; o < 2; o++) { // diagonal orbits 1, 3
-                const int i0 = 4 + 8 * o;
-                const float cxs = K.c[2 * o + 1] * K.inv_dx, cys = K.c[2 * o + 1] * K.inv_dy;
-                put(i0 + 0, fma(cxs, PX(i0 + 0), cys * PY(i0 + 0)));
-                put(i0 + 1, fma(cys, PY(i0 + 1), -cxs * NX(i0 + 1)));
-                put(i0 + 2, -(fma(cxs, NX(i0 + 2), cys * NY(i0 + 2))));
-                put(i0 + 3, fma(cxs, PX(i0 + 3), -cys * NY(i0 + 3)));
-            }
+    for (int o = 0; o < 2; o++) { // diagonal orbits 1, 3
+        const int i0 = 4 + 8 * o;
+        const float cxs = K.c[2 * o + 1] * K.inv_dx, cys = K.c[2 * o + 1] * K.inv_dy;
+        V2 f0;
+        f0 = F0(i0 + 0);
+        put(i0 + 0, f0, fma(cxs, PX(i0 + 0), cys * PY(i0 + 0, f0)));
+        f0 = F0(i0 + 1);
+        put(i0 + 1, f0, fma(cys, PY(i0 + 1, f0), -cxs * NX(i0 + 1)));
+        f0 = F0(i0 + 2);
+        put(i0 + 2, f0, -(fma(cxs, NX(i0 + 2), cys * NY(i0 + 2, f0))));
+        f0 = F0(i0 + 3);
+        put(i0 + 3, f0, fma(cxs, PX(i0 + 3), -cys * NY(i0 + 3, f0)));
+    }
+#undef ROW
+#undef F0
 #undef PX
 #undef NX
 #undef PY
 #undef NY
-            if (act1) {
-                float2* q = reinterpret_cast<float2*>(out + 16 * K.plane + g);
-                if constexpr (AVG)
-                    ln = fma(V2(wp), V2(*reinterpret_cast<const float2*>(pv + 16 * K.plane + g)),
-                             V2(wn) * ln);
-                *q = ln.v;
-            } else if (act0) {
-                float* q = out + 16 * K.plane + g;
-                *q = AVG ? fmaf(wp, pv[16 * K.plane + g], wn * ln.x()) : ln.x();
-            }
+}
 
-            // TNE statistics of the state being stepped (Eqs. (90)-(91)); sums of Delta_k
-            // and d^2 accumulate as packed pairs, folded at the end of the strip
-            if (do_tne) {
-                if (act1) {
-                    V2 d2(0.f);
+// ---------------- the kernel -----------------------------------------------------
+template <int REC, bool GEN, bool AVG>
+__global__ void __launch_bounds__(MT, 3)
+    march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* smem_f = reinterpret_cast<float*>(smem);
+    float* ring = smem_f;
+    double* tsum = reinterpret_cast<double*>(smem + OFF_TSUM);
+    float* tmm = reinterpret_cast<float*>(smem + OFF_TMM);
+    const uint32_t mbar0 = smem_addr(smem + OFF_MBAR);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wpair = warp >> 1, t = tid & 63, lx = XO + 2 * t;
+    const int nx = K.nx, ny = K.ny;
+    const float* __restrict__ in = static_cast<const float*>(a.in);
+
+    const DfConst C = df_constants(K);
+    const int64_t step = a.ctr->step;
+    // AVG stages reduce no TNE
+    const bool do_tne = !AVG && a.tne_every > 0 && (step % a.tne_every) == 0;
+    if (tid < NSUM) tsum[tid] = 0.0;
+    if (tid < NMB) mbar_init(mbar0 + 8 * tid, 1 + 64);
+    fence_async_shared();
+    __syncthreads();
+
+    float tmin[TNE_K], tmax[TNE_K];
 #pragma unroll
-                    for (int k = 0; k < TNE_K; k++) {
-                        const V2 Dk = D[k];
-                        d2 = fma(Dk, Dk, d2);
-                        tsp[k] += Dk;
-                        tsm[TNE_K + k] += fabsf(Dk.x()) + fabsf(Dk.y());
-                        tmin[k] = fminf(tmin[k], fminf(Dk.x(), Dk.y()));
-                        tmax[k] = fmaxf(tmax[k], fmaxf(Dk.x(), Dk.y()));
-                    }
-                    tsm[2 * TNE_K] += sqrt_approx(d2.x()) + sqrt_approx(d2.y());
-                    td2 += d2;
-                } else if (act0) {
-                    float d2 = 0.f;
+    for (int k = 0; k < TNE_K; k++) tmin[k] = FLT_MAX, tmax[k] = -FLT_MAX;
+    int bad = 0;
+    bool timeout = false;
+
+    const int nsx = (nx + BW - 1) / BW, nsy = (ny + strip_rows - 1) / strip_rows;
+    const int nstrips = nsx * nsy;
+    uint32_t q_issued = 0, q_waited = 0; // row pairs of this block, in order
+    auto mb_of = [&](uint32_t q) { return mbar0 + 8 * (q % NMB); };
+    auto wait_pair = [&](uint32_t q) {
+        if (mbar_wait(mb_of(q), (q / NMB) & 1u))
+            q_waited = q + 1;
+        else
+            timeout = true;
+    };
+
+    for (int s = blockIdx.x; s < nstrips; s += gridDim.x) {
+        const int x0 = (s / nsy) * BW, y0 = (s % nsy) * strip_rows;
+        const int yend = y0 + strip_rows < ny ? y0 + strip_rows : ny;
+        const int cx = x0 + 2 * t;
+        const bool act0 = cx < nx, act1 = cx + 1 < nx;
+        const int npairs = (yend - y0 + 5) / 2; // rows y0-2 .. yend+1
+        const uint32_t q0 = q_issued;
+        TneAcc acc;
 #pragma unroll
-                    for (int k = 0; k < TNE_K; k++) {
-                        const float Dk = D[k].x();
-                        d2 = fmaf(Dk, Dk, d2);
-                        tsp[k] += V2(Dk, 0.f);
-                        tsm[TNE_K + k] += fabsf(Dk);
-                        tmin[k] = fminf(tmin[k], Dk);
-                        tmax[k] = fmaxf(tmax[k], Dk);
-                    }
-                    tsm[2 * TNE_K] += sqrt_approx(d2);
-                    td2 += V2(d2, 0.f);
+        for (int k = 0; k < TNE_K; k++) acc.sum[k] = acc.abs[k] = 0.f;
+        acc.dsum = acc.d2sum = 0.f;
+
+        __syncthreads(); // the previous strip is done with the ring
+        // rows y0-2 .. y0+3 now; rows y0+4, y0+5 share ring slots with rows y0-2, y0-1
+        // (the v_y = 0 and v_y < 0 classes keep fewer rows), so they follow once the
+        // macros of row y0-1 have been recovered
+        for (int j = 0; j < npairs && j < NMB - 1; j++)
+            issue_pair<GEN>(in, ring, mb_of(q0 + j), y0 - 2 + 2 * j, yend + 1, x0, K);
+        q_issued = q0 + (npairs < NMB - 1 ? npairs : NMB - 1);
+        wait_pair(q0);
+        wait_pair(q0 + 1);
+        // walls: ghost rows among rows y0-2 .. y0+1 (warp pair 0: y0-1, y0+1; 1: y0-2, y0)
+        if constexpr (GEN) {
+            wall_fix<GEN>(ring, wpair ? y0 - 2 : y0 - 1, K, lx);
+            wall_fix<GEN>(ring, wpair ? y0 : y0 + 1, K, lx);
+        }
+        __syncthreads();
+        // rho, u, T of rows y0 (pair 0) and y0+1 (pair 1), u, v of row y0-1 (pair 0)
+        Mac cur = recover_row<REC>(smem_f, ring, y0 + wpair, t, K, C, bad, act0, act1);
+        if (wpair == 0) (void)recover_row<REC>(smem_f, ring, y0 - 1, t, K, C, bad, act0, act1);
+        if (__syncthreads_or(timeout)) break;
+        if (npairs > NMB - 1) {
+            issue_pair<GEN>(in, ring, mb_of(q0 + NMB - 1), y0 + 4, yend + 1, x0, K);
+            q_issued = q0 + NMB;
+        }
+
+        bool stop = false;
+        for (int k = 0;; k++) {
+            const int y = y0 + 2 * k;
+            if (y >= yend) break;
+            if (y + 2 <= yend + 1) wait_pair(q0 + k + 2);
+            const int rr = y + 2 + wpair; // the row this pair recovers
+            if constexpr (GEN)
+                if (rr <= yend + 1) wall_fix<GEN>(ring, rr, K, lx);
+            Mac nxt = cur;
+            if (rr <= yend) nxt = recover_row<REC>(smem_f, ring, rr, t, K, C, bad, act0, act1);
+            if (__syncthreads_or(timeout)) {
+                stop = true;
+                break;
+            }
+            if (y + wpair < yend)
+                update_row<REC, AVG>(smem_f, ring, y + wpair, x0, t, K, a, cur, act0, act1, do_tne, acc,
+                                     tmin, tmax);
+            cur = nxt;
+            __syncthreads();
+            if (k + 4 < npairs) {
+                issue_pair<GEN>(in, ring, mb_of(q0 + k + 4), y + 6, yend + 1, x0, K);
+                q_issued = q0 + k + 5;
+            }
+        }
+        if (stop) break;
+        // the strip's TNE sums: per-thread FP32 partials (32 cells), added in FP64 in a
+        // fixed order: four threads per quantity, 32 partials each, then a shuffle
+        if (do_tne) {
+            __syncthreads(); // every copy has been waited for: the ring is idle
+            float* part = ring;
+#pragma unroll
+            for (int k = 0; k < TNE_K; k++) {
+                part[k * MT + tid] = acc.sum[k];
+                part[(TNE_K + k) * MT + tid] = acc.abs[k];
+            }
+            part[2 * TNE_K * MT + tid] = acc.dsum;
+            part[(2 * TNE_K + 1) * MT + tid] = acc.d2sum;
+            __syncthreads();
+            double s2 = 0.0;
+            if (tid < 4 * NSUM) {
+                const float* src = part + (tid >> 2) * MT + (tid & 3) * 32;
+                double e0 = 0.0, e1 = 0.0;
+#pragma unroll 4
+                for (int j = 0; j < 32; j += 2) {
+                    e0 += f2d_fast(src[j]);
+                    e1 += f2d_fast(src[j + 1]);
                 }
+                s2 = e0 + e1;
             }
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+            if (tid < 4 * NSUM && (tid & 3) == 0) tsum[tid >> 2] += s2;
         }
-        cp_wait<0>();
-        if (do_tne) { // per strip: warp sums in FP32, then FP64 per warp
-#pragma unroll
-            for (int k = 0; k < TNE_K; k++) tsm[k] = tsp[k].x() + tsp[k].y();
-            tsm[2 * TNE_K + 1] = td2.x() + td2.y();
-#pragma unroll
-            for (int q = 0; q < NSUM; q++) {
-                const float v = warp_sum(tsm[q]);
-                if (lane == 0) tsum[warp * NSUM + q] += (double)v;
-            }
-        }
+        q_issued = q0 + npairs;
+    }
+    if (__syncthreads_or(timeout)) {
+        // a copy did not land in time: wait (bounded) for every copy still in flight,
+        // so none lands after the block has left, and report
+        for (uint32_t q = q_waited; q < q_issued; q++) (void)mbar_wait(mb_of(q), (q / NMB) & 1u);
+        if (tid == 0) atomicOr(&a.ctr->status, 2);
     }
 
-    // end of step: status, TNE partials, arrival count; the last block finishes
+    // end of step: status, TNE partials, arrival count
     if (__syncthreads_or(bad) && tid == 0) atomicOr(&a.ctr->status, 1);
     if (do_tne) {
 #pragma unroll
@@ -573,11 +702,8 @@ __global__ void __launch_bounds__(MT, 4)
         __syncthreads();
         double* part = a.partials + blockIdx.x; // quantity-major, stride gridDim.x
         const size_t ps = gridDim.x;
-        for (int q = tid; q < NSUM; q += MT) {
-            double sacc = 0.0;
-            for (int w = 0; w < NWM; w++) sacc += tsum[w * NSUM + q];
-            part[ps * (q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K))] = sacc;
-        }
+        for (int q = tid; q < NSUM; q += MT)
+            part[ps * (q < 2 * TNE_K ? q : 4 * TNE_K + (q - 2 * TNE_K))] = tsum[q];
         for (int q = tid; q < NMM; q += MT) {
             float v = tmm[q];
             for (int w = 1; w < NWM; w++)
@@ -633,15 +759,6 @@ int resident_min()
     return a < 0 || b < 0 ? -1 : (a < b ? a : b);
 }
 
-} // namespace
-
-// Blocks resident on the whole GPU, and the strip height: the number of strips
-// per column of the grid is chosen so that the strips fill whole waves of the
-// resident blocks while each strip stays long compared with its 3-row
-// prologue (rows staged and macros recovered before the first update).
-// mode = recovery | (general boundaries << 1): the general variant carries walls,
-// Dirichlet and specular sides; the plain one only index maps.
-namespace {
 int resident_blocks(int mode)
 {
     static int sms = -1;
@@ -656,15 +773,31 @@ int resident_blocks(int mode)
                        : m == 2 ? resident_min<0, true>() : resident_min<1, true>();
     return per_sm < 0 ? -1 : per_sm * sms;
 }
+
+template <int REC, bool GEN>
+void launch_variant(bool avg, const ModelConst<float>& K, const StepLaunch& a, int rows,
+                    cudaStream_t s)
+{
+    if (avg)
+        march_kernel<REC, GEN, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+    else
+        march_kernel<REC, GEN, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+}
+
 } // namespace
 
+// Blocks resident on the whole GPU, and the strip height: the number of strips per
+// column of the grid is chosen so that the strips fill whole waves of the resident
+// blocks while each strip stays long compared with its prologue (four rows staged and
+// three recovered before the first update).
+// mode = recovery | (general boundaries << 1): the general variant carries walls,
+// Dirichlet and specular sides; the plain one only index maps.
 void march_plan(int mode, int nx, int ny, int* grid, int* strip_rows)
 {
     const int G = resident_blocks(mode);
     const int nsx = (nx + BW - 1) / BW;
-    // 32-row strips measured best at 4096^2 (16: -12 %, 64: -11 %, one wave of
-    // 293-row strips: -36 %); smaller grids use shorter strips so that every
-    // resident block gets work
+    // 32-row strips; smaller grids use shorter strips so that every resident block
+    // gets work
     int rows = 32;
     while (rows > 8 && (long)nsx * ((ny + rows - 1) / rows) < G) rows /= 2;
     if (rows > ny) rows = ny;
@@ -683,18 +816,6 @@ int march_grid(int mode, int nx, int ny)
     march_plan(mode, nx, ny, &g, &r);
     return g;
 }
-
-namespace {
-template <int REC, bool GEN>
-void launch_variant(bool avg, const ModelConst<float>& K, const StepLaunch& a, int rows,
-                    cudaStream_t s)
-{
-    if (avg)
-        march_kernel<REC, GEN, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
-    else
-        march_kernel<REC, GEN, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
-}
-} // namespace
 
 cudaError_t launch_march(int mode, const ModelConst<float>& K, const StepLaunch& a, cudaStream_t s)
 {

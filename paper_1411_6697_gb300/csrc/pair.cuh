@@ -186,6 +186,68 @@ __device__ __forceinline__ void recover_pair(const V2* f, const DfConst& C,
     }
 }
 
+// Branch-free forms of the two conversions for the states a step produces (normal
+// binary32 values, zeros): binary32 -> binary64 exactly by moving the IEEE-754 fields,
+// zeros and subnormal inputs to a signed zero; binary64 -> binary32 rounded to nearest
+// even, results below the normal binary32 range to a signed zero. Infinite and NaN
+// inputs are not converted faithfully: the recovery flags such cells from their FP32
+// sums before it converts anything.
+__device__ __forceinline__ double f2d_fast(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned hi = (b & 0x80000000u) | (e ? (((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)) : 0u);
+    const unsigned lo = e ? (b << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float d2f_fast(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    // the 29 dropped bits: above half rounds up, exactly half rounds to even
+    const unsigned up = ((lo & 0x1fffffffu) + (m & 1u)) > 0x10000000u ? 1u : 0u;
+    const unsigned r = (hi & 0x80000000u) | (((unsigned)e << 23) + m + up);
+    return __uint_as_float(e >= 1 ? r : (hi & 0x80000000u));
+}
+__device__ __forceinline__ double df_to_f64_fast(float hi, float lo) { return f2d_fast(hi) + f2d_fast(lo); }
+
+// recover_pair with the branch-free conversions; cells whose conserved sums are not
+// finite in FP32 are flagged before anything is converted.
+template <int REC>
+__device__ __forceinline__ void recover_pair_fast(const V2* f, const DfConst& C,
+                                                  const ModelConst<float>& K, V2& rho, V2& ux,
+                                                  V2& uy, V2& T, bool& ig0, bool& ig1, bool& ok0,
+                                                  bool& ok1)
+{
+    if constexpr (REC == 1) {
+        recover_pair_df(f, C, rho, ux, uy, T, ig0, ig1, ok0, ok1);
+    } else {
+        D2 m1, m2, m3, m4;
+        conserved_pair(f, C, m1, m2, m3, m4);
+        double u0, v0, t0, u1, v1, t1;
+        const double r0 = df_to_f64_fast(m1.hi.x(), m1.lo.x());
+        const double r1 = df_to_f64_fast(m1.hi.y(), m1.lo.y());
+        recover_one_f64(m1.hi.x(), r0, df_to_f64_fast(m2.hi.x(), m2.lo.x()),
+                        df_to_f64_fast(m3.hi.x(), m3.lo.x()), df_to_f64_fast(m4.hi.x(), m4.lo.x()),
+                        K.inv_DId, u0, v0, t0);
+        recover_one_f64(m1.hi.y(), r1, df_to_f64_fast(m2.hi.y(), m2.lo.y()),
+                        df_to_f64_fast(m3.hi.y(), m3.lo.y()), df_to_f64_fast(m4.hi.y(), m4.lo.y()),
+                        K.inv_DId, u1, v1, t1);
+        rho = m1.hi; // the exact sum rounded to FP32
+        ux = V2(d2f_fast(u0), d2f_fast(u1));
+        uy = V2(d2f_fast(v0), d2f_fast(v1));
+        T = V2(d2f_fast(t0), d2f_fast(t1));
+        const long long tig = dbits(K.T_igd), dmax = dbits(DBL_MAX);
+        ig0 = dbits(t0) > tig;
+        ig1 = dbits(t1) > tig;
+        const bool f0 = fabsf(m1.hi.x()) <= FLT_MAX && fabsf(m4.hi.x()) <= FLT_MAX;
+        const bool f1 = fabsf(m1.hi.y()) <= FLT_MAX && fabsf(m4.hi.y()) <= FLT_MAX;
+        ok0 = f0 && dbits(r0) > 0 && dbits(t0) > 0 && dbits(t0) <= dmax;
+        ok1 = f1 && dbits(r1) > 0 && dbits(t1) > 0 && dbits(t1) <= dmax;
+    }
+}
+
 // Split constants of the conserved-moment recovery (split on the host, so they stay
 // constant-bank operands instead of registers).
 __device__ __forceinline__ DfConst df_constants(const ModelConst<float>& K)
@@ -231,31 +293,65 @@ __device__ __forceinline__ Q6 load6(const float* row, int lx)
     const float2 Cc = *reinterpret_cast<const float2*>(row + lx + 2);
     return {A.x, A.y, B.x, B.y, Cc.x, Cc.y};
 }
+// |minmod(a, b)|: min(|a|, |b|) carrying sign(a) xor sign(b), then clamped at 0 (so 0
+// unless a and b share a sign). Every nonzero minmod in an NND difference around the
+// slope d has the sign of d, so mm(d, d') - mm(d'', d) = sign(d) (|mm(d, d')| -
+// |mm(d'', d)|): the same value, rounded the same way.
+__device__ __forceinline__ float mmag(float a, float b)
+{
+    float r;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return fmaxf(r, 0.0f);
+}
+// x with its sign flipped where s is negative
+__device__ __forceinline__ float sgnmul(float x, float s)
+{
+    return __uint_as_float(__float_as_uint(x) ^ (__float_as_uint(s) & 0x80000000u));
+}
+__device__ __forceinline__ V2 sgnmul(V2 x, V2 s) { return V2(sgnmul(x.x(), s.x()), sgnmul(x.y(), s.y())); }
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 // upwind side v > 0: (d1 + (mm(d1,d2) - mm(d0,d1))/2) for both cells
 __device__ __forceinline__ V2 nnd_pos_x(const Q6& q)
 {
     const float d0 = q.b - q.a, d1 = q.c - q.b, d2 = q.d - q.c, d3 = q.e - q.d;
-    const float m01 = mm1(d0, d1), m12 = mm1(d1, d2), m23 = mm1(d2, d3);
-    return fma(V2(0.5f), V2(m12, m23) - V2(m01, m12), V2(d1, d2));
+    const float r01 = mmag(d0, d1), r12 = mmag(d1, d2), r23 = mmag(d2, d3);
+    const V2 s(d1, d2);
+    return fma(V2(0.5f), sgnmul(V2(r12, r23) - V2(r01, r12), s), s);
 }
 // upwind side v < 0: (d2 - (mm(d2,d3) - mm(d1,d2))/2) for both cells
 __device__ __forceinline__ V2 nnd_neg_x(const Q6& q)
 {
     const float d1 = q.c - q.b, d2 = q.d - q.c, d3 = q.e - q.d, d4 = q.g - q.e;
-    const float m12 = mm1(d1, d2), m23 = mm1(d2, d3), m34 = mm1(d3, d4);
-    return fma(V2(-0.5f), V2(m23, m34) - V2(m12, m23), V2(d2, d3));
+    const float r12 = mmag(d1, d2), r23 = mmag(d2, d3), r34 = mmag(d3, d4);
+    const V2 s(d2, d3);
+    return fma(V2(-0.5f), sgnmul(V2(r23, r34) - V2(r12, r23), s), s);
 }
 __device__ __forceinline__ V2 ldv(const float* p) { return V2(*reinterpret_cast<const float2*>(p)); }
 // along y from rows y-2..y+1 (v > 0) or y-1..y+2 (v < 0), packed over the pair
 __device__ __forceinline__ V2 nnd_pos_y(V2 qm2, V2 qm1, V2 q0, V2 qp1)
 {
     const V2 d0 = qm1 - qm2, d1 = q0 - qm1, d2 = qp1 - q0;
-    return fma(V2(0.5f), mm2(d1, d2) - mm2(d0, d1), d1);
+    const V2 r12(mmag(d1.x(), d2.x()), mmag(d1.y(), d2.y()));
+    const V2 r01(mmag(d0.x(), d1.x()), mmag(d0.y(), d1.y()));
+    return fma(V2(0.5f), sgnmul(r12 - r01, d1), d1);
 }
 __device__ __forceinline__ V2 nnd_neg_y(V2 qm1, V2 q0, V2 qp1, V2 qp2)
 {
     const V2 d1 = q0 - qm1, d2 = qp1 - q0, d3 = qp2 - qp1;
-    return fma(V2(-0.5f), mm2(d2, d3) - mm2(d1, d2), d2);
+    const V2 r23(mmag(d2.x(), d3.x()), mmag(d2.y(), d3.y()));
+    const V2 r12(mmag(d1.x(), d2.x()), mmag(d1.y(), d2.y()));
+    return fma(V2(-0.5f), sgnmul(r23 - r12, d2), d2);
 }
 
 } // namespace lbk

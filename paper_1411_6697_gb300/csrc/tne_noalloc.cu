@@ -10,8 +10,12 @@
 // loads the library holds these arrays (about 0.8 MB) until the process exits.
 #include <cuda_runtime.h>
 #include <float.h>
+#include <limits.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
+
+#include <atomic>
 
 #include "lbkm.h"
 #include "cell.cuh"
@@ -33,9 +37,12 @@ constexpr int NA_SUMS = 2 * TNE_K + 2;
 static __device__ __align__(256) double g_na_partials[NA_MAX_BLOCKS * TNE_PART];
 static __device__ __align__(256) unsigned int g_na_arrivals;
 
+// Device addresses of the two arrays, per device ordinal, as the last lookup on that
+// device found them. Calls outside stream capture look them up again (a device reset
+// or a new primary context moves them); calls during capture use the stored value.
 constexpr int NA_MAX_DEVICES = 64;
-double* g_partials_addr[NA_MAX_DEVICES];
-unsigned int* g_arrivals_addr[NA_MAX_DEVICES];
+std::atomic<uintptr_t> g_partials_addr[NA_MAX_DEVICES];
+std::atomic<uintptr_t> g_arrivals_addr[NA_MAX_DEVICES];
 
 __device__ __forceinline__ double na_warp_sum(double v)
 {
@@ -174,6 +181,7 @@ extern "C" lbkm_status lbkm_tne_noalloc(const lbkm_params* p, const void* state,
     if (!p || !state || !out) return na_fail(LBKM_EINVAL, "params, state and out are required");
     if (p->nx < 1 || p->ny < 1) return na_fail(LBKM_EINVAL, "nx and ny must be >= 1");
     if (pitch < p->nx) return na_fail(LBKM_EINVAL, "pitch must be >= nx");
+    if (pitch > INT_MAX) return na_fail(LBKM_EINVAL, "pitch must be <= 2147483647 elements");
     if (p->precision != LBKM_F64 && p->precision != LBKM_F32)
         return na_fail(LBKM_EINVAL, "precision must be LBKM_F64 or LBKM_F32");
     if (!(p->gamma > 1.0 && p->gamma <= 2.0))
@@ -196,36 +204,43 @@ extern "C" lbkm_status lbkm_tne_noalloc(const lbkm_params* p, const void* state,
     fill_model_const<double>(hm, p->S, p->Q, p->omega1, p->omega2, p->T_ig, p->dx, p->dy, p->dt,
                              p->nx, p->ny, (int)pitch, p->bc_x, p->bc_y, &K);
 
-    // set-up once per device, with that device current: device addresses of the
-    // file-scope scratch (the names are host-side stand-ins in host code)
+    // device addresses of the file-scope scratch (the names are host-side stand-ins in
+    // host code), looked up with the calling device current
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(LBKM_ECUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= NA_MAX_DEVICES) return na_fail(LBKM_EINVAL, "device ordinal too large");
-    if (!g_partials_addr[dev] || !g_arrivals_addr[dev]) {
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return na_fail(LBKM_ECUDA, cudaGetErrorString(e));
+    if (cap == cudaStreamCaptureStatusNone) {
         void* a = nullptr;
         void* b = nullptr;
         e = cudaGetSymbolAddress(&a, g_na_partials);
         if (e != cudaSuccess) return na_fail(LBKM_ECUDA, cudaGetErrorString(e));
         e = cudaGetSymbolAddress(&b, g_na_arrivals);
         if (e != cudaSuccess) return na_fail(LBKM_ECUDA, cudaGetErrorString(e));
-        g_partials_addr[dev] = static_cast<double*>(a);
-        g_arrivals_addr[dev] = static_cast<unsigned int*>(b);
+        g_partials_addr[dev].store(reinterpret_cast<uintptr_t>(a), std::memory_order_release);
+        g_arrivals_addr[dev].store(reinterpret_cast<uintptr_t>(b), std::memory_order_release);
     }
-    cudaStream_t s = (cudaStream_t)cuda_stream;
+    double* partials = reinterpret_cast<double*>(g_partials_addr[dev].load(std::memory_order_acquire));
+    unsigned int* arrivals =
+        reinterpret_cast<unsigned int*>(g_arrivals_addr[dev].load(std::memory_order_acquire));
+    if (!partials || !arrivals)
+        return na_fail(LBKM_ESTATE, "lbkm_tne_noalloc: the first call on a device must come "
+                                    "before any stream capture");
     // the arrival counter must start at zero whatever an earlier call left behind
-    e = cudaMemsetAsync(g_arrivals_addr[dev], 0, sizeof(unsigned int), s);
+    e = cudaMemsetAsync(arrivals, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return na_fail(LBKM_ECUDA, cudaGetErrorString(e));
     TneRecord* o = reinterpret_cast<TneRecord*>(out);
     const double area = p->dx * p->dy;
     if (p->precision == LBKM_F64)
         tne_noalloc_kernel<double><<<(unsigned)blocks, NA_THREADS, 0, s>>>(
-            K, static_cast<const double*>(state), pitch, delta, g_partials_addr[dev],
-            g_arrivals_addr[dev], o, area);
+            K, static_cast<const double*>(state), pitch, delta, partials, arrivals, o, area);
     else
         tne_noalloc_kernel<float><<<(unsigned)blocks, NA_THREADS, 0, s>>>(
-            K, static_cast<const float*>(state), pitch, delta, g_partials_addr[dev],
-            g_arrivals_addr[dev], o, area);
+            K, static_cast<const float*>(state), pitch, delta, partials, arrivals, o, area);
     e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(LBKM_ECUDA, cudaGetErrorString(e));
     return LBKM_OK;
