@@ -1,30 +1,31 @@
 // march.cu -- the FP32 2-D step kernel: y-marching strips, two rows per iteration,
-// two cells per thread, rows staged by bulk asynchronous copies.
+// two cells per thread, rows moved by bulk asynchronous copies in both directions.
 //
 // A block of 128 threads (4 warps) owns a strip of 128 columns x `strip_rows` rows
 // and marches up it two rows per iteration: warps 0-1 (warp pair 0) update row y,
 // warps 2-3 (warp pair 1) row y + 1. Thread t of a warp pair updates the cells
 // (x0 + 2t, y + r) and (x0 + 2t + 1, y + r) together, so most arithmetic runs as
-// packed FP32 pairs.
+// packed FP32 pairs. Two blocks share an SM.
 //
-// Shared memory keeps the staged rows of the 17 planes in rings sized per plane
-// class (the upwind side of the NND y-stencil is fixed by the sign of v_y): a plane
-// with v_y > 0 keeps rows y-2..y+5, v_y < 0 rows y-1..y+5, v_y = 0 rows y..y+5, lambda
-// y-2..y+5. Rows y+2, y+3 are recovered (rho, u, T) in the iteration, rows y+4, y+5
-// are in flight. Each staged plane row holds columns x0-4 .. x0+131 and is filled by
-// one bulk asynchronous copy (the TMA unit's non-tensor mode: both addresses and the
-// size multiples of 16 bytes), completing on an mbarrier per pair of rows; columns
-// that no such copy can reach (the wrapped or clamped halo at the grid's x-edges,
-// the tail of a row whose length is not a multiple of 4, ghost rows of Dirichlet or
-// specular sides) are filled by per-element asynchronous copies that arrive on the
-// same mbarrier, or by stores of the side's equilibrium.
+// Shared memory holds a ring of eight staged rows (row r in slot r & 7), each with
+// all 17 planes: rows y-2..y+3 are read in an iteration (stencils, and the recovery
+// of rows y+2, y+3), rows y+4, y+5 are in flight. Each staged plane row holds columns
+// x0-4 .. x0+131 and is filled by one bulk asynchronous copy (the TMA unit's
+// non-tensor mode: both addresses and the size multiples of 16 bytes) completing on
+// an mbarrier per pair of rows; columns no such copy can reach (the wrapped or clamped
+// halo at the grid's x-edges, the tail of a row whose length is not a multiple of 4,
+// ghost rows of Dirichlet or specular sides) are filled by per-element asynchronous
+// copies that arrive on the same mbarrier, or by stores of the side's equilibrium.
+// The updated rows are written into an output buffer in shared memory and leave by
+// bulk asynchronous stores (the few columns of a row tail past its last multiple of 4
+// by plain stores).
 //
 // Per iteration (rows y, y+1): wait for rows y+2, y+3; warp pair r recovers rho, u, T
 // of row y+2+r from its exact conserved sums (kept in registers: the same pair
-// updates that row in the next iteration; u, v also go to a shared ring of five rows
-// for the neighbours' gradients); one barrier; warp pair r updates row y+r; one
-// barrier; warp 0 and warps 2-3 issue the copies of rows y+6, y+7 into the slots of
-// rows y-2, y-1.
+// updates that row in the next iteration; u, v also go to a ring of eight rows for
+// the neighbours' gradients); one barrier; warp pair r updates row y+r into the
+// output buffer; one barrier; warp 0 and warps 2-3 issue the copies of rows y+6, y+7
+// into the slots of rows y-2, y-1, warp 1 the stores of rows y, y+1.
 // The conserved moments are summed exactly (double-float butterflies); rho, u, T are
 // then formed in FP64 (REC = 0) or in double-float on the FP32 pipes (REC = 1), and
 // the ignition test T > T_ig is taken in that precision. The TNE statistics of the
@@ -48,92 +49,30 @@ constexpr int NWM = MT / 32;     // warps per block
 constexpr int BW = 128;          // columns per strip
 constexpr int XO = 4;            // column x0 sits at element XO of a staged row
 constexpr int RW = BW + 2 * XO;  // staged row: columns x0-4 .. x0+BW+3 (544 bytes)
-constexpr int UVR = 5;           // rows of (u, v) kept: y-1 .. y+3
-
-enum { C_UP = 0, C_DN = 1, C_FLAT = 2, C_LAM = 3 };
-constexpr int NROWS[4] = {8, 7, 6, 8};  // y-2..y+5, y-1..y+5, y..y+5, y-2..y+5
-constexpr int NPL[4] = {6, 6, 4, 1};    // planes per class
-__host__ __device__ constexpr int pclass(int p)
-{
-    return p == 16 ? C_LAM
-                   : ((p & 3) == 0 || (p & 3) == 2) && ((p >> 2) & 1) == 0
-                         ? C_FLAT
-                         : (((p >> 2) & 1) == 0 ? ((p & 3) == 1 ? C_UP : C_DN)
-                                                 : ((p & 3) < 2 ? C_UP : C_DN));
-}
-// index of plane p within its class, planes in increasing order (o = orbit,
-// k = velocity within the orbit)
-__host__ __device__ constexpr int pindex(int p)
-{
-    const int o = p >> 2, k = p & 3;
-    return p == 16 ? 0
-                   : pclass(p) == C_FLAT ? (o >> 1) * 2 + (k >> 1)
-                                         : (o >> 1) * 3 + ((o & 1) ? (pclass(p) == C_UP ? 1 + k : k - 1) : 0);
-}
-__host__ __device__ constexpr bool class_layout_ok()
-{
-    int seen[4][8] = {};
-    for (int p = 0; p < NPLANE; p++) {
-        const int c = pclass(p), i = pindex(p);
-        if (i < 0 || i >= NPL[c] || seen[c][i]) return false;
-        seen[c][i] = 1;
-    }
-    return true;
-}
-static_assert(class_layout_ok(), "every plane has its own slot in its class");
-static_assert(pclass(1) == C_UP && pclass(3) == C_DN && pclass(0) == C_FLAT && pclass(2) == C_FLAT &&
-                  pclass(4) == C_UP && pclass(5) == C_UP && pclass(6) == C_DN && pclass(7) == C_DN &&
-                  pclass(8) == C_FLAT && pclass(9) == C_UP && pclass(11) == C_DN &&
-                  pclass(13) == C_UP && pclass(14) == C_DN && pindex(15) == 5 && pindex(10) == 3,
-              "plane classes follow the orbit layout axis, diagonal, axis, diagonal");
+constexpr int NSLOT = 8;         // staged rows kept: y-2 .. y+5
+constexpr int ROWF = NPLANE * RW; // floats of one staged row (17 planes)
 
 // shared-memory layout (floats from the 16-byte aligned start)
-constexpr int CB0 = 0;
-constexpr int CB1 = CB0 + NROWS[0] * NPL[0] * RW;
-constexpr int CB2 = CB1 + NROWS[1] * NPL[1] * RW;
-constexpr int CB3 = CB2 + NROWS[2] * NPL[2] * RW;
-constexpr int RING_FLOATS = CB3 + NROWS[3] * NPL[3] * RW;
-constexpr int UVB = RING_FLOATS;                 // (u, v) ring: [UVR][2][RW]
-constexpr int SMEM_FLOATS = UVB + UVR * 2 * RW;
-static_assert(RW % 4 == 0 && CB1 % 4 == 0 && CB2 % 4 == 0 && CB3 % 4 == 0 && UVB % 4 == 0,
-              "every staged row starts on a 16-byte boundary");
+constexpr int UVB = NSLOT * ROWF;                // (u, v) of rows: [NSLOT][2][RW]
+constexpr int OBUF = UVB + NSLOT * 2 * RW;       // updated rows: [2][NPLANE][BW]
+constexpr int SMEM_FLOATS = OBUF + 2 * NPLANE * BW;
+static_assert(RW % 4 == 0 && ROWF % 4 == 0 && UVB % 4 == 0 && OBUF % 4 == 0,
+              "every staged and output row starts on a 16-byte boundary");
 constexpr size_t OFF_TSUM = (size_t)SMEM_FLOATS * 4;            // double[NSUM]
 constexpr size_t OFF_TMM = OFF_TSUM + (size_t)NSUM * 8;           // float[NWM][NMM]
 constexpr size_t OFF_MBAR = (OFF_TMM + (size_t)NWM * NMM * 4 + 15) / 16 * 16;
 constexpr int NMB = 4;                                            // row pairs in flight or in use
 constexpr size_t MARCH_SMEM = OFF_MBAR + NMB * 8;
-static_assert(MARCH_SMEM <= 74 * 1024, "three blocks per SM need <= 74 KB each");
-static_assert(NSUM * MT <= RING_FLOATS && 4 * NSUM <= MT, "the strip's TNE partials fit in the idle ring, four threads per sum");
+static_assert(MARCH_SMEM <= 112 * 1024, "two blocks per SM need <= 112 KB each");
+static_assert(NSUM * MT <= UVB && 4 * NSUM <= MT,
+              "the strip's TNE partials fit in the idle ring, four threads per sum");
 
-// start of the staged row r of class c
-template <int CL>
-__device__ __forceinline__ float* class_row(float* ring, int r)
-{
-    constexpr int N = NROWS[CL], np = NPL[CL];
-    constexpr int base = CL == 0 ? CB0 : CL == 1 ? CB1 : CL == 2 ? CB2 : CB3;
-    return ring + base + ((r + 16 * N) % N) * np * RW;
-}
-// the staged row r of plane p (p a compile-time constant after unrolling)
-__device__ __forceinline__ float* plane_row(float* ring, int p, int r)
-{
-    const int c = pclass(p);
-    float* b = c == C_UP ? class_row<C_UP>(ring, r)
-                         : c == C_DN ? class_row<C_DN>(ring, r)
-                                     : c == C_FLAT ? class_row<C_FLAT>(ring, r) : class_row<C_LAM>(ring, r);
-    return b + pindex(p) * RW;
-}
-// the same for a plane index known only at run time
-__device__ __forceinline__ float* plane_row_rt(float* ring, int p, int r)
-{
-    float* b = ring;
-#pragma unroll
-    for (int q = 0; q < NPLANE; q++)
-        if (q == p) b = plane_row(ring, q, r);
-    return b;
-}
+// staged row r (all planes) and plane p of it
+__device__ __forceinline__ float* srow(float* ring, int r) { return ring + (r & (NSLOT - 1)) * ROWF; }
+__device__ __forceinline__ float* plane_row(float* ring, int p, int r) { return srow(ring, r) + p * RW; }
 __device__ __forceinline__ float* uv_row(float* smem_f, int r, int field)
 {
-    return smem_f + UVB + (((r + 16 * UVR) % UVR) * 2 + field) * RW;
+    return smem_f + UVB + ((r & (NSLOT - 1)) * 2 + field) * RW;
 }
 
 // ---------------- mbarriers and bulk copies -------------------------------------
@@ -244,7 +183,7 @@ __device__ __forceinline__ void issue_pair(const float* __restrict__ in, float* 
                 row_source<GEN>(K, r, p, gy, sp, dir);
                 if (r <= rmax && dir < 0 && ce > cs) {
                     src[u] = in + sp * K.plane + (int64_t)gy * K.pitch + cs;
-                    dst[u] = smem_addr(plane_row_rt(ring, p, r) + (cs - (x0 - XO)));
+                    dst[u] = smem_addr(plane_row(ring, p, r) + (cs - (x0 - XO)));
                     nb[u] = (uint32_t)(ce - cs) * 4u;
                     bytes += nb[u];
                 }
@@ -258,6 +197,15 @@ __device__ __forceinline__ void issue_pair(const float* __restrict__ in, float* 
         for (int u = 0; u < 2; u++)
             if (nb[u]) bulk_g2s(dst[u], src[u], nb[u], mb);
     } else if (warp >= 2) {
+        // nothing to fill when the bulk copies cover columns x0-2 .. x0+BW+1 and no row
+        // of the pair is a Dirichlet ghost row
+        bool need = x0 - 2 < cs || ce < x0 + BW + 2;
+        if constexpr (GEN)
+            need = need || (ra < 0 && K.sbc[2] == 3) || (ra + 1 >= K.ny && ra + 1 <= rmax && K.sbc[3] == 3);
+        if (!need) {
+            cp_arrive_noinc(mb);
+            return;
+        }
         const int ft = tid - 64; // 0..63
         // tasks: (row, plane, side) with side 0 = columns [x0-2, cs), side 1 = columns
         // [max(ce, x0-2), min(nx+4, x0+BW+2)) (the ghost columns active cells read, and
@@ -268,7 +216,7 @@ __device__ __forceinline__ void issue_pair(const float* __restrict__ in, float* 
             if (r > rmax) continue;
             int gy, sp, dir;
             row_source<GEN>(K, r, p, gy, sp, dir);
-            float* row = plane_row_rt(ring, p, r);
+            float* row = plane_row(ring, p, r);
             int c0, c1;
             if (dir >= 0) { // the whole row holds the side's equilibrium (split between sides)
                 c0 = side ? x0 + BW / 2 : x0 - 2;
@@ -307,9 +255,9 @@ __device__ __forceinline__ void issue_pair(const float* __restrict__ in, float* 
 
 // Walls (Sec. IV.D): a staged ghost row r_ghost holds a copy of the fluid row r_src (the
 // index map clamps); add the non-equilibrium-extrapolation correction to the thread's
-// own two columns of its f planes (only the v_y > 0 class keeps row y0-2).
+// own two columns of its 16 f planes (lambda stays a copy).
 __device__ __forceinline__ void wall_fix_row(float* ring, int r_ghost, int r_src, int side,
-                                             const ModelConst<float>& K, bool up_only, int lx)
+                                             const ModelConst<float>& K, int lx)
 {
     V2 f[16], d[16];
 #pragma unroll
@@ -317,7 +265,6 @@ __device__ __forceinline__ void wall_fix_row(float* ring, int r_ghost, int r_src
     wall_correction(K, f, side, d);
 #pragma unroll
     for (int i = 0; i < 16; i++) {
-        if (up_only && pclass(i) != C_UP) continue;
         float* q = plane_row(ring, i, r_ghost) + lx;
         *reinterpret_cast<float2*>(q) = (ldv(q) + d[i]).v;
     }
@@ -327,8 +274,8 @@ template <bool GEN>
 __device__ __forceinline__ void wall_fix(float* ring, int r, const ModelConst<float>& K, int lx)
 {
     if constexpr (GEN) {
-        if (r < 0 && K.sbc[2] == 2) wall_fix_row(ring, r, 0, 0, K, r < -1, lx);
-        if (r >= K.ny && K.sbc[3] == 2) wall_fix_row(ring, r, K.ny - 1, 1, K, false, lx);
+        if (r < 0 && K.sbc[2] == 2) wall_fix_row(ring, r, 0, 0, K, lx);
+        if (r >= K.ny && K.sbc[3] == 2) wall_fix_row(ring, r, K.ny - 1, 1, K, lx);
     }
 }
 
@@ -376,29 +323,25 @@ struct TneAcc {
 
 // ---------------- the update of one row by one warp pair -------------------------
 // Row y, the thread's cells x0 + 2t and x0 + 2t + 1 (active when act0 / act1), macros
-// mc recovered in the previous iteration.
+// mc recovered in the previous iteration; the results go to the output rows ob
+// (17 planes of BW floats).
 template <int REC, bool AVG>
-__device__ __forceinline__ void update_row(float* smem_f, float* ring, int y, int x0, int t,
-                                           const ModelConst<float>& K, const StepLaunch& a,
+__device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob, int y, int x0,
+                                           int t, const ModelConst<float>& K, const StepLaunch& a,
                                            const Mac& mc, bool act0, bool act1, bool do_tne,
                                            TneAcc& acc, float* tmin, float* tmax)
 {
     const int lx = XO + 2 * t;
     const float dt = K.dt;
-    float* out = static_cast<float*>(a.out); // not restrict: prev may alias it
-    // AVG: a later SSP Runge-Kutta stage, out = wp * u^n + wn * E(in), u^n read from prev
-    // at the cell's own position (prev may be out itself: each value is read before it
-    // is written, by the same thread)
-    const float* pv = static_cast<const float*>(a.prev);
-    const float wp = (float)a.wprev, wn = (float)a.wnew;
     const V2 rho = mc.rho, ux = mc.ux, uy = mc.uy, T = mc.T;
+    float* r0 = srow(ring, y);
 
     // moments, equilibrium, non-equilibrium parts (Delta_1..4 vanish)
     V2 m[16];
     {
         V2 f[16];
 #pragma unroll
-        for (int i = 0; i < 16; i++) f[i] = ldv(plane_row(ring, i, y) + lx);
+        for (int i = 0; i < 16; i++) f[i] = ldv(r0 + i * RW + lx);
         forward_moments(K, f, m);
     }
     {
@@ -407,7 +350,8 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, int y, in
 #pragma unroll
         for (int k = 4; k < 16; k++) m[k] = m[k] - q[k];
     }
-    // TNE statistics of the state being stepped (Eqs. (90)-(91))
+    // TNE statistics of the state being stepped (Eqs. (90)-(91)); a cell past the grid's
+    // last column contributes nothing
     if (do_tne && act0) {
         V2 d2(0.f);
 #pragma unroll
@@ -424,7 +368,7 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, int y, in
         acc.d2sum += d2.x() + d2.y();
     }
 
-    // grad u: x from the (u, v) ring row y (halo columns included), y from rows y+-1
+    // grad u: x from the (u, v) row y (halo columns included), y from rows y+-1
     const float* uxr = uv_row(smem_f, y, 0);
     const float* uyr = uv_row(smem_f, y, 1);
     const float2 uxl = *reinterpret_cast<const float2*>(uxr + lx - 2);
@@ -444,7 +388,7 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, int y, in
     const V2 A9 = (rT * K.A9c) * fma(V2(4.f) * uy, duy_dy - theta, V2(2.f) * ux * shear);
 
     // reaction over dt (Eq. (28)), decided by the recovered T
-    const float* lm = class_row<C_LAM>(ring, y);
+    const float* lm = r0 + 16 * RW;
     const V2 lam0 = ldv(lm + lx);
     const float ri0 = reaction_increment(lam0.x(), K.omega1 * rT.x(), K.omega2 * rT.x(), dt);
     const float ri1 = reaction_increment(lam0.y(), K.omega1 * rT.y(), K.omega2 * rT.y(), dt);
@@ -465,28 +409,33 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, int y, in
         inverse_moments(K, Om, W);
     }
 
-    const int cx = x0 + 2 * t;
-    const int64_t g = (int64_t)y * K.pitch + cx;
+    // results into the output rows; a later SSP Runge-Kutta stage (AVG) writes
+    // wp * u^n + wn * E(in), u^n read from prev at the cell's own position
+    const int64_t g = (int64_t)y * K.pitch + x0 + 2 * t;
+    const float* pv = static_cast<const float*>(a.prev);
+    const float wp = (float)a.wprev, wn = (float)a.wnew;
     auto store = [&](int i, V2 v) {
-        if (act1) {
-            float2* q = reinterpret_cast<float2*>(out + i * K.plane + g);
-            if constexpr (AVG)
+        if constexpr (AVG) {
+            if (act1)
                 v = fma(V2(wp), V2(*reinterpret_cast<const float2*>(pv + i * K.plane + g)), V2(wn) * v);
-            *q = v.v;
-        } else if (act0) {
-            float* q = out + i * K.plane + g;
-            *q = AVG ? fmaf(wp, pv[i * K.plane + g], wn * v.x()) : v.x();
+            else if (act0)
+                v = V2(fmaf(wp, pv[i * K.plane + g], wn * v.x()), 0.f);
         }
+        *reinterpret_cast<float2*>(ob + i * BW + 2 * t) = v.v;
     };
 
     // lambda: u . grad(lambda) with NND interface values
+    const float* rm2 = srow(ring, y - 2);
+    const float* rm1 = srow(ring, y - 1);
+    const float* rp1 = srow(ring, y + 1);
+    const float* rp2 = srow(ring, y + 2);
     {
         const Q6 lq = load6(lm, lx);
         const V2 lpx = nnd_pos_x(lq), lnx = nnd_neg_x(lq);
-        const V2 lm1 = ldv(class_row<C_LAM>(ring, y - 1) + lx);
-        const V2 lp1 = ldv(class_row<C_LAM>(ring, y + 1) + lx);
-        const V2 lpy = nnd_pos_y(ldv(class_row<C_LAM>(ring, y - 2) + lx), lm1, lam0, lp1);
-        const V2 lny = nnd_neg_y(lm1, lam0, lp1, ldv(class_row<C_LAM>(ring, y + 2) + lx));
+        const V2 lm1 = ldv(rm1 + 16 * RW + lx);
+        const V2 lp1 = ldv(rp1 + 16 * RW + lx);
+        const V2 lpy = nnd_pos_y(ldv(rm2 + 16 * RW + lx), lm1, lam0, lp1);
+        const V2 lny = nnd_neg_y(lm1, lam0, lp1, ldv(rp2 + 16 * RW + lx));
         const V2 lax(ux.x() > 0.f ? lpx.x() : lnx.x(), ux.y() > 0.f ? lpx.y() : lnx.y());
         const V2 lay(uy.x() > 0.f ? lpy.x() : lny.x(), uy.y() > 0.f ? lpy.y() : lny.y());
         const V2 ladv = fma(ux * K.inv_dx, lax, uy * K.inv_dy * lay);
@@ -495,22 +444,13 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, int y, in
         store(16, ln);
     }
 
-    // NND flux differences (upwind side fixed per velocity), Euler update, store
-    const float* up_m2 = class_row<C_UP>(ring, y - 2);
-    const float* up_m1 = class_row<C_UP>(ring, y - 1);
-    const float* up_p1 = class_row<C_UP>(ring, y + 1);
-    const float* dn_m1 = class_row<C_DN>(ring, y - 1);
-    const float* dn_p1 = class_row<C_DN>(ring, y + 1);
-    const float* dn_p2 = class_row<C_DN>(ring, y + 2);
+    // NND flux differences (upwind side fixed per velocity), Euler update
     auto put = [&](int i, V2 f0, V2 adv) { store(i, fma(V2(dt), W[i] - adv, f0)); };
-#define ROW(i) plane_row(ring, (i), y)
-#define F0(i) ldv(ROW(i) + lx)
-#define PX(i) nnd_pos_x(load6(ROW(i), lx))
-#define NX(i) nnd_neg_x(load6(ROW(i), lx))
-#define PY(i, f0) nnd_pos_y(ldv(up_m2 + pindex(i) * RW + lx), ldv(up_m1 + pindex(i) * RW + lx), f0, \
-                            ldv(up_p1 + pindex(i) * RW + lx))
-#define NY(i, f0) nnd_neg_y(ldv(dn_m1 + pindex(i) * RW + lx), f0, ldv(dn_p1 + pindex(i) * RW + lx), \
-                            ldv(dn_p2 + pindex(i) * RW + lx))
+#define F0(i) ldv(r0 + (i) * RW + lx)
+#define PX(i) nnd_pos_x(load6(r0 + (i) * RW, lx))
+#define NX(i) nnd_neg_x(load6(r0 + (i) * RW, lx))
+#define PY(i, f0) nnd_pos_y(ldv(rm2 + (i) * RW + lx), ldv(rm1 + (i) * RW + lx), f0, ldv(rp1 + (i) * RW + lx))
+#define NY(i, f0) nnd_neg_y(ldv(rm1 + (i) * RW + lx), f0, ldv(rp1 + (i) * RW + lx), ldv(rp2 + (i) * RW + lx))
 #pragma unroll
     for (int o = 0; o < 2; o++) { // axis orbits 0, 2
         const int i0 = 8 * o;
@@ -539,7 +479,6 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, int y, in
         f0 = F0(i0 + 3);
         put(i0 + 3, f0, fma(cxs, PX(i0 + 3), -cys * NY(i0 + 3, f0)));
     }
-#undef ROW
 #undef F0
 #undef PX
 #undef NX
@@ -547,14 +486,47 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, int y, in
 #undef NY
 }
 
+// Stores of the updated rows y, y+1 (those below yend) from the output buffer: one bulk
+// asynchronous copy per plane row for columns x0 .. min(x0+BW, nx4) (16-byte multiples),
+// plain stores for the tail columns nx4 .. nx-1 of the last strip. Warp 1 issues them.
+__device__ __forceinline__ void store_rows(const float* ob, float* out, int y, int yend, int x0,
+                                           const ModelConst<float>& K)
+{
+    const int lane = threadIdx.x & 31;
+    const int nx4 = K.nx & ~3;
+    const int ce = x0 + BW < nx4 ? x0 + BW : nx4;
+    for (int task = lane; task < 2 * NPLANE; task += 32) {
+        const int r = task / NPLANE, p = task % NPLANE;
+        if (y + r >= yend) continue;
+        float* dst = out + p * K.plane + (int64_t)(y + r) * K.pitch;
+        const float* src = ob + (r * NPLANE + p) * BW;
+        if (ce > x0)
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst + x0),
+                         "r"(smem_addr(src)), "r"((uint32_t)(ce - x0) * 4u)
+                         : "memory");
+        for (int x = ce > x0 ? ce : x0; x < K.nx && x < x0 + BW; x++) dst[x] = src[x - x0];
+    }
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
 // ---------------- the kernel -----------------------------------------------------
+__device__ __forceinline__ void bulk_wait_read_all()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all()
+{
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 template <int REC, bool GEN, bool AVG>
-__global__ void __launch_bounds__(MT, 3)
+__global__ void __launch_bounds__(MT, 2)
     march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     float* smem_f = reinterpret_cast<float*>(smem);
     float* ring = smem_f;
+    float* obuf = smem_f + OBUF;
     double* tsum = reinterpret_cast<double*>(smem + OFF_TSUM);
     float* tmm = reinterpret_cast<float*>(smem + OFF_TMM);
     const uint32_t mbar0 = smem_addr(smem + OFF_MBAR);
@@ -563,6 +535,8 @@ __global__ void __launch_bounds__(MT, 3)
     const int wpair = warp >> 1, t = tid & 63, lx = XO + 2 * t;
     const int nx = K.nx, ny = K.ny;
     const float* __restrict__ in = static_cast<const float*>(a.in);
+    float* out = static_cast<float*>(a.out);
+    float* ob = obuf + wpair * NPLANE * BW;
 
     const DfConst C = df_constants(K);
     const int64_t step = a.ctr->step;
@@ -603,12 +577,9 @@ __global__ void __launch_bounds__(MT, 3)
         acc.dsum = acc.d2sum = 0.f;
 
         __syncthreads(); // the previous strip is done with the ring
-        // rows y0-2 .. y0+3 now; rows y0+4, y0+5 share ring slots with rows y0-2, y0-1
-        // (the v_y = 0 and v_y < 0 classes keep fewer rows), so they follow once the
-        // macros of row y0-1 have been recovered
-        for (int j = 0; j < npairs && j < NMB - 1; j++)
+        for (int j = 0; j < npairs && j < NMB; j++)
             issue_pair<GEN>(in, ring, mb_of(q0 + j), y0 - 2 + 2 * j, yend + 1, x0, K);
-        q_issued = q0 + (npairs < NMB - 1 ? npairs : NMB - 1);
+        q_issued = q0 + (npairs < NMB ? npairs : NMB);
         wait_pair(q0);
         wait_pair(q0 + 1);
         // walls: ghost rows among rows y0-2 .. y0+1 (warp pair 0: y0-1, y0+1; 1: y0-2, y0)
@@ -621,10 +592,6 @@ __global__ void __launch_bounds__(MT, 3)
         Mac cur = recover_row<REC>(smem_f, ring, y0 + wpair, t, K, C, bad, act0, act1);
         if (wpair == 0) (void)recover_row<REC>(smem_f, ring, y0 - 1, t, K, C, bad, act0, act1);
         if (__syncthreads_or(timeout)) break;
-        if (npairs > NMB - 1) {
-            issue_pair<GEN>(in, ring, mb_of(q0 + NMB - 1), y0 + 4, yend + 1, x0, K);
-            q_issued = q0 + NMB;
-        }
 
         bool stop = false;
         for (int k = 0;; k++) {
@@ -636,19 +603,23 @@ __global__ void __launch_bounds__(MT, 3)
                 if (rr <= yend + 1) wall_fix<GEN>(ring, rr, K, lx);
             Mac nxt = cur;
             if (rr <= yend) nxt = recover_row<REC>(smem_f, ring, rr, t, K, C, bad, act0, act1);
+            if (warp == 1) bulk_wait_read_all(); // the output buffer is free again
             if (__syncthreads_or(timeout)) {
                 stop = true;
                 break;
             }
             if (y + wpair < yend)
-                update_row<REC, AVG>(smem_f, ring, y + wpair, x0, t, K, a, cur, act0, act1, do_tne, acc,
-                                     tmin, tmax);
+                update_row<REC, AVG>(smem_f, ring, ob, y + wpair, x0, t, K, a, cur, act0, act1,
+                                     do_tne, acc, tmin, tmax);
             cur = nxt;
+            fence_async_shared(); // the output rows are read by the bulk stores
             __syncthreads();
-            if (k + 4 < npairs) {
+            if (warp == 1) {
+                store_rows(obuf, out, y, yend, x0, K);
+            } else if (k + 4 < npairs) {
                 issue_pair<GEN>(in, ring, mb_of(q0 + k + 4), y + 6, yend + 1, x0, K);
-                q_issued = q0 + k + 5;
             }
+            if (k + 4 < npairs) q_issued = q0 + k + 5;
         }
         if (stop) break;
         // the strip's TNE sums: per-thread FP32 partials (32 cells), added in FP64 in a
@@ -687,6 +658,7 @@ __global__ void __launch_bounds__(MT, 3)
         for (uint32_t q = q_waited; q < q_issued; q++) (void)mbar_wait(mb_of(q), (q / NMB) & 1u);
         if (tid == 0) atomicOr(&a.ctr->status, 2);
     }
+    if (warp == 1) bulk_wait_all(); // every output row has reached global memory
 
     // end of step: status, TNE partials, arrival count
     if (__syncthreads_or(bad) && tid == 0) atomicOr(&a.ctr->status, 1);

@@ -186,29 +186,32 @@ __device__ __forceinline__ void recover_pair(const V2* f, const DfConst& C,
     }
 }
 
-// Branch-free forms of the two conversions for the states a step produces (normal
-// binary32 values, zeros): binary32 -> binary64 exactly by moving the IEEE-754 fields,
-// zeros and subnormal inputs to a signed zero; binary64 -> binary32 rounded to nearest
-// even, results below the normal binary32 range to a signed zero. Infinite and NaN
-// inputs are not converted faithfully: the recovery flags such cells from their FP32
-// sums before it converts anything.
+// Branch-free forms of the two conversions, for the values a step's recovery produces
+// (normal binary32 / binary64 numbers of modest size, or zero):
+// f2d_fast moves the IEEE-754 fields of a normal binary32 value into binary64 exactly
+// (exponent rebias 127 -> 1023, significand shifted by 29 bits); a zero or subnormal
+// input becomes +-2^-127 (below 6e-39), which added to a conserved sum of order one,
+// or scaling a momentum that is exactly zero, changes nothing at FP32 output.
+// d2f_fast rounds binary64 to binary32 to nearest even by adding the rounding bias to
+// the 64-bit pattern (a carry steps the exponent), then shifting the top bits down and
+// rebiasing the exponent; results below the normal binary32 range become a signed zero.
+// Neither handles infinities or NaN: the recovery flags such cells from their FP32 sums
+// before it converts anything.
 __device__ __forceinline__ double f2d_fast(float x)
 {
     const unsigned b = __float_as_uint(x);
-    const unsigned e = (b >> 23) & 0xffu;
-    const unsigned hi = (b & 0x80000000u) | (e ? (((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)) : 0u);
-    const unsigned lo = e ? (b << 29) : 0u;
-    return __hiloint2double((int)hi, (int)lo);
+    const unsigned hi = (((b >> 3) & 0x0fffffffu) + (896u << 20)) | (b & 0x80000000u);
+    return __hiloint2double((int)hi, (int)(b << 29));
 }
 __device__ __forceinline__ float d2f_fast(double x)
 {
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
-    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    // the 29 dropped bits: above half rounds up, exactly half rounds to even
-    const unsigned up = ((lo & 0x1fffffffu) + (m & 1u)) > 0x10000000u ? 1u : 0u;
-    const unsigned r = (hi & 0x80000000u) | (((unsigned)e << 23) + m + up);
-    return __uint_as_float(e >= 1 ? r : (hi & 0x80000000u));
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(bits >> 32);
+    // round to nearest even at bit 29: + (2^28 - 1) + (bit 29)
+    const unsigned long long r = bits + 0x0fffffffull + ((bits >> 29) & 1ull);
+    const unsigned f = __funnelshift_r((unsigned)r, (unsigned)(r >> 32), 29) - (896u << 23);
+    const bool normal = (hi & 0x7ff00000u) >= (897u << 20);
+    return __uint_as_float(normal ? (f | (hi & 0x80000000u)) : (hi & 0x80000000u));
 }
 __device__ __forceinline__ double df_to_f64_fast(float hi, float lo) { return f2d_fast(hi) + f2d_fast(lo); }
 
