@@ -39,6 +39,7 @@ struct lbkm {
     cudaStream_t capture_stream;
     void* buf[2];
     void* buf3;  // the middle-stage state of the three-stage scheme (time_scheme 2)
+    TmaDesc tm_load[3], tm_store[3]; // tensor maps of buf[0], buf[1], buf3 (FP32 2-D)
     int cur;
     double* partials;
     int grid, tgrid;
@@ -114,6 +115,9 @@ StepLaunch step_args(const lbkm* h, int from, int stage = 0, const void* src = n
     a.tne_every = h->p.tne_every;
     a.grid = h->grid;
     a.cell_area = h->p.dx * h->p.dy;
+    auto map_of = [&](const void* b) { return b == h->buf[0] ? 0 : (b == h->buf[1] ? 1 : 2); };
+    a.tm_in = &h->tm_load[map_of(a.in)];
+    a.tm_out = &h->tm_store[map_of(a.out)];
     return a;
 }
 
@@ -372,6 +376,15 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
     if (p.time_scheme == 2) {
         if ((e = cudaMalloc(&h->buf3, h->state_bytes_dev)) != cudaSuccess) return bail(e, "state C");
         if ((e = cudaMemset(h->buf3, 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
+    }
+    if (h->precision == LBKM_F32 && h->two_d) {
+        void* bufs[3] = {h->buf[0], h->buf[1], h->buf3};
+        for (int b = 0; b < 3; b++) {
+            if (!bufs[b]) continue;
+            e = march_tensor_maps(bufs[b], h->nx, h->ny, h->pitch, (int64_t)h->plane_elems,
+                                  &h->tm_load[b], &h->tm_store[b]);
+            if (e != cudaSuccess) return bail(e, "tensor maps");
+        }
     }
     h->grid = step_grid(h->precision, h->recovery, h->two_d, h->nx, h->ny, sbc);
     if (h->grid < 1) return bail(cudaGetLastError(), "step grid");

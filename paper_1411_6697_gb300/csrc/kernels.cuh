@@ -25,6 +25,11 @@ struct TneRecord {
     int64_t step;
 };
 
+// An encoded TMA tensor map (the driver's opaque 128-byte CUtensorMap).
+struct alignas(64) TmaDesc {
+    unsigned long long w[16];
+};
+
 struct StepLaunch {
     const void* in;      // state at t_n  [17][ny][pitch]
     void* out;           // state at t_n+1
@@ -42,6 +47,8 @@ struct StepLaunch {
     int tne_every;       // 0 = off
     int grid;            // blocks launched
     double cell_area;    // dx * dy
+    const TmaDesc* tm_in;  // host copies of the tensor maps of in (loads) and out (stores),
+    const TmaDesc* tm_out; // FP32 2-D grids only
 };
 
 // Grid-wide TNE record of the partials a step left (if its schedule reduced TNE): one
@@ -132,6 +139,10 @@ cudaError_t launch_adj_rho0(const ModelConst<double>& K, const AdjArgs& a, doubl
 
 // FP32 2-D step: y-marching strips, two cells per thread (march.cu)
 // mode = recovery | (general side conditions << 1)
+// Tensor maps of an FP32 state buffer for the step kernel's bulk tensor copies: loads of
+// a box of BW + 8 columns x 2 rows x 17 planes, stores of BW x 2 x 17.
+cudaError_t march_tensor_maps(const void* state, int nx, int ny, int pitch, int64_t plane,
+                              TmaDesc* load, TmaDesc* store);
 int march_grid(int mode, int nx, int ny);
 cudaError_t launch_march(int mode, const ModelConst<float>& K, const StepLaunch& a,
                          cudaStream_t s);

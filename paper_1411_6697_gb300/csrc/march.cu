@@ -31,6 +31,7 @@
 // the ignition test T > T_ig is taken in that precision. The TNE statistics of the
 // updated state's input (Delta_5..Delta_16, Sec. VI, Eqs. (90)-(91)) accumulate per
 // thread in FP32 over a strip (32 cells) and from there on in FP64.
+#include <cuda.h>
 #include <float.h>
 #include <stdlib.h>
 
@@ -49,27 +50,35 @@ constexpr int NWM = MT / 32;     // warps per block
 constexpr int BW = 128;          // columns per strip
 constexpr int XO = 4;            // column x0 sits at element XO of a staged row
 constexpr int RW = BW + 2 * XO;  // staged row: columns x0-4 .. x0+BW+3 (544 bytes)
-constexpr int NSLOT = 8;         // staged rows kept: y-2 .. y+5
-constexpr int ROWF = NPLANE * RW; // floats of one staged row (17 planes)
+constexpr int NSLOT = 8;         // staged rows kept: y-2 .. y+5, in four row pairs
+constexpr int PST = 2 * RW;      // floats from one plane of a row pair to the next
+// a row pair's slot: [plane][row of the pair][RW], as a tensor copy of a box of RW
+// columns x 2 rows x 17 planes lays it out, padded to a multiple of 128 bytes (the
+// alignment of a tensor copy's shared-memory address)
+constexpr int PSLOT = (NPLANE * PST * 4 + 127) / 128 * 128 / 4;
 
-// shared-memory layout (floats from the 16-byte aligned start)
-constexpr int UVB = NSLOT * ROWF;                // (u, v) of rows: [NSLOT][2][RW]
-constexpr int OBUF = UVB + NSLOT * 2 * RW;       // updated rows: [2][NPLANE][BW]
-constexpr int SMEM_FLOATS = OBUF + 2 * NPLANE * BW;
-static_assert(RW % 4 == 0 && ROWF % 4 == 0 && UVB % 4 == 0 && OBUF % 4 == 0,
-              "every staged and output row starts on a 16-byte boundary");
+// shared-memory layout (floats from a 128-byte aligned start)
+constexpr int OBUF = NSLOT / 2 * PSLOT;          // updated rows: [NPLANE][2][BW]
+constexpr int UVB = OBUF + NPLANE * 2 * BW;      // (u, v) of rows: [NSLOT][2][RW]
+constexpr int SMEM_FLOATS = UVB + NSLOT * 2 * RW;
+static_assert(RW % 4 == 0 && PSLOT % 32 == 0 && OBUF % 32 == 0 && UVB % 4 == 0,
+              "staged rows on 16-byte, row-pair slots and the output rows on 128-byte boundaries");
 constexpr size_t OFF_TSUM = (size_t)SMEM_FLOATS * 4;            // double[NSUM]
 constexpr size_t OFF_TMM = OFF_TSUM + (size_t)NSUM * 8;           // float[NWM][NMM]
 constexpr size_t OFF_MBAR = (OFF_TMM + (size_t)NWM * NMM * 4 + 15) / 16 * 16;
 constexpr int NMB = 4;                                            // row pairs in flight or in use
-constexpr size_t MARCH_SMEM = OFF_MBAR + NMB * 8;
+constexpr size_t MARCH_SMEM = OFF_MBAR + NMB * 8 + 128;           // + room to align the start
 static_assert(MARCH_SMEM <= 112 * 1024, "two blocks per SM need <= 112 KB each");
-static_assert(NSUM * MT <= UVB && 4 * NSUM <= MT,
+static_assert(NSUM * MT <= OBUF && 4 * NSUM <= MT,
               "the strip's TNE partials fit in the idle ring, four threads per sum");
+constexpr uint32_t PAIR_BYTES = NPLANE * PST * 4; // one tensor copy of a row pair
 
-// staged row r (all planes) and plane p of it
-__device__ __forceinline__ float* srow(float* ring, int r) { return ring + (r & (NSLOT - 1)) * ROWF; }
-__device__ __forceinline__ float* plane_row(float* ring, int p, int r) { return srow(ring, r) + p * RW; }
+// staged row r (plane p at + p * PST) and plane p of it
+__device__ __forceinline__ float* srow(float* ring, int r)
+{
+    return ring + ((r >> 1) & (NSLOT / 2 - 1)) * PSLOT + (r & 1) * RW;
+}
+__device__ __forceinline__ float* plane_row(float* ring, int p, int r) { return srow(ring, r) + p * PST; }
 __device__ __forceinline__ float* uv_row(float* smem_f, int r, int field)
 {
     return smem_f + UVB + ((r & (NSLOT - 1)) * 2 + field) * RW;
@@ -115,6 +124,24 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
         "l"(src), "r"(bytes), "r"(mb)
         : "memory");
 }
+// a box of RW columns x 2 rows x 17 planes from column x, row y (tensor map of the input)
+__device__ __forceinline__ void tma_load_pair(uint32_t dst, const CUtensorMap* tm, int x, int y, uint32_t mb)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(tm), "r"(x), "r"(y), "r"(0), "r"(mb)
+        : "memory");
+}
+// a box of BW columns x 2 rows x 17 planes to column x, row y (tensor map of the output;
+// parts of the box outside the grid are not written)
+__device__ __forceinline__ void tma_store_pair(const CUtensorMap* tm, int x, int y, uint32_t src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tm),
+                 "r"(x), "r"(y), "r"(0), "r"(src)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
 __device__ __forceinline__ void cp4(uint32_t dst, const void* src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
@@ -156,16 +183,30 @@ __device__ __forceinline__ void row_source(const ModelConst<float>& K, int r, in
 }
 
 // Issue the copies of staged rows ra, ra+1 (pair mbarrier mb) for the strip at x0;
-// rows above rmax are not needed. Warp 0: one bulk copy per plane row for the columns
+// rows above rmax are not needed. A pair whose rows and staged columns all lie inside
+// the grid arrives by one tensor copy (thread 0). Otherwise warp 0: one bulk copy per
+// plane row for the columns
 // [cs, ce) (16-byte aligned), after arming the mbarrier with their byte count.
 // Warps 2-3: the remaining columns x0-2 .. x0+BW+1 that active cells read (edges of
 // the grid, a row tail past the last multiple of 4, Dirichlet rows), element by
 // element, then one arrival each on the mbarrier once their copies have landed.
 template <bool GEN>
 __device__ __forceinline__ void issue_pair(const float* __restrict__ in, float* ring, uint32_t mb,
-                                           int ra, int rmax, int x0, const ModelConst<float>& K)
+                                           int ra, int rmax, int x0, const ModelConst<float>& K,
+                                           const CUtensorMap* tm)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // both rows inside the grid, every staged column inside it: one tensor copy
+    if (x0 >= XO && x0 + BW + XO <= K.nx && ra >= 0 && ra + 1 < K.ny) {
+        if (tid == 0) {
+            mbar_expect_tx(mb, PAIR_BYTES);
+            fence_async_shared();
+            tma_load_pair(smem_addr(srow(ring, ra)), tm, x0 - XO, ra, mb);
+        } else if (warp >= 2) {
+            cp_arrive_noinc(mb);
+        }
+        return;
+    }
     const int nx4 = K.nx & ~3;
     const int cs = x0 - XO > 0 ? x0 - XO : 0;
     const int ce = x0 + BW + XO < nx4 ? x0 + BW + XO : nx4;
@@ -341,7 +382,7 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
     {
         V2 f[16];
 #pragma unroll
-        for (int i = 0; i < 16; i++) f[i] = ldv(r0 + i * RW + lx);
+        for (int i = 0; i < 16; i++) f[i] = ldv(r0 + i * PST + lx);
         forward_moments(K, f, m);
     }
     {
@@ -388,7 +429,7 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
     const V2 A9 = (rT * K.A9c) * fma(V2(4.f) * uy, duy_dy - theta, V2(2.f) * ux * shear);
 
     // reaction over dt (Eq. (28)), decided by the recovered T
-    const float* lm = r0 + 16 * RW;
+    const float* lm = r0 + 16 * PST;
     const V2 lam0 = ldv(lm + lx);
     const float ri0 = reaction_increment(lam0.x(), K.omega1 * rT.x(), K.omega2 * rT.x(), dt);
     const float ri1 = reaction_increment(lam0.y(), K.omega1 * rT.y(), K.omega2 * rT.y(), dt);
@@ -421,7 +462,7 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
             else if (act0)
                 v = V2(fmaf(wp, pv[i * K.plane + g], wn * v.x()), 0.f);
         }
-        *reinterpret_cast<float2*>(ob + i * BW + 2 * t) = v.v;
+        *reinterpret_cast<float2*>(ob + i * 2 * BW + 2 * t) = v.v;
     };
 
     // lambda: u . grad(lambda) with NND interface values
@@ -432,10 +473,10 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
     {
         const Q6 lq = load6(lm, lx);
         const V2 lpx = nnd_pos_x(lq), lnx = nnd_neg_x(lq);
-        const V2 lm1 = ldv(rm1 + 16 * RW + lx);
-        const V2 lp1 = ldv(rp1 + 16 * RW + lx);
-        const V2 lpy = nnd_pos_y(ldv(rm2 + 16 * RW + lx), lm1, lam0, lp1);
-        const V2 lny = nnd_neg_y(lm1, lam0, lp1, ldv(rp2 + 16 * RW + lx));
+        const V2 lm1 = ldv(rm1 + 16 * PST + lx);
+        const V2 lp1 = ldv(rp1 + 16 * PST + lx);
+        const V2 lpy = nnd_pos_y(ldv(rm2 + 16 * PST + lx), lm1, lam0, lp1);
+        const V2 lny = nnd_neg_y(lm1, lam0, lp1, ldv(rp2 + 16 * PST + lx));
         const V2 lax(ux.x() > 0.f ? lpx.x() : lnx.x(), ux.y() > 0.f ? lpx.y() : lnx.y());
         const V2 lay(uy.x() > 0.f ? lpy.x() : lny.x(), uy.y() > 0.f ? lpy.y() : lny.y());
         const V2 ladv = fma(ux * K.inv_dx, lax, uy * K.inv_dy * lay);
@@ -446,11 +487,11 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
 
     // NND flux differences (upwind side fixed per velocity), Euler update
     auto put = [&](int i, V2 f0, V2 adv) { store(i, fma(V2(dt), W[i] - adv, f0)); };
-#define F0(i) ldv(r0 + (i) * RW + lx)
-#define PX(i) nnd_pos_x(load6(r0 + (i) * RW, lx))
-#define NX(i) nnd_neg_x(load6(r0 + (i) * RW, lx))
-#define PY(i, f0) nnd_pos_y(ldv(rm2 + (i) * RW + lx), ldv(rm1 + (i) * RW + lx), f0, ldv(rp1 + (i) * RW + lx))
-#define NY(i, f0) nnd_neg_y(ldv(rm1 + (i) * RW + lx), f0, ldv(rp1 + (i) * RW + lx), ldv(rp2 + (i) * RW + lx))
+#define F0(i) ldv(r0 + (i) * PST + lx)
+#define PX(i) nnd_pos_x(load6(r0 + (i) * PST, lx))
+#define NX(i) nnd_neg_x(load6(r0 + (i) * PST, lx))
+#define PY(i, f0) nnd_pos_y(ldv(rm2 + (i) * PST + lx), ldv(rm1 + (i) * PST + lx), f0, ldv(rp1 + (i) * PST + lx))
+#define NY(i, f0) nnd_neg_y(ldv(rm1 + (i) * PST + lx), f0, ldv(rp1 + (i) * PST + lx), ldv(rp2 + (i) * PST + lx))
 #pragma unroll
     for (int o = 0; o < 2; o++) { // axis orbits 0, 2
         const int i0 = 8 * o;
@@ -486,29 +527,6 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
 #undef NY
 }
 
-// Stores of the updated rows y, y+1 (those below yend) from the output buffer: one bulk
-// asynchronous copy per plane row for columns x0 .. min(x0+BW, nx4) (16-byte multiples),
-// plain stores for the tail columns nx4 .. nx-1 of the last strip. Warp 1 issues them.
-__device__ __forceinline__ void store_rows(const float* ob, float* out, int y, int yend, int x0,
-                                           const ModelConst<float>& K)
-{
-    const int lane = threadIdx.x & 31;
-    const int nx4 = K.nx & ~3;
-    const int ce = x0 + BW < nx4 ? x0 + BW : nx4;
-    for (int task = lane; task < 2 * NPLANE; task += 32) {
-        const int r = task / NPLANE, p = task % NPLANE;
-        if (y + r >= yend) continue;
-        float* dst = out + p * K.plane + (int64_t)(y + r) * K.pitch;
-        const float* src = ob + (r * NPLANE + p) * BW;
-        if (ce > x0)
-            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst + x0),
-                         "r"(smem_addr(src)), "r"((uint32_t)(ce - x0) * 4u)
-                         : "memory");
-        for (int x = ce > x0 ? ce : x0; x < K.nx && x < x0 + BW; x++) dst[x] = src[x - x0];
-    }
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-
 // ---------------- the kernel -----------------------------------------------------
 __device__ __forceinline__ void bulk_wait_read_all()
 {
@@ -521,9 +539,12 @@ __device__ __forceinline__ void bulk_wait_all()
 
 template <int REC, bool GEN, bool AVG>
 __global__ void __launch_bounds__(MT, 2)
-    march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows)
+    march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows,
+                 const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // the tensor copies want a 128-byte aligned start
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     float* smem_f = reinterpret_cast<float*>(smem);
     float* ring = smem_f;
     float* obuf = smem_f + OBUF;
@@ -535,8 +556,7 @@ __global__ void __launch_bounds__(MT, 2)
     const int wpair = warp >> 1, t = tid & 63, lx = XO + 2 * t;
     const int nx = K.nx, ny = K.ny;
     const float* __restrict__ in = static_cast<const float*>(a.in);
-    float* out = static_cast<float*>(a.out);
-    float* ob = obuf + wpair * NPLANE * BW;
+    float* ob = obuf + wpair * BW;
 
     const DfConst C = df_constants(K);
     const int64_t step = a.ctr->step;
@@ -578,7 +598,7 @@ __global__ void __launch_bounds__(MT, 2)
 
         __syncthreads(); // the previous strip is done with the ring
         for (int j = 0; j < npairs && j < NMB; j++)
-            issue_pair<GEN>(in, ring, mb_of(q0 + j), y0 - 2 + 2 * j, yend + 1, x0, K);
+            issue_pair<GEN>(in, ring, mb_of(q0 + j), y0 - 2 + 2 * j, yend + 1, x0, K, &tin);
         q_issued = q0 + (npairs < NMB ? npairs : NMB);
         wait_pair(q0);
         wait_pair(q0 + 1);
@@ -615,9 +635,11 @@ __global__ void __launch_bounds__(MT, 2)
             fence_async_shared(); // the output rows are read by the bulk stores
             __syncthreads();
             if (warp == 1) {
-                store_rows(obuf, out, y, yend, x0, K);
+                // rows y, y+1 leave in one tensor copy; a row at or past ny is clipped (a
+                // strip ends on an even row unless it ends at ny)
+                if (lane == 0) tma_store_pair(&tout, x0, y, smem_addr(obuf));
             } else if (k + 4 < npairs) {
-                issue_pair<GEN>(in, ring, mb_of(q0 + k + 4), y + 6, yend + 1, x0, K);
+                issue_pair<GEN>(in, ring, mb_of(q0 + k + 4), y + 6, yend + 1, x0, K, &tin);
             }
             if (k + 4 < npairs) q_issued = q0 + k + 5;
         }
@@ -750,10 +772,12 @@ template <int REC, bool GEN>
 void launch_variant(bool avg, const ModelConst<float>& K, const StepLaunch& a, int rows,
                     cudaStream_t s)
 {
+    const CUtensorMap& tin = *reinterpret_cast<const CUtensorMap*>(a.tm_in);
+    const CUtensorMap& tout = *reinterpret_cast<const CUtensorMap*>(a.tm_out);
     if (avg)
-        march_kernel<REC, GEN, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+        march_kernel<REC, GEN, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
     else
-        march_kernel<REC, GEN, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows);
+        march_kernel<REC, GEN, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
 }
 
 } // namespace
@@ -773,9 +797,9 @@ void march_plan(int mode, int nx, int ny, int* grid, int* strip_rows)
     int rows = 32;
     while (rows > 8 && (long)nsx * ((ny + rows - 1) / rows) < G) rows /= 2;
     if (rows > ny) rows = ny;
-    if (const char* env = getenv("LBKM_MARCH_ROWS")) { // tuning override
-        const int r = atoi(env);
-        if (r >= 1) rows = r < ny ? r : ny;
+    if (const char* env = getenv("LBKM_MARCH_ROWS")) { // tuning override (even)
+        const int r = (atoi(env) + 1) & ~1;
+        if (r >= 2) rows = r < ny ? r : ny;
     }
     const long strips = (long)nsx * ((ny + rows - 1) / rows);
     *grid = G < 0 ? -1 : (int)(strips < G ? strips : G);
@@ -789,6 +813,42 @@ int march_grid(int mode, int nx, int ny)
     return g;
 }
 
+// The state viewed as a 3-D tensor (columns, rows, planes) with row stride pitch and
+// plane stride plane elements: monotonic strides, 16-byte multiples.
+cudaError_t march_tensor_maps(const void* state, int nx, int ny, int pitch, int64_t plane,
+                              TmaDesc* load, TmaDesc* store)
+{
+    static_assert(sizeof(TmaDesc) == sizeof(CUtensorMap), "opaque tensor map size");
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<Encode>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)NPLANE};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)plane * 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint32_t box_ld[3] = {RW, 2, NPLANE}, box_st[3] = {BW, 2, NPLANE};
+    void* base = const_cast<void*>(state);
+    if (encode(reinterpret_cast<CUtensorMap*>(load), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
+               strides, box_ld, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    if (encode(reinterpret_cast<CUtensorMap*>(store), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
+               strides, box_st, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
 cudaError_t launch_march(int mode, const ModelConst<float>& K, const StepLaunch& a, cudaStream_t s)
 {
     int g, rows;
@@ -796,6 +856,7 @@ cudaError_t launch_march(int mode, const ModelConst<float>& K, const StepLaunch&
     if (g < 0) return cudaErrorInvalidConfiguration;
     if (g != a.grid) return cudaErrorInvalidConfiguration; // partial buffers sized for a.grid
     const bool avg = a.stage >= 2;
+    if (!a.tm_in || !a.tm_out) return cudaErrorInvalidValue;
     switch (mode & 3) {
     case 0: launch_variant<0, false>(avg, K, a, rows, s); break;
     case 1: launch_variant<1, false>(avg, K, a, rows, s); break;
