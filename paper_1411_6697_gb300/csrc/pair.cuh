@@ -77,6 +77,68 @@ __device__ __forceinline__ void conserved_pair(const V2* f, const DfConst& C, D2
                d_add(d_mul_c(E[0], C.wh[1], C.wl[1]), d_mul_c(E[1], C.wh[3], C.wl[3])));
 }
 
+// The same conserved moments with the (hi, lo) pairs carried unnormalized through the
+// butterflies: every hi + hi is an exact TwoSum (or TwoDiff), the lo parts and the
+// rounding errors add in FP32 (each of size ulp(hi), so their own rounding is far below
+// it), products with the split constants keep their error terms unnormalized, and each
+// moment is normalized once at the end (FastTwoSum). Relative error about 2^-46.
+__device__ __forceinline__ D2 two_diff(V2 a, V2 b)
+{
+    V2 s = a - b;
+    V2 bb = s - a;
+    V2 e = (a - (s - bb)) - (b + bb);
+    return {s, e};
+}
+__device__ __forceinline__ D2 dd_add(D2 a, D2 b)
+{
+    const D2 s = two_sum(a.hi, b.hi);
+    return {s.hi, (a.lo + b.lo) + s.lo};
+}
+__device__ __forceinline__ D2 dd_sub(D2 a, D2 b)
+{
+    const D2 s = two_diff(a.hi, b.hi);
+    return {s.hi, (a.lo - b.lo) + s.lo};
+}
+__device__ __forceinline__ D2 dd_mul_c(D2 a, float ch, float cl)
+{
+    const V2 p = a.hi * ch;
+    V2 e = fma(a.hi, V2(ch), -p);
+    e = fma(a.hi, V2(cl), e);
+    e = fma(a.lo, V2(ch), e);
+    return {p, e};
+}
+__device__ __forceinline__ D2 dd_norm(D2 a) { return fast_two_sum(a.hi, a.lo); }
+
+__device__ __forceinline__ void conserved_pair_u(const V2* f, const DfConst& C, D2& m1, D2& m2,
+                                                 D2& m3, D2& m4)
+{
+    D2 P[2], E[2], AX[4], AY[4]; // sector slots: axis0, axis2 | diag1, diag3
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        const int b = 8 * a;
+        P[a] = dd_add(two_sum(f[b], f[b + 2]), two_sum(f[b + 1], f[b + 3]));
+        AX[a] = two_diff(f[b], f[b + 2]);
+        AY[a] = two_diff(f[b + 1], f[b + 3]);
+    }
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+        const int b = 4 + 8 * d;
+        const D2 s01 = two_sum(f[b], f[b + 1]), d01 = two_diff(f[b], f[b + 1]);
+        const D2 s23 = two_sum(f[b + 2], f[b + 3]), d23 = two_diff(f[b + 2], f[b + 3]);
+        E[d] = dd_add(s01, s23);
+        AY[2 + d] = dd_sub(s01, s23);
+        AX[2 + d] = dd_sub(d01, d23);
+    }
+    // slot -> orbit: 0 -> 0, 1 -> 2, 2 -> 1, 3 -> 3
+    m1 = dd_norm(dd_add(dd_add(P[0], P[1]), dd_add(E[0], E[1])));
+    m2 = dd_norm(dd_add(dd_add(dd_mul_c(AX[0], C.ch[0], C.cl[0]), dd_mul_c(AX[1], C.ch[2], C.cl[2])),
+                        dd_add(dd_mul_c(AX[2], C.ch[1], C.cl[1]), dd_mul_c(AX[3], C.ch[3], C.cl[3]))));
+    m3 = dd_norm(dd_add(dd_add(dd_mul_c(AY[0], C.ch[0], C.cl[0]), dd_mul_c(AY[1], C.ch[2], C.cl[2])),
+                        dd_add(dd_mul_c(AY[2], C.ch[1], C.cl[1]), dd_mul_c(AY[3], C.ch[3], C.cl[3]))));
+    m4 = dd_norm(dd_add(dd_add(dd_mul_c(P[0], C.wh[0], C.wl[0]), dd_mul_c(P[1], C.wh[2], C.wl[2])),
+                        dd_add(dd_mul_c(E[0], C.wh[1], C.wl[1]), dd_mul_c(E[1], C.wh[3], C.wl[3]))));
+}
+
 // Double-float recovery: rho, u, T by corrected quotients on the FP32 pipes.
 __device__ __forceinline__ void recover_pair_df(const V2* f, const DfConst& C, V2& rho, V2& ux,
                                                 V2& uy, V2& T, bool& ig0, bool& ig1, bool& ok0,
@@ -227,7 +289,7 @@ __device__ __forceinline__ void recover_pair_fast(const V2* f, const DfConst& C,
         recover_pair_df(f, C, rho, ux, uy, T, ig0, ig1, ok0, ok1);
     } else {
         D2 m1, m2, m3, m4;
-        conserved_pair(f, C, m1, m2, m3, m4);
+        conserved_pair_u(f, C, m1, m2, m3, m4);
         double u0, v0, t0, u1, v1, t1;
         const double r0 = df_to_f64_fast(m1.hi.x(), m1.lo.x());
         const double r1 = df_to_f64_fast(m1.hi.y(), m1.lo.y());
