@@ -359,7 +359,7 @@ __device__ __forceinline__ Mac recover_row(float* smem_f, float* ring, int r, in
 
 // per-thread TNE statistics of one strip (FP32) and of the whole launch (min, max)
 struct TneAcc {
-    float sum[TNE_K], abs[TNE_K], dsum, d2sum;
+    V2 sum[TNE_K], abs[TNE_K], dsum, d2sum; // the two cells of the thread apart
 };
 
 // ---------------- the update of one row by one warp pair -------------------------
@@ -393,20 +393,32 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
     }
     // TNE statistics of the state being stepped (Eqs. (90)-(91)); a cell past the grid's
     // last column contributes nothing
-    if (do_tne && act0) {
+    if (do_tne && act1) {
         V2 d2(0.f);
 #pragma unroll
         for (int k = 0; k < TNE_K; k++) {
-            const V2 Dk = act1 ? m[k + 4] : V2(m[k + 4].x(), 0.f);
+            const V2 Dk = m[k + 4];
             d2 = fma(Dk, Dk, d2);
-            acc.sum[k] += Dk.x() + Dk.y();
-            acc.abs[k] += fabsf(Dk.x()) + fabsf(Dk.y());
-            const float hi = act1 ? Dk.y() : Dk.x();
-            tmin[k] = fmin3(tmin[k], Dk.x(), hi);
-            tmax[k] = fmax3(tmax[k], Dk.x(), hi);
+            acc.sum[k] += Dk;
+            acc.abs[k] += V2(fabsf(Dk.x()), fabsf(Dk.y()));
+            tmin[k] = fmin3(tmin[k], Dk.x(), Dk.y());
+            tmax[k] = fmax3(tmax[k], Dk.x(), Dk.y());
         }
-        acc.dsum += sqrt_approx(d2.x()) + sqrt_approx(d2.y());
-        acc.d2sum += d2.x() + d2.y();
+        acc.dsum += V2(sqrt_approx(d2.x()), sqrt_approx(d2.y()));
+        acc.d2sum += d2;
+    } else if (do_tne && act0) { // the last cell of a row, alone in its pair
+        float d2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < TNE_K; k++) {
+            const float Dk = m[k + 4].x();
+            d2 = fmaf(Dk, Dk, d2);
+            acc.sum[k] += V2(Dk, 0.f);
+            acc.abs[k] += V2(fabsf(Dk), 0.f);
+            tmin[k] = fminf(tmin[k], Dk);
+            tmax[k] = fmaxf(tmax[k], Dk);
+        }
+        acc.dsum += V2(sqrt_approx(d2), 0.f);
+        acc.d2sum += V2(d2, 0.f);
     }
 
     // grad u: x from the (u, v) row y (halo columns included), y from rows y+-1
@@ -593,8 +605,8 @@ __global__ void __launch_bounds__(MT, 2)
         const uint32_t q0 = q_issued;
         TneAcc acc;
 #pragma unroll
-        for (int k = 0; k < TNE_K; k++) acc.sum[k] = acc.abs[k] = 0.f;
-        acc.dsum = acc.d2sum = 0.f;
+        for (int k = 0; k < TNE_K; k++) acc.sum[k] = acc.abs[k] = V2(0.f);
+        acc.dsum = acc.d2sum = V2(0.f);
 
         __syncthreads(); // the previous strip is done with the ring
         for (int j = 0; j < npairs && j < NMB; j++)
@@ -651,11 +663,11 @@ __global__ void __launch_bounds__(MT, 2)
             float* part = ring;
 #pragma unroll
             for (int k = 0; k < TNE_K; k++) {
-                part[k * MT + tid] = acc.sum[k];
-                part[(TNE_K + k) * MT + tid] = acc.abs[k];
+                part[k * MT + tid] = acc.sum[k].x() + acc.sum[k].y();
+                part[(TNE_K + k) * MT + tid] = acc.abs[k].x() + acc.abs[k].y();
             }
-            part[2 * TNE_K * MT + tid] = acc.dsum;
-            part[(2 * TNE_K + 1) * MT + tid] = acc.d2sum;
+            part[2 * TNE_K * MT + tid] = acc.dsum.x() + acc.dsum.y();
+            part[(2 * TNE_K + 1) * MT + tid] = acc.d2sum.x() + acc.d2sum.y();
             __syncthreads();
             double s2 = 0.0;
             if (tid < 4 * NSUM) {

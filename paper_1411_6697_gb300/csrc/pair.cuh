@@ -277,6 +277,23 @@ __device__ __forceinline__ float d2f_fast(double x)
 }
 __device__ __forceinline__ double df_to_f64_fast(float hi, float lo) { return f2d_fast(hi) + f2d_fast(lo); }
 
+// FP64 recovery of one cell with fewer FP64 operations: 1/m1 seeded by a double-float
+// reciprocal formed on the FP32 pipes (the FP32 estimate r corrected by r (1 - m1 r),
+// about 46 correct bits) and finished by one FP64 Newton step; u = m2 q, v = m3 q; and
+// T = q (m4 - m2 u - m3 v) / (D+I), which equals (m4 q - u^2 - v^2) / (D+I).
+__device__ __forceinline__ void recover_one_f64_fast(float m1h, float m1l, double m1, double m2,
+                                                     double m3, double m4, double inv_DI,
+                                                     double& u, double& v, double& t)
+{
+    const float r = rcp_approx(m1h);
+    const float e = fmaf(-m1h, r, 1.0f) - m1l * r; // 1 - m1 r to FP32 accuracy
+    double q = f2d_fast(r) + f2d_fast(r * e);
+    q = ::fma(q, ::fma(-m1, q, 1.0), q);
+    u = m2 * q;
+    v = m3 * q;
+    t = ::fma(-m3, v, ::fma(-m2, u, m4)) * (q * inv_DI);
+}
+
 // recover_pair with the branch-free conversions; cells whose conserved sums are not
 // finite in FP32 are flagged before anything is converted.
 template <int REC>
@@ -293,12 +310,12 @@ __device__ __forceinline__ void recover_pair_fast(const V2* f, const DfConst& C,
         double u0, v0, t0, u1, v1, t1;
         const double r0 = df_to_f64_fast(m1.hi.x(), m1.lo.x());
         const double r1 = df_to_f64_fast(m1.hi.y(), m1.lo.y());
-        recover_one_f64(m1.hi.x(), r0, df_to_f64_fast(m2.hi.x(), m2.lo.x()),
-                        df_to_f64_fast(m3.hi.x(), m3.lo.x()), df_to_f64_fast(m4.hi.x(), m4.lo.x()),
-                        K.inv_DId, u0, v0, t0);
-        recover_one_f64(m1.hi.y(), r1, df_to_f64_fast(m2.hi.y(), m2.lo.y()),
-                        df_to_f64_fast(m3.hi.y(), m3.lo.y()), df_to_f64_fast(m4.hi.y(), m4.lo.y()),
-                        K.inv_DId, u1, v1, t1);
+        recover_one_f64_fast(m1.hi.x(), m1.lo.x(), r0, df_to_f64_fast(m2.hi.x(), m2.lo.x()),
+                             df_to_f64_fast(m3.hi.x(), m3.lo.x()), df_to_f64_fast(m4.hi.x(), m4.lo.x()),
+                             K.inv_DId, u0, v0, t0);
+        recover_one_f64_fast(m1.hi.y(), m1.lo.y(), r1, df_to_f64_fast(m2.hi.y(), m2.lo.y()),
+                             df_to_f64_fast(m3.hi.y(), m3.lo.y()), df_to_f64_fast(m4.hi.y(), m4.lo.y()),
+                             K.inv_DId, u1, v1, t1);
         rho = m1.hi; // the exact sum rounded to FP32
         ux = V2(d2f_fast(u0), d2f_fast(u1));
         uy = V2(d2f_fast(v0), d2f_fast(v1));
