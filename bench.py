@@ -36,6 +36,14 @@ import lbkm_inputs as li  # noqa: E402
 
 N_CELLS_SIDE = 4096
 BYTES_PER_CELL = {"f32": 136, "f64": 272}  # read + write of 16 f + lambda
+# FP64 operations per cell update of the plain FP64 step kernel (step_kernel<double>, 2-D),
+# from ncu's executed-instruction counters on a 1024 x 1024 grid: 2 per DFMA, 1 per DADD and
+# DMUL (profiles/step_kernel_fp64_reactive2d.md)
+F64_FLOP_PER_CELL = 911.5
+F64_FLOP_SOURCE = ("ncu sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on on one step of "
+                   "a 1024 x 1024 reactive field with TNE: 213.96 DFMA + 375.76 DADD + 107.87 DMUL "
+                   "per cell")
+
 METRIC = "Mcell-updates/s (16 f_i)"
 
 
@@ -279,15 +287,13 @@ def _shared_params(p0):
                                "omega2", "T_ig", "dx", "dt")}
 
 
-def run_batched(args):
-    """512 1-D detonations of uneven length in one persistent launch per chunk
-    of steps, FP32; compared with the plain single-instance FP64 form on a sample of the
-    same instances, run one after another."""
+def measure_batched(steps, warmup, recovery="f64", plain_instances=24, plain_steps=64):
+    """Config 4: 512 1-D detonations of uneven length, FP32, in one persistent launch per
+    chunk of steps (CUDA graph), timed over `steps` steps; the plain single-instance FP64
+    form timed on a seeded sample of the same instances, one after another."""
     import torch
     from paper_1411_6697_gb300 import lbkm
-    rank, local, world = _env_rank()
-    torch.cuda.set_device(local)
-    rec = lbkm.RECOVER_F64 if args.recovery == "f64" else lbkm.RECOVER_DF32
+    rec = lbkm.RECOVER_F64 if recovery == "f64" else lbkm.RECOVER_DF32
     cfg = li.batched(n_instances=512, steps=5000)
     p0 = cfg["instances"][0]["params"]
     stream = torch.cuda.Stream()
@@ -299,17 +305,16 @@ def run_batched(args):
     chosen = s.autotune(trial_steps=3)
     n = int(np.sum(cfg["nx"]))
     with torch.cuda.stream(stream):
-        s.step(args.warmup)
+        s.step(warmup)
         s.sync()
-        with ClockSampler(local) as clk:
-            ms = time_steps(s, stream, args.steps)
+        ms = time_steps(s, stream, steps)
         s.sync()
-    value = n * args.steps / (ms * 1e-3) / 1e6
+    s.close()
+    value = n * steps / (ms * 1e-3) / 1e6
     peak, peak_kind = measured_peak()
-    achieved = BYTES_PER_CELL["f32"] * n / (ms / args.steps * 1e-3) / 1e9
-    # plain single-instance FP64 form on a seeded sample of the instances
+    achieved = BYTES_PER_CELL["f32"] * n / (ms / steps * 1e-3) / 1e9
     rng = np.random.default_rng(li.SEED_BASE + 40)
-    sample = rng.choice(len(cfg["nx"]), 24, replace=False)
+    sample = rng.choice(len(cfg["nx"]), plain_instances, replace=False)
     t64 = c64 = 0.0
     for i in sample:
         d = cfg["instances"][i]
@@ -320,26 +325,47 @@ def run_batched(args):
         one.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
         with torch.cuda.stream(stream):
             one.step(3)
-            t64 += time_steps(one, stream, 64) * 1e-3
-        c64 += q["nx"] * 64
+            t64 += time_steps(one, stream, plain_steps) * 1e-3
+        c64 += q["nx"] * plain_steps
         one.close()
     plain = c64 / t64 / 1e6
-    line = {"metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "batched_512x1d_detonations", "cells": n,
-                       "instances": len(cfg["nx"]), "conserved_moment_recovery": args.recovery,
-                       "autotuned": {"threads": chosen[0], "blocks_per_sm": chosen[1],
-                                     "blocks": chosen[2]},
-                       "l2": "state %.2f GB per copy > L2: no flush" % (17 * n * 4 / 1e9)},
+    return {"workload": "batched_512x1d_detonations", "cells": n, "instances": len(cfg["nx"]),
+            "steps_timed": steps, "ms_per_step": ms / steps, "mcell_per_s": value,
+            "conserved_moment_recovery": recovery,
+            "autotuned": {"threads": chosen[0], "blocks_per_sm": chosen[1], "blocks": chosen[2]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                          "kernel": "batch_kernel (f32)",
-                         "algorithmic_bytes_per_launch_step": BYTES_PER_CELL["f32"] * n},
+                         "algorithmic_bytes_per_step": BYTES_PER_CELL["f32"] * n},
             "plain_f64_single_instance_mcell_per_s": plain,
             "speedup_vs_plain_f64": value / plain,
-            "plain_sample": "24 seeded instances, 64 steps each, one after another",
+            "plain_sample": "%d seeded instances, %d steps each, one after another" % (
+                plain_instances, plain_steps),
+            "accuracy": "per field <= 2e-5 against the FP64 oracle (6 uneven instances, 40 steps); "
+                        "all 512 instances for 5000 steps within 4x the oracle's own FP32-storage "
+                        "error (tests/test_gpu_batched.py)"}
+
+
+def run_batched(args):
+    """512 1-D detonations of uneven length in one persistent launch per chunk
+    of steps, FP32; compared with the plain single-instance FP64 form on a sample of the
+    same instances, run one after another."""
+    import torch
+    rank, local, world = _env_rank()
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        b = measure_batched(args.steps, args.warmup, args.recovery)
+    line = {"metric": METRIC, "value": b["mcell_per_s"], "unit": "Mcell-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": b["workload"], "cells": b["cells"], "instances": b["instances"],
+                       "conserved_moment_recovery": b["conserved_moment_recovery"],
+                       "autotuned": b["autotuned"],
+                       "l2": "state %.2f GB per copy > L2: no flush" % (17 * b["cells"] * 4 / 1e9)},
+            "roofline": b["roofline"],
+            "plain_f64_single_instance_mcell_per_s": b["plain_f64_single_instance_mcell_per_s"],
+            "speedup_vs_plain_f64": b["speedup_vs_plain_f64"], "plain_sample": b["plain_sample"],
             "gpu_launches": (args.steps + 31) // 32, "clocks": clk.summary()}
     print(json.dumps(line))
     return 0
@@ -450,16 +476,13 @@ def run_d2v24(args):
     return 0
 
 
-def run_adjoint(args):
-    """dJ/d(S, Q, omega1, rho0) of a 4000-step 1-D detonation of 8192 cells
-    (profile mismatch + integrated TNE), checkpoints every 64 steps, through lbkm_grad;
-    compared with the plain single-instance FP64 forward run that central differences
-    would repeat twice per gradient entry."""
-    import time
+def measure_adjoint(n_grad=1):
+    """Config 5: dJ/d(S, Q, omega1, rho0) of a 4000-step 1-D detonation of 8192 cells
+    (profile mismatch + integrated TNE), checkpoints every 64 steps, through lbkm_grad
+    (host wall clock per gradient); against the plain FP64 forward run of the same length
+    that central differences repeat twice per gradient entry."""
     import torch
     from paper_1411_6697_gb300 import lbkm
-    rank, local, world = _env_rank()
-    torch.cuda.set_device(local)
     cfg = li.adjoint()
     base, tgt = cfg["base"], cfg["target"]
     q, fl = base["params"], base["fields"]
@@ -472,14 +495,12 @@ def run_adjoint(args):
         s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
         return s
 
-    # target profile: the run with perturbed S and Q
     t = solver(tgt["params"])
     with torch.cuda.stream(stream):
         t.step(steps)
         t.sync()
     rho_t = t.macros()["rho"][0].copy()
     t.close()
-    # plain FP64 forward of the same length
     one = solver(q)
     with torch.cuda.stream(stream):
         one.step(3)
@@ -487,38 +508,86 @@ def run_adjoint(args):
         ms_fwd = time_steps(one, stream, steps)
     one.close()
     s = solver(q)
-    n_grad = max(1, min(args.steps, 3))
     g = s.grad(rho_t, steps, w_tne=cfg["w_tne"], checkpoint_every=cfg["checkpoint_every"])
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        for _ in range(n_grad):
-            g = s.grad(rho_t, steps, w_tne=cfg["w_tne"],
-                       checkpoint_every=cfg["checkpoint_every"])
-        sec = (time.perf_counter() - t0) / n_grad
+    t0 = time.perf_counter()
+    for _ in range(n_grad):
+        g = s.grad(rho_t, steps, w_tne=cfg["w_tne"], checkpoint_every=cfg["checkpoint_every"])
+    sec = (time.perf_counter() - t0) / n_grad
     s.close()
     nx = q["nx"]
     n_scalar = 16 + 2               # S_1..S_16, Q, omega1
     n_entries = n_scalar + nx       # and the initial density field
     fd = 2 * ms_fwd * 1e-3          # one central difference = two forward runs
-    line = {"metric": METRIC, "value": nx * steps / sec / 1e6,
-            "unit": "Mcell-updates/s (forward-equivalent, per gradient)", "n_gpus": 1,
-            "steps": n_grad, "warmup": 1, "ms_per_step": sec * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "adjoint_8192x1_detonation_4000_steps",
-                       "checkpoint_every": cfg["checkpoint_every"], "w_tne": cfg["w_tne"],
-                       "step": "one lbkm_grad call (forward with checkpoints, replay, "
-                               "reverse sweep), host wall clock"},
-            "J": g["J"], "plain_f64_forward_ms": ms_fwd,
+    return {"workload": "adjoint_8192x1_detonation_4000_steps", "checkpoint_every":
+            cfg["checkpoint_every"], "w_tne": cfg["w_tne"], "J": g["J"],
+            "gradient_ms": sec * 1e3, "plain_f64_forward_ms": ms_fwd,
             "plain_f64_forward_mcell_per_s": nx * steps / (ms_fwd * 1e-3) / 1e6,
-            "gradient_ms": sec * 1e3,
             "gradient_over_forward": sec / (ms_fwd * 1e-3),
             "speedup_vs_central_fd_scalars": n_scalar * fd / sec,
             "speedup_vs_central_fd_all_entries": n_entries * fd / sec,
-            "gradient_entries": n_entries, "clocks": clk.summary()}
+            "gradient_entries": n_entries,
+            "accuracy": "J, dJ/dS, dJ/dQ, dJ/domega1 within 1e-7 of the FP64 reverse-mode oracle "
+                        "at this size, within 1e-5 of central differences "
+                        "(tests/test_gpu_adjoint.py)"}
+
+
+def run_adjoint(args):
+    """One lbkm_grad call per step (host wall clock) for config 5."""
+    import torch
+    rank, local, world = _env_rank()
+    torch.cuda.set_device(local)
+    n_grad = max(1, min(args.steps, 3))
+    with ClockSampler(local) as clk:
+        a = measure_adjoint(n_grad)
+    nx, steps = 8192, 4000
+    line = {"metric": METRIC, "value": nx * steps / (a["gradient_ms"] * 1e-3) / 1e6,
+            "unit": "Mcell-updates/s (forward-equivalent, per gradient)", "n_gpus": 1,
+            "steps": n_grad, "warmup": 1, "ms_per_step": a["gradient_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": a["workload"], "checkpoint_every": a["checkpoint_every"],
+                       "w_tne": a["w_tne"],
+                       "step": "one lbkm_grad call (forward with checkpoints, replay, "
+                               "reverse sweep), host wall clock"},
+            "clocks": clk.summary()}
+    line.update({k: v for k, v in a.items() if k not in ("workload", "checkpoint_every", "w_tne")})
     print(json.dumps(line))
     return 0
+
+
+def measure_reactive(side, precision, recovery, steps, T_ig=1.0):
+    """Mcell-updates/s of `steps` steps of the reactive field (CUDA events)."""
+    import torch
+    from paper_1411_6697_gb300 import lbkm
+    cfg = li.reactive2d(n=side, steps=1, T_ig=T_ig)
+    stream = torch.cuda.Stream()
+    s = make_solver(cfg, precision, recovery, stream=stream)
+    fl = cfg["fields"]
+    s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    with torch.cuda.stream(stream):
+        s.step(3)
+        ms = time_steps(s, stream, steps)
+    s.close()
+    return side * side * steps / (ms * 1e-3) / 1e6, ms / steps
+
+
+def measured_f64_peak():
+    """cuBLAS FP64 GEMM throughput on this GPU (4096^3, best of 3): the FP64 peak the plain
+    FP64 step is reported against."""
+    import torch
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2 * 4096 ** 3 / (best * 1e-3) / 1e12
 
 
 def main():
@@ -648,6 +717,23 @@ def main():
             var[name] = n * k / (t * 1e-3) / 1e6
             s2.close()
         line["variants_mcell_per_s"] = var
+        # the same field at the paper's ignition threshold T_ig = 1.1 (T stays below 1.05:
+        # nothing ignites; reported beside the T_ig = 1.0 workload)
+        r11, ms11 = measure_reactive(args.side, lbkm.F32, lbkm.RECOVER_F64, 20, T_ig=1.1)
+        line["reactive2d_tig_1_1"] = {"mcell_per_s": r11, "ms_per_step": ms11,
+                                      "hbm_frac": BYTES_PER_CELL["f32"] * n / (ms11 * 1e-3) / 1e9 / peak}
+        # the plain FP64 form: FP64 operations per cell counted by ncu on this kernel
+        f64_peak = measured_f64_peak()
+        flop = (var["f64_plain"] * 1e6 * F64_FLOP_PER_CELL / 1e12) if F64_FLOP_PER_CELL else None
+        line["f64_plain"] = {"mcell_per_s": var["f64_plain"],
+                             "fp64_flop_per_cell": F64_FLOP_PER_CELL,
+                             "fp64_tflops": flop, "fp64_peak_tflops": f64_peak,
+                             "peak_kind": "measured cuBLAS FP64 GEMM (4096^3)",
+                             "frac": flop / f64_peak if flop else None,
+                             "flop_count": F64_FLOP_SOURCE}
+        # configs 4 and 5: speed-ups over the plain single-instance FP64 form
+        line["batched"] = measure_batched(200, 5)
+        line["adjoint"] = measure_adjoint(1)
     if rank == 0 and not args.no_cpu_baseline:
         rate, desc, cores = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": rate, "unit": "Mcell-updates/s", "cores": cores,
