@@ -170,12 +170,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_solver(cfg, precision, recovery, stream=None, tne_every=1):
+def make_solver(cfg, precision, recovery, stream=None, tne_every=1, S=None, collision=0):
     from paper_1411_6697_gb300 import lbkm
     p = cfg["params"]
     return lbkm.Solver(nx=p["nx"], ny=p["ny"], precision=precision, recovery=recovery,
                        gamma=p["gamma"], orbit_kind=p["orbit_kind"], orbit_speed=p["orbit_speed"],
-                       orbit_eta=p["orbit_eta"], S=p["S"], Q=p["Q"], omega1=p["omega1"],
+                       orbit_eta=p["orbit_eta"], S=p["S"] if S is None else S, Q=p["Q"],
+                       omega1=p["omega1"], collision=collision,
                        omega2=p["omega2"], T_ig=p["T_ig"], dx=p["dx"], dy=p["dx"], dt=p["dt"],
                        bc=(p["bc_x"], p["bc_y"]), tne_every=tne_every,
                        tne_capacity=4096, stream=stream)
@@ -731,6 +732,21 @@ def main():
                              "peak_kind": "measured cuBLAS FP64 GEMM (4096^3)",
                              "frac": flop / f64_peak if flop else None,
                              "flop_count": F64_FLOP_SOURCE}
+        # single- against multiple-relaxation-time cost (Sec. V, Table I: the paper's MRT
+        # D2V24 takes 3 % longer than its SRT form on one CPU core): equal rates, no TNE,
+        # the fast path (collision 0) against the moment-space kernel (collision 1)
+        eq = {}
+        for form, coll in (("srt", 0), ("mrt", 1)):
+            s3 = make_solver(cfg, lbkm.F32, lbkm.RECOVER_F64, stream=stream, tne_every=0,
+                             S=np.full(16, 5e4), collision=coll)
+            s3.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+            with torch.cuda.stream(stream):
+                s3.step(3)
+                t3 = time_steps(s3, stream, 20)
+            eq[form + "_mcell_per_s"] = n * 20 / (t3 * 1e-3) / 1e6
+            s3.close()
+        eq["mrt_over_srt_time"] = eq["srt_mcell_per_s"] / eq["mrt_mcell_per_s"]
+        line["equal_rates_no_tne"] = eq
         # configs 4 and 5: speed-ups over the plain single-instance FP64 form
         line["batched"] = measure_batched(200, 5)
         line["adjoint"] = measure_adjoint(1)

@@ -139,6 +139,23 @@ typedef struct {
                               u2 = 3/4 u^n + 1/4 E(E(u^n)), u^{n+1} = 1/3 u^n + 2/3 E(u2)
                               (third order; three launches per step, a third state
                               copy); TNE of u^n; not for batched instances or lbkm_grad */
+    int32_t collision;     /* 0: the single-relaxation-time fast path wherever it applies
+                              (S_5..S_16 all equal, tne_every = 0, LBKM_F32 on a 2-D grid,
+                              forward Euler, periodic or zero-gradient sides; Sec. V): the
+                              collision -S (f - f^eq) + C of Eq. (87) in velocity space
+                              needs one inverse transform and no forward one; 1: always
+                              the moment-space form of Eq. (1) */
+    /* Caller-owned device memory (an interface of this library, no counterpart in the
+       paper): if alloc is not NULL, every device buffer of the handle and of its calls
+       (states, TNE partials and history, counters, batched tables, temporaries of
+       init_fields / macros / tne, workspaces of lbkm_grad and lbkm_autotune) comes from
+       alloc(bytes, cuda_stream, alloc_ctx) and goes back through free(ptr, cuda_stream,
+       alloc_ctx), with the handle's stream; a temporary is freed only after that stream
+       has been synchronised. Blocks must be aligned to 256 bytes (else LBKM_EINVAL); NULL
+       from alloc gives LBKM_ENOMEM. Set both or neither. */
+    void* (*alloc)(size_t bytes, void* cuda_stream, void* ctx);
+    void (*free)(void* ptr, void* cuda_stream, void* ctx);
+    void* alloc_ctx;
 } lbkm_params;
 
 /* Grid-wide TNE measures of one state (Sec. VI). Sums are weighted by dx*dy;

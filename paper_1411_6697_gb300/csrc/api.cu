@@ -41,6 +41,7 @@ struct lbkm {
     void* buf3;  // the middle-stage state of the three-stage scheme (time_scheme 2)
     TmaDesc tm_load[3], tm_store[3]; // tensor maps of buf[0], buf[1], buf3 (FP32 2-D)
     int cur;
+    int srt;     // the FP32 2-D step takes the single-relaxation-time fast path
     double* partials;
     int grid, tgrid;
     DevCounters* ctr;
@@ -98,6 +99,49 @@ const void* model_ptr(const lbkm* h)
 // buffers (u1 = E(u^n) into buf[1-from]); stage 2: last stage from `src` (u1 for RK2, u2
 // for RK3) back into buf[from] with weights (wp, wn) on (u^n, E(src)); stage 3: the
 // middle RK3 stage, u2 = 3/4 u^n + 1/4 E(u1) into buf3
+// Device memory of a handle: the caller's allocator (lbkm_params.alloc / free, with the
+// handle's stream) when it set one, else cudaMalloc / cudaFree.
+cudaError_t dmalloc(const lbkm* h, void** ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    if (!h->p.alloc) return cudaMalloc(ptr, bytes);
+    void* q = h->p.alloc(bytes, (void*)h->stream, h->p.alloc_ctx);
+    if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(q) & 255u) {
+        h->p.free(q, (void*)h->stream, h->p.alloc_ctx);
+        return cudaErrorMisalignedAddress;
+    }
+    *ptr = q;
+    return cudaSuccess;
+}
+template <typename T>
+cudaError_t dmalloc(const lbkm* h, T** ptr, size_t bytes)
+{
+    return dmalloc(h, reinterpret_cast<void**>(ptr), bytes);
+}
+void dfree(const lbkm* h, void* ptr)
+{
+    if (!ptr) return;
+    if (h->p.alloc)
+        h->p.free(ptr, (void*)h->stream, h->p.alloc_ctx);
+    else
+        cudaFree(ptr);
+}
+// a temporary of one call: freed (after its stream has drained) when the call returns
+struct DevTemp {
+    const lbkm* h;
+    void* p = nullptr;
+    explicit DevTemp(const lbkm* hh) : h(hh) {}
+    ~DevTemp()
+    {
+        if (p) {
+            cudaStreamSynchronize(h->stream);
+            dfree(h, p);
+        }
+    }
+};
+
 StepLaunch step_args(const lbkm* h, int from, int stage = 0, const void* src = nullptr,
                      double wp = 0.0, double wn = 1.0)
 {
@@ -118,6 +162,7 @@ StepLaunch step_args(const lbkm* h, int from, int stage = 0, const void* src = n
     auto map_of = [&](const void* b) { return b == h->buf[0] ? 0 : (b == h->buf[1] ? 1 : 2); };
     a.tm_in = &h->tm_load[map_of(a.in)];
     a.tm_out = &h->tm_store[map_of(a.out)];
+    a.srt = h->srt;
     return a;
 }
 
@@ -140,17 +185,17 @@ void release(lbkm* h)
     for (int i = 0; i < 2; i++)
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
-    cudaFree(h->buf[0]);
-    cudaFree(h->buf[1]);
-    cudaFree(h->buf3);
-    cudaFree(h->partials);
-    cudaFree(h->ctr);
-    cudaFree(h->hist);
-    cudaFree(h->tne_out);
-    cudaFree(h->d_inst);
-    cudaFree(h->d_items);
-    cudaFree(h->d_bar);
-    cudaFree(h->d_inst_tne);
+    dfree(h, h->buf[0]);
+    dfree(h, h->buf[1]);
+    dfree(h, h->buf3);
+    dfree(h, h->partials);
+    dfree(h, h->ctr);
+    dfree(h, h->hist);
+    dfree(h, h->tne_out);
+    dfree(h, h->d_inst);
+    dfree(h, h->d_items);
+    dfree(h, h->d_bar);
+    dfree(h, h->d_inst_tne);
 }
 
 // Work items of the batched kernel for segments of `seg` cells.
@@ -159,9 +204,9 @@ cudaError_t build_items(lbkm* h, int seg)
     std::vector<BatchItem> items;
     for (int i = 0; i < h->n_inst; i++)
         for (int x0 = 0; x0 < h->inst_nx[i]; x0 += seg) items.push_back({i, x0});
-    cudaFree(h->d_items);
+    dfree(h, h->d_items);
     h->d_items = nullptr;
-    cudaError_t e = cudaMalloc(&h->d_items, sizeof(BatchItem) * items.size());
+    cudaError_t e = dmalloc(h, &h->d_items, sizeof(BatchItem) * items.size());
     if (e != cudaSuccess) return e;
     h->nitems = (int)items.size();
     return cudaMemcpy(h->d_items, items.data(), sizeof(BatchItem) * items.size(),
@@ -312,6 +357,10 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
                     "time_scheme must be 0 (Euler), 1 (SSP-RK2) or 2 (SSP-RK3)");
     if (p.tne_every < 0 || p.tne_capacity < 1)
         return fail(nullptr, LBKM_EINVAL, "tne_every must be >= 0 and tne_capacity >= 1");
+    if (p.collision != 0 && p.collision != 1)
+        return fail(nullptr, LBKM_EINVAL, "collision must be 0 (fast path where it applies) or 1");
+    if ((p.alloc == nullptr) != (p.free == nullptr))
+        return fail(nullptr, LBKM_EINVAL, "alloc and free must be set together");
 
     lbkm* h = new lbkm();
     h->p = p;
@@ -362,21 +411,33 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
     h->stream = (cudaStream_t)cuda_stream;
 
     auto bail = [&](cudaError_t e, const char* what) {
-        std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+        std::string m = std::string(what) + ": " +
+                        (e == cudaErrorMisalignedAddress ? "alloc returned a block not aligned to 256 bytes"
+                                                         : cudaGetErrorString(e));
         release(h);
         delete h;
-        return fail(nullptr, e == cudaErrorMemoryAllocation ? LBKM_ENOMEM : LBKM_ECUDA, "%s",
-                    m.c_str());
+        return fail(nullptr,
+                    e == cudaErrorMemoryAllocation ? LBKM_ENOMEM
+                    : e == cudaErrorMisalignedAddress ? LBKM_EINVAL : LBKM_ECUDA,
+                    "%s", m.c_str());
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&h->buf[0], h->state_bytes_dev)) != cudaSuccess) return bail(e, "state A");
-    if ((e = cudaMalloc(&h->buf[1], h->state_bytes_dev)) != cudaSuccess) return bail(e, "state B");
+    if ((e = dmalloc(h, &h->buf[0], h->state_bytes_dev)) != cudaSuccess) return bail(e, "state A");
+    if ((e = dmalloc(h, &h->buf[1], h->state_bytes_dev)) != cudaSuccess) return bail(e, "state B");
     if ((e = cudaMemset(h->buf[0], 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemset(h->buf[1], 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
     if (p.time_scheme == 2) {
-        if ((e = cudaMalloc(&h->buf3, h->state_bytes_dev)) != cudaSuccess) return bail(e, "state C");
+        if ((e = dmalloc(h, &h->buf3, h->state_bytes_dev)) != cudaSuccess) return bail(e, "state C");
         if ((e = cudaMemset(h->buf3, 0, h->state_bytes_dev)) != cudaSuccess) return bail(e, "memset");
     }
+    // single-relaxation-time fast path (Sec. V, Eq. (87)): equal R_5..R_16, no TNE,
+    // forward Euler, FP32 2-D, periodic or zero-gradient sides
+    bool equal = true;
+    for (int k = 5; k < 16; k++) equal = equal && p.S[k] == p.S[4];
+    h->srt = (p.collision == 0 && equal && p.tne_every == 0 && p.time_scheme == 0 &&
+              h->precision == LBKM_F32 && h->two_d && sbc[0] <= 1 && sbc[1] <= 1 && sbc[2] <= 1 &&
+              sbc[3] <= 1)
+                 ? 1 : 0;
     if (h->precision == LBKM_F32 && h->two_d) {
         void* bufs[3] = {h->buf[0], h->buf[1], h->buf3};
         for (int b = 0; b < 3; b++) {
@@ -390,13 +451,13 @@ lbkm_status lbkm_create(const lbkm_params* pin, void* cuda_stream, lbkm_t* out)
     if (h->grid < 1) return bail(cudaGetLastError(), "step grid");
     h->tgrid = tne_grid(h->nx, h->ny);
     int pg = h->grid > h->tgrid ? h->grid : h->tgrid;
-    if ((e = cudaMalloc(&h->partials, sizeof(double) * TNE_PART * (size_t)pg)) != cudaSuccess)
+    if ((e = dmalloc(h, &h->partials, sizeof(double) * TNE_PART * (size_t)pg)) != cudaSuccess)
         return bail(e, "partials");
-    if ((e = cudaMalloc(&h->ctr, sizeof(DevCounters))) != cudaSuccess) return bail(e, "counters");
+    if ((e = dmalloc(h, &h->ctr, sizeof(DevCounters))) != cudaSuccess) return bail(e, "counters");
     if ((e = cudaMemset(h->ctr, 0, sizeof(DevCounters))) != cudaSuccess) return bail(e, "memset");
-    if ((e = cudaMalloc(&h->hist, sizeof(TneRecord) * (size_t)p.tne_capacity)) != cudaSuccess)
+    if ((e = dmalloc(h, &h->hist, sizeof(TneRecord) * (size_t)p.tne_capacity)) != cudaSuccess)
         return bail(e, "history");
-    if ((e = cudaMalloc(&h->tne_out, sizeof(TneRecord))) != cudaSuccess) return bail(e, "tne out");
+    if ((e = dmalloc(h, &h->tne_out, sizeof(TneRecord))) != cudaSuccess) return bail(e, "tne out");
     if ((e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(e, "capture stream");
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "synchronize");
@@ -425,10 +486,12 @@ lbkm_status lbkm_init_fields(lbkm_t h, const double* rho, const double* ux, cons
     if (!h) return LBKM_EINVAL;
     if (!rho || !ux || !uy || !T) return fail(h, LBKM_EINVAL, "rho, ux, uy and T are required");
     const size_t n = (size_t)h->nx * h->ny, nb = n * sizeof(double);
+    DevTemp tt(h);
     double* tmp = nullptr;
     const double *r = rho, *u = ux, *v = uy, *t = T, *l = lambda;
     if (!on_device) {
-        CUDA_TRY(h, cudaMallocAsync((void**)&tmp, nb * 5, h->stream));
+        CUDA_TRY(h, dmalloc(h, &tt.p, nb * 5));
+        tmp = static_cast<double*>(tt.p);
         const double* src[5] = {rho, ux, uy, T, lambda};
         for (int k = 0; k < 5; k++) {
             if (!src[k]) continue;
@@ -443,7 +506,6 @@ lbkm_status lbkm_init_fields(lbkm_t h, const double* rho, const double* ux, cons
     h->cur = 0;
     CUDA_TRY(h, launch_init(h->precision, h->Kd, r, u, v, t, l, h->buf[0], h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->ctr, 0, sizeof(DevCounters), h->stream));
-    if (tmp) CUDA_TRY(h, cudaFreeAsync(tmp, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     h->initialized = true;
     h->host_steps = 0;
@@ -566,9 +628,10 @@ lbkm_status lbkm_macros(lbkm_t h, double* rho, double* ux, double* uy, double* T
     const size_t n = (size_t)h->nx * h->ny, nb = n * sizeof(double);
     double* outs[6] = {rho, ux, uy, T, p, lambda};
     double* dev[6] = {rho, ux, uy, T, p, lambda};
-    double* tmp = nullptr;
+    DevTemp tt(h);
     if (!on_device) {
-        CUDA_TRY(h, cudaMallocAsync((void**)&tmp, nb * 6, h->stream));
+        CUDA_TRY(h, dmalloc(h, &tt.p, nb * 6));
+        double* tmp = static_cast<double*>(tt.p);
         for (int k = 0; k < 6; k++) dev[k] = outs[k] ? tmp + k * n : nullptr;
     }
     CUDA_TRY(h, launch_macros(h->precision, h->Kd, h->buf[h->cur], dev[0], dev[1], dev[2], dev[3],
@@ -577,7 +640,6 @@ lbkm_status lbkm_macros(lbkm_t h, double* rho, double* ux, double* uy, double* T
         for (int k = 0; k < 6; k++)
             if (outs[k])
                 CUDA_TRY(h, cudaMemcpyAsync(outs[k], dev[k], nb, cudaMemcpyDeviceToHost, h->stream));
-        CUDA_TRY(h, cudaFreeAsync(tmp, h->stream));
     }
     return check_status(h);
 }
@@ -599,16 +661,16 @@ lbkm_status lbkm_tne(lbkm_t h, double* delta, lbkm_tne_global* g, int on_device)
     if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_tne before lbkm_init_fields");
     const size_t n = (size_t)h->nx * h->ny, nb = 16 * n * sizeof(double);
     double* dd = delta;
+    DevTemp tt(h);
     double* tmp = nullptr;
     if (delta && !on_device) {
-        CUDA_TRY(h, cudaMallocAsync((void**)&tmp, nb, h->stream));
-        dd = tmp;
+        CUDA_TRY(h, dmalloc(h, &tt.p, nb));
+        tmp = dd = static_cast<double*>(tt.p);
     }
     CUDA_TRY(h, launch_tne(h->precision, h->Kd, h->buf[h->cur], dd, h->partials, h->tgrid, h->ctr,
                            h->tne_out, h->p.dx * h->p.dy, h->stream));
     if (tmp) {
         CUDA_TRY(h, cudaMemcpyAsync(delta, tmp, nb, cudaMemcpyDeviceToHost, h->stream));
-        CUDA_TRY(h, cudaFreeAsync(tmp, h->stream));
     }
     TneRecord r;
     CUDA_TRY(h, cudaMemcpyAsync(&r, h->tne_out, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
@@ -751,13 +813,13 @@ lbkm_status lbkm_create_batched(const lbkm_params* pin, int32_t n_instances,
     h->inst_nx.assign(inst_nx, inst_nx + n_instances);
     h->wait_ns = 2000000000LL;
     h->phantom = 0;
-    cudaError_t e = cudaMalloc(&h->d_inst, sizeof(InstParam) * n_instances);
+    cudaError_t e = dmalloc(h, &h->d_inst, sizeof(InstParam) * n_instances);
     if (e == cudaSuccess)
         e = cudaMemcpy(h->d_inst, ip.data(), sizeof(InstParam) * n_instances,
                        cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_bar, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = dmalloc(h, &h->d_bar, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(h->d_bar, 0, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_inst_tne, sizeof(TneRecord) * n_instances);
+    if (e == cudaSuccess) e = dmalloc(h, &h->d_inst_tne, sizeof(TneRecord) * n_instances);
     int sms = 0, dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -825,8 +887,9 @@ lbkm_status lbkm_autotune(lbkm_t h, int32_t trial_steps, int32_t* chosen)
     CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     // keep the state and counters; every trial starts from them
-    void* saved = nullptr;
-    CUDA_TRY(h, cudaMalloc(&saved, h->state_bytes_dev));
+    DevTemp saved_t(h);
+    CUDA_TRY(h, dmalloc(h, &saved_t.p, h->state_bytes_dev));
+    void* saved = saved_t.p;
     DevCounters c0;
     const int cur0 = h->cur;
     const int64_t steps0 = h->host_steps;
@@ -872,7 +935,6 @@ lbkm_status lbkm_autotune(lbkm_t h, int32_t trial_steps, int32_t* chosen)
     }
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
-    cudaFree(saved);
     h->host_steps = steps0;
     h->cur = cur0;
     h->bt = best_bt;
@@ -912,20 +974,21 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     double *work = nullptr, *mats = nullptr;
     DevCounters* sctr = nullptr;
     auto cleanup = [&]() {
-        cudaFree(ck);
-        cudaFree(seg);
-        cudaFree(work);
-        cudaFree(mats);
-        cudaFree(sctr);
+        cudaStreamSynchronize(h->stream);
+        dfree(h, ck);
+        dfree(h, seg);
+        dfree(h, work);
+        dfree(h, mats);
+        dfree(h, sctr);
     };
     // work: mac 4n, mb 16n, loc 6n, gb 2n, fbA/fbB 32n, lbA/lbB 2n, rho_t n, drho0 n,
     //       pacc NPAR*G, jtne G, jmis G
     const size_t nwork = (size_t)nx * (4 + 16 + 6 + 2 + 32 + 2 + 1 + 1) + (size_t)(ADJ_NPAR + 2) * G;
-    cudaError_t e = cudaMalloc(&ck, SB * nck);
-    if (e == cudaSuccess) e = cudaMalloc(&seg, SB * (size_t)(C + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&work, sizeof(double) * nwork);
-    if (e == cudaSuccess) e = cudaMalloc(&mats, sizeof(double) * (256 + 256 + 16));
-    if (e == cudaSuccess) e = cudaMalloc(&sctr, sizeof(DevCounters));
+    cudaError_t e = dmalloc(h, &ck, SB * nck);
+    if (e == cudaSuccess) e = dmalloc(h, &seg, SB * (size_t)(C + 1));
+    if (e == cudaSuccess) e = dmalloc(h, &work, sizeof(double) * nwork);
+    if (e == cudaSuccess) e = dmalloc(h, &mats, sizeof(double) * (256 + 256 + 16));
+    if (e == cudaSuccess) e = dmalloc(h, &sctr, sizeof(DevCounters));
     if (e != cudaSuccess) {
         cleanup();
         return fail(h, e == cudaErrorMemoryAllocation ? LBKM_ENOMEM : LBKM_ECUDA,

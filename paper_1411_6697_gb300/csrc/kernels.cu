@@ -555,7 +555,7 @@ cudaError_t launch_step(int precision, int recovery, bool two_d, const void* K,
         return two_d ? K2D<double, 0>::launch(K, a, s) : K1D<double, 0>::launch(K, a, s);
     if (two_d) {
         const ModelConst<float>& Kf = *static_cast<const ModelConst<float>*>(K);
-        return launch_march(recovery | (general_sides(Kf.sbc) ? 2 : 0), Kf, a, s);
+        return launch_march(recovery | (general_sides(Kf.sbc) ? 2 : 0) | (a.srt ? 4 : 0), Kf, a, s);
     }
     return recovery == 1 ? K1D<float, 1>::launch(K, a, s) : K1D<float, 0>::launch(K, a, s);
 }

@@ -49,6 +49,7 @@ struct StepLaunch {
     double cell_area;    // dx * dy
     const TmaDesc* tm_in;  // host copies of the tensor maps of in (loads) and out (stores),
     const TmaDesc* tm_out; // FP32 2-D grids only
+    int srt;               // 1: single-relaxation-time collision (equal rates, no TNE)
 };
 
 // Grid-wide TNE record of the partials a step left (if its schedule reduced TNE): one

@@ -366,7 +366,7 @@ struct TneAcc {
 // Row y, the thread's cells x0 + 2t and x0 + 2t + 1 (active when act0 / act1), macros
 // mc recovered in the previous iteration; the results go to the output rows ob
 // (17 planes of BW floats).
-template <int REC, bool AVG>
+template <int REC, bool AVG, bool SRT>
 __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob, int y, int x0,
                                            int t, const ModelConst<float>& K, const StepLaunch& a,
                                            const Mac& mc, bool act0, bool act1, bool do_tne,
@@ -377,6 +377,29 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
     const V2 rho = mc.rho, ux = mc.ux, uy = mc.uy, T = mc.T;
     float* r0 = srow(ring, y);
 
+    // reaction over dt (Eq. (28)), decided by the recovered T
+    const V2 rT = rho * T;
+    const float* lm = r0 + 16 * PST;
+    const V2 lam0 = ldv(lm + lx);
+    const float ri0 = reaction_increment(lam0.x(), K.omega1 * rT.x(), K.omega2 * rT.x(), dt);
+    const float ri1 = reaction_increment(lam0.y(), K.omega1 * rT.y(), K.omega2 * rT.y(), dt);
+    const V2 dlam(mc.ig0 ? ri0 : 0.f, mc.ig1 ? ri1 : 0.f);
+    const V2 cr = dlam * K.chem;
+
+    V2 W[16]; // M^-1 of the moment-space collision, or of S f_hat^eq + C_hat (SRT)
+    if constexpr (SRT) {
+        // single-relaxation-time collision (Sec. V, Eq. (87)): Omega = -S (f - f^eq) + C
+        // with f^eq = M^-1 f_hat^eq and C = M^-1 C_hat, i.e. W - S f with
+        // W = M^-1 (S f_hat^eq + C_hat); the rates being equal, A_hat vanishes
+        // (Eqs. (3)-(4)) and no forward transform is needed
+        const float Srt = K.S[4];
+        V2 q[16], dq[16];
+        feq_moments(V2(K.DI), rho, ux, uy, T, q);
+        dfeq_dT(V2(K.DI), rho, ux, uy, T, dq);
+#pragma unroll
+        for (int k = 0; k < 16; k++) q[k] = k < 3 ? V2(Srt) * q[k] : fma(V2(Srt), q[k], dq[k] * cr);
+        inverse_moments(K, q, W);
+    } else {
     // moments, equilibrium, non-equilibrium parts (Delta_1..4 vanish)
     V2 m[16];
     {
@@ -436,20 +459,10 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
                       K.half_inv_dy;
     const V2 theta = (dux_dx + duy_dy) * K.inv_DI;
     const V2 shear = duy_dx + dux_dy;
-    const V2 rT = rho * T;
     const V2 A8 = (rT * K.A8c) * fma(V2(4.f) * ux, dux_dx - theta, V2(2.f) * uy * shear);
     const V2 A9 = (rT * K.A9c) * fma(V2(4.f) * uy, duy_dy - theta, V2(2.f) * ux * shear);
 
-    // reaction over dt (Eq. (28)), decided by the recovered T
-    const float* lm = r0 + 16 * PST;
-    const V2 lam0 = ldv(lm + lx);
-    const float ri0 = reaction_increment(lam0.x(), K.omega1 * rT.x(), K.omega2 * rT.x(), dt);
-    const float ri1 = reaction_increment(lam0.y(), K.omega1 * rT.y(), K.omega2 * rT.y(), dt);
-    const V2 dlam(mc.ig0 ? ri0 : 0.f, mc.ig1 ? ri1 : 0.f);
-    const V2 cr = dlam * K.chem;
-
     // collision in moment space and back
-    V2 W[16];
     {
         V2 dq[16], Om[16];
         dfeq_dT(V2(K.DI), rho, ux, uy, T, dq);
@@ -460,6 +473,8 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
         Om[7] += A8;
         Om[8] += A9;
         inverse_moments(K, Om, W);
+    }
+
     }
 
     // results into the output rows; a later SSP Runge-Kutta stage (AVG) writes
@@ -498,7 +513,11 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
     }
 
     // NND flux differences (upwind side fixed per velocity), Euler update
-    auto put = [&](int i, V2 f0, V2 adv) { store(i, fma(V2(dt), W[i] - adv, f0)); };
+    auto put = [&](int i, V2 f0, V2 adv) {
+        V2 w = W[i];
+        if constexpr (SRT) w = fma(V2(-K.S[4]), f0, w); // the -S f of the SRT collision
+        store(i, fma(V2(dt), w - adv, f0));
+    };
 #define F0(i) ldv(r0 + (i) * PST + lx)
 #define PX(i) nnd_pos_x(load6(r0 + (i) * PST, lx))
 #define NX(i) nnd_neg_x(load6(r0 + (i) * PST, lx))
@@ -549,7 +568,7 @@ __device__ __forceinline__ void bulk_wait_all()
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-template <int REC, bool GEN, bool AVG>
+template <int REC, bool GEN, bool AVG, bool SRT>
 __global__ void __launch_bounds__(MT, 2)
     march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows,
                  const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout)
@@ -641,7 +660,7 @@ __global__ void __launch_bounds__(MT, 2)
                 break;
             }
             if (y + wpair < yend)
-                update_row<REC, AVG>(smem_f, ring, ob, y + wpair, x0, t, K, a, cur, act0, act1,
+                update_row<REC, AVG, SRT>(smem_f, ring, ob, y + wpair, x0, t, K, a, cur, act0, act1,
                                      do_tne, acc, tmin, tmax);
             cur = nxt;
             fence_async_shared(); // the output rows are read by the bulk stores
@@ -733,24 +752,25 @@ __global__ void __launch_bounds__(MT, 2)
     }
 }
 
-template <int REC, bool GEN, bool AVG>
+template <int REC, bool GEN, bool AVG, bool SRT>
 cudaError_t march_prepare()
 {
-    static cudaError_t done = cudaFuncSetAttribute(march_kernel<REC, GEN, AVG>,
+    static cudaError_t done = cudaFuncSetAttribute(march_kernel<REC, GEN, AVG, SRT>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)MARCH_SMEM);
     return done;
 }
 
 // resident blocks per SM of a variant; the averaging stage of a step shares the grid
-// of its first stage, so both must fit that many blocks (checked at launch)
-template <int REC, bool GEN, bool AVG>
+// of its first stage, and the single-relaxation-time variant the grid of the general
+// one, so all must fit that many blocks (checked at launch)
+template <int REC, bool GEN, bool AVG, bool SRT>
 int resident_of()
 {
     static int per_sm = -1;
     if (per_sm < 0) {
-        if (march_prepare<REC, GEN, AVG>() != cudaSuccess) return -1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<REC, GEN, AVG>,
+        if (march_prepare<REC, GEN, AVG, SRT>() != cudaSuccess) return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<REC, GEN, AVG, SRT>,
                                                           MT, MARCH_SMEM) != cudaSuccess)
             return -1;
         if (per_sm < 1) per_sm = 1;
@@ -761,7 +781,11 @@ int resident_of()
 template <int REC, bool GEN>
 int resident_min()
 {
-    const int a = resident_of<REC, GEN, false>(), b = resident_of<REC, GEN, true>();
+    int a = resident_of<REC, GEN, false, false>(), b = resident_of<REC, GEN, true, false>();
+    if constexpr (!GEN) {
+        const int c = resident_of<REC, false, false, true>();
+        b = c < b ? c : b;
+    }
     return a < 0 || b < 0 ? -1 : (a < b ? a : b);
 }
 
@@ -781,15 +805,17 @@ int resident_blocks(int mode)
 }
 
 template <int REC, bool GEN>
-void launch_variant(bool avg, const ModelConst<float>& K, const StepLaunch& a, int rows,
+void launch_variant(bool avg, bool srt, const ModelConst<float>& K, const StepLaunch& a, int rows,
                     cudaStream_t s)
 {
     const CUtensorMap& tin = *reinterpret_cast<const CUtensorMap*>(a.tm_in);
     const CUtensorMap& tout = *reinterpret_cast<const CUtensorMap*>(a.tm_out);
     if (avg)
-        march_kernel<REC, GEN, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
+        march_kernel<REC, GEN, true, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
+    else if (srt && !GEN)
+        march_kernel<REC, false, false, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
     else
-        march_kernel<REC, GEN, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
+        march_kernel<REC, GEN, false, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
 }
 
 } // namespace
@@ -798,8 +824,9 @@ void launch_variant(bool avg, const ModelConst<float>& K, const StepLaunch& a, i
 // column of the grid is chosen so that the strips fill whole waves of the resident
 // blocks while each strip stays long compared with its prologue (four rows staged and
 // three recovered before the first update).
-// mode = recovery | (general boundaries << 1): the general variant carries walls,
-// Dirichlet and specular sides; the plain one only index maps.
+// mode = recovery | (general boundaries << 1) | (single relaxation time << 2): the
+// general variant carries walls, Dirichlet and specular sides, the plain one only index
+// maps; the single-relaxation-time variant exists for the plain forward-Euler step.
 void march_plan(int mode, int nx, int ny, int* grid, int* strip_rows)
 {
     const int G = resident_blocks(mode);
@@ -870,11 +897,12 @@ cudaError_t launch_march(int mode, const ModelConst<float>& K, const StepLaunch&
     if (g != a.grid) return cudaErrorInvalidConfiguration; // partial buffers sized for a.grid
     const bool avg = a.stage >= 2;
     if (!a.tm_in || !a.tm_out) return cudaErrorInvalidValue;
+    const bool srt = (mode & 4) != 0;
     switch (mode & 3) {
-    case 0: launch_variant<0, false>(avg, K, a, rows, s); break;
-    case 1: launch_variant<1, false>(avg, K, a, rows, s); break;
-    case 2: launch_variant<0, true>(avg, K, a, rows, s); break;
-    default: launch_variant<1, true>(avg, K, a, rows, s); break;
+    case 0: launch_variant<0, false>(avg, srt, K, a, rows, s); break;
+    case 1: launch_variant<1, false>(avg, srt, K, a, rows, s); break;
+    case 2: launch_variant<0, true>(avg, srt, K, a, rows, s); break;
+    default: launch_variant<1, true>(avg, srt, K, a, rows, s); break;
     }
     return cudaGetLastError();
 }

@@ -41,6 +41,11 @@ class LbkmError(RuntimeError):
         self.code = code
 
 
+# caller-owned device memory (lbkm_params.alloc / free)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class Params(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
@@ -59,7 +64,37 @@ class Params(ctypes.Structure):
         ("side_ux", ctypes.c_double * 4), ("side_uy", ctypes.c_double * 4),
         ("side_T", ctypes.c_double * 4), ("side_lam", ctypes.c_double * 4),
         ("time_scheme", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
+
+
+class TorchAllocator:
+    """Device memory of a handle from torch's caching allocator, through lbkm_params.alloc
+    and free: each block is a uint8 CUDA tensor held here until the library frees it
+    (torch's blocks are aligned to 512 bytes). Pass as Solver(..., allocator=...)."""
+
+    def __init__(self):
+        self.blocks = {}
+        self.allocated = 0   # blocks handed out so far
+        self._alloc = ALLOC_FN(self._a)
+        self._free = FREE_FN(self._f)
+
+    def _a(self, nbytes, stream, ctx):
+        try:
+            import torch
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        except Exception:  # out of memory: the library reports LBKM_ENOMEM
+            return None
+        self.blocks[t.data_ptr()] = t
+        self.allocated += 1
+        return t.data_ptr()
+
+    def _f(self, ptr, stream, ctx):
+        self.blocks.pop(ptr, None)
+
+    def install(self, params):
+        params.alloc, params.free = self._alloc, self._free
 
 
 class Objective(ctypes.Structure):
@@ -274,11 +309,14 @@ class Solver:
     _PREFIX = "lbkm_"
     _Tne = TneGlobal
 
-    def __init__(self, params: Params = None, stream=None, **kw):
+    def __init__(self, params: Params = None, stream=None, allocator=None, **kw):
         lib = load()
         self._lib = lib
         self._api = _Api(lib, self._PREFIX)
         self.params = params if params is not None else self._default(**kw)
+        self.allocator = allocator  # kept alive as long as the handle
+        if allocator is not None:
+            allocator.install(self.params)
         self.nx, self.ny = int(self.params.nx), int(self.params.ny)
         h = ctypes.c_void_p()
         rc = self._api.create(ctypes.byref(self.params), ctypes.c_void_p(_stream_ptr(stream)),

@@ -6,16 +6,16 @@ from oracle import oracle
 from paper_1411_6697_gb300 import lbkm
 
 KEYS = ("gamma", "orbit_kind", "orbit_speed", "orbit_eta", "S", "Q", "omega1", "omega2",
-        "T_ig", "dx", "dt", "walls", "sides", "time_scheme")
+        "T_ig", "dx", "dt", "walls", "sides", "time_scheme", "collision")
 
 
-def solver(params, precision, recovery=0, tne_every=0, tne_capacity=1, **over):
+def solver(params, precision, recovery=0, tne_every=0, tne_capacity=1, allocator=None, **over):
     p = dict(params)
     p.update(over)
     kw = {k: p[k] for k in KEYS if k in p}
     return lbkm.Solver(nx=p["nx"], ny=p["ny"], precision=precision, recovery=recovery,
                        dy=p.get("dy", p["dx"]), bc=(p["bc_x"], p["bc_y"]),
-                       tne_every=tne_every, tne_capacity=tne_capacity, **kw)
+                       tne_every=tne_every, tne_capacity=tne_capacity, allocator=allocator, **kw)
 
 
 def make_oracle(params, **over):

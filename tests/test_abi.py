@@ -48,7 +48,8 @@ int main(void) {
   printf("tne %zu\n", sizeof(lbkm_tne_global));
   F(lbkm_params, gamma) F(lbkm_params, orbit_kind) F(lbkm_params, orbit_speed)
   F(lbkm_params, S) F(lbkm_params, Q) F(lbkm_params, T_ig) F(lbkm_params, dt)
-  F(lbkm_params, bc_x) F(lbkm_params, tne_capacity)
+  F(lbkm_params, bc_x) F(lbkm_params, tne_capacity) F(lbkm_params, time_scheme)
+  F(lbkm_params, collision) F(lbkm_params, alloc) F(lbkm_params, free) F(lbkm_params, alloc_ctx)
   F(lbkm_tne_global, d_sum) F(lbkm_tne_global, step)
   return 0; }
 """
@@ -61,7 +62,7 @@ int main(void) {
     assert int(out["params"]) == ctypes.sizeof(lbkm.Params)
     assert int(out["tne"]) == ctypes.sizeof(lbkm.TneGlobal)
     for m in ("gamma", "orbit_kind", "orbit_speed", "S", "Q", "T_ig", "dt", "bc_x",
-              "tne_capacity"):
+              "tne_capacity", "time_scheme", "collision", "alloc", "free", "alloc_ctx"):
         assert int(out[m]) == getattr(lbkm.Params, m).offset, m
     assert int(out["d_sum"]) == lbkm.TneGlobal.d_sum.offset
     assert int(out["step"]) == lbkm.TneGlobal.step.offset

@@ -409,6 +409,61 @@ def test_detonation_full_config(detonation_ref, prec, rec, steps):
         assert e <= tol, (k, e, tol)
 
 
+# ------------------------------------------------------------------ single relaxation time
+@pytest.mark.parametrize("rec", [0, 1], ids=["f32", "f32-df"])
+@pytest.mark.parametrize("nx,ny,bc", [(300, 77, (0, 0)), (262, 40, (1, 1)), (45, 19, (1, 0))])
+def test_srt_fast_path_matches_oracle_and_moment_form(rec, nx, ny, bc):
+    """Equal rates R_5..R_16 without TNE select the single-relaxation-time kernel (Sec. V,
+    Eq. (87): -S (f - f^eq) + C in velocity space, no forward transform): against the
+    oracle's moment-space step, whose BGK limit it is (relative L2 <= 2e-5 per field), and
+    against the moment-space kernel forced by collision = 1 (rounding differences only)."""
+    params, fields = mixed_2d(nx, ny, bc=bc, seed=nx)
+    params = dict(params, S=np.full(16, 6e4))
+    steps = 20
+    s, ob, f, lam = start(params, fields, lbkm.F32, rec, noise_seed=ny)
+    m_, _, _, _ = start(params, fields, lbkm.F32, rec, noise_seed=ny, collision=1)
+    s.step(steps)
+    m_.step(steps)
+    f_ref, lam_ref = ob.run(f, lam, steps)
+    got, mrt = s.f_planes(), m_.f_planes()
+    for i in range(16):
+        assert rel_l2(got[i], f_ref[i]) <= TOL[lbkm.F32], ("f", i + 1)
+        assert rel_l2(got[i], mrt[i]) <= 1e-5, ("vs moment form", i + 1)
+    assert rel_l2(got[16], lam_ref) <= TOL[lbkm.F32]
+    s.close()
+    m_.close()
+
+
+# ------------------------------------------------------------------ caller-owned memory
+def test_torch_allocator_owns_every_buffer():
+    """lbkm_params.alloc / free backed by torch's caching allocator: the handle, its
+    temporaries (macros to host) and lbkm_tne's fields come from torch tensors, and the
+    results are bitwise those of a handle that allocates for itself."""
+    import torch
+    params, fields = mixed_2d(130, 37, bc=(0, 0), seed=4)
+    talloc = lbkm.TorchAllocator()
+    before = torch.cuda.memory_allocated()
+    a, ob, f, lam = start(params, fields, lbkm.F32, 0, noise_seed=2, allocator=talloc,
+                          tne_every=1, tne_capacity=4)
+    n_create = talloc.allocated
+    assert n_create >= 6 and torch.cuda.memory_allocated() > before
+    b, _, _, _ = start(params, fields, lbkm.F32, 0, noise_seed=2, tne_every=1, tne_capacity=4)
+    for s in (a, b):
+        s.step(7)
+    ma, mb = a.macros(), b.macros()
+    assert talloc.allocated > n_create  # the host copy of the macros used a torch block
+    for k in ma:
+        assert np.array_equal(ma[k], mb[k]), k
+    assert np.array_equal(a.f_planes(), b.f_planes())
+    da, ga = a.tne(fields=True)
+    db, gb = b.tne(fields=True)
+    assert np.array_equal(da, db) and np.array_equal(ga["sum"], gb["sum"])
+    live = len(talloc.blocks)
+    a.close()
+    b.close()
+    assert len(talloc.blocks) == 0 < live  # every block went back through free
+
+
 # ------------------------------------------------------------------ config 3 at length
 @pytest.fixture(scope="module")
 def reactive_window_ref():

@@ -44,6 +44,8 @@ def create(**kw):
     (dict(time_scheme=3), 1),
     (dict(tne_capacity=0), 1),
     (dict(omega1=-1.0), 1),
+    (dict(collision=2), 1),                     # 0 (fast path where it applies) or 1
+    (dict(alloc_ctx=None, alloc=lbkm.ALLOC_FN(lambda n, s, c: None)), 1),  # alloc without free
     # the paper's first two rings (shared speed and eta): singular M
     (dict(orbit_speed=(2.7, 2.7, 2.2, 2.2), orbit_eta=(5.0, 5.0, 3.0, 3.0)), 4),
 ])
