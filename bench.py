@@ -478,10 +478,11 @@ def run_d2v24(args):
 
 
 def measure_adjoint(n_grad=1):
-    """Config 5: dJ/d(S, Q, omega1, rho0) of a 4000-step 1-D detonation of 8192 cells
-    (profile mismatch + integrated TNE), checkpoints every 64 steps, through lbkm_grad
-    (host wall clock per gradient); against the plain FP64 forward run of the same length
-    that central differences repeat twice per gradient entry."""
+    """Config 5: dJ/d(S, Q, omega1, omega2, rho0) of a 4000-step 1-D detonation of 8192
+    cells (profile mismatch + integrated TNE), checkpoints every 64 steps, through
+    lbkm_grad (host wall clock per gradient); against the plain FP64 forward run of the
+    same length that central differences repeat twice per gradient entry. The same
+    gradient with the FP32 forward (FP64 adjoint along the FP32 trajectory) beside it."""
     import torch
     from paper_1411_6697_gb300 import lbkm
     cfg = li.adjoint()
@@ -490,8 +491,8 @@ def measure_adjoint(n_grad=1):
     steps = base["steps"]
     stream = torch.cuda.Stream()
 
-    def solver(p):
-        s = lbkm.Solver(nx=p["nx"], ny=1, precision=lbkm.F64, S=p["S"], Q=p["Q"], bc=(1, 0),
+    def solver(p, prec=lbkm.F64):
+        s = lbkm.Solver(nx=p["nx"], ny=1, precision=prec, S=p["S"], Q=p["Q"], bc=(1, 0),
                         dy=p["dx"], stream=stream, **_shared_params(p))
         s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
         return s
@@ -516,8 +517,17 @@ def measure_adjoint(n_grad=1):
         g = s.grad(rho_t, steps, w_tne=cfg["w_tne"], checkpoint_every=cfg["checkpoint_every"])
     sec = (time.perf_counter() - t0) / n_grad
     s.close()
+    s32 = solver(q, lbkm.F32)
+    g32 = s32.grad(rho_t, steps, w_tne=cfg["w_tne"], checkpoint_every=cfg["checkpoint_every"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_grad):
+        g32 = s32.grad(rho_t, steps, w_tne=cfg["w_tne"],
+                       checkpoint_every=cfg["checkpoint_every"])
+    sec32 = (time.perf_counter() - t0) / n_grad
+    s32.close()
     nx = q["nx"]
-    n_scalar = 16 + 2               # S_1..S_16, Q, omega1
+    n_scalar = 16 + 3               # S_1..S_16, Q, omega1, omega2
     n_entries = n_scalar + nx       # and the initial density field
     fd = 2 * ms_fwd * 1e-3          # one central difference = two forward runs
     return {"workload": "adjoint_8192x1_detonation_4000_steps", "checkpoint_every":
@@ -530,7 +540,14 @@ def measure_adjoint(n_grad=1):
             "gradient_entries": n_entries,
             "accuracy": "J, dJ/dS, dJ/dQ, dJ/domega1 within 1e-7 of the FP64 reverse-mode oracle "
                         "at this size, within 1e-5 of central differences "
-                        "(tests/test_gpu_adjoint.py)"}
+                        "(tests/test_gpu_adjoint.py)",
+            "fp32_forward": {
+                "gradient_ms": sec32 * 1e3, "J": g32["J"],
+                "speedup_vs_f64_gradient": sec / sec32,
+                "speedup_vs_central_fd_scalars": n_scalar * fd / sec32,
+                "accuracy": "every entry within 4x what FP32 storage alone does to the FP64 "
+                            "oracle's gradient (tests/test_gpu_adjoint.py::"
+                            "test_adjoint_of_the_fp32_forward_full_config)"}}
 
 
 def run_adjoint(args):
@@ -681,7 +698,8 @@ def main():
         "config": {"workload": "reactive2d_%dx%d" % (args.side, args.side),
                    "cells_per_gpu": n, "precision": tag,
                    "conserved_moment_recovery": args.recovery,
-                   "tne": "every step, FP64 grid-wide reduction",
+                   "tne": "every step; per-thread sums of Delta_k, |Delta_k| exact, "
+                          "FP64 across threads, blocks and the grid",
                    "l2": "state %.2f GB per copy > L2 (129 MB): no flush" % (
                        17 * n * (4 if tag == "f32" else 8) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},

@@ -278,17 +278,25 @@ typedef struct {
     double* drho0;             /* [nx] host or NULL: dJ/drho of the start, with u, T fixed,
                                   for a start made by lbkm_init_fields (equilibrium) */
     double* df0;               /* [16][nx] host or NULL: dJ/df of the start state */
+    double domega2;            /* dJ/domega2 (Eq. (28); defined at omega2 = 0 too) */
 } lbkm_grad_out;
 
-/* Gradient of J by the discrete adjoint of the FP64 step (reverse mode through
- * every step, hand-written kernels): the forward run keeps a state every
+/* Gradient of J by the discrete adjoint of the step (reverse mode through every
+ * step, hand-written FP64 kernels): the forward run keeps a state every
  * checkpoint_every steps and each segment is recomputed from its checkpoint
- * before its steps are reversed, so memory is (N/C + C) states. The ignition
+ * before its steps are reversed, so memory is (N/C + C) states. With an LBKM_F32
+ * handle the forward run is the FP32 step and its checkpoints are FP32 states; each
+ * segment is then recomputed in FP64 from its checkpoint widened to FP64 and reversed
+ * in FP64 (J and its derivative are those of FP64 segments restarted from the FP32
+ * run's states). The exact adjoint of the FP32 step itself is not offered: over long
+ * runs FP32 rounding decides the limiter's branches on flat stretches every step, and
+ * the limiter's linearisation about such states amplifies the adjoint. The reaction's
+ * derivative covers omega2 != 0 (the closed form of Eq. (28)). The ignition
  * switch T > T_ig stays a hard switch (no derivative through it); minmod and the
  * lambda clamp follow the branch the forward values take. The handle's state is
- * left unchanged. Needs an LBKM_F64 handle with ny = 1 and omega2 = 0 (not
- * batched). Errors: LBKM_EINVAL, LBKM_ESTATE, LBKM_ENOMEM, LBKM_ECUDA,
- * LBKM_EUNSTABLE. Synchronises. */
+ * left unchanged. Needs a handle with ny = 1, periodic or zero-gradient ends and
+ * forward Euler (not batched). Errors: LBKM_EINVAL, LBKM_ESTATE, LBKM_ENOMEM,
+ * LBKM_ECUDA, LBKM_EUNSTABLE. Synchronises. */
 lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* obj, lbkm_grad_out* out);
 
 /* Many independent 1-D instances of uneven length in one handle (zero-gradient

@@ -188,12 +188,21 @@ class Model1D:
 
 
 def objective(model, rho0, ux0, uy0, T0, lam0, S, Q, omega1, steps, rho_target, w_tne,
-              checkpoint_every=0):
+              checkpoint_every=0, restarts=None):
     """J = 1/2 sum_x (rho_N - rho*)^2 dx + w_tne sum_{n<N} sum_x d_n^2 dx dt, d_n^2 = sum_k
-    Delta_k^2 of the state entering step n. Returns (J, mismatch part, TNE part)."""
+    Delta_k^2 of the state entering step n. Returns (J, mismatch part, TNE part).
+    omega2 of the model may be a tensor that requires a gradient.
+
+    restarts: (f, lambda) for the steps 0, C, 2C, ... (C = checkpoint_every): each
+    segment of C steps starts from the given state instead of the one the previous
+    segment reached, the derivative passing to the reached state unchanged -- the
+    objective and gradient of FP64 segments restarted from another run's states."""
+
     f = model.init(rho0, ux0, uy0, T0)
     lam = lam0
     tne = torch.zeros((), dtype=torch.float64)
+    if restarts is not None and not checkpoint_every:
+        raise ValueError("restarts need checkpoint_every")
 
     def seg(f, lam, S, Q, omega1, n):
         t = torch.zeros((), dtype=torch.float64)
@@ -204,6 +213,10 @@ def objective(model, rho0, ux0, uy0, T0, lam0, S, Q, omega1, steps, rho_target, 
 
     done = 0
     while done < steps:
+        if restarts is not None:
+            rf, rl = restarts[done // checkpoint_every]
+            f = f + (torch.as_tensor(rf, dtype=torch.float64) - f).detach()
+            lam = lam + (torch.as_tensor(rl, dtype=torch.float64) - lam).detach()
         n = min(checkpoint_every or steps, steps - done)
         if checkpoint_every:
             from torch.utils.checkpoint import checkpoint

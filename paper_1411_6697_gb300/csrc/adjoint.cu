@@ -2,8 +2,9 @@
 //
 // For one step (f, lambda)_n -> (f, lambda)_{n+1} of the fused kernel and adjoints
 // (fb, lb)_{n+1} = dJ/d(state_{n+1}), these kernels produce (fb, lb)_n and add the
-// step's contributions to dJ/dS_5..16, dJ/dQ, dJ/domega1. The forward values are
-// recomputed from the stored state n. Conventions at non-smooth points: the
+// step's contributions to dJ/dS_5..16, dJ/dQ, dJ/domega1, dJ/domega2. The forward
+// values are recomputed from the stored FP64 state n (for an FP32 forward run, a state of
+// the FP64 segment recomputed from the run's checkpoint, widened by adj_widen). Conventions at non-smooth points: the
 // ignition switch T > T_ig is a hard switch (no derivative), minmod follows the
 // branch the values select (a on a tie), the clamp of lambda passes the
 // derivative when the unclamped value lies in [0, 1] (inclusive), the upwind
@@ -70,6 +71,36 @@ __device__ __forceinline__ void nnd_coef(double vsign, const double* q, double* 
 
 constexpr int ADJ_THREADS = 128;
 
+// The increment of lambda over dt (Eq. (28), m = n = 1: the closed form of
+// d lambda/dt = (1 - lambda)(a + b lambda), evaluated as the step evaluates it) and its
+// partial derivatives with respect to lambda, a = omega1 p and b = omega2 p. With
+// mu0 = 1 - lambda, k = a + b, e = exp(-k dt): mu = k mu0 e / (k - b mu0 (1 - e)) and
+// dl = mu0 - mu; for b = 0, mu = mu0 e, whose derivative in b is the limit b -> 0.
+__device__ __forceinline__ void reaction_partials(double lam, double a, double b, double dt,
+                                                  double& dl, double& d_lam, double& d_a,
+                                                  double& d_b)
+{
+    const double mu0 = 1.0 - lam;
+    if (b == 0.0) {
+        const double g = -expm1(-a * dt), e = 1.0 - g;
+        const double ga = a > 0.0 ? g / a : dt; // (1 - e) / a
+        dl = mu0 * g;
+        d_lam = -g;
+        d_a = mu0 * dt * e;
+        d_b = mu0 * e * dt - mu0 * mu0 * e * ga;
+        return;
+    }
+    const double k = a + b, e = exp(-k * dt), g = 1.0 - e;
+    const double Dn = k - b * mu0 * g;
+    const double mu = k * mu0 * e / Dn;
+    const double mu_k = (mu0 * e * (1.0 - k * dt) - mu * (1.0 - b * mu0 * dt * e)) / Dn;
+    const double mu_m0 = (k * e + mu * b * g) / Dn;
+    dl = mu0 - mu;
+    d_lam = mu_m0 - 1.0;
+    d_a = -mu_k;
+    d_b = -(mu_k + mu * mu0 * g / Dn);
+}
+
 // block sum of v in fixed order, added by thread 0 to acc[blockIdx.x]
 __device__ void block_add(double v, double* acc, double* sred)
 {
@@ -112,11 +143,11 @@ __global__ void __launch_bounds__(ADJ_THREADS)
         const double A8c = K.A8c, A9c = K.A9c;
         const double X8 = 4.0 * ux * gx * (1.0 - 1.0 / DI) + 2.0 * uy * gy;
         const double X9 = -4.0 * uy * gx / DI + 2.0 * ux * gy;
-        // reaction (omega2 = 0)
+        // reaction over dt, decided by T > T_ig (Eq. (28))
         const bool ig = T > K.T_igd;
-        const double ar = K.omega1 * rho * T;
-        const double e = exp(-ar * dt);
-        const double dl = ig ? (1.0 - lam) * (-expm1(-ar * dt)) : 0.0;
+        const double pr = rho * T;
+        double dl = 0.0, dl_lam = 0.0, dl_a = 0.0, dl_b = 0.0;
+        if (ig) reaction_partials(lam, K.omega1 * pr, K.omega2 * pr, dt, dl, dl_lam, dl_a, dl_b);
         const double cr = dl * K.chem;
         // lambda update and its clamp
         double lq[5];
@@ -150,12 +181,13 @@ __global__ void __launch_bounds__(ADJ_THREADS)
         pS[12] += dl * (2.0 / (DI * dt)) * crb; // dQ
         double rhob = 0.0, uxb = 0.0, uyb = 0.0, Tb = 0.0, lamb = lbc, gxb = 0.0, gyb = 0.0;
         if (ig) {
-            lamb += -(1.0 - e) * dlb;
-            const double eb = -(1.0 - lam) * dlb;
-            const double ab = -dt * e * eb;
-            pS[13] += rho * T * ab; // domega1
-            rhob += K.omega1 * T * ab;
-            Tb += K.omega1 * rho * ab;
+            lamb += dl_lam * dlb;
+            const double ab = dl_a * dlb, bb = dl_b * dlb;
+            pS[13] += pr * ab; // domega1
+            pS[14] += pr * bb; // domega2
+            const double pb = K.omega1 * ab + K.omega2 * bb;
+            rhob += T * pb;
+            Tb += rho * pb;
         }
         // A_hat_8 = rho T A8c X8, A_hat_9 = rho T A9c X9
         {
@@ -336,6 +368,14 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     }
 }
 
+// an FP32 checkpoint widened to FP64, element by element (exact)
+__global__ void adj_widen(const float* __restrict__ in, double* __restrict__ out, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
 } // namespace
 
 int adj_grid(int nx)
@@ -361,6 +401,12 @@ cudaError_t launch_adj_seed(const ModelConst<double>& K, const AdjArgs& a, const
                             double w, int grid, cudaStream_t s)
 {
     adj_seed<<<grid, ADJ_THREADS, 0, s>>>(K, a, rho_t, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_widen(const float* in, double* out, size_t n, int grid, cudaStream_t s)
+{
+    adj_widen<<<grid, ADJ_THREADS, 0, s>>>(in, out, n);
     return cudaGetLastError();
 }
 

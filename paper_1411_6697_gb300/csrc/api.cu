@@ -955,9 +955,8 @@ lbkm_status lbkm_autotune(lbkm_t h, int32_t trial_steps, int32_t* chosen)
 lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
 {
     if (!h || !ob || !out) return LBKM_EINVAL;
-    if (h->precision != LBKM_F64 || h->ny != 1 || h->batched)
-        return fail(h, LBKM_EINVAL, "lbkm_grad needs a single LBKM_F64 grid with ny = 1");
-    if (h->p.omega2 != 0.0) return fail(h, LBKM_EINVAL, "lbkm_grad needs omega2 = 0");
+    if (h->ny != 1 || h->batched)
+        return fail(h, LBKM_EINVAL, "lbkm_grad needs a single grid with ny = 1");
     if (h->p.bc_x == LBKM_BC_SIDES)
         return fail(h, LBKM_EINVAL, "lbkm_grad needs periodic or zero-gradient ends");
     if (h->p.time_scheme != 0) return fail(h, LBKM_EINVAL, "lbkm_grad needs forward Euler");
@@ -968,8 +967,16 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     const int64_t N = ob->steps;
     const int C = ob->checkpoint_every;
     const int64_t nck = (N + C - 1) / C;
-    const size_t SB = h->state_bytes_dev;
     const int G = adj_grid(nx);
+    // With an FP32 handle the forward run is the FP32 step and keeps FP32 checkpoints;
+    // each segment is recomputed in FP64 from its checkpoint widened to FP64 and reversed
+    // in FP64, so the derivative is taken along FP64 segments restarted from the FP32
+    // run's states. (The exact adjoint of the FP32 step itself is not usable over long
+    // runs: on flat stretches FP32 rounding decides the limiter's branches every step,
+    // and the limiter's linearisation about such a state amplifies the adjoint.)
+    const bool f32 = h->precision != LBKM_F64;
+    const size_t SBf = h->state_bytes_dev;                  // forward states, checkpoints
+    const size_t SBd = (size_t)NPLANE * h->plane_elems * 8; // FP64 segment states
     char *ck = nullptr, *seg = nullptr;
     double *work = nullptr, *mats = nullptr;
     DevCounters* sctr = nullptr;
@@ -984,8 +991,8 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     // work: mac 4n, mb 16n, loc 6n, gb 2n, fbA/fbB 32n, lbA/lbB 2n, rho_t n, drho0 n,
     //       pacc NPAR*G, jtne G, jmis G
     const size_t nwork = (size_t)nx * (4 + 16 + 6 + 2 + 32 + 2 + 1 + 1) + (size_t)(ADJ_NPAR + 2) * G;
-    cudaError_t e = dmalloc(h, &ck, SB * nck);
-    if (e == cudaSuccess) e = dmalloc(h, &seg, SB * (size_t)(C + 1));
+    cudaError_t e = dmalloc(h, &ck, SBf * nck);
+    if (e == cudaSuccess) e = dmalloc(h, &seg, SBd * (size_t)(C + 1));
     if (e == cudaSuccess) e = dmalloc(h, &work, sizeof(double) * nwork);
     if (e == cudaSuccess) e = dmalloc(h, &mats, sizeof(double) * (256 + 256 + 16));
     if (e == cudaSuccess) e = dmalloc(h, &sctr, sizeof(DevCounters));
@@ -1017,8 +1024,8 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
                 hm[512 + 4 * o + q] = h->hm.c[o] * (h->p.orbit_kind[o] == 0 ? ax[q] : dg[q]);
     }
     cudaStream_t st = h->stream;
-    auto S = [&](int64_t k) { return seg + (size_t)k * SB; };
-    auto K_ = [&](int64_t k) { return ck + (size_t)k * SB; };
+    auto S = [&](int64_t k) { return seg + (size_t)k * SBd; };
+    auto K_ = [&](int64_t k) { return ck + (size_t)k * SBf; };
 #define GT(call)                                                                              \
     do {                                                                                      \
         e = (call);                                                                           \
@@ -1031,17 +1038,19 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     GT(cudaMemcpyAsync(rho_t, ob->rho_target, sizeof(double) * nx, cudaMemcpyHostToDevice, st));
     GT(cudaMemsetAsync(pacc, 0, sizeof(double) * (ADJ_NPAR + 2) * G, st));
     GT(cudaMemsetAsync(sctr, 0, sizeof(DevCounters), st));
-    GT(cudaMemcpyAsync(K_(0), h->buf[h->cur], SB, cudaMemcpyDeviceToDevice, st));
+    GT(cudaMemcpyAsync(K_(0), h->buf[h->cur], SBf, cudaMemcpyDeviceToDevice, st));
     StepLaunch sl = step_args(h, 0);
     sl.ctr = sctr;
     sl.tne_every = 0;
-    // forward run, keeping a state every C steps
+    StepLaunch sd = sl; // the FP64 step of the recomputed segments
+    sd.grid = step_grid(0, 0, false, nx, 1, h->Kd.sbc);
+    // forward run in the handle's precision, keeping a state every C steps
     for (int64_t n = 0; n < N; n++) {
         sl.in = n == 0 ? (const void*)K_(0) : (const void*)S(n % 2);
         sl.out = S((n + 1) % 2);
-        GT(launch_step(0, 0, false, &h->Kd, sl, st));
+        GT(launch_step(h->precision, h->recovery, false, model_ptr(h), sl, st));
         if ((n + 1) % C == 0 && n + 1 < N)
-            GT(cudaMemcpyAsync(K_((n + 1) / C), S((n + 1) % 2), SB, cudaMemcpyDeviceToDevice, st));
+            GT(cudaMemcpyAsync(K_((n + 1) / C), S((n + 1) % 2), SBf, cudaMemcpyDeviceToDevice, st));
     }
     AdjArgs a;
     memset(&a, 0, sizeof(a));
@@ -1055,22 +1064,33 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     a.vx = mats + 512;
     a.tne_w = ob->w_tne * h->p.dx * h->p.dt;
     a.jw = a.tne_w;
-    // seed with the mismatch of the final state
-    a.f = reinterpret_cast<const double*>(S(N % 2));
+    // FP64 forward: seed with the mismatch of the final state now; FP32 forward: once the
+    // last segment has been recomputed in FP64
     a.fb0 = fbA;
     a.lb0 = lbA;
-    a.jacc = jmis;
-    GT(launch_adj_seed(h->Kd, a, rho_t, ob->w_mismatch, G, st));
-    a.jacc = jtne;
+    auto seed = [&](const void* final_state) -> cudaError_t {
+        a.f = static_cast<const double*>(final_state);
+        a.jacc = jmis;
+        const cudaError_t se = launch_adj_seed(h->Kd, a, rho_t, ob->w_mismatch, G, st);
+        a.jacc = jtne;
+        return se;
+    };
+    if (!f32) GT(seed(S(N % 2)));
     double *fc = fbA, *fn = fbB, *lc = lbA, *ln = lbB;
     for (int64_t sg = nck - 1; sg >= 0; sg--) {
         const int64_t n0 = sg * C, n1 = (n0 + C < N) ? n0 + C : N;
-        GT(cudaMemcpyAsync(S(0), K_(sg), SB, cudaMemcpyDeviceToDevice, st));
-        for (int64_t n = n0; n < n1 - 1; n++) {
-            sl.in = S(n - n0);
-            sl.out = S(n - n0 + 1);
-            GT(launch_step(0, 0, false, &h->Kd, sl, st));
+        const bool last = f32 && sg == nck - 1; // recompute through the final state
+        if (f32)
+            GT(launch_adj_widen(reinterpret_cast<const float*>(K_(sg)), reinterpret_cast<double*>(S(0)),
+                                (size_t)NPLANE * h->plane_elems, G, st));
+        else
+            GT(cudaMemcpyAsync(S(0), K_(sg), SBf, cudaMemcpyDeviceToDevice, st));
+        for (int64_t n = n0; n < (last ? n1 : n1 - 1); n++) {
+            sd.in = S(n - n0);
+            sd.out = S(n - n0 + 1);
+            GT(launch_step(0, 0, false, &h->Kd, sd, st));
         }
+        if (last) GT(seed(S(n1 - n0)));
         for (int64_t n = n1 - 1; n >= n0; n--) {
             const double* state = reinterpret_cast<const double*>(S(n - n0));
             GT(launch_macros(0, h->Kd, state, mac, mac + nx, mac + 2 * (size_t)nx,
@@ -1085,7 +1105,9 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
             std::swap(lc, ln);
         }
     }
-    a.f = reinterpret_cast<const double*>(K_(0));
+    // dJ/drho0 at the start: the FP64 state (for an FP32 handle its widening, which the
+    // first segment's recomputation left in S(0))
+    a.f = reinterpret_cast<const double*>(f32 ? S(0) : K_(0));
     a.fb1 = fc;
     GT(launch_adj_rho0(h->Kd, a, drho0, G, st));
     std::vector<double> hp((size_t)(ADJ_NPAR + 2) * G);
@@ -1110,6 +1132,7 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     for (int k = 0; k < 16; k++) out->dS[k] = k < 4 ? 0.0 : sums[k - 4];
     out->dQ = sums[12];
     out->domega1 = sums[13];
+    out->domega2 = sums[14];
     out->J_tne = sums[ADJ_NPAR];
     out->J_mismatch = sums[ADJ_NPAR + 1];
     out->J = out->J_mismatch + out->J_tne;

@@ -8,8 +8,8 @@
 // the FP32 pipes first), and kept in shared memory; the equilibrium moments, the 20
 // non-conserved moments, the relaxation, the back-transform, the chemical term of
 // Eq. (24) and the NND update run in the storage type R (FP64 or FP32); the TNE
-// partials of the state being read are reduced per block in FP64 when due, and an
-// 82-block kernel turns them into one history record.
+// partials of the state being read are reduced per block when due (sums in FP64,
+// extremes exactly in R), and an 82-block kernel turns them into one history record.
 //
 // M and M^-1 act in block form: butterflies inside each orbit of four velocities
 // (axis: f1+f3, f2+f4, f1-f3, f2-f4; diagonal: the sum and the three sign patterns)
@@ -351,37 +351,70 @@ __host__ __device__ __forceinline__ void feq24(F I, F DI, F rho, F ux, F uy, F T
     q[23] = ry * IT * (u2 + (F(4) + F(3) * I) * T);
 }
 
-// Block reduction of the TNE quantities of this thread's cell into partials
-// [q * nblocks + b] (warps by shuffle tree, then warps in order: deterministic).
+// Block reduction of the TNE quantities of the block's cells into partials
+// [q * nblocks + b], q in the record's order (sums of Delta_k, of |Delta_k|, minima,
+// maxima, sum of d, sum of d^2). Each thread leaves its cell's Delta_5..24, d and d^2
+// (formed in R) in shared memory; each quantity is then reduced in three parts of a
+// third of the block's cells (one thread per part; the block's threads take the parts
+// in turn), in a fixed order: the 42 sums in FP64, the 40 extremes in R (exact); one
+// thread per quantity joins the three parts. Deterministic for any block size <= BT.
 template <typename R>
 __device__ __forceinline__ void block_tne(const R* Dk, bool active, double* partials, int nblocks,
                                           int b)
 {
-    __shared__ double red[BT / 32][NQ];
-    const int t = threadIdx.x + threadIdx.y * blockDim.x, lane = t & 31, w = t >> 5;
-    double d2 = 0.0;
+    constexpr int LD = BT + 1;            // padded rows: the readers walk along a row
+    constexpr int NS = 2 * TK + 2;        // sums: Delta_k, |Delta_k|, d, d^2
+    constexpr int NE = 2 * TK;            // extremes: min and max of Delta_k
+    __shared__ R sD[TK + 2][LD];
+    __shared__ unsigned char sact[BT];
+    __shared__ double spart[NQ][3];
+    const int t = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+    const int per = (nt + 2) / 3; // cells per part
+    R d2 = R(0);
 #pragma unroll
-    for (int k = 0; k < TK; k++) d2 += active ? (double)Dk[k] * (double)Dk[k] : 0.0;
-#pragma unroll
-    for (int q = 0; q < NQ; q++) {
-        const int kind = tkind(q);
-        double v;
-        if (q < TK) v = active ? (double)Dk[q] : 0.0;
-        else if (q < 2 * TK) v = active ? fabs((double)Dk[q - TK]) : 0.0;
-        else if (q < 3 * TK) v = active ? (double)Dk[q - 2 * TK] : DBL_MAX;
-        else if (q < 4 * TK) v = active ? (double)Dk[q - 3 * TK] : -DBL_MAX;
-        else if (q == 4 * TK) v = active ? sqrt(d2) : 0.0;
-        else v = d2;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = tcomb(kind, v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) red[w][q] = v;
+    for (int k = 0; k < TK; k++) {
+        sD[k][t] = Dk[k];
+        d2 = fma(Dk[k], Dk[k], d2);
+    }
+    sD[TK][t] = sqrt(d2);
+    sD[TK + 1][t] = d2;
+    sact[t] = active ? 1 : 0;
+    __syncthreads();
+    for (int w = t; w < 3 * NS; w += nt) {
+        const int s = w / 3, part = w - 3 * s;
+        const int q = s < 2 * TK ? s : 4 * TK + (s - 2 * TK);
+        const int row = s < TK ? s : (s < 2 * TK ? s - TK : TK + (s - 2 * TK));
+        const bool absv = s >= TK && s < 2 * TK;
+        const int j1 = min((part + 1) * per, nt);
+        double acc = 0.0;
+        for (int j = part * per; j < j1; j++) {
+            if (!sact[j]) continue;
+            const double v = (double)sD[row][j];
+            acc += absv ? fabs(v) : v;
+        }
+        spart[q][part] = acc;
+    }
+    for (int w = t; w < 3 * NE; w += nt) {
+        const int e = w / 3, part = w - 3 * e;
+        const bool mn = e < TK;
+        const int k = mn ? e : e - TK;
+        const int j1 = min((part + 1) * per, nt);
+        bool any = false;
+        R m = R(0);
+        for (int j = part * per; j < j1; j++) {
+            if (!sact[j]) continue;
+            const R v = sD[k][j];
+            m = !any ? v : (mn ? fmin(m, v) : fmax(m, v));
+            any = true;
+        }
+        spart[2 * TK + e][part] = any ? (double)m : (mn ? DBL_MAX : -DBL_MAX);
     }
     __syncthreads();
-    const int nt = blockDim.x * blockDim.y, nw = (nt + 31) / 32;
     for (int q = t; q < NQ; q += nt) {
-        double v = red[0][q];
-        for (int k = 1; k < nw; k++) v = tcomb(tkind(q), v, red[k][q]);
-        partials[(size_t)q * nblocks + b] = v;
+        const int kind = tkind(q);
+        partials[(size_t)q * nblocks + b] =
+            tcomb(kind, tcomb(kind, spart[q][0], spart[q][1]), spart[q][2]);
     }
 }
 

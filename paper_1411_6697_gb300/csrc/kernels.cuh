@@ -111,7 +111,7 @@ cudaError_t launch_tne_instances(int precision, const ModelConst<double>& Kd, co
                                  double area, cudaStream_t s);
 
 // Discrete adjoint of the FP64 1-D step (adjoint.cu).
-constexpr int ADJ_NPAR = 14; // dJ/dS_5..S_16, dJ/dQ, dJ/domega1
+constexpr int ADJ_NPAR = 15; // dJ/dS_5..S_16, dJ/dQ, dJ/domega1, dJ/domega2
 struct AdjArgs {
     const double* f;     // state n: 17 planes with the handle's pitch
     const double* mac;   // [4][nx] rho, ux, uy, T of state n
@@ -137,6 +137,8 @@ cudaError_t launch_adj_seed(const ModelConst<double>& K, const AdjArgs& a, const
                             double w, int grid, cudaStream_t s);
 cudaError_t launch_adj_rho0(const ModelConst<double>& K, const AdjArgs& a, double* drho0,
                             int grid, cudaStream_t s);
+// n floats widened to doubles (an FP32 forward run's checkpoint, to restart a segment in FP64)
+cudaError_t launch_adj_widen(const float* in, double* out, size_t n, int grid, cudaStream_t s);
 
 // FP32 2-D step: y-marching strips, two cells per thread (march.cu)
 // mode = recovery | (general side conditions << 1)

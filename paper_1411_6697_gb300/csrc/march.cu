@@ -30,7 +30,8 @@
 // then formed in FP64 (REC = 0) or in double-float on the FP32 pipes (REC = 1), and
 // the ignition test T > T_ig is taken in that precision. The TNE statistics of the
 // updated state's input (Delta_5..Delta_16, Sec. VI, Eqs. (90)-(91)) accumulate per
-// thread in FP32 over a strip (32 cells) and from there on in FP64.
+// thread over a strip (32 cells per column), the sums of Delta_k and |Delta_k| exactly
+// (TwoSum pairs), and from there on in FP64.
 #include <cuda.h>
 #include <float.h>
 #include <stdlib.h>
@@ -69,7 +70,7 @@ constexpr size_t OFF_MBAR = (OFF_TMM + (size_t)NWM * NMM * 4 + 15) / 16 * 16;
 constexpr int NMB = 4;                                            // row pairs in flight or in use
 constexpr size_t MARCH_SMEM = OFF_MBAR + NMB * 8 + 128;           // + room to align the start
 static_assert(MARCH_SMEM <= 112 * 1024, "two blocks per SM need <= 112 KB each");
-static_assert(NSUM * MT <= OBUF && 4 * NSUM <= MT,
+static_assert(2 * NSUM * MT <= OBUF && 4 * NSUM <= MT,
               "the strip's TNE partials fit in the idle ring, four threads per sum");
 constexpr uint32_t PAIR_BYTES = NPLANE * PST * 4; // one tensor copy of a row pair
 
@@ -357,10 +358,24 @@ __device__ __forceinline__ Mac recover_row(float* smem_f, float* ring, int r, in
     return o;
 }
 
-// per-thread TNE statistics of one strip (FP32) and of the whole launch (min, max)
+// per-thread TNE statistics of one strip and of the whole launch (min, max). The sums of
+// Delta_k and |Delta_k| are carried as unevaluated pairs s + c of FP32 values: every
+// addition's rounding error is recovered exactly (TwoSum) and added to c, so s + c is the
+// exact sum of the FP32 terms up to the rounding of c itself (of order u^2 per term,
+// u = 2^-24). The sums of d and d^2 (one-signed, each term already rounded to about 12 u
+// by its own FP32 evaluation) are plain FP32 sums of at most 32 terms per column
+// (relative error <= 31 u). Past the thread everything is FP64.
 struct TneAcc {
     V2 sum[TNE_K], abs[TNE_K], dsum, d2sum; // the two cells of the thread apart
+    float sumc[TNE_K], absc[TNE_K];         // the compensating terms, both columns
 };
+
+__device__ __forceinline__ void acc_exact(V2& s, float& c, V2 x)
+{
+    const D2 t = two_sum(s, x);
+    s = t.hi;
+    c += t.lo.x() + t.lo.y();
+}
 
 // ---------------- the update of one row by one warp pair -------------------------
 // Row y, the thread's cells x0 + 2t and x0 + 2t + 1 (active when act0 / act1), macros
@@ -422,8 +437,8 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
         for (int k = 0; k < TNE_K; k++) {
             const V2 Dk = m[k + 4];
             d2 = fma(Dk, Dk, d2);
-            acc.sum[k] += Dk;
-            acc.abs[k] += V2(fabsf(Dk.x()), fabsf(Dk.y()));
+            acc_exact(acc.sum[k], acc.sumc[k], Dk);
+            acc_exact(acc.abs[k], acc.absc[k], V2(fabsf(Dk.x()), fabsf(Dk.y())));
             tmin[k] = fmin3(tmin[k], Dk.x(), Dk.y());
             tmax[k] = fmax3(tmax[k], Dk.x(), Dk.y());
         }
@@ -435,8 +450,8 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
         for (int k = 0; k < TNE_K; k++) {
             const float Dk = m[k + 4].x();
             d2 = fmaf(Dk, Dk, d2);
-            acc.sum[k] += V2(Dk, 0.f);
-            acc.abs[k] += V2(fabsf(Dk), 0.f);
+            acc_exact(acc.sum[k], acc.sumc[k], V2(Dk, 0.f));
+            acc_exact(acc.abs[k], acc.absc[k], V2(fabsf(Dk), 0.f));
             tmin[k] = fminf(tmin[k], Dk);
             tmax[k] = fmaxf(tmax[k], Dk);
         }
@@ -624,7 +639,10 @@ __global__ void __launch_bounds__(MT, 2)
         const uint32_t q0 = q_issued;
         TneAcc acc;
 #pragma unroll
-        for (int k = 0; k < TNE_K; k++) acc.sum[k] = acc.abs[k] = V2(0.f);
+        for (int k = 0; k < TNE_K; k++) {
+            acc.sum[k] = acc.abs[k] = V2(0.f);
+            acc.sumc[k] = acc.absc[k] = 0.f;
+        }
         acc.dsum = acc.d2sum = V2(0.f);
 
         __syncthreads(); // the previous strip is done with the ring
@@ -675,27 +693,29 @@ __global__ void __launch_bounds__(MT, 2)
             if (k + 4 < npairs) q_issued = q0 + k + 5;
         }
         if (stop) break;
-        // the strip's TNE sums: per-thread FP32 partials (32 cells), added in FP64 in a
-        // fixed order: four threads per quantity, 32 partials each, then a shuffle
+        // the strip's TNE sums: each thread's partials (both columns and the compensating
+        // terms) joined in FP64, then added in FP64 in a fixed order: four threads per
+        // quantity, 32 partials each, then a shuffle
         if (do_tne) {
             __syncthreads(); // every copy has been waited for: the ring is idle
-            float* part = ring;
+            double* part = reinterpret_cast<double*>(ring);
+            auto join = [](V2 s) { return f2d_fast(s.x()) + f2d_fast(s.y()); };
 #pragma unroll
             for (int k = 0; k < TNE_K; k++) {
-                part[k * MT + tid] = acc.sum[k].x() + acc.sum[k].y();
-                part[(TNE_K + k) * MT + tid] = acc.abs[k].x() + acc.abs[k].y();
+                part[k * MT + tid] = join(acc.sum[k]) + f2d_fast(acc.sumc[k]);
+                part[(TNE_K + k) * MT + tid] = join(acc.abs[k]) + f2d_fast(acc.absc[k]);
             }
-            part[2 * TNE_K * MT + tid] = acc.dsum.x() + acc.dsum.y();
-            part[(2 * TNE_K + 1) * MT + tid] = acc.d2sum.x() + acc.d2sum.y();
+            part[2 * TNE_K * MT + tid] = join(acc.dsum);
+            part[(2 * TNE_K + 1) * MT + tid] = join(acc.d2sum);
             __syncthreads();
             double s2 = 0.0;
             if (tid < 4 * NSUM) {
-                const float* src = part + (tid >> 2) * MT + (tid & 3) * 32;
+                const double* src = part + (tid >> 2) * MT + (tid & 3) * 32;
                 double e0 = 0.0, e1 = 0.0;
 #pragma unroll 4
                 for (int j = 0; j < 32; j += 2) {
-                    e0 += f2d_fast(src[j]);
-                    e1 += f2d_fast(src[j + 1]);
+                    e0 += src[j];
+                    e1 += src[j + 1];
                 }
                 s2 = e0 + e1;
             }

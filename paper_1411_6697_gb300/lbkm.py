@@ -107,7 +107,8 @@ class GradOut(ctypes.Structure):
     _fields_ = [("J", ctypes.c_double), ("J_mismatch", ctypes.c_double),
                 ("J_tne", ctypes.c_double), ("dS", ctypes.c_double * 16),
                 ("dQ", ctypes.c_double), ("domega1", ctypes.c_double),
-                ("drho0", ctypes.c_void_p), ("df0", ctypes.c_void_p)]
+                ("drho0", ctypes.c_void_p), ("df0", ctypes.c_void_p),
+                ("domega2", ctypes.c_double)]
 
 
 class Params24(ctypes.Structure):
@@ -380,7 +381,7 @@ class Solver:
 
     def grad(self, rho_target, steps, w_mismatch=1.0, w_tne=1.0, checkpoint_every=64,
              want_f0=False):
-        """lbkm_grad: J and dJ/d(S, Q, omega1, rho0 [, f0]) over `steps` steps from the
+        """lbkm_grad: J and dJ/d(S, Q, omega1, omega2, rho0 [, f0]) over `steps` steps from the
         current state (which is left unchanged)."""
         rt = np.ascontiguousarray(np.broadcast_to(np.asarray(rho_target, np.float64),
                                                   (self.nx,)))
@@ -394,6 +395,7 @@ class Solver:
         self._check(self._lib.lbkm_grad(self._h, ctypes.byref(ob), ctypes.byref(out)))
         return {"J": out.J, "J_mismatch": out.J_mismatch, "J_tne": out.J_tne,
                 "dS": np.array(out.dS[:]), "dQ": out.dQ, "domega1": out.domega1,
+                "domega2": out.domega2,
                 "drho0": drho0, "df0": df0}
 
     def set_wait_limit(self, timeout_ns, phantom_blocks=0):

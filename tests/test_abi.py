@@ -46,6 +46,8 @@ def test_struct_layout_matches_header(lib):
 int main(void) {
   printf("params %zu\n", sizeof(lbkm_params));
   printf("tne %zu\n", sizeof(lbkm_tne_global));
+  printf("gradout %zu\n", sizeof(lbkm_grad_out));
+  F(lbkm_grad_out, domega1) F(lbkm_grad_out, drho0) F(lbkm_grad_out, domega2)
   F(lbkm_params, gamma) F(lbkm_params, orbit_kind) F(lbkm_params, orbit_speed)
   F(lbkm_params, S) F(lbkm_params, Q) F(lbkm_params, T_ig) F(lbkm_params, dt)
   F(lbkm_params, bc_x) F(lbkm_params, tne_capacity) F(lbkm_params, time_scheme)
@@ -66,6 +68,9 @@ int main(void) {
         assert int(out[m]) == getattr(lbkm.Params, m).offset, m
     assert int(out["d_sum"]) == lbkm.TneGlobal.d_sum.offset
     assert int(out["step"]) == lbkm.TneGlobal.step.offset
+    assert int(out["gradout"]) == ctypes.sizeof(lbkm.GradOut)
+    for m in ("domega1", "drho0", "domega2"):
+        assert int(out[m]) == getattr(lbkm.GradOut, m).offset, m
 
 
 def test_default_params_are_host_only(lib):

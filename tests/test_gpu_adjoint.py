@@ -1,6 +1,8 @@
 """The CUDA discrete adjoint (lbkm_grad) against the FP64 reverse-mode oracle
 (oracle/torch_oracle.py, itself pinned to the C oracle and to central differences):
-objective value and gradients with respect to S, Q, omega1 and the initial density."""
+objective value and gradients with respect to S, Q, omega1, omega2 and the initial
+density, for the FP64 forward and for the FP32 forward (FP64 segments restarted from the
+FP32 run's checkpoints, against the oracle restarted from the same states)."""
 import numpy as np
 import pytest
 import torch
@@ -19,7 +21,7 @@ def gpu():
     __graft_entry__.build()
 
 
-def problem(nx, steps, omega1, driver):
+def problem(nx, steps, omega1, driver, omega2=0.0):
     # the ripple keeps the minmod branches of the f_i away from rounding-level
     # differences; on flat stretches the gradient would depend on how each side rounds
     # (without it the oracle's own drho0 near the boundary differs by ~10 % between an
@@ -28,7 +30,7 @@ def problem(nx, steps, omega1, driver):
     p = dict(c["params"])
     m = to.Model1D(nx, gamma=p["gamma"], orbit_kind=p["orbit_kind"],
                    orbit_speed=p["orbit_speed"], orbit_eta=p["orbit_eta"], T_ig=p["T_ig"],
-                   dx=p["dx"], dt=p["dt"])
+                   dx=p["dx"], dt=p["dt"], omega2=omega2)
     fl = c["fields"]
     # target: the run with perturbed rates and heat release (as the adjoint workload)
     rng = np.random.default_rng(li.SEED_BASE + 5)
@@ -43,26 +45,35 @@ def problem(nx, steps, omega1, driver):
     return c, p, m, rho_t
 
 
-def oracle_grad(c, p, m, rho_t, steps, w_tne, ck=0):
+def oracle_grad(c, p, m, rho_t, steps, w_tne, ck=0, restarts=None):
     fl = c["fields"]
     rho0 = to.to_t(fl["rho"][0]).requires_grad_(True)
     S = to.to_t(p["S"]).requires_grad_(True)
     Q = torch.tensor(p["Q"], dtype=torch.float64, requires_grad=True)
     k = torch.tensor(p["omega1"], dtype=torch.float64, requires_grad=True)
-    J, mis, tne = to.objective(m, rho0, to.to_t(fl["ux"][0]), to.to_t(fl["uy"][0]),
-                               to.to_t(fl["T"][0]), to.to_t(fl["lam"][0]), S, Q, k, steps,
-                               to.to_t(rho_t), w_tne, checkpoint_every=ck)
-    J.backward()
+    w2 = float(m.omega2)
+    m.omega2 = torch.tensor(w2, dtype=torch.float64, requires_grad=True)
+    try:
+        J, mis, tne = to.objective(m, rho0, to.to_t(fl["ux"][0]), to.to_t(fl["uy"][0]),
+                                   to.to_t(fl["T"][0]), to.to_t(fl["lam"][0]), S, Q, k, steps,
+                                   to.to_t(rho_t), w_tne, checkpoint_every=ck,
+                                   restarts=restarts)
+        J.backward()
+        # at omega2 = 0 the oracle takes the b = 0 closed form, which has no omega2 in it
+        dw2 = float(m.omega2.grad) if m.omega2.grad is not None else 0.0
+    finally:
+        m.omega2 = w2
     return dict(J=float(J), J_mismatch=float(mis), dS=S.grad.numpy(), dQ=float(Q.grad),
-                domega1=float(k.grad), drho0=rho0.grad.numpy())
+                domega1=float(k.grad), domega2=dw2, drho0=rho0.grad.numpy())
 
 
-def gpu_grad(c, p, rho_t, steps, w_tne, ck):
+def gpu_grad(c, p, rho_t, steps, w_tne, ck, precision=lbkm.F64, recovery=0, omega2=0.0):
     fl = c["fields"]
-    s = lbkm.Solver(nx=p["nx"], ny=1, precision=lbkm.F64, gamma=p["gamma"],
-                    orbit_kind=p["orbit_kind"], orbit_speed=p["orbit_speed"],
+    s = lbkm.Solver(nx=p["nx"], ny=1, precision=precision, recovery=recovery,
+                    gamma=p["gamma"], orbit_kind=p["orbit_kind"], orbit_speed=p["orbit_speed"],
                     orbit_eta=p["orbit_eta"], S=p["S"], Q=p["Q"], omega1=p["omega1"],
-                    T_ig=p["T_ig"], dx=p["dx"], dy=p["dx"], dt=p["dt"], bc=(1, 0))
+                    omega2=omega2, T_ig=p["T_ig"], dx=p["dx"], dy=p["dx"], dt=p["dt"],
+                    bc=(1, 0))
     s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
     before = s.get_state()
     g = s.grad(rho_t, steps, w_tne=w_tne, checkpoint_every=ck)
@@ -80,15 +91,87 @@ def compare(g, r, tol, tol_rho0=None):
     assert abs(g["domega1"] - r["domega1"]) <= tol * abs(r["domega1"])
     t0 = tol if tol_rho0 is None else tol_rho0
     assert np.abs(g["drho0"] - r["drho0"]).max() <= t0 * np.abs(r["drho0"]).max()
+    if r["domega2"] != 0.0:
+        assert abs(g["domega2"] - r["domega2"]) <= tol * abs(r["domega2"])
 
 
-@pytest.mark.parametrize("ck", [16, 7, 60])
-def test_adjoint_matches_reverse_mode_oracle_small(ck):
+def fp32_checkpoints(c, p, steps, ck, omega2=0.0):
+    """The FP32 run's states at steps 0, ck, 2 ck, ... (the checkpoints lbkm_grad keeps on
+    an FP32 handle: the same kernel and launches), as (f, lambda) in FP64."""
+    fl = c["fields"]
+    s = lbkm.Solver(nx=p["nx"], ny=1, precision=lbkm.F32, gamma=p["gamma"],
+                    orbit_kind=p["orbit_kind"], orbit_speed=p["orbit_speed"],
+                    orbit_eta=p["orbit_eta"], S=p["S"], Q=p["Q"], omega1=p["omega1"],
+                    omega2=omega2, T_ig=p["T_ig"], dx=p["dx"], dy=p["dx"], dt=p["dt"],
+                    bc=(1, 0))
+    s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    out = []
+    for n0 in range(0, steps, ck):
+        pl = s.f_planes()
+        out.append((pl[:16, 0].copy(), pl[16, 0].copy()))
+        s.step(min(ck, steps - n0))
+    s.close()
+    return out
+
+
+def report_fp32(g, r, label, W=None):
+    """Relative differences of the FP32 forward's gradient from the FP64 oracle's
+    (drho0 through the rows of W when given)."""
+    rep = {}
+    for key in ("J", "dS", "dQ", "domega1", "domega2", "drho0"):
+        a, b = (np.atleast_1d(np.asarray(x[key], float)) for x in (g, r))
+        if key == "dS":
+            a, b = a[4:], b[4:]
+        if key == "drho0" and W is not None:
+            a, b = W @ a, W @ b
+        scale = np.abs(b).max()
+        if scale > 0.0:
+            rep[key] = float(np.abs(a - b).max() / scale)
+    print(label, "relative difference from the FP64 gradient:",
+          {k: "%.2e" % v for k, v in rep.items()})
+    return rep
+
+
+def test_adjoint_with_omega2_matches_reverse_mode_oracle():
+    """omega2 != 0: the reaction's general closed form (Eq. (28), m = n = 1) in the
+    adjoint, and dJ/domega2."""
+    nx, steps = 96, 60
+    c, p, m, rho_t = problem(nx, steps, omega1=2e3, driver=16, omega2=800.0)
+    r = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0)
+    g = gpu_grad(c, p, rho_t, steps, w_tne=1.0, ck=16, omega2=800.0)
+    assert r["domega2"] != 0.0
+    compare(g, r, 1e-9)
+
+
+def test_adjoint_domega2_at_zero_is_the_limit():
+    """At omega2 = 0 the step takes the b = 0 closed form; dJ/domega2 there is the limit
+    of the general form's derivative. J is smooth in omega2, so the oracle's derivative
+    at omega2 = 1e-6 (b/a = 5e-10) stands in for it."""
     nx, steps = 96, 60
     c, p, m, rho_t = problem(nx, steps, omega1=2e3, driver=16)
+    g = gpu_grad(c, p, rho_t, steps, w_tne=1.0, ck=16)
+    m.omega2 = 1e-6
     r = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0)
-    g = gpu_grad(c, p, rho_t, steps, w_tne=1.0, ck=ck)
-    compare(g, r, 1e-9)
+    assert r["domega2"] != 0.0
+    assert abs(g["domega2"] - r["domega2"]) <= 1e-7 * abs(r["domega2"]), (g["domega2"], r["domega2"])
+
+
+@pytest.mark.parametrize("rec", [0, 1], ids=["f64-recovery", "df32-recovery"])
+def test_adjoint_of_the_fp32_forward_small(rec):
+    """lbkm_grad on an FP32 handle: the forward run and its checkpoints in FP32, each
+    segment recomputed and reversed in FP64 from its checkpoint. Against the oracle's
+    gradient of FP64 segments restarted from the same checkpoints (1e-9), and within the
+    FP32 tolerance (2e-5) of the FP64 forward's gradient."""
+    nx, steps, ck = 96, 60, 16
+    c, p, m, rho_t = problem(nx, steps, omega1=2e3, driver=16, omega2=800.0)
+    g = gpu_grad(c, p, rho_t, steps, w_tne=1.0, ck=ck, precision=lbkm.F32, recovery=rec,
+                 omega2=800.0)
+    rs = fp32_checkpoints(c, p, steps, ck, omega2=800.0)
+    compare(g, oracle_grad(c, p, m, rho_t, steps, w_tne=1.0, ck=ck, restarts=rs), 1e-9)
+    rep = report_fp32(g, oracle_grad(c, p, m, rho_t, steps, w_tne=1.0),
+                      "fp32 forward 96 x 60 rec %d" % rec)
+    for key in ("J", "dS", "dQ", "domega1", "domega2"):
+        assert rep[key] <= 2e-5, (key, rep[key])
 
 
 def bumps(nx, width=64.0, every=256):
@@ -96,8 +179,16 @@ def bumps(nx, width=64.0, every=256):
     return np.stack([np.exp(-0.5 * ((x - c0) / width) ** 2) for c0 in range(every // 2, nx, every)])
 
 
+@pytest.fixture(scope="module")
+def full_config():
+    nx, steps = 8192, 4000
+    c, p, m, rho_t = problem(nx, steps, omega1=2e4, driver=50)
+    r = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0, ck=64)
+    return c, p, m, rho_t, r
+
+
 @pytest.mark.slow
-def test_adjoint_full_config_size():
+def test_adjoint_full_config_size(full_config):
     """8192 cells, 4000 steps, checkpoints every 64, with the parameters of the
     16384-cell detonation (k = 2e4).
 
@@ -109,13 +200,32 @@ def test_adjoint_full_config_size():
     4e-11. Directional derivatives along smooth profiles are stable (the same flips
     move them by 1.6e-6), so drho0 is compared through 32 Gaussian bumps of width 64."""
     nx, steps = 8192, 4000
-    c, p, m, rho_t = problem(nx, steps, omega1=2e4, driver=50)
-    r = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0, ck=64)
+    c, p, m, rho_t, r = full_config
     g = gpu_grad(c, p, rho_t, steps, w_tne=1.0, ck=64)
     compare(g, r, 1e-7, tol_rho0=np.inf)
     W = bumps(nx)
     pg, pr = W @ g["drho0"], W @ r["drho0"]
     assert np.abs(pg - pr).max() <= 2e-5 * np.abs(pr).max(), (pg, pr)
+
+
+@pytest.mark.slow
+def test_adjoint_of_the_fp32_forward_full_config(full_config):
+    """The config-5 problem (8192 cells, 4000 steps, checkpoints every 64) on an FP32
+    handle: against the oracle restarted from the same FP32 checkpoints as tightly as the
+    FP64 path against the plain oracle (drho0 through the 32 smooth bumps), and reported
+    against the FP64 forward's gradient."""
+    nx, steps, ck = 8192, 4000, 64
+    c, p, m, rho_t, r = full_config
+    g = gpu_grad(c, p, rho_t, steps, w_tne=1.0, ck=ck, precision=lbkm.F32)
+    rs = fp32_checkpoints(c, p, steps, ck)
+    rr = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0, ck=ck, restarts=rs)
+    compare(g, rr, 1e-7, tol_rho0=np.inf)
+    W = bumps(nx)
+    pg, pr = W @ g["drho0"], W @ rr["drho0"]
+    assert np.abs(pg - pr).max() <= 2e-5 * np.abs(pr).max(), (pg, pr)
+    rep = report_fp32(g, r, "fp32 forward 8192 x 4000", W=W)
+    for key in ("J", "dS", "dQ", "domega1"):
+        assert rep[key] <= 1e-3, (key, rep[key])
 
 
 @pytest.mark.slow

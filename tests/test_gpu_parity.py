@@ -594,6 +594,59 @@ def test_tne_fields_and_on_the_fly_records(prec, rec):
     assert np.all(delta[:4] == 0)
 
 
+@pytest.mark.parametrize("rec", [0, 1], ids=["f32", "f32-df"])
+@pytest.mark.parametrize("nx,ny", [(300, 140), (1030, 261)])
+def test_tne_record_within_the_fp32_arithmetic_bound(rec, nx, ny):
+    """The FP32 step kernel's on-the-fly TNE record (Sec. VI, Eqs. (90)-(91)) against the
+    oracle's record of the very state the kernel stepped (read back before each step), so
+    no trajectory difference enters. What is left is the FP32 arithmetic of each cell's
+    Delta_k = f_hat_k - f_hat^eq_k and the summation. A moment passes at most seven
+    rounded operations (two butterfly levels, a four-term dot product, one more sum), an
+    equilibrium moment at most eight from the FP32-rounded macros (its terms share one
+    sign), the difference one more, so per cell |dDelta_k| <= 16 u S_k with u = 2^-24
+    and S_k = sum_i |M_ki| |f_i| + |f_hat^eq_k|.
+    The sums of Delta_k and |Delta_k| over cells are exact (each thread's FP32 sums carry
+    their rounding errors; everything past the thread is FP64), so they may differ from
+    the oracle's by no more than the sums of those per-cell bounds; the one-signed sums of
+    d and d^2 add at most 31 u of themselves (FP32 over 32 terms per column)."""
+    u = 2.0 ** -24
+    params, fields = mixed_2d(nx, ny, seed=nx + ny)
+    s, ob, f, lam = start(params, fields, lbkm.F32, rec, noise_seed=7, tne_every=1,
+                          tne_capacity=8)
+    area = params["dx"] * params["dx"]
+    absM = np.abs(ob.M)
+    worst = {}
+    for k in range(3):
+        fs = s.f_planes()[:16]
+        s.step(1)
+        h = s.tne_history()[-1]
+        assert h["step"] == k
+        delta, r = ob.tne(fs, fields=True)
+        fh = np.einsum("ki,iyx->kyx", ob.M, fs)
+        S = (np.einsum("ki,iyx->kyx", absM, np.abs(fs)) + np.abs(fh - delta))[4:]
+        E = 16 * u * S
+        D = delta[4:]
+        d = np.sqrt((D ** 2).sum(axis=0))
+        bound = dict(
+            sum=area * E.sum(axis=(1, 2)), abs_sum=area * E.sum(axis=(1, 2)),
+            min=E.max(axis=(1, 2)), max=E.max(axis=(1, 2)),
+            # d: the per-cell bound on the vector of errors, the FP32 accumulation of
+            # twelve squares and the hardware square root (relative 2^-23)
+            d_sum=area * (np.sqrt((E ** 2).sum(axis=0)) + (8 + 31) * u * d).sum(),
+            d2_sum=area * ((2 * np.abs(D) * E + E ** 2).sum(axis=0) + (12 + 31) * u * d ** 2).sum())
+        for key, b in bound.items():
+            got, want = np.asarray(h[key], float), np.asarray(r[key], float)
+            if got.ndim:  # index k - 1 holds Delta_k; Delta_1..4 vanish
+                got, want = got[4:], want[4:]
+            err = np.abs(got - want)
+            ratio = float(np.max(err / b))
+            worst[key] = max(worst.get(key, 0.0), ratio)
+            assert ratio <= 1.0, (k, key, ratio)
+    print("TNE record %dx%d rec %d: error / arithmetic bound" % (nx, ny, rec),
+          {k: round(v, 4) for k, v in worst.items()})
+    s.close()
+
+
 # ------------------------------------------------------------------ runtime behaviour
 def test_graph_chunks_equal_single_steps():
     params, fields = mixed_2d(50, 20, seed=9)
