@@ -189,9 +189,11 @@ void lbkm_destroy(lbkm_t h);
 lbkm_status lbkm_set_stream(lbkm_t h, void* cuda_stream);
 
 /* Equilibrium start, f = M^-1 f_hat^eq(rho, u, T) (Eq. (16)), and lambda.
- * rho, ux, uy, T, lambda: [ny][nx] FP64, host (on_device = 0) or device.
- * lambda may be NULL (then lambda = 0). Resets the step counter to 0 and the
- * TNE history. Errors: LBKM_EINVAL (NULL field), LBKM_ECUDA. */
+ * rho, ux, uy, T, lambda: [ny][nx] FP64, host (on_device = 0) or device. Host
+ * fields that are all page-locked (pinned) are read by the kernel in place; others
+ * go through a device temporary. lambda may be NULL (then lambda = 0). Resets the
+ * step counter to 0 and the TNE history. Synchronises.
+ * Errors: LBKM_EINVAL (NULL field), LBKM_ECUDA. */
 lbkm_status lbkm_init_fields(lbkm_t h, const double* rho, const double* ux, const double* uy,
                              const double* T, const double* lambda, int on_device);
 
@@ -212,7 +214,9 @@ int64_t lbkm_steps_taken(lbkm_t h);
 
 /* Macroscopic fields of the current state (Eqs. (5)-(7)): rho, u_x, u_y, T,
  * p = rho T and lambda, each [ny][nx] FP64, host or device; NULL pointers are
- * skipped. Synchronises. Errors: LBKM_ESTATE, LBKM_EUNSTABLE, LBKM_ECUDA. */
+ * skipped. Host outputs that are all page-locked (pinned) are written by the kernel in
+ * place; others through a device temporary. Synchronises.
+ * Errors: LBKM_ESTATE, LBKM_EUNSTABLE, LBKM_ECUDA. */
 lbkm_status lbkm_macros(lbkm_t h, double* rho, double* ux, double* uy, double* T, double* p,
                         double* lambda, int on_device);
 

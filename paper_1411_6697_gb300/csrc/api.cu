@@ -128,6 +128,18 @@ void dfree(const lbkm* h, void* ptr)
     else
         cudaFree(ptr);
 }
+// Page-locked host memory mapped into the device's address space at the same address
+// (any pinned buffer under unified addressing): kernels read or write it in place.
+bool device_addressable_host(const void* p)
+{
+    if (!p) return true;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost && at.devicePointer == p;
+}
 // a temporary of one call: freed (after its stream has drained) when the call returns
 struct DevTemp {
     const lbkm* h;
@@ -489,7 +501,11 @@ lbkm_status lbkm_init_fields(lbkm_t h, const double* rho, const double* ux, cons
     DevTemp tt(h);
     double* tmp = nullptr;
     const double *r = rho, *u = ux, *v = uy, *t = T, *l = lambda;
-    if (!on_device) {
+    // pinned host fields are read by the kernel in place
+    const bool in_place = on_device || (device_addressable_host(rho) && device_addressable_host(ux) &&
+                                        device_addressable_host(uy) && device_addressable_host(T) &&
+                                        device_addressable_host(lambda));
+    if (!in_place) {
         CUDA_TRY(h, dmalloc(h, &tt.p, nb * 5));
         tmp = static_cast<double*>(tt.p);
         const double* src[5] = {rho, ux, uy, T, lambda};
@@ -629,14 +645,20 @@ lbkm_status lbkm_macros(lbkm_t h, double* rho, double* ux, double* uy, double* T
     double* outs[6] = {rho, ux, uy, T, p, lambda};
     double* dev[6] = {rho, ux, uy, T, p, lambda};
     DevTemp tt(h);
-    if (!on_device) {
+    // pinned host outputs are written by the kernel in place
+    bool in_place = on_device;
+    if (!in_place) {
+        in_place = true;
+        for (int k = 0; k < 6; k++) in_place = in_place && device_addressable_host(outs[k]);
+    }
+    if (!in_place) {
         CUDA_TRY(h, dmalloc(h, &tt.p, nb * 6));
         double* tmp = static_cast<double*>(tt.p);
         for (int k = 0; k < 6; k++) dev[k] = outs[k] ? tmp + k * n : nullptr;
     }
     CUDA_TRY(h, launch_macros(h->precision, h->Kd, h->buf[h->cur], dev[0], dev[1], dev[2], dev[3],
                               dev[4], dev[5], h->stream));
-    if (!on_device) {
+    if (!in_place) {
         for (int k = 0; k < 6; k++)
             if (outs[k])
                 CUDA_TRY(h, cudaMemcpyAsync(outs[k], dev[k], nb, cudaMemcpyDeviceToHost, h->stream));

@@ -648,6 +648,32 @@ def test_tne_record_within_the_fp32_arithmetic_bound(rec, nx, ny):
 
 
 # ------------------------------------------------------------------ runtime behaviour
+def test_pinned_host_fields_are_used_in_place():
+    """init_fields from page-locked host tensors (read by the kernel in place) leaves the
+    state init_fields from pageable arrays leaves; macros into page-locked outputs
+    (written in place) equal macros into pageable arrays, bit for bit."""
+    import torch
+    nx, ny = 70, 37
+    params, fields = mixed_2d(nx, ny, seed=2)
+    names = ("rho", "ux", "uy", "T", "lam")
+    a, b = solver(params, lbkm.F32), solver(params, lbkm.F32)
+    a.init_fields(*[fields[k] for k in names])
+    pinned = [torch.from_numpy(np.array(np.broadcast_to(fields[k], (ny, nx)), np.float64)).pin_memory()
+              for k in names]
+    b.init_fields(*pinned)
+    assert np.array_equal(a.get_state(), b.get_state())
+    a.step(5)
+    b.step(5)
+    want = a.macros()
+    outs = {k: torch.full((ny, nx), np.nan, dtype=torch.float64).pin_memory()
+            for k in ("rho", "ux", "uy", "T", "p", "lam")}
+    b.macros(out=outs)
+    for k, t in outs.items():
+        assert np.array_equal(t.numpy(), want[k]), k
+    a.close()
+    b.close()
+
+
 def test_graph_chunks_equal_single_steps():
     params, fields = mixed_2d(50, 20, seed=9)
     a = solver(params, lbkm.F64, tne_every=3, tne_capacity=64)
