@@ -80,7 +80,7 @@ STEP_KERNEL_SOURCES = {
               "model.h"),
     "step": ("kernels.cu", "cell.cuh", "kernels.cuh", "model.h", "reduce.cuh"),
 }
-PROFILE = {"march": "march_kernel_reactive2d.md", "step": "step_kernel_fp64.md"}
+PROFILE = {"march": "march_kernel_reactive2d.md", "step": "step_kernel_fp64_reactive2d.md"}
 
 
 def step_kernel_digest(kernel="march"):
@@ -217,6 +217,22 @@ def cpu_oracle_rate(budget_s=12.0, side=1024):
     desc = "FP64 C oracle (OpenMP, %d threads) on a %dx%d window of the same recipe, %d steps, " \
            "%.1f s" % (int(os.environ["OMP_NUM_THREADS"]), side, side, steps, dt)
     return rate, desc, int(os.environ["OMP_NUM_THREADS"])
+
+
+def cpu_oracle_rate_single(budget_s=8.0, side=256):
+    """The same oracle on one host core: a child process started with OMP_NUM_THREADS=1
+    (OpenMP reads it when the oracle's first parallel region starts), a side x side window.
+    Returns (Mcell/s, desc) or (None, why)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = ("import json, bench; r = bench.cpu_oracle_rate(%r, %d); "
+            "print(json.dumps(r))" % (budget_s, side))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, check=True,
+                             capture_output=True, text=True, timeout=300).stdout
+        rate, desc, threads = json.loads(out.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return None, "single-thread run failed: %s" % e
+    return (rate, desc) if threads == 1 else (None, "the child ran %d threads" % threads)
 
 
 def cpu_oracle_rate_d2v24(budget_s=10.0, side=256):
@@ -775,8 +791,10 @@ def main():
         line["adjoint"] = measure_adjoint(1)
     if rank == 0 and not args.no_cpu_baseline:
         rate, desc, cores = cpu_oracle_rate()
+        rate1, desc1 = cpu_oracle_rate_single()
         line["cpu_baseline"] = {"value": rate, "unit": "Mcell-updates/s", "cores": cores,
-                                "kind": "oracle", "sample": desc}
+                                "kind": "oracle", "sample": desc,
+                                "single_thread": {"value": rate1, "sample": desc1}}
     if rank == 0:
         print(json.dumps(line))
     solver.close()
