@@ -169,7 +169,12 @@ typedef struct {
 /* Fill *p with defaults: D2V16 orbits (axis 2.7/eta 5, diagonal 2.2/eta 0,
  * axis 1.2/eta 3, diagonal 1.0/eta 0), gamma 1.4, S_k = 1e5, Q = 0, T_ig = 1.1,
  * dx = dy = 1e-3, dt = 1e-5, zero-gradient x, periodic y, LBKM_F64, TNE off,
- * tne_capacity 1. nx, ny are set to 0 and must be filled in. */
+ * tne_capacity 1. nx, ny are set to 0 and must be filled in.
+ * The default orbits carry the Sod tube, the steady detonation, the 2-D reactive field
+ * and Couette flow. Stronger shocks need faster orbits: the Lax tube runs with these
+ * speeds times 1.5, and the regular shock reflection of Sec. IV.C stays stable with them
+ * only to t ~ 0.11 (then it breaks down behind the reflection point, in the oracle too);
+ * the D2V24 handle (lbkm24.h) runs it to t = 0.5 with the paper's own set. */
 void lbkm_default_params(lbkm_params* p);
 
 /* Validate p, build M (rows m_1..m_16), invert it in block form and keep the

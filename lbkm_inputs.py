@@ -365,27 +365,30 @@ def _mode_sum(ks, amp, ph, nx, ny, deriv=None):
     return -((sy.T * w) @ cx + (cy.T * w) @ sx)
 
 
-def reactive2d(n=4096, steps=500, T_ig=1.0, seed_offset=3):
-    """2-D periodic reactive field on n x n cells: rho, T = 1 + 0.05 phi/max|phi| with phi
-    a sum of 32 random Fourier modes (1 <= |k| <= 16), solenoidal u of peak 0.1 from a
-    second mode set, lambda ~ U[0, 0.2], S ~ U[1e4, 1e5], Q = 1, k = 2e4.
+def reactive2d(n=4096, steps=500, T_ig=1.0, seed_offset=3, ny=None):
+    """2-D periodic reactive field on n x n cells (n x ny with ny): rho, T = 1 + 0.05
+    phi/max|phi| with phi a sum of 32 random Fourier modes (1 <= |k| <= 16), solenoidal u
+    of peak 0.1 from a second mode set, lambda ~ U[0, 0.2], S ~ U[1e4, 1e5], Q = 1, k = 2e4.
     T_ig defaults to 1.0: with T <= 1.05 the paper's 1.1 would leave the field inert."""
     rng = np.random.default_rng(SEED_BASE + seed_offset)
-    kmax = min(16, n // 4)
+    nx, ny = n, (n if ny is None else ny)
+    kmax = min(16, min(nx, ny) // 4)
     fields = {}
     for name in ("rho", "T"):
-        phi = _mode_sum(*_modes(rng, 32, kmax), n, n)
+        phi = _mode_sum(*_modes(rng, 32, kmax), nx, ny)
         fields[name] = 1.0 + 0.05 * phi / np.abs(phi).max()
     ks, amp, ph = _modes(rng, 32, kmax)
-    ux = _mode_sum(ks, amp, ph, n, n, deriv="y")
-    uy = -_mode_sum(ks, amp, ph, n, n, deriv="x")
+    ux = _mode_sum(ks, amp, ph, nx, ny, deriv="y")
+    uy = -_mode_sum(ks, amp, ph, nx, ny, deriv="x")
+    if nx != ny:  # u = (d/dy, -d/dx) of the stream function, each axis in its own units
+        ux, uy = ux / ny, uy / nx
     umax = np.sqrt(ux * ux + uy * uy).max()
     fields["ux"], fields["uy"] = 0.1 * ux / umax, 0.1 * uy / umax
-    fields["lam"] = rng.uniform(0.0, 0.2, (n, n))
+    fields["lam"] = rng.uniform(0.0, 0.2, (ny, nx))
     S = rng.uniform(1e4, 1e5, 16)
-    return dict(params=_base(nx=n, ny=n, S=S, Q=1.0, omega1=2e4, T_ig=T_ig, dx=1e-3,
+    return dict(params=_base(nx=nx, ny=ny, S=S, Q=1.0, omega1=2e4, T_ig=T_ig, dx=1e-3,
                              dt=5e-6, bc_x=0, bc_y=0),
-                steps=steps, fields=fields, name="reactive2d_%dx%d" % (n, n))
+                steps=steps, fields=fields, name="reactive2d_%dx%d" % (nx, ny))
 
 
 def batched(n_instances=512, steps=5000, nx_min=1024, nx_max=65536, driver=50):

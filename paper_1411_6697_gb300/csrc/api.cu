@@ -713,11 +713,17 @@ lbkm_status lbkm_tne_history(lbkm_t h, lbkm_tne_global* out, int32_t max_records
     const int cap = h->p.tne_capacity;
     int64_t have = c.hist_count < cap ? c.hist_count : cap;
     int64_t take = have < max_records ? have : max_records;
-    for (int64_t k = 0; k < take; k++) {
-        int64_t idx = (c.hist_count - have + k) % cap;
-        TneRecord r;
-        CUDA_TRY(h, cudaMemcpy(&r, h->hist + idx, sizeof(r), cudaMemcpyDeviceToHost));
-        record_to_global(r, out + k);
+    if (take > 0) {
+        // the oldest records kept, in order: one copy up to the ring's end, one after it
+        std::vector<TneRecord> r((size_t)take);
+        const int64_t start = (c.hist_count - have) % cap;
+        const int64_t n1 = take < cap - start ? take : cap - start;
+        CUDA_TRY(h, cudaMemcpy(r.data(), h->hist + start, sizeof(TneRecord) * n1,
+                               cudaMemcpyDeviceToHost));
+        if (take > n1)
+            CUDA_TRY(h, cudaMemcpy(r.data() + n1, h->hist, sizeof(TneRecord) * (take - n1),
+                                   cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < take; k++) record_to_global(r[k], out + k);
     }
     *n_out = (int32_t)take;
     return LBKM_OK;

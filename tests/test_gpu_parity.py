@@ -471,7 +471,10 @@ def reactive_window_ref():
     full 500 steps from the FP32-rounded start (with the TNE record of every step), and the
     same run with its state rounded to FP32 after every step (FP64 arithmetic): the cost
     of FP32 storage alone, per plane."""
-    c = li.reactive2d(n=1024, steps=500)
+    return _storage_ref(li.reactive2d(n=1024, steps=500))
+
+
+def _storage_ref(c):
     fl = c["fields"]
     ob = make_oracle(c["params"])
     f32 = lambda a: np.asarray(a).astype(np.float32).astype(np.float64)
@@ -522,6 +525,41 @@ def test_reactive2d_window_full_length(reactive_window_ref, prec, rec):
         assert np.all(np.abs(recs[n]["sum"] - want["sum"]) <= tol * sscale), n
         assert np.all(np.abs(recs[n]["abs_sum"] - want["abs_sum"]) <= tol * sscale), n
         assert abs(recs[n]["d_sum"] - want["d_sum"]) <= tol * dscale, n
+
+
+@pytest.fixture(scope="module")
+def wrapping_strips_ref():
+    """The oracle on a periodic 2310 x 1050 field of the same recipe, 100 steps, and the
+    same run with its state rounded to FP32 after every step."""
+    return _storage_ref(li.reactive2d(n=2310, ny=1050, steps=100))
+
+
+@pytest.mark.parametrize("prec,rec", [(lbkm.F32, 0), (lbkm.F32, 1)], ids=["f32", "f32-df"])
+def test_reactive2d_strips_of_the_bench_wrap(wrapping_strips_ref, prec, rec):
+    """The strip shape the bench runs (64 rows x 128 columns) on a grid of 19 x 17 = 323
+    strips for 304 resident blocks, so the persistent strip loop wraps; a 6-column strip
+    at the x edge and a 26-row strip at the y edge; 100 steps against the oracle, every
+    plane element by element, bound as in the 1024 x 1024 window test."""
+    c, ob, f0, l0, f_ref, lam_ref, hist, storage = wrapping_strips_ref
+    s = solver(c["params"], prec, rec, tne_every=1, tne_capacity=100)
+    s.set_state(state_bytes(np.concatenate([f0, l0[None]]), prec))
+    s.step(c["steps"])
+    got = s.f_planes()
+    errs = [rel_l2(got[i], f_ref[i]) for i in range(16)] + [rel_l2(got[16], lam_ref)]
+    print("reactive2d 2310x1050 x 100: plane errors", np.round(np.array(errs) / 1e-5, 2).tolist(),
+          "x1e-5; FP32 storage alone", np.round(np.array(storage) / 1e-5, 2).tolist(), "x1e-5")
+    for i, e in enumerate(errs):
+        assert e <= max(2e-5, 2 * storage[i]), (i, e, storage[i])
+    recs = s.tne_history()
+    assert [r["step"] for r in recs] == list(range(c["steps"]))
+    area = c["params"]["dx"] ** 2
+    fh = np.abs(np.einsum("ki,iyx->kyx", ob.M, f0))
+    sscale = fh.sum(axis=(1, 2)) * area
+    for n in (0, 99):
+        want = oracle_unpack(hist[n])
+        tol = 2e-5 if n == 0 else 2 * max(2e-5, 2 * max(storage))
+        assert np.all(np.abs(recs[n]["abs_sum"] - want["abs_sum"]) <= tol * sscale), n
+    s.close()
 
 
 # ------------------------------------------------------------------ full 2-D size, sampled
@@ -687,6 +725,27 @@ def test_graph_chunks_equal_single_steps():
     ha, hb = a.tne_history(), b.tne_history()
     assert len(ha) == 24 and [h["step"] for h in ha] == list(range(0, 71, 3))
     assert all(np.array_equal(x["sum"], y["sum"]) for x, y in zip(ha, hb))
+
+
+def test_tne_history_ring_keeps_the_newest_records():
+    """A history ring of 8 after 20 recorded steps holds steps 12..19, in order and equal
+    to those records of a run with room for all of them (the copy wraps at the ring's end)."""
+    params, fields = mixed_2d(45, 19, seed=6)
+    a = solver(params, lbkm.F32, tne_every=1, tne_capacity=8)
+    b = solver(params, lbkm.F32, tne_every=1, tne_capacity=32)
+    for s in (a, b):
+        s.init_fields(fields["rho"], fields["ux"], fields["uy"], fields["T"], fields["lam"])
+        s.step(20)
+    ha, hb = a.tne_history(), b.tne_history()
+    assert [h["step"] for h in ha] == list(range(12, 20))
+    assert [h["step"] for h in hb] == list(range(20))
+    for x, y in zip(ha, hb[12:]):
+        for k in ("sum", "abs_sum", "min", "max"):
+            assert np.array_equal(x[k], y[k]), k
+        assert x["d_sum"] == y["d_sum"] and x["d2_sum"] == y["d2_sum"]
+    assert [h["step"] for h in a.tne_history(max_records=3)] == [12, 13, 14]
+    a.close()
+    b.close()
 
 
 def test_checkpoint_resume_is_bitwise():
