@@ -79,8 +79,10 @@ STEP_KERNEL_SOURCES = {
     "march": ("march.cu", "pair.cuh", "vec2.cuh", "reduce.cuh", "cell.cuh", "kernels.cuh",
               "model.h"),
     "step": ("kernels.cu", "cell.cuh", "kernels.cuh", "model.h", "reduce.cuh"),
+    "batch": ("batch.cu", "cell.cuh", "pair.cuh", "vec2.cuh", "kernels.cuh", "model.h"),
 }
-PROFILE = {"march": "march_kernel_reactive2d.md", "step": "step_kernel_fp64_reactive2d.md"}
+PROFILE = {"march": "march_kernel_reactive2d.md", "step": "step_kernel_fp64_reactive2d.md",
+           "batch": "batch_kernel_batched.md"}
 
 
 def step_kernel_digest(kernel="march"):
@@ -110,7 +112,8 @@ def profile_traffic(kernel, kernel_tag):
     if kv.get("source_sha256") != digest:
         return None
     try:
-        return float(kv.get("traffic_bytes_per_launch_%s" % kernel_tag))
+        return float(kv.get(kernel_tag if kernel_tag.startswith("traffic_") else
+                            "traffic_bytes_per_launch_%s" % kernel_tag))
     except (TypeError, ValueError):
         return None
 
@@ -351,7 +354,8 @@ def measure_batched(steps, warmup, recovery="f64", plain_instances=24, plain_ste
             "conserved_moment_recovery": recovery,
             "autotuned": {"threads": chosen[0], "blocks_per_sm": chosen[1], "blocks": chosen[2]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak,
+                         "traffic": profile_traffic("batch", "traffic_bytes_per_step_f32"), "peak_kind": peak_kind,
                          "kernel": "batch_kernel (f32)",
                          "algorithmic_bytes_per_step": BYTES_PER_CELL["f32"] * n},
             "plain_f64_single_instance_mcell_per_s": plain,
