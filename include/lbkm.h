@@ -123,7 +123,10 @@ typedef struct {
     double dx, dy, dt;     /* grid spacing and time step */
     int32_t bc_x, bc_y;    /* lbkm_bc for each direction */
     int32_t tne_every;     /* 0: no on-the-fly TNE; k > 0: reduce the TNE of the
-                              input state of every k-th step into the history */
+                              input state of every k-th step into the history (the
+                              FP32 2-D step then gathers the statistics on every step
+                              and reduces them on the k-th: a step costs the same for
+                              any k > 0, and with 0 it carries no TNE work at all) */
     int32_t tne_capacity;  /* records kept in the device history ring (>= 1) */
     double wall_ux[2], wall_uy[2], wall_T[2]; /* bc_y = LBKM_BC_WALL: velocity and
                               temperature of the wall below row 0 ([0]) and above

@@ -251,7 +251,9 @@ __device__ __forceinline__ void issue_pair(const float* __restrict__ in, float* 
         const int ft = tid - 64; // 0..63
         // tasks: (row, plane, side) with side 0 = columns [x0-2, cs), side 1 = columns
         // [max(ce, x0-2), min(nx+4, x0+BW+2)) (the ghost columns active cells read, and
-        // two more that only an inactive neighbour reads); Dirichlet rows: every column
+        // two more that only an inactive neighbour reads; with periodic or zero-gradient
+        // sides every column up to x0+BW+2, so that a cell past the grid holds a real
+        // cell's values); Dirichlet rows: every column
         for (int task = ft; task < 4 * NPLANE; task += 64) {
             const int side = task & 1, rp = task >> 1;
             const int r = ra + rp / NPLANE, p = rp % NPLANE;
@@ -265,7 +267,7 @@ __device__ __forceinline__ void issue_pair(const float* __restrict__ in, float* 
                 c1 = side ? x0 + BW + 2 : x0 + BW / 2;
             } else {
                 c0 = side ? (ce > x0 - 2 ? ce : x0 - 2) : x0 - 2;
-                c1 = side ? (K.nx + 4 < x0 + BW + 2 ? K.nx + 4 : x0 + BW + 2) : cs;
+                c1 = side ? (!GEN ? x0 + BW + 2 : (K.nx + 4 < x0 + BW + 2 ? K.nx + 4 : x0 + BW + 2)) : cs;
                 if (!side && ce <= cs) c1 = x0 - 2; // no bulk copy: side 1 takes the row
                 if (side && ce <= cs) c0 = x0 - 2;
             }
@@ -380,12 +382,16 @@ __device__ __forceinline__ void acc_exact(V2& s, float& c, V2 x)
 // ---------------- the update of one row by one warp pair -------------------------
 // Row y, the thread's cells x0 + 2t and x0 + 2t + 1 (active when act0 / act1), macros
 // mc recovered in the previous iteration; the results go to the output rows ob
-// (17 planes of BW floats).
-template <int REC, bool AVG, bool SRT>
+// (17 planes of BW floats). TNE: the row's TNE statistics join the thread's sums. With
+// periodic or zero-gradient sides (!GEN) a cell past the grid's last column holds a real
+// cell's values (staging fills the whole box through the side map), so the statistics
+// run without a branch: the sums take Delta_k times the lane mask am (1 active, 0 not),
+// the extremes the unmasked values. With general sides they take the active cells only.
+template <int REC, bool AVG, bool SRT, bool TNE, bool GEN>
 __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob, int y, int x0,
                                            int t, const ModelConst<float>& K, const StepLaunch& a,
-                                           const Mac& mc, bool act0, bool act1, bool do_tne,
-                                           TneAcc& acc, float* tmin, float* tmax)
+                                           const Mac& mc, bool act0, bool act1, V2 am, TneAcc& acc,
+                                           float* tmin, float* tmax)
 {
     const int lx = XO + 2 * t;
     const float dt = K.dt;
@@ -431,32 +437,39 @@ __device__ __forceinline__ void update_row(float* smem_f, float* ring, float* ob
     }
     // TNE statistics of the state being stepped (Eqs. (90)-(91)); a cell past the grid's
     // last column contributes nothing
-    if (do_tne && act1) {
-        V2 d2(0.f);
+    if constexpr (TNE) {
+        auto both = [&](V2 mask) {
+            V2 d2(0.f);
 #pragma unroll
-        for (int k = 0; k < TNE_K; k++) {
-            const V2 Dk = m[k + 4];
-            d2 = fma(Dk, Dk, d2);
-            acc_exact(acc.sum[k], acc.sumc[k], Dk);
-            acc_exact(acc.abs[k], acc.absc[k], V2(fabsf(Dk.x()), fabsf(Dk.y())));
-            tmin[k] = fmin3(tmin[k], Dk.x(), Dk.y());
-            tmax[k] = fmax3(tmax[k], Dk.x(), Dk.y());
-        }
-        acc.dsum += V2(sqrt_approx(d2.x()), sqrt_approx(d2.y()));
-        acc.d2sum += d2;
-    } else if (do_tne && act0) { // the last cell of a row, alone in its pair
-        float d2 = 0.f;
+            for (int k = 0; k < TNE_K; k++) {
+                const V2 Dk = m[k + 4], Dm = Dk * mask;
+                d2 = fma(Dm, Dm, d2);
+                acc_exact(acc.sum[k], acc.sumc[k], Dm);
+                acc_exact(acc.abs[k], acc.absc[k], V2(fabsf(Dm.x()), fabsf(Dm.y())));
+                tmin[k] = fmin3(tmin[k], Dk.x(), Dk.y());
+                tmax[k] = fmax3(tmax[k], Dk.x(), Dk.y());
+            }
+            acc.dsum += V2(sqrt_approx(d2.x()), sqrt_approx(d2.y()));
+            acc.d2sum += d2;
+        };
+        if constexpr (!GEN) {
+            both(am);
+        } else if (act1) {
+            both(V2(1.f));
+        } else if (act0) { // the last cell of a row, alone in its pair
+            float d2 = 0.f;
 #pragma unroll
-        for (int k = 0; k < TNE_K; k++) {
-            const float Dk = m[k + 4].x();
-            d2 = fmaf(Dk, Dk, d2);
-            acc_exact(acc.sum[k], acc.sumc[k], V2(Dk, 0.f));
-            acc_exact(acc.abs[k], acc.absc[k], V2(fabsf(Dk), 0.f));
-            tmin[k] = fminf(tmin[k], Dk);
-            tmax[k] = fmaxf(tmax[k], Dk);
+            for (int k = 0; k < TNE_K; k++) {
+                const float Dk = m[k + 4].x();
+                d2 = fmaf(Dk, Dk, d2);
+                acc_exact(acc.sum[k], acc.sumc[k], V2(Dk, 0.f));
+                acc_exact(acc.abs[k], acc.absc[k], V2(fabsf(Dk), 0.f));
+                tmin[k] = fminf(tmin[k], Dk);
+                tmax[k] = fmaxf(tmax[k], Dk);
+            }
+            acc.dsum += V2(sqrt_approx(d2), 0.f);
+            acc.d2sum += V2(d2, 0.f);
         }
-        acc.dsum += V2(sqrt_approx(d2), 0.f);
-        acc.d2sum += V2(d2, 0.f);
     }
 
     // grad u: x from the (u, v) row y (halo columns included), y from rows y+-1
@@ -583,7 +596,9 @@ __device__ __forceinline__ void bulk_wait_all()
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-template <int REC, bool GEN, bool AVG, bool SRT>
+// TNE: the TNE statistics are accumulated on every step (the tne_every > 0 handles) and
+// reduced into the step's partials when the step is due; no TNE code otherwise
+template <int REC, bool GEN, bool AVG, bool SRT, bool TNE>
 __global__ void __launch_bounds__(MT, 2)
     march_kernel(const ModelConst<float> K, const StepLaunch a, int strip_rows,
                  const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout)
@@ -607,7 +622,7 @@ __global__ void __launch_bounds__(MT, 2)
     const DfConst C = df_constants(K);
     const int64_t step = a.ctr->step;
     // AVG stages reduce no TNE
-    const bool do_tne = !AVG && a.tne_every > 0 && (step % a.tne_every) == 0;
+    const bool do_tne = TNE && !AVG && a.tne_every > 0 && (step % a.tne_every) == 0;
     if (tid < NSUM) tsum[tid] = 0.0;
     if (tid < NMB) mbar_init(mbar0 + 8 * tid, 1 + 64);
     fence_async_shared();
@@ -635,6 +650,7 @@ __global__ void __launch_bounds__(MT, 2)
         const int yend = y0 + strip_rows < ny ? y0 + strip_rows : ny;
         const int cx = x0 + 2 * t;
         const bool act0 = cx < nx, act1 = cx + 1 < nx;
+        const V2 am(act0 ? 1.f : 0.f, act1 ? 1.f : 0.f); // lanes whose cells are in the grid
         const int npairs = (yend - y0 + 5) / 2; // rows y0-2 .. yend+1
         const uint32_t q0 = q_issued;
         TneAcc acc;
@@ -678,8 +694,8 @@ __global__ void __launch_bounds__(MT, 2)
                 break;
             }
             if (y + wpair < yend)
-                update_row<REC, AVG, SRT>(smem_f, ring, ob, y + wpair, x0, t, K, a, cur, act0, act1,
-                                     do_tne, acc, tmin, tmax);
+                update_row<REC, AVG, SRT, TNE, GEN>(smem_f, ring, ob, y + wpair, x0, t, K, a, cur,
+                                                    act0, act1, am, acc, tmin, tmax);
             cur = nxt;
             fence_async_shared(); // the output rows are read by the bulk stores
             __syncthreads();
@@ -772,10 +788,10 @@ __global__ void __launch_bounds__(MT, 2)
     }
 }
 
-template <int REC, bool GEN, bool AVG, bool SRT>
+template <int REC, bool GEN, bool AVG, bool SRT, bool TNE>
 cudaError_t march_prepare()
 {
-    static cudaError_t done = cudaFuncSetAttribute(march_kernel<REC, GEN, AVG, SRT>,
+    static cudaError_t done = cudaFuncSetAttribute(march_kernel<REC, GEN, AVG, SRT, TNE>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)MARCH_SMEM);
     return done;
@@ -784,13 +800,13 @@ cudaError_t march_prepare()
 // resident blocks per SM of a variant; the averaging stage of a step shares the grid
 // of its first stage, and the single-relaxation-time variant the grid of the general
 // one, so all must fit that many blocks (checked at launch)
-template <int REC, bool GEN, bool AVG, bool SRT>
+template <int REC, bool GEN, bool AVG, bool SRT, bool TNE>
 int resident_of()
 {
     static int per_sm = -1;
     if (per_sm < 0) {
-        if (march_prepare<REC, GEN, AVG, SRT>() != cudaSuccess) return -1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<REC, GEN, AVG, SRT>,
+        if (march_prepare<REC, GEN, AVG, SRT, TNE>() != cudaSuccess) return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<REC, GEN, AVG, SRT, TNE>,
                                                           MT, MARCH_SMEM) != cudaSuccess)
             return -1;
         if (per_sm < 1) per_sm = 1;
@@ -801,12 +817,12 @@ int resident_of()
 template <int REC, bool GEN>
 int resident_min()
 {
-    int a = resident_of<REC, GEN, false, false>(), b = resident_of<REC, GEN, true, false>();
-    if constexpr (!GEN) {
-        const int c = resident_of<REC, false, false, true>();
-        b = c < b ? c : b;
-    }
-    return a < 0 || b < 0 ? -1 : (a < b ? a : b);
+    int r[4] = {resident_of<REC, GEN, false, false, true>(), resident_of<REC, GEN, false, false, false>(),
+                resident_of<REC, GEN, true, false, false>(),
+                GEN ? 1 << 20 : resident_of<REC, false, false, true, false>()};
+    int m = r[0];
+    for (int i = 1; i < 4; i++) m = r[i] < 0 || m < 0 ? -1 : (r[i] < m ? r[i] : m);
+    return m;
 }
 
 int resident_blocks(int mode)
@@ -831,11 +847,13 @@ void launch_variant(bool avg, bool srt, const ModelConst<float>& K, const StepLa
     const CUtensorMap& tin = *reinterpret_cast<const CUtensorMap*>(a.tm_in);
     const CUtensorMap& tout = *reinterpret_cast<const CUtensorMap*>(a.tm_out);
     if (avg)
-        march_kernel<REC, GEN, true, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
+        march_kernel<REC, GEN, true, false, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
     else if (srt && !GEN)
-        march_kernel<REC, false, false, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
+        march_kernel<REC, false, false, true, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
+    else if (a.tne_every > 0)
+        march_kernel<REC, GEN, false, false, true><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
     else
-        march_kernel<REC, GEN, false, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
+        march_kernel<REC, GEN, false, false, false><<<a.grid, MT, MARCH_SMEM, s>>>(K, a, rows, tin, tout);
 }
 
 } // namespace
