@@ -565,12 +565,13 @@ def test_reactive2d_strips_of_the_bench_wrap(wrapping_strips_ref, prec, rec):
 # ------------------------------------------------------------------ full 2-D size, sampled
 @pytest.mark.parametrize("prec,rec", [(lbkm.F32, 0), (lbkm.F32, 1)], ids=["f32", "f32-df"])
 def test_reactive2d_full_size_sampled(prec, rec):
-    """4096 x 4096 periodic reactive field, 3 steps: sampled cells against the oracle run
-    on a periodic patch around each sample (the update has radius 2 per step)."""
+    """4096 x 4096 periodic reactive field, 3 steps in the bench's configuration (TNE every
+    step): sampled cells against the oracle run on a periodic patch around each sample
+    (the update has radius 2 per step)."""
     import torch
     c = li.reactive2d(n=4096, steps=3)
     fl = c["fields"]
-    s = solver(c["params"], prec, rec)
+    s = solver(c["params"], prec, rec, tne_every=1, tne_capacity=4)
     s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
     steps = c["steps"]
     s.step(steps)
@@ -593,6 +594,40 @@ def test_reactive2d_full_size_sampled(prec, rec):
         got = planes[:, yy, xx].double().cpu().numpy()
         assert np.abs(got - want).max() <= 2e-5 * np.abs(want).max(), (yy, xx)
     del torch
+
+
+@pytest.mark.parametrize("rec", [0, 1], ids=["f32", "f32-df"])
+def test_reactive2d_full_size_tne_record(rec):
+    """The bench's workload at full size (4096 x 4096, TNE every step): the on-the-fly record
+    of step 2 against the oracle's record of the very state the kernel stepped there, read
+    back, within the FP32-arithmetic bound of test_tne_record_within_the_fp32_arithmetic_bound
+    (per cell |dDelta_k| <= 16 u S_k; exact sums)."""
+    u = 2.0 ** -24
+    c = li.reactive2d(n=4096, steps=3)
+    fl = c["fields"]
+    s = solver(c["params"], lbkm.F32, rec, tne_every=1, tne_capacity=4)
+    s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    s.step(2)
+    fs = s.f_planes()[:16]
+    s.step(1)
+    h = s.tne_history()[-1]
+    assert h["step"] == 2
+    s.close()
+    ob = make_oracle(c["params"])
+    delta, r = ob.tne(fs, fields=True)
+    area = c["params"]["dx"] ** 2
+    fh = np.einsum("ki,iyx->kyx", ob.M, fs)
+    S = np.einsum("ki,iyx->kyx", np.abs(ob.M), np.abs(fs))
+    S += np.abs(fh - delta)
+    E = 16 * u * S[4:]
+    del fh, S
+    for key, b in (("sum", area * E.sum(axis=(1, 2))), ("abs_sum", area * E.sum(axis=(1, 2))),
+                   ("min", E.max(axis=(1, 2))), ("max", E.max(axis=(1, 2)))):
+        err = np.abs(np.asarray(h[key])[4:] - np.asarray(r[key])[4:])
+        assert np.all(err <= b), (key, float(np.max(err / b)))
+    d = np.sqrt((delta[4:] ** 2).sum(axis=0))
+    bd = area * (np.sqrt((E ** 2).sum(axis=0)) + (8 + 31) * u * d).sum()
+    assert abs(h["d_sum"] - r["d_sum"]) <= bd
 
 
 # ------------------------------------------------------------------ TNE
