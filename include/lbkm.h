@@ -306,7 +306,7 @@ typedef struct {
  * derivative covers omega2 != 0 (the closed form of Eq. (28)). The ignition
  * switch T > T_ig stays a hard switch (no derivative through it); minmod and the
  * lambda clamp follow the branch the forward values take. The handle's state is
- * left unchanged. Needs a handle with ny = 1, periodic or zero-gradient ends and
+ * left unchanged. Needs a handle with ny = 1, periodic (nx >= 5) or zero-gradient ends and
  * forward Euler (not batched). Errors: LBKM_EINVAL, LBKM_ESTATE, LBKM_ENOMEM,
  * LBKM_ECUDA, LBKM_EUNSTABLE. Synchronises. */
 lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* obj, lbkm_grad_out* out);

@@ -5,7 +5,7 @@ gradient of the discrete forward map by reverse-mode automatic differentiation,
 against which the hand-written CUDA adjoint is checked. It implements the same
 step as ``lbkm_oracle.c`` (Sec. II of the paper, CE sign of A_hat per Eq. (29),
 chemical term in moment space per Eqs. (19)-(23), reaction Eq. (28) integrated
-exactly over dt, NND advection, forward Euler) for Ny = 1 with zero-gradient
+exactly over dt, NND advection, forward Euler) for Ny = 1 with zero-gradient (or periodic)
 ghost cells, written independently with whole-array operations.
 
 Non-smooth points take the conventions the adjoint uses: the ignition test
@@ -93,8 +93,11 @@ def record_branches(fn):
         _RECORD = None
 
 
-def _pad(a):
-    """Two zero-gradient ghost cells on each side along the last axis."""
+def _pad(a, periodic=False):
+    """Two ghost cells on each side along the last axis: zero-gradient copies of the end
+    cells, or the periodic images."""
+    if periodic:
+        return torch.cat([a[..., -2:], a, a[..., :2]], dim=-1)
     return torch.cat([a[..., :1], a[..., :1], a, a[..., -1:], a[..., -1:]], dim=-1)
 
 
@@ -102,7 +105,7 @@ class Model1D:
     """Set-up shared by the forward map and its objective."""
 
     def __init__(self, nx, *, gamma, orbit_kind, orbit_speed, orbit_eta, T_ig, dx, dt,
-                 omega2=0.0):
+                 omega2=0.0, periodic=False):
         self.nx = nx
         self.vx, self.vy, self.eta = _velocities(orbit_kind, orbit_speed, orbit_eta)
         self.M = _moment_rows(self.vx, self.vy, self.eta)
@@ -110,6 +113,7 @@ class Model1D:
         self.I = 2.0 / (gamma - 1.0) - D
         self.DI = D + self.I
         self.T_ig, self.dx, self.dt, self.omega2 = T_ig, dx, dt, omega2
+        self.periodic = periodic
 
     def init(self, rho, ux, uy, T):
         return self.Minv @ _feq(rho, ux, uy, T, self.DI)
@@ -131,7 +135,7 @@ class Model1D:
         m, rho, ux, uy, T = self.macros(f)
         q = _feq(rho, ux, uy, T, DI)
         Dk = m[4:] - q[4:]
-        uxp, uyp = _pad(ux), _pad(uy)
+        uxp, uyp = _pad(ux, self.periodic), _pad(uy, self.periodic)
         gx = (uxp[3:-1] - uxp[1:-3]) / (2 * dx)
         gy = (uyp[3:-1] - uyp[1:-3]) / (2 * dx)
         th = gx / DI
@@ -157,7 +161,7 @@ class Model1D:
         om_hat = om_hat + torch.stack([torch.zeros_like(A8)] * 7 + [A8, A9] +
                                       [torch.zeros_like(A8)] * 7)
         Om = self.Minv @ om_hat
-        fp = _pad(f)
+        fp = _pad(f, self.periodic)
         adv = []
         for i in range(16):
             v = float(self.vx[i])
@@ -173,7 +177,7 @@ class Model1D:
             else:
                 adv.append(torch.zeros(self.nx, dtype=f.dtype))
         f_new = f + dt * (Om - torch.stack(adv))
-        lp = _pad(lam0)
+        lp = _pad(lam0, self.periodic)
         g = [lp[k:k + self.nx] for k in range(5)]
         Lp = (g[2] + 0.5 * _mm(g[2] - g[1], g[3] - g[2])) - (g[1] + 0.5 * _mm(g[1] - g[0], g[2] - g[1]))
         Ln = (g[3] - 0.5 * _mm(g[3] - g[2], g[4] - g[3])) - (g[2] - 0.5 * _mm(g[2] - g[1], g[3] - g[2]))

@@ -32,6 +32,15 @@ namespace {
 
 __device__ __forceinline__ int bmap(int j, int n, int bc) { return map_index(j, n, bc); }
 
+// the cell at distance d from j whose stencil may read j: its periodic image, or -1 past
+// a zero-gradient end (nx >= 5 keeps the periodic candidates of d = -2..2 distinct)
+__device__ __forceinline__ int neighbour(int j, int d, int n, int bc)
+{
+    const int jp = j + d;
+    if (bc == 0) return jp < 0 ? jp + n : (jp >= n ? jp - n : jp);
+    return jp < 0 || jp >= n ? -1 : jp;
+}
+
 // minmod branch of mm(a, b): alpha = derivative w.r.t. a, beta w.r.t. b
 __device__ __forceinline__ void mm_branch(double a, double b, double& al, double& be)
 {
@@ -271,8 +280,9 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nx; j += gridDim.x * blockDim.x) {
         // velocity gradients of the neighbours that read u_j
         double uxb = a.loc[nx + j], uyb = a.loc[2 * nx + j];
-        for (int jp = j - 1; jp <= j + 1; jp++) {
-            if (jp < 0 || jp >= nx) continue;
+        for (int d = -1; d <= 1; d++) {
+            const int jp = neighbour(j, d, nx, bc);
+            if (jp < 0) continue;
             if (bmap(jp + 1, nx, bc) == j) uxb += K.half_inv_dx * a.gb[jp], uyb += K.half_inv_dx * a.gb[nx + jp];
             if (bmap(jp - 1, nx, bc) == j) uxb -= K.half_inv_dx * a.gb[jp], uyb -= K.half_inv_dx * a.gb[nx + jp];
         }
@@ -300,8 +310,9 @@ __global__ void __launch_bounds__(ADJ_THREADS)
             const double v = a.vx[i];
             if (v != 0.0) {
                 const double* fi = a.f + (size_t)i * K.plane;
-                for (int jp = j - 2; jp <= j + 2; jp++) {
-                    if (jp < 0 || jp >= nx) continue;
+                for (int d = -2; d <= 2; d++) {
+                    const int jp = neighbour(j, d, nx, bc);
+                    if (jp < 0) continue;
                     double qv[5], c[5];
                     for (int o = -2; o <= 2; o++) qv[o + 2] = fi[bmap(jp + o, nx, bc)];
                     nnd_coef(v, qv, c);
@@ -315,8 +326,9 @@ __global__ void __launch_bounds__(ADJ_THREADS)
         // lambda: local parts and the transposed stencil of u.grad(lambda)
         double lb = a.loc[4 * nx + j];
         const double* la = a.f + (size_t)16 * K.plane;
-        for (int jp = j - 2; jp <= j + 2; jp++) {
-            if (jp < 0 || jp >= nx) continue;
+        for (int d = -2; d <= 2; d++) {
+            const int jp = neighbour(j, d, nx, bc);
+            if (jp < 0) continue;
             const double uxp = a.mac[nx + jp];
             if (uxp == 0.0) continue;
             double qv[5], c[5];

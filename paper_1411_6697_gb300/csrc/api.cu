@@ -987,6 +987,8 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
         return fail(h, LBKM_EINVAL, "lbkm_grad needs a single grid with ny = 1");
     if (h->p.bc_x == LBKM_BC_SIDES)
         return fail(h, LBKM_EINVAL, "lbkm_grad needs periodic or zero-gradient ends");
+    if (h->p.bc_x == LBKM_BC_PERIODIC && h->nx < 5)
+        return fail(h, LBKM_EINVAL, "lbkm_grad needs nx >= 5 on a periodic grid");
     if (h->p.time_scheme != 0) return fail(h, LBKM_EINVAL, "lbkm_grad needs forward Euler");
     if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_grad before lbkm_init_fields");
     if (!ob->rho_target || ob->steps < 1 || ob->checkpoint_every < 1)

@@ -21,16 +21,19 @@ def gpu():
     __graft_entry__.build()
 
 
-def problem(nx, steps, omega1, driver, omega2=0.0):
+def problem(nx, steps, omega1, driver, omega2=0.0, periodic=False):
     # the ripple keeps the minmod branches of the f_i away from rounding-level
     # differences; on flat stretches the gradient would depend on how each side rounds
     # (without it the oracle's own drho0 near the boundary differs by ~10 % between an
     # x86 and an Arm host)
     c = li.detonation(nx=nx, steps=steps, driver=driver, omega1=omega1, ripple=1e-3)
+    if periodic:  # the driver straddles the ends
+        c["fields"] = {k: np.roll(np.asarray(v, float), nx // 2 + 10, axis=-1)
+                       for k, v in c["fields"].items()}
     p = dict(c["params"])
     m = to.Model1D(nx, gamma=p["gamma"], orbit_kind=p["orbit_kind"],
                    orbit_speed=p["orbit_speed"], orbit_eta=p["orbit_eta"], T_ig=p["T_ig"],
-                   dx=p["dx"], dt=p["dt"], omega2=omega2)
+                   dx=p["dx"], dt=p["dt"], omega2=omega2, periodic=periodic)
     fl = c["fields"]
     # target: the run with perturbed rates and heat release (as the adjoint workload)
     rng = np.random.default_rng(li.SEED_BASE + 5)
@@ -67,13 +70,14 @@ def oracle_grad(c, p, m, rho_t, steps, w_tne, ck=0, restarts=None):
                 domega1=float(k.grad), domega2=dw2, drho0=rho0.grad.numpy())
 
 
-def gpu_grad(c, p, rho_t, steps, w_tne, ck, precision=lbkm.F64, recovery=0, omega2=0.0):
+def gpu_grad(c, p, rho_t, steps, w_tne, ck, precision=lbkm.F64, recovery=0, omega2=0.0,
+             bc=(1, 0)):
     fl = c["fields"]
     s = lbkm.Solver(nx=p["nx"], ny=1, precision=precision, recovery=recovery,
                     gamma=p["gamma"], orbit_kind=p["orbit_kind"], orbit_speed=p["orbit_speed"],
                     orbit_eta=p["orbit_eta"], S=p["S"], Q=p["Q"], omega1=p["omega1"],
                     omega2=omega2, T_ig=p["T_ig"], dx=p["dx"], dy=p["dx"], dt=p["dt"],
-                    bc=(1, 0))
+                    bc=bc)
     s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
     before = s.get_state()
     g = s.grad(rho_t, steps, w_tne=w_tne, checkpoint_every=ck)
@@ -130,6 +134,25 @@ def report_fp32(g, r, label, W=None):
     print(label, "relative difference from the FP64 gradient:",
           {k: "%.2e" % v for k, v in rep.items()})
     return rep
+
+
+@pytest.mark.parametrize("ck", [16, 7, 60])
+def test_adjoint_matches_reverse_mode_oracle_small(ck):
+    nx, steps = 96, 60
+    c, p, m, rho_t = problem(nx, steps, omega1=2e3, driver=16)
+    r = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0)
+    g = gpu_grad(c, p, rho_t, steps, w_tne=1.0, ck=ck)
+    compare(g, r, 1e-9)
+
+
+def test_adjoint_periodic_ends_match_reverse_mode_oracle():
+    """Periodic ends, the detonation straddling them: the transposed stencils reach across
+    the ends (the cells whose stencils read j are its periodic neighbours)."""
+    nx, steps = 96, 60
+    c, p, m, rho_t = problem(nx, steps, omega1=2e3, driver=16, periodic=True)
+    r = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0)
+    g = gpu_grad(c, p, rho_t, steps, w_tne=1.0, ck=16, bc=(0, 0))
+    compare(g, r, 1e-9)
 
 
 def test_adjoint_with_omega2_matches_reverse_mode_oracle():

@@ -185,3 +185,27 @@ def test_restarts_at_the_trajectory_s_own_states_change_nothing():
     a, b = run(None), run(restarts)
     assert a[0] == b[0]
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_periodic_forward_matches_c_oracle(oracle_mod):
+    """The periodic ends (images of the far cells as ghosts) against the C oracle with
+    bc_x = periodic, on a state whose fronts cross both ends."""
+    nx, steps = 96, 80
+    c, p, _ = setup(nx, steps, omega1=2e4)
+    m = to.Model1D(nx, gamma=p["gamma"], orbit_kind=p["orbit_kind"],
+                   orbit_speed=p["orbit_speed"], orbit_eta=p["orbit_eta"], T_ig=p["T_ig"],
+                   dx=p["dx"], dt=p["dt"], periodic=True)
+    q = dict(p, bc_x=0)
+    q.pop("nx"), q.pop("ny")
+    ob = oracle_mod.Oracle(nx, 1, **q)
+    fl = c["fields"]
+    # the driver straddles the end: the state is shifted by half the grid
+    fl = {k: np.roll(np.asarray(v, float), nx // 2 + 10, axis=-1) for k, v in fl.items()}
+    f, lam = ob.run(ob.init(fl["rho"], fl["ux"], fl["uy"], fl["T"]), fl["lam"], steps)
+    ft = m.init(*[to.to_t(fl[k][0]) for k in ("rho", "ux", "uy", "T")])
+    lt = to.to_t(fl["lam"][0])
+    S, Q, k = to.to_t(p["S"]), torch.tensor(p["Q"]), torch.tensor(p["omega1"])
+    for _ in range(steps):
+        ft, lt, _ = m.step(ft, lt, S, Q, k)
+    assert np.abs(ft.numpy() - f[:, 0]).max() <= 1e-13 * np.abs(f).max()
+    assert np.abs(lt.numpy() - lam[0]).max() <= 1e-13
