@@ -16,10 +16,13 @@
 // and the local part of u.grad(lambda) -- giving adjoints of rho, u, T of cell j,
 // of the velocity gradients gx, gy (which belong to the neighbours), of the
 // non-conserved moments, of lambda, and the parameter partials.
+// Pass A also forms, for each plane of its cell jp, the NND stencil's coefficients times
+// the plane's upwind weight (-dt v f_b / dx for f_i, -dt u_x lambda_b / dx for lambda),
+// one set per cell, branches decided by the forward values.
 // Pass B (one thread per cell j): gathers what depends on neighbours -- the
 // central differences of u, the transposed NND stencils of every f_i and of
-// lambda (branches recomputed from the forward values) -- then the macro chain
-// rho, u, T <- conserved moments and M^T.
+// lambda (the coefficients that pass A left at the neighbours) -- then the macro
+// chain rho, u, T <- conserved moments and M^T.
 #include <float.h>
 #include <math.h>
 
@@ -166,6 +169,22 @@ __global__ void __launch_bounds__(ADJ_THREADS)
         const double lsel = ux > 0.0 ? Lp : (ux < 0.0 ? Ln : 0.0);
         const double raw = lam - dt * (ux * lsel * K.inv_dx) + dl;
         const double lbc = (raw >= 0.0 && raw <= 1.0) ? a.lb1[j] : 0.0;
+        // the weighted NND coefficients of this cell's stencils, for pass B to gather
+        {
+            double c[5];
+            nnd_coef(ux, lq, c);
+            const double wl = -dt * ux * K.inv_dx * lbc;
+            for (int o = 0; o < 5; o++) a.cw[((size_t)16 * 5 + o) * nx + j] = wl * c[o];
+            for (int i = 0; i < 16; i++) {
+                const double v = a.vx[i];
+                if (v == 0.0) continue;
+                double qv[5];
+                for (int o = -2; o <= 2; o++) qv[o + 2] = a.f[i * K.plane + bmap(j + o, nx, K.bc_x)];
+                nnd_coef(v, qv, c);
+                const double w = -dt * v * K.inv_dx * a.fb1[i * nx + j];
+                for (int o = 0; o < 5; o++) a.cw[((size_t)i * 5 + o) * nx + j] = w * c[o];
+            }
+        }
 
         // ---- reverse sweep ----
         double Wb[16], Omb[16];
@@ -276,8 +295,25 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     adj_pass_b(const ModelConst<double> K, const AdjArgs a)
 {
     const int nx = K.nx, bc = K.bc_x;
-    const double DI = K.DI, dt = K.dt;
+    const double DI = K.DI;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nx; j += gridDim.x * blockDim.x) {
+        // sum over the cells jp whose stencil reads j of their weighted coefficient at j:
+        // inside the grid jp = j - o reads j at offset o; near the ends every pair is tested
+        const bool inner = j >= 2 && j < nx - 2;
+        auto gather = [&](const double* cwp) {
+            double g = 0.0;
+            if (inner) {
+                for (int o = -2; o <= 2; o++) g += cwp[(size_t)(o + 2) * nx + (j - o)];
+            } else {
+                for (int d = -2; d <= 2; d++) {
+                    const int jp = neighbour(j, d, nx, bc);
+                    if (jp < 0) continue;
+                    for (int o = -2; o <= 2; o++)
+                        if (bmap(jp + o, nx, bc) == j) g += cwp[(size_t)(o + 2) * nx + jp];
+                }
+            }
+            return g;
+        };
         // velocity gradients of the neighbours that read u_j
         double uxb = a.loc[nx + j], uyb = a.loc[2 * nx + j];
         for (int d = -1; d <= 1; d++) {
@@ -307,38 +343,11 @@ __global__ void __launch_bounds__(ADJ_THREADS)
         for (int i = 0; i < 16; i++) {
             double s = a.fb1[i * nx + j];
             for (int k = 0; k < 16; k++) s += a.M[k * 16 + i] * mb[k];
-            const double v = a.vx[i];
-            if (v != 0.0) {
-                const double* fi = a.f + (size_t)i * K.plane;
-                for (int d = -2; d <= 2; d++) {
-                    const int jp = neighbour(j, d, nx, bc);
-                    if (jp < 0) continue;
-                    double qv[5], c[5];
-                    for (int o = -2; o <= 2; o++) qv[o + 2] = fi[bmap(jp + o, nx, bc)];
-                    nnd_coef(v, qv, c);
-                    const double w = -dt * v * K.inv_dx * a.fb1[i * nx + jp];
-                    for (int o = -2; o <= 2; o++)
-                        if (bmap(jp + o, nx, bc) == j) s += w * c[o + 2];
-                }
-            }
+            if (a.vx[i] != 0.0) s += gather(a.cw + (size_t)i * 5 * nx);
             a.fb0[i * nx + j] = s;
         }
         // lambda: local parts and the transposed stencil of u.grad(lambda)
-        double lb = a.loc[4 * nx + j];
-        const double* la = a.f + (size_t)16 * K.plane;
-        for (int d = -2; d <= 2; d++) {
-            const int jp = neighbour(j, d, nx, bc);
-            if (jp < 0) continue;
-            const double uxp = a.mac[nx + jp];
-            if (uxp == 0.0) continue;
-            double qv[5], c[5];
-            for (int o = -2; o <= 2; o++) qv[o + 2] = la[bmap(jp + o, nx, bc)];
-            nnd_coef(uxp, qv, c);
-            const double w = -dt * uxp * K.inv_dx * a.loc[5 * nx + jp];
-            for (int o = -2; o <= 2; o++)
-                if (bmap(jp + o, nx, bc) == j) lb += w * c[o + 2];
-        }
-        a.lb0[j] = lb;
+        a.lb0[j] = a.loc[4 * nx + j] + gather(a.cw + (size_t)16 * 5 * nx);
     }
 }
 

@@ -1019,8 +1019,8 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
         dfree(h, sctr);
     };
     // work: mac 4n, mb 16n, loc 6n, gb 2n, fbA/fbB 32n, lbA/lbB 2n, rho_t n, drho0 n,
-    //       pacc NPAR*G, jtne G, jmis G
-    const size_t nwork = (size_t)nx * (4 + 16 + 6 + 2 + 32 + 2 + 1 + 1) + (size_t)(ADJ_NPAR + 2) * G;
+    //       cw 85n, pacc NPAR*G, jtne G, jmis G
+    const size_t nwork = (size_t)nx * (4 + 16 + 6 + 2 + 32 + 2 + 1 + 1 + 85) + (size_t)(ADJ_NPAR + 2) * G;
     cudaError_t e = dmalloc(h, &ck, SBf * nck);
     if (e == cudaSuccess) e = dmalloc(h, &seg, SBd * (size_t)(C + 1));
     if (e == cudaSuccess) e = dmalloc(h, &work, sizeof(double) * nwork);
@@ -1041,7 +1041,8 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     double* lbB = lbA + nx;
     double* rho_t = lbB + nx;
     double* drho0 = rho_t + nx;
-    double* pacc = drho0 + nx;
+    double* cw = drho0 + nx;
+    double* pacc = cw + 85 * (size_t)nx;
     double* jtne = pacc + (size_t)ADJ_NPAR * G;
     double* jmis = jtne + G;
     std::vector<double> hm(256 + 256 + 16);
@@ -1088,6 +1089,7 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     a.mb = mb;
     a.loc = loc;
     a.gb = gb;
+    a.cw = cw;
     a.pacc = pacc;
     a.M = mats;
     a.Minv = mats + 256;

@@ -120,6 +120,8 @@ struct AdjArgs {
     double* mb;          // [16][nx] pass A -> B: adjoint of the moments
     double* loc;         // [6][nx] pass A -> B: rho_b, ux_b, uy_b, T_b, lambda_b, clamped lambda_b
     double* gb;          // [2][nx] pass A -> B: adjoints of du_x/dx, du_y/dx
+    double* cw;          // [17][5][nx] pass A -> B: weighted NND coefficients of each cell's
+                         // stencil (planes f_1..f_16, lambda; offsets -2..+2)
     double* fb0;         // dJ/df of state n, [16][nx]
     double* lb0;         // dJ/dlambda of state n, [nx]
     double* pacc;        // [ADJ_NPAR][grid] per-block parameter accumulators
