@@ -134,7 +134,6 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     __shared__ double sred[ADJ_THREADS / 32];
     const int nx = K.nx;
     const double DI = K.DI, dt = K.dt;
-    const double* Minv = a.Minv;
     double pS[ADJ_NPAR];
     for (int q = 0; q < ADJ_NPAR; q++) pS[q] = 0.0;
     double jt = 0.0;
@@ -189,11 +188,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
         // ---- reverse sweep ----
         double Wb[16], Omb[16];
         for (int i = 0; i < 16; i++) Wb[i] = dt * a.fb1[i * nx + j];
-        for (int k = 0; k < 16; k++) {
-            double s = 0.0;
-            for (int i = 0; i < 16; i++) s += Minv[i * 16 + k] * Wb[i];
-            Omb[k] = s;
-        }
+        inverse_moments_t(K, Wb, Omb); // Omega_b = M^-T W_b (block form)
         double crb = 0.0, dqb[16], Db[16];
         for (int k = 3; k < 16; k++) {
             dqb[k] = cr * Omb[k];
@@ -339,10 +334,11 @@ __global__ void __launch_bounds__(ADJ_THREADS)
         mb[1] = r * uxb;
         mb[2] = r * uyb;
         mb[3] = r * Eb;
-        // M^T mb, identity and transposed NND stencils (x only)
+        // M^T mb (block form), identity and transposed NND stencils (x only)
+        double mtm[16];
+        forward_moments_t(K, mb, mtm);
         for (int i = 0; i < 16; i++) {
-            double s = a.fb1[i * nx + j];
-            for (int k = 0; k < 16; k++) s += a.M[k * 16 + i] * mb[k];
+            double s = a.fb1[i * nx + j] + mtm[i];
             if (a.vx[i] != 0.0) s += gather(a.cw + (size_t)i * 5 * nx);
             a.fb0[i * nx + j] = s;
         }
@@ -379,12 +375,10 @@ __global__ void __launch_bounds__(ADJ_THREADS)
         double f[16], m[16], fb[16];
         for (int i = 0; i < 16; i++) f[i] = a.f[i * K.plane + j], fb[i] = a.fb1[i * nx + j];
         forward_moments(K, f, m);
+        double qb[16];
+        inverse_moments_t(K, fb, qb);
         double s = 0.0;
-        for (int k = 0; k < 16; k++) {
-            double qb = 0.0;
-            for (int i = 0; i < 16; i++) qb += a.Minv[i * 16 + k] * fb[i];
-            s += qb * m[k];
-        }
+        for (int k = 0; k < 16; k++) s += qb[k] * m[k];
         drho0[j] = s / m[0];
     }
 }

@@ -1024,7 +1024,7 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     cudaError_t e = dmalloc(h, &ck, SBf * nck);
     if (e == cudaSuccess) e = dmalloc(h, &seg, SBd * (size_t)(C + 1));
     if (e == cudaSuccess) e = dmalloc(h, &work, sizeof(double) * nwork);
-    if (e == cudaSuccess) e = dmalloc(h, &mats, sizeof(double) * (256 + 256 + 16));
+    if (e == cudaSuccess) e = dmalloc(h, &mats, sizeof(double) * 16);
     if (e == cudaSuccess) e = dmalloc(h, &sctr, sizeof(DevCounters));
     if (e != cudaSuccess) {
         cleanup();
@@ -1045,14 +1045,12 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     double* pacc = cw + 85 * (size_t)nx;
     double* jtne = pacc + (size_t)ADJ_NPAR * G;
     double* jmis = jtne + G;
-    std::vector<double> hm(256 + 256 + 16);
-    memcpy(hm.data(), h->hm.M, 256 * sizeof(double));
-    memcpy(hm.data() + 256, h->hm.Minv, 256 * sizeof(double));
+    std::vector<double> hm(16); // x-velocities of the 16 f_i
     {
         static const int ax[4] = {1, 0, -1, 0}, dg[4] = {1, -1, -1, 1};
         for (int o = 0; o < 4; o++)
             for (int q = 0; q < 4; q++)
-                hm[512 + 4 * o + q] = h->hm.c[o] * (h->p.orbit_kind[o] == 0 ? ax[q] : dg[q]);
+                hm[4 * o + q] = h->hm.c[o] * (h->p.orbit_kind[o] == 0 ? ax[q] : dg[q]);
     }
     cudaStream_t st = h->stream;
     auto S = [&](int64_t k) { return seg + (size_t)k * SBd; };
@@ -1091,9 +1089,7 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     a.gb = gb;
     a.cw = cw;
     a.pacc = pacc;
-    a.M = mats;
-    a.Minv = mats + 256;
-    a.vx = mats + 512;
+    a.vx = mats;
     a.tne_w = ob->w_tne * h->p.dx * h->p.dt;
     a.jw = a.tne_w;
     // FP64 forward: seed with the mismatch of the final state now; FP32 forward: once the

@@ -134,6 +134,103 @@ __device__ __forceinline__ void inverse_moments(const ModelConst<R>& K, const L*
     }
 }
 
+// y = A^T x for an N x N block A (the transpose of matvec)
+template <int N, typename T, typename L>
+__device__ __forceinline__ void matvec_t(const T* A, const L* x, L* y)
+{
+#pragma unroll
+    for (int c = 0; c < N; c++) {
+        L s = A[c] * x[0];
+#pragma unroll
+        for (int r = 1; r < N; r++) s = fma(A[r * N + c], x[r], s);
+        y[c] = s;
+    }
+}
+
+// fb = M^T mb: the transpose of forward_moments, its steps reversed (moment placement,
+// sector blocks, the sector sums, the orbit butterflies), for the adjoint.
+template <typename R, typename L>
+__device__ __forceinline__ void forward_moments_t(const ModelConst<R>& K, const L* mb, L* fb)
+{
+    L pes[4] = {mb[0], mb[3], L(0.5) * (mb[4] + mb[6]), L(0.5) * (mb[13] + mb[15])};
+    L pea[2] = {L(0.5) * (mb[4] - mb[6]), L(0.5) * (mb[13] - mb[15])};
+    L px[4] = {mb[1], mb[7], mb[9], mb[11]}, py[4] = {mb[2], mb[8], mb[12], mb[10]};
+    L po[2] = {mb[5], mb[14]};
+    L es[4], ea[2], xo[4], yo[4], oo[2];
+    matvec_t<4>(K.Bes, pes, es);
+    matvec_t<2>(K.Bea, pea, ea);
+    matvec_t<4>(K.Bodd, px, xo);
+    matvec_t<4>(K.Bodd, py, yo);
+    matvec_t<2>(K.Boo, po, oo);
+    // axis orbits 0 (f0..f3) and 2 (f8..f11): es[a] = sx + sy, ea[a] = sx - sy
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        const L sx = es[a] + ea[a], sy = es[a] - ea[a];
+        fb[8 * a + 0] = sx + xo[a];
+        fb[8 * a + 2] = sx - xo[a];
+        fb[8 * a + 1] = sy + yo[a];
+        fb[8 * a + 3] = sy - yo[a];
+    }
+    // diagonal orbits 1 (f4..f7) and 3 (f12..f15): e = s01 + s23, a_y = s01 - s23,
+    // a_x = d01 - d23, o = d01 + d23
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+        const L e = es[2 + d], ax = xo[2 + d], ay = yo[2 + d], o = oo[d];
+        const L s01 = e + ay, s23 = e - ay, d01 = ax + o, d23 = o - ax;
+        fb[4 + 8 * d + 0] = s01 + d01;
+        fb[4 + 8 * d + 1] = s01 - d01;
+        fb[4 + 8 * d + 2] = s23 + d23;
+        fb[4 + 8 * d + 3] = s23 - d23;
+    }
+}
+
+// mb = M^-T fb: the transpose of inverse_moments, its steps reversed, for the adjoint.
+template <typename R, typename L>
+__device__ __forceinline__ void inverse_moments_t(const ModelConst<R>& K, const L* fb, L* mb)
+{
+    L pes[4], pea[2], px[4], py[4], po[2];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        const L pp = fb[8 * a + 0] + fb[8 * a + 2], pm = fb[8 * a + 1] + fb[8 * a + 3];
+        px[a] = fb[8 * a + 0] - fb[8 * a + 2];
+        py[a] = fb[8 * a + 1] - fb[8 * a + 3];
+        pes[a] = pp + pm;
+        pea[a] = pp - pm;
+    }
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+        const L f0 = fb[4 + 8 * d + 0], f1 = fb[4 + 8 * d + 1];
+        const L f2 = fb[4 + 8 * d + 2], f3 = fb[4 + 8 * d + 3];
+        const L eo = f0 + f2, xp = f0 - f2, em = f1 + f3, xm = f3 - f1;
+        pes[2 + d] = eo + em;
+        po[d] = eo - em;
+        px[2 + d] = xp + xm;
+        py[2 + d] = xp - xm;
+    }
+    L es[4], ea[2], xo[4], yo[4], oo[2];
+    matvec_t<4>(K.Ies, pes, es);
+    matvec_t<2>(K.Iea, pea, ea);
+    matvec_t<4>(K.Iodd, px, xo);
+    matvec_t<4>(K.Iodd, py, yo);
+    matvec_t<2>(K.Ioo, po, oo);
+    mb[0] = es[0];
+    mb[3] = es[1];
+    mb[4] = es[2] + ea[0];
+    mb[6] = es[2] - ea[0];
+    mb[13] = es[3] + ea[1];
+    mb[15] = es[3] - ea[1];
+    mb[1] = xo[0];
+    mb[7] = xo[1];
+    mb[9] = xo[2];
+    mb[11] = xo[3];
+    mb[2] = yo[0];
+    mb[8] = yo[1];
+    mb[12] = yo[2];
+    mb[10] = yo[3];
+    mb[5] = oo[0];
+    mb[14] = oo[1];
+}
+
 // Conserved moments rho, rho u, rho[(D+I)T + u^2] (Eqs. (5)-(7)) from the 16 f
 // in FP64, and rho, u, T from them, also in FP64.
 template <typename F>

@@ -126,9 +126,7 @@ struct AdjArgs {
     double* lb0;         // dJ/dlambda of state n, [nx]
     double* pacc;        // [ADJ_NPAR][grid] per-block parameter accumulators
     double* jacc;        // [grid] per-block objective accumulators
-    const double* M;     // [16][16] moment matrix (row = moment)
-    const double* Minv;  // [16][16]
-    const double* vx;    // [16] x-velocities
+    const double* vx;    // [16] x-velocities (M, M^-1 and their transposes act in block form)
     double tne_w;        // w_tne dx dt: Delta_b += 2 tne_w Delta
     double jw;           // w_tne dx dt for the objective value
 };
