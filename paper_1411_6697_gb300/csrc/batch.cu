@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(BT)
                 for (int i = 0; i < 16; i++) f[i] = ldv(sb + i * C::SW + lx);
                 V2 rho, ux, uy, T;
                 bool ig0, ig1, ok0, ok1;
-                recover_pair<REC>(f, Cd, K, rho, ux, uy, T, ig0, ig1, ok0, ok1);
+                recover_pair_fast<REC>(f, Cd, K, rho, ux, uy, T, ig0, ig1, ok0, ok1);
                 if ((act0 && !ok0) || (act1 && !ok1)) bad = 1;
                 *reinterpret_cast<float2*>(mac + 0 * C::MWB + mi) = rho.v;
                 *reinterpret_cast<float2*>(mac + 1 * C::MWB + mi) = ux.v;
