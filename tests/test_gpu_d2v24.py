@@ -179,8 +179,11 @@ def test_reactive2d_parity(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PID)
-def test_tne_fields_and_on_the_fly_records(prec):
-    cfg = mixed_2d(40, 17, seed=3)
+@pytest.mark.parametrize("nx,ny", [(40, 17), (300, 1)], ids=["2d", "1d-one-warp-blocks"])
+def test_tne_fields_and_on_the_fly_records(prec, nx, ny):
+    """Per-step TNE records against the oracle's; a short 1-D grid runs one-warp blocks
+    (the block reduction then has 32 threads for its 82 quantities), its last one ragged."""
+    cfg = mixed_2d(nx, ny, seed=3)
     steps = 5
     s, ob, f, lam = start(cfg, prec, noise_seed=5, tne_every=1, tne_capacity=16)
     s.step(steps)
