@@ -783,6 +783,31 @@ def test_tne_history_ring_keeps_the_newest_records():
     b.close()
 
 
+@pytest.mark.parametrize("rec", [0, 1], ids=["f32", "f32-df"])
+def test_tne_every_k_matches_every_step_fp32(rec):
+    """The FP32 2-D step with tne_every = 3 (statistics gathered every step, reduced on the
+    due ones) records steps 0, 3, 6, ... exactly as the run that records every step, and
+    leaves the same state; a handle without TNE (the kernel without any TNE code) leaves
+    that state too. Ragged strips in x and y."""
+    params, fields = mixed_2d(150, 70, seed=12)
+    runs = {}
+    for k in (1, 3, 0):
+        s = solver(params, lbkm.F32, rec, tne_every=k, tne_capacity=16)
+        s.init_fields(fields["rho"], fields["ux"], fields["uy"], fields["T"], fields["lam"])
+        s.step(10)
+        runs[k] = (s.get_state(), s.tne_history() if k else [])
+        s.close()
+    every, third = runs[1][1], runs[3][1]
+    assert [h["step"] for h in third] == [0, 3, 6, 9]
+    for h in third:
+        g = every[h["step"]]
+        for key in ("sum", "abs_sum", "min", "max"):
+            assert np.array_equal(h[key], g[key]), (h["step"], key)
+        assert h["d_sum"] == g["d_sum"] and h["d2_sum"] == g["d2_sum"]
+    assert np.array_equal(runs[3][0], runs[1][0])
+    assert np.array_equal(runs[0][0], runs[1][0])
+
+
 def test_checkpoint_resume_is_bitwise():
     params, fields = mixed_2d(33, 12, seed=4)
     a = solver(params, lbkm.F32)
