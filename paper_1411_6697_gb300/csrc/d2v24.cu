@@ -52,6 +52,19 @@ constexpr int BT = 128;          // threads per block: 128 x 1 or 32 x 1 (1-D gr
 constexpr int MAC_CELLS = 390;   // macros staged per block: (128 + 2) x 3 >= (32 + 2) x 6
 constexpr int GRAPH_CHUNK = 32;  // even: a replay leaves the ping-pong index unchanged
 
+// signs of v_x, v_y of velocity i = 8 g + 4 o + j (speed group g, o = 0 axis orbit with
+// (1,0) (0,1) (-1,0) (0,-1), o = 1 diagonal orbit with (1,1) (-1,1) (-1,-1) (1,-1)); the
+// speeds are positive, so the upwind side of every plane is fixed at compile time
+__host__ __device__ constexpr int vsign_x(int i)
+{
+    return ((i >> 2) & 1) == 0 ? ((i & 3) == 0 ? 1 : ((i & 3) == 2 ? -1 : 0))
+                               : (((i & 3) == 0 || (i & 3) == 3) ? 1 : -1);
+}
+__host__ __device__ constexpr int vsign_y(int i)
+{
+    return ((i >> 2) & 1) == 0 ? ((i & 3) == 1 ? 1 : ((i & 3) == 3 ? -1 : 0)) : ((i & 3) < 2 ? 1 : -1);
+}
+
 // parity sectors: sizes, offsets of their blocks, and the moment (0-based) at each
 // sector-ordered position p = 0..23 (ee 0..8, oe 9..14, eo 15..20, oo 21..23)
 constexpr int NSEC = 4;
@@ -561,14 +574,14 @@ __global__ void __launch_bounds__(BT, sizeof(R) == 4 ? 3 : 1) step_kernel(const 
             }
             const R* pl = in + (size_t)i * K.plane;
             R adv = R(0);
-            if (K.vx[i] > R(0))
+            if (vsign_x(i) > 0)
                 adv = K.vxs[i] * nnd_pos(LX(i, -2), LX(i, -1), f[i], LX(i, 1));
-            else if (K.vx[i] < R(0))
+            else if (vsign_x(i) < 0)
                 adv = K.vxs[i] * nnd_neg(LX(i, -1), f[i], LX(i, 1), LX(i, 2));
             if (K.ny > 1) {
-                if (K.vy[i] > R(0))
+                if (vsign_y(i) > 0)
                     adv += K.vys[i] * nnd_pos(LY(i, -2), LY(i, -1), f[i], LY(i, 1));
-                else if (K.vy[i] < R(0))
+                else if (vsign_y(i) < 0)
                     adv += K.vys[i] * nnd_neg(LY(i, -1), f[i], LY(i, 1), LY(i, 2));
             }
             out[(size_t)i * K.plane + g] = f[i] + K.dt_r * (om - adv);
