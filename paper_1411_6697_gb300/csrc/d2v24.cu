@@ -369,8 +369,9 @@ __host__ __device__ __forceinline__ void feq24(F I, F DI, F rho, F ux, F uy, F T
 // maxima, sum of d, sum of d^2). Each thread leaves its cell's Delta_5..24, d and d^2
 // (formed in R) in shared memory; each quantity is then reduced in three parts of a
 // third of the block's cells (one thread per part; the block's threads take the parts
-// in turn), in a fixed order: the 42 sums in FP64, the 40 extremes in R (exact); one
-// thread per quantity joins the three parts. Deterministic for any block size <= BT.
+// in turn), in a fixed order: the 42 sums exactly (FP64, or FP32 TwoSum pairs for an
+// FP32 state), the 40 extremes in R (exact); one thread per quantity joins the three
+// parts in FP64. Deterministic for any block size <= BT.
 template <typename R>
 __device__ __forceinline__ void block_tne(const R* Dk, bool active, double* partials, int nblocks,
                                           int b)
@@ -400,13 +401,28 @@ __device__ __forceinline__ void block_tne(const R* Dk, bool active, double* part
         const int row = s < TK ? s : (s < 2 * TK ? s - TK : TK + (s - 2 * TK));
         const bool absv = s >= TK && s < 2 * TK;
         const int j1 = min((part + 1) * per, nt);
-        double acc = 0.0;
-        for (int j = part * per; j < j1; j++) {
-            if (!sact[j]) continue;
-            const double v = (double)sD[row][j];
-            acc += absv ? fabs(v) : v;
+        if constexpr (sizeof(R) == 4) {
+            // FP32 terms summed exactly: each addition's rounding error (TwoSum) goes to
+            // a compensating term, the pair joined in FP64 once (the FP64 unit runs at
+            // 1/58 of the FP32 rate on this part)
+            float sum = 0.f, comp = 0.f;
+            for (int j = part * per; j < j1; j++) {
+                if (!sact[j]) continue;
+                const float v = absv ? fabsf(sD[row][j]) : sD[row][j];
+                const lbk::df t2 = lbk::two_sum(sum, v);
+                sum = t2.hi;
+                comp += t2.lo;
+            }
+            spart[q][part] = (double)sum + (double)comp;
+        } else {
+            double acc = 0.0;
+            for (int j = part * per; j < j1; j++) {
+                if (!sact[j]) continue;
+                const double v = (double)sD[row][j];
+                acc += absv ? fabs(v) : v;
+            }
+            spart[q][part] = acc;
         }
-        spart[q][part] = acc;
     }
     for (int w = t; w < 3 * NE; w += nt) {
         const int e = w / 3, part = w - 3 * e;
