@@ -536,6 +536,17 @@ def measure_adjoint(n_grad=1):
     for _ in range(n_grad):
         g = s.grad(rho_t, steps, w_tne=cfg["w_tne"], checkpoint_every=cfg["checkpoint_every"])
     sec = (time.perf_counter() - t0) / n_grad
+
+    def objective_sec(sv):
+        # J alone (lbkm_objective_value: the run and one d^2 reduction per state)
+        sv.objective(rho_t, steps, w_tne=cfg["w_tne"], checkpoint_every=cfg["checkpoint_every"])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        v = sv.objective(rho_t, steps, w_tne=cfg["w_tne"],
+                         checkpoint_every=cfg["checkpoint_every"])
+        return time.perf_counter() - t1, v["J"]
+
+    sec_j, j_only = objective_sec(s)
     s.close()
     s32 = solver(q, lbkm.F32)
     g32 = s32.grad(rho_t, steps, w_tne=cfg["w_tne"], checkpoint_every=cfg["checkpoint_every"])
@@ -545,6 +556,7 @@ def measure_adjoint(n_grad=1):
         g32 = s32.grad(rho_t, steps, w_tne=cfg["w_tne"],
                        checkpoint_every=cfg["checkpoint_every"])
     sec32 = (time.perf_counter() - t0) / n_grad
+    sec32_j, j32_only = objective_sec(s32)
     s32.close()
     nx = q["nx"]
     n_scalar = 16 + 3               # S_1..S_16, Q, omega1, omega2
@@ -553,6 +565,7 @@ def measure_adjoint(n_grad=1):
     return {"workload": "adjoint_8192x1_detonation_4000_steps", "checkpoint_every":
             cfg["checkpoint_every"], "w_tne": cfg["w_tne"], "J": g["J"],
             "gradient_ms": sec * 1e3, "plain_f64_forward_ms": ms_fwd,
+            "objective_only_ms": sec_j * 1e3, "objective_only_J": j_only,
             "plain_f64_forward_mcell_per_s": nx * steps / (ms_fwd * 1e-3) / 1e6,
             "gradient_over_forward": sec / (ms_fwd * 1e-3),
             "speedup_vs_central_fd_scalars": n_scalar * fd / sec,
@@ -563,6 +576,7 @@ def measure_adjoint(n_grad=1):
                         "(tests/test_gpu_adjoint.py)",
             "fp32_forward": {
                 "gradient_ms": sec32 * 1e3, "J": g32["J"],
+                "objective_only_ms": sec32_j * 1e3, "objective_only_J": j32_only,
                 "speedup_vs_f64_gradient": sec / sec32,
                 "speedup_vs_central_fd_scalars": n_scalar * fd / sec32,
                 "method": "FP32 forward run and checkpoints; each segment recomputed and "

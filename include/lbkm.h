@@ -311,6 +311,16 @@ typedef struct {
  * LBKM_ECUDA, LBKM_EUNSTABLE. Synchronises. */
 lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* obj, lbkm_grad_out* out);
 
+/* The objective J of lbkm_grad alone (same definition, Sec. VI, Eqs. (90)-(91); for an
+ * LBKM_F32 handle the same FP64 segments restarted every checkpoint_every steps from the
+ * FP32 run's states), without its derivative: the run and one d^2 reduction per state,
+ * no reverse sweep and no checkpoints kept. *J receives J; J_mismatch and J_tne (each
+ * may be NULL) its two terms. It agrees with lbkm_grad's J up to the order of the FP64
+ * additions. Same conditions and errors as lbkm_grad; the handle's state is left
+ * unchanged. Synchronises. */
+lbkm_status lbkm_objective_value(lbkm_t h, const lbkm_objective* obj, double* J,
+                                 double* J_mismatch, double* J_tne);
+
 /* Many independent 1-D instances of uneven length in one handle (zero-gradient
  * boundaries per instance), advanced together by one persistent kernel per
  * chunk of steps (replayed from a CUDA graph). p gives everything the instances

@@ -26,6 +26,7 @@
 #include <float.h>
 #include <math.h>
 
+#include "adjoint.cuh"
 #include "cell.cuh"
 #include "kernels.cuh"
 
@@ -383,6 +384,28 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     }
 }
 
+// the objective's TNE term of one state alone: w_tne dx dt sum_x sum_k Delta_k^2
+__global__ void __launch_bounds__(ADJ_THREADS)
+    adj_jtne(const ModelConst<double> K, const AdjArgs a)
+{
+    __shared__ double sred[ADJ_THREADS / 32];
+    const int nx = K.nx;
+    double jt = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nx; j += gridDim.x * blockDim.x) {
+        double f[16], m[16], q[16];
+        for (int i = 0; i < 16; i++) f[i] = a.f[i * K.plane + j];
+        double rho, ux, uy, T; // as the macros kernel forms them for the reverse sweep
+        recover_f64(K.cd, K.wd, K.inv_DId, f, rho, ux, uy, T);
+        forward_moments(K, f, m);
+        feq_moments(K.DI, rho, ux, uy, T, q);
+        for (int k = 4; k < 16; k++) {
+            const double D = m[k] - q[k];
+            jt += D * D;
+        }
+    }
+    block_add(jt * a.jw, a.jacc, sred);
+}
+
 // an FP32 checkpoint widened to FP64, element by element (exact)
 __global__ void adj_widen(const float* __restrict__ in, double* __restrict__ out, size_t n)
 {
@@ -416,6 +439,12 @@ cudaError_t launch_adj_seed(const ModelConst<double>& K, const AdjArgs& a, const
                             double w, int grid, cudaStream_t s)
 {
     adj_seed<<<grid, ADJ_THREADS, 0, s>>>(K, a, rho_t, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_jtne(const ModelConst<double>& K, const AdjArgs& a, int grid, cudaStream_t s)
+{
+    adj_jtne<<<grid, ADJ_THREADS, 0, s>>>(K, a);
     return cudaGetLastError();
 }
 

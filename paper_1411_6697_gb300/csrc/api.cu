@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "lbkm.h"
+#include "adjoint.cuh"
 #include "kernels.cuh"
 #include "model.h"
 
@@ -980,19 +981,29 @@ lbkm_status lbkm_autotune(lbkm_t h, int32_t trial_steps, int32_t* chosen)
     return LBKM_OK;
 }
 
+// the conditions lbkm_grad and lbkm_objective_value share
+static lbkm_status objective_check(lbkm_t h, const lbkm_objective* ob, const char* fn)
+{
+    if (h->ny != 1 || h->batched)
+        return fail(h, LBKM_EINVAL, "%s needs a single grid with ny = 1", fn);
+    if (h->p.bc_x == LBKM_BC_SIDES)
+        return fail(h, LBKM_EINVAL, "%s needs periodic or zero-gradient ends", fn);
+    if (h->p.bc_x == LBKM_BC_PERIODIC && h->nx < 5)
+        return fail(h, LBKM_EINVAL, "%s needs nx >= 5 on a periodic grid", fn);
+    if (h->p.time_scheme != 0) return fail(h, LBKM_EINVAL, "%s needs forward Euler", fn);
+    if (!h->initialized) return fail(h, LBKM_ESTATE, "%s before lbkm_init_fields", fn);
+    if (!ob->rho_target || ob->steps < 1 || ob->checkpoint_every < 1)
+        return fail(h, LBKM_EINVAL, "rho_target, steps >= 1 and checkpoint_every >= 1 needed");
+    return LBKM_OK;
+}
+
 lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
 {
     if (!h || !ob || !out) return LBKM_EINVAL;
-    if (h->ny != 1 || h->batched)
-        return fail(h, LBKM_EINVAL, "lbkm_grad needs a single grid with ny = 1");
-    if (h->p.bc_x == LBKM_BC_SIDES)
-        return fail(h, LBKM_EINVAL, "lbkm_grad needs periodic or zero-gradient ends");
-    if (h->p.bc_x == LBKM_BC_PERIODIC && h->nx < 5)
-        return fail(h, LBKM_EINVAL, "lbkm_grad needs nx >= 5 on a periodic grid");
-    if (h->p.time_scheme != 0) return fail(h, LBKM_EINVAL, "lbkm_grad needs forward Euler");
-    if (!h->initialized) return fail(h, LBKM_ESTATE, "lbkm_grad before lbkm_init_fields");
-    if (!ob->rho_target || ob->steps < 1 || ob->checkpoint_every < 1)
-        return fail(h, LBKM_EINVAL, "rho_target, steps >= 1 and checkpoint_every >= 1 needed");
+    {
+        const lbkm_status cs = objective_check(h, ob, "lbkm_grad");
+        if (cs != LBKM_OK) return cs;
+    }
     const int nx = h->nx;
     const int64_t N = ob->steps;
     const int C = ob->checkpoint_every;
@@ -1164,6 +1175,139 @@ lbkm_status lbkm_grad(lbkm_t h, const lbkm_objective* ob, lbkm_grad_out* out)
     out->J_tne = sums[ADJ_NPAR];
     out->J_mismatch = sums[ADJ_NPAR + 1];
     out->J = out->J_mismatch + out->J_tne;
+    return LBKM_OK;
+}
+
+lbkm_status lbkm_objective_value(lbkm_t h, const lbkm_objective* ob, double* J,
+                                 double* J_mismatch, double* J_tne)
+{
+    if (!h || !ob || !J) return LBKM_EINVAL;
+    {
+        const lbkm_status cs = objective_check(h, ob, "lbkm_objective_value");
+        if (cs != LBKM_OK) return cs;
+    }
+    const int nx = h->nx;
+    const int64_t N = ob->steps;
+    const int C = ob->checkpoint_every;
+    const int G = adj_grid(nx);
+    // the same J as lbkm_grad: an FP64 handle's own run; for an FP32 handle, FP64 segments
+    // of C steps restarted from the FP32 run's state at their start (the FP32 run goes on
+    // beside them, so no checkpoint is kept)
+    const bool f32 = h->precision != LBKM_F64;
+    const size_t SBf = h->state_bytes_dev;
+    const size_t SBd = (size_t)NPLANE * h->plane_elems * 8;
+    char *run = nullptr, *seg = nullptr;
+    double* work = nullptr;
+    DevCounters* sctr = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(h->stream);
+        dfree(h, run);
+        dfree(h, seg);
+        dfree(h, work);
+        dfree(h, sctr);
+    };
+    // work: fb 16n, lb n (written by the seed kernel), rho_t n, jtne G, jmis G
+    const size_t nwork = (size_t)nx * (16 + 1 + 1) + (size_t)2 * G;
+    cudaError_t e = dmalloc(h, &run, SBf * 2);
+    if (e == cudaSuccess && f32) e = dmalloc(h, &seg, SBd * 2);
+    if (e == cudaSuccess) e = dmalloc(h, &work, sizeof(double) * nwork);
+    if (e == cudaSuccess) e = dmalloc(h, &sctr, sizeof(DevCounters));
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(h, e == cudaErrorMemoryAllocation ? LBKM_ENOMEM : LBKM_ECUDA,
+                    "lbkm_objective_value allocation: %s", cudaGetErrorString(e));
+    }
+    double* fb = work;
+    double* lb = fb + 16 * (size_t)nx;
+    double* rho_t = lb + nx;
+    double* jtne = rho_t + nx;
+    double* jmis = jtne + G;
+    cudaStream_t st = h->stream;
+#define GT(call)                                                                              \
+    do {                                                                                      \
+        e = (call);                                                                           \
+        if (e != cudaSuccess) {                                                               \
+            cleanup();                                                                        \
+            return fail(h, LBKM_ECUDA, "lbkm_objective_value: %s: %s", #call,                \
+                        cudaGetErrorString(e));                                               \
+        }                                                                                     \
+    } while (0)
+    GT(cudaMemcpyAsync(rho_t, ob->rho_target, sizeof(double) * nx, cudaMemcpyHostToDevice, st));
+    GT(cudaMemsetAsync(jtne, 0, sizeof(double) * 2 * G, st));
+    GT(cudaMemsetAsync(sctr, 0, sizeof(DevCounters), st));
+    StepLaunch sl = step_args(h, 0);
+    sl.ctr = sctr;
+    sl.tne_every = 0;
+    StepLaunch sd = sl; // the FP64 step of the segments
+    sd.grid = step_grid(0, 0, false, nx, 1, h->Kd.sbc);
+    AdjArgs a;
+    memset(&a, 0, sizeof(a));
+    a.fb0 = fb;
+    a.lb0 = lb;
+    a.jacc = jtne;
+    a.jw = ob->w_tne * h->p.dx * h->p.dt;
+    // the TNE term of one FP64 state
+    auto tne_term = [&](const void* state) -> cudaError_t {
+        a.f = static_cast<const double*>(state);
+        return launch_adj_jtne(h->Kd, a, G, st);
+    };
+    // the run in the handle's precision: m steps taken so far, its state in cur
+    const void* cur = h->buf[h->cur];
+    int64_t m = 0;
+    auto advance = [&]() -> cudaError_t {
+        sl.in = cur;
+        sl.out = run + (size_t)(m % 2) * SBf;
+        const cudaError_t se = launch_step(h->precision, h->recovery, false, model_ptr(h), sl, st);
+        cur = sl.out;
+        m++;
+        return se;
+    };
+    const void* fin = nullptr; // the FP64 state after N steps
+    if (!f32) {
+        for (int64_t n = 0; n < N; n++) {
+            GT(tne_term(cur));
+            GT(advance());
+        }
+        fin = cur;
+    } else {
+        for (int64_t n0 = 0; n0 < N; n0 += C) {
+            const int64_t n1 = (n0 + C < N) ? n0 + C : N;
+            const bool last = n1 == N;
+            GT(launch_adj_widen(static_cast<const float*>(cur), reinterpret_cast<double*>(seg),
+                                (size_t)NPLANE * h->plane_elems, G, st));
+            for (int64_t n = n0; n < n1; n++) {
+                const int64_t k = n - n0;
+                GT(tne_term(seg + (size_t)(k % 2) * SBd));
+                if (n + 1 < n1 || last) {
+                    sd.in = seg + (size_t)(k % 2) * SBd;
+                    sd.out = seg + (size_t)((k + 1) % 2) * SBd;
+                    GT(launch_step(0, 0, false, &h->Kd, sd, st));
+                }
+            }
+            if (last)
+                fin = seg + (size_t)((n1 - n0) % 2) * SBd;
+            else
+                for (int64_t n = n0; n < n1; n++) GT(advance());
+        }
+    }
+    a.f = static_cast<const double*>(fin);
+    a.jacc = jmis;
+    GT(launch_adj_seed(h->Kd, a, rho_t, ob->w_mismatch, G, st));
+    std::vector<double> hp((size_t)2 * G);
+    GT(cudaMemcpyAsync(hp.data(), jtne, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
+    GT(cudaStreamSynchronize(st));
+#undef GT
+    int stat = 0;
+    cudaMemcpy(&stat, &sctr->status, sizeof(int), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (stat & 1)
+        return fail(h, LBKM_EUNSTABLE, "the forward run reached a non-physical state");
+    double jt = 0.0, jm = 0.0;
+    for (int b = 0; b < G; b++) jt += hp[b];
+    for (int b = 0; b < G; b++) jm += hp[(size_t)G + b];
+    *J = jm + jt;
+    if (J_mismatch) *J_mismatch = jm;
+    if (J_tne) *J_tne = jt;
     return LBKM_OK;
 }
 

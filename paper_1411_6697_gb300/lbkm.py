@@ -28,7 +28,7 @@ EXPORTED = ["lbkm_default_params", "lbkm_create", "lbkm_destroy", "lbkm_set_stre
             "lbkm_tne", "lbkm_tne_history", "lbkm_state_bytes", "lbkm_get_state",
             "lbkm_set_state", "lbkm_last_error", "lbkm_version", "lbkm_tne_noalloc",
             "lbkm_create_batched", "lbkm_instances", "lbkm_tne_instances", "lbkm_autotune",
-            "lbkm_set_wait_limit", "lbkm_grad"]
+            "lbkm_set_wait_limit", "lbkm_grad", "lbkm_objective_value"]
 EXPORTED24 = ["lbkm24_default_params", "lbkm24_create", "lbkm24_destroy", "lbkm24_init_fields",
               "lbkm24_step", "lbkm24_sync", "lbkm24_steps_taken", "lbkm24_macros", "lbkm24_tne",
               "lbkm24_tne_history", "lbkm24_state_bytes", "lbkm24_get_state", "lbkm24_set_state",
@@ -199,6 +199,9 @@ def load():
     lib.lbkm_autotune.restype = ctypes.c_int
     lib.lbkm_grad.argtypes = [H, ctypes.POINTER(Objective), ctypes.POINTER(GradOut)]
     lib.lbkm_grad.restype = ctypes.c_int
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.lbkm_objective_value.argtypes = [H, ctypes.POINTER(Objective), D, D, D]
+    lib.lbkm_objective_value.restype = ctypes.c_int
     lib.lbkm_set_wait_limit.argtypes = [H, ctypes.c_int64, ctypes.c_int32]
     lib.lbkm_set_wait_limit.restype = ctypes.c_int
     for name in ("lbkm_create", "lbkm_set_stream", "lbkm_init_fields", "lbkm_step", "lbkm_sync",
@@ -397,6 +400,17 @@ class Solver:
                 "dS": np.array(out.dS[:]), "dQ": out.dQ, "domega1": out.domega1,
                 "domega2": out.domega2,
                 "drho0": drho0, "df0": df0}
+
+    def objective(self, rho_target, steps, w_mismatch=1.0, w_tne=1.0, checkpoint_every=64):
+        """lbkm_objective_value: the J of `grad` (and its two terms) without the derivative."""
+        rt = np.ascontiguousarray(np.broadcast_to(np.asarray(rho_target, np.float64),
+                                                  (self.nx,)))
+        ob = Objective(rt.ctypes.data, float(w_mismatch), float(w_tne), int(steps),
+                       int(checkpoint_every))
+        J, Jm, Jt = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.lbkm_objective_value(self._h, ctypes.byref(ob), ctypes.byref(J),
+                                                   ctypes.byref(Jm), ctypes.byref(Jt)))
+        return {"J": J.value, "J_mismatch": Jm.value, "J_tne": Jt.value}
 
     def set_wait_limit(self, timeout_ns, phantom_blocks=0):
         self._check(self._lib.lbkm_set_wait_limit(self._h, int(timeout_ns), int(phantom_blocks)))

@@ -200,6 +200,38 @@ def test_adjoint_of_the_fp32_forward_small(rec):
         assert rep[key] <= 1e-4, (key, rep[key])
 
 
+@pytest.mark.parametrize("precision,periodic,ck", [(lbkm.F64, False, 16), (lbkm.F64, True, 16),
+                                                   (lbkm.F32, False, 7), (lbkm.F32, False, 60)],
+                         ids=["f64", "f64-periodic", "f32-ck7", "f32-one-segment"])
+def test_objective_value_is_the_J_of_the_gradient(precision, periodic, ck):
+    """lbkm_objective_value: the J of lbkm_grad without the reverse sweep -- the same FP64
+    run, or the same FP64 segments restarted from the FP32 run's states (a ragged last
+    segment with ck = 7 over 60 steps; one segment with ck = 60). Its terms equal
+    lbkm_grad's up to the order of the FP64 additions (1e-12), and J equals the oracle's
+    (plain, or restarted from the same FP32 states) to 1e-9; the handle is untouched."""
+    nx, steps = 96, 60
+    c, p, m, rho_t = problem(nx, steps, omega1=2e3, driver=16, omega2=800.0, periodic=periodic)
+    fl = c["fields"]
+    s = lbkm.Solver(nx=nx, ny=1, precision=precision, gamma=p["gamma"],
+                    orbit_kind=p["orbit_kind"], orbit_speed=p["orbit_speed"],
+                    orbit_eta=p["orbit_eta"], S=p["S"], Q=p["Q"], omega1=p["omega1"],
+                    omega2=800.0, T_ig=p["T_ig"], dx=p["dx"], dy=p["dx"], dt=p["dt"],
+                    bc=(0 if periodic else 1, 0))
+    s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    before = s.get_state()
+    v = s.objective(rho_t, steps, w_tne=1.0, checkpoint_every=ck)
+    assert np.array_equal(s.get_state(), before)
+    g = s.grad(rho_t, steps, w_tne=1.0, checkpoint_every=ck)
+    s.close()
+    for key in ("J", "J_mismatch", "J_tne"):
+        assert v[key] > 0.0
+        assert abs(v[key] - g[key]) <= 1e-12 * abs(g[key]), (key, v[key], g[key])
+    rs = fp32_checkpoints(c, p, steps, ck, omega2=800.0) if precision == lbkm.F32 else None
+    r = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0, ck=ck if rs else 0, restarts=rs)
+    assert abs(v["J"] - r["J"]) <= 1e-9 * abs(r["J"]), (v["J"], r["J"])
+    assert abs(v["J_mismatch"] - r["J_mismatch"]) <= 1e-9 * abs(r["J_mismatch"])
+
+
 def bumps(nx, width=64.0, every=256):
     x = np.arange(nx)
     return np.stack([np.exp(-0.5 * ((x - c0) / width) ** 2) for c0 in range(every // 2, nx, every)])
@@ -323,3 +355,36 @@ def test_autograd_function_backward():
     assert np.allclose(S.grad.numpy()[4:], 2 * r["dS"][4:], rtol=0,
                        atol=1e-9 * np.abs(r["dS"]).max())
     assert abs(float(Q.grad) - 2 * r["dQ"]) <= 1e-9 * abs(r["dQ"])
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_detonation_objective_omega2_and_value_only(precision):
+    """autograd.detonation_objective: with omega2 a tensor that requires a gradient,
+    backward gives dJ/domega2 (and the rest) of lbkm_grad on a handle of that precision;
+    without gradients recorded (torch.no_grad) it takes J alone from
+    lbkm_objective_value, the same value to 1e-12."""
+    from paper_1411_6697_gb300.autograd import detonation_objective
+    nx, steps, ck = 64, 40, 16
+    c, p, m, rho_t = problem(nx, steps, omega1=2e3, driver=12, omega2=800.0)
+    setup = dict(params=p, fields=c["fields"], rho_target=rho_t, steps=steps, w_tne=1.0,
+                 checkpoint_every=ck, precision=precision)
+    rho0 = torch.tensor(c["fields"]["rho"][0], dtype=torch.float64, requires_grad=True)
+    S = torch.tensor(p["S"], dtype=torch.float64, requires_grad=True)
+    Q = torch.tensor(p["Q"], dtype=torch.float64)
+    k1 = torch.tensor(p["omega1"], dtype=torch.float64)
+    k2 = torch.tensor(800.0, dtype=torch.float64, requires_grad=True)
+    J = detonation_objective(rho0, S, Q, k1, setup, k2)
+    J.backward()
+    prec = lbkm.F64 if precision == "f64" else lbkm.F32
+    g = gpu_grad(c, p, rho_t, steps, w_tne=1.0, ck=ck, precision=prec, omega2=800.0)
+    assert float(J) == g["J"]
+    assert g["domega2"] != 0.0 and float(k2.grad) == g["domega2"]
+    assert np.array_equal(S.grad.numpy(), g["dS"])
+    assert np.array_equal(rho0.grad.numpy(), g["drho0"])
+    with torch.no_grad():
+        J0 = detonation_objective(rho0, S, Q, k1, setup, k2)
+    assert not J0.requires_grad
+    assert abs(float(J0) - g["J"]) <= 1e-12 * abs(g["J"])
+    r = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0)
+    if precision == "f64":
+        assert abs(float(k2.grad) - r["domega2"]) <= 1e-9 * abs(r["domega2"])
