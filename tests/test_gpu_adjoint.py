@@ -66,7 +66,7 @@ def oracle_grad(c, p, m, rho_t, steps, w_tne, ck=0, restarts=None):
         dw2 = float(m.omega2.grad) if m.omega2.grad is not None else 0.0
     finally:
         m.omega2 = w2
-    return dict(J=float(J.detach()), J_mismatch=float(mis), dS=S.grad.numpy(), dQ=float(Q.grad),
+    return dict(J=float(J.detach()), J_mismatch=float(mis.detach()), dS=S.grad.numpy(), dQ=float(Q.grad),
                 domega1=float(k.grad), domega2=dw2, drho0=rho0.grad.numpy())
 
 
