@@ -388,3 +388,49 @@ def test_detonation_objective_omega2_and_value_only(precision):
     r = oracle_grad(c, p, m, rho_t, steps, w_tne=1.0)
     if precision == "f64":
         assert abs(float(k2.grad) - r["domega2"]) <= 1e-9 * abs(r["domega2"])
+
+
+def test_grad_and_objective_reject_unsupported_handles():
+    """lbkm_grad and lbkm_objective_value share their conditions: a 1-D forward-Euler
+    handle with periodic (nx >= 5) or zero-gradient ends, initialised, steps >= 1 and
+    checkpoint_every >= 1; anything else returns LBKM_EINVAL (LBKM_ESTATE before
+    lbkm_init_fields) without touching the device state."""
+    c, p, m, rho_t = problem(64, 10, omega1=2e3, driver=12)
+    fl = c["fields"]
+    base = dict(gamma=p["gamma"], orbit_kind=p["orbit_kind"], orbit_speed=p["orbit_speed"],
+                orbit_eta=p["orbit_eta"], S=p["S"], Q=p["Q"], omega1=p["omega1"],
+                T_ig=p["T_ig"], dx=p["dx"], dy=p["dx"], dt=p["dt"])
+    ones = np.ones(64)
+
+    def codes(s, rt, steps=10, ck=4):
+        out = []
+        for call in (lambda: s.grad(rt, steps, checkpoint_every=ck),
+                     lambda: s.objective(rt, steps, checkpoint_every=ck)):
+            with pytest.raises(lbkm.LbkmError) as e:
+                call()
+            out.append(e.value.code)
+        return out
+
+    EINVAL, ESTATE = 1, 7
+    assert lbkm.STATUS[EINVAL] == "LBKM_EINVAL" and lbkm.STATUS[ESTATE] == "LBKM_ESTATE"
+    s = lbkm.Solver(nx=64, ny=1, precision=lbkm.F64, bc=(1, 0), **base)
+    assert codes(s, ones) == [ESTATE, ESTATE]  # before init_fields
+    s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    before = s.get_state()
+    assert codes(s, ones, steps=0) == [EINVAL, EINVAL]
+    assert codes(s, ones, ck=0) == [EINVAL, EINVAL]
+    assert np.array_equal(s.get_state(), before)
+    s.close()
+    s = lbkm.Solver(nx=64, ny=4, precision=lbkm.F64, bc=(1, 0), **base)
+    s.init_fields(*(np.broadcast_to(np.asarray(fl[k], float)[:1], (4, 64)).copy()
+                    for k in ("rho", "ux", "uy", "T", "lam")))
+    assert codes(s, ones) == [EINVAL, EINVAL]  # a 2-D grid
+    s.close()
+    s = lbkm.Solver(nx=64, ny=1, precision=lbkm.F64, bc=(1, 0), time_scheme=1, **base)
+    s.init_fields(fl["rho"], fl["ux"], fl["uy"], fl["T"], fl["lam"])
+    assert codes(s, ones) == [EINVAL, EINVAL]  # a Runge-Kutta scheme
+    s.close()
+    s = lbkm.Solver(nx=4, ny=1, precision=lbkm.F64, bc=(0, 0), **base)
+    s.init_fields(*(np.asarray(fl[k], float)[:, :4].copy() for k in ("rho", "ux", "uy", "T", "lam")))
+    assert codes(s, np.ones(4)) == [EINVAL, EINVAL]  # periodic with nx < 5
+    s.close()
