@@ -474,13 +474,31 @@ class Solver:
     def steps_taken(self):
         return int(self._api.steps_taken(self._h))
 
+    def _out_ptr(self, a, name, device):
+        # a caller's output buffer: ny * nx contiguous float64 values where `device` says
+        n = self.ny * self.nx
+        if _is_torch(a):
+            import torch
+            ok = (a.dtype == torch.float64 and a.is_contiguous() and a.numel() == n
+                  and a.is_cuda == bool(device))
+            if not ok:
+                raise ValueError("out[%r] must be a contiguous float64 %s tensor of %d values"
+                                 % (name, "CUDA" if device else "CPU", n))
+            return a.data_ptr()
+        if device:
+            raise ValueError("out[%r] must be a CUDA tensor when device=True" % name)
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                and a.size == n and a.flags.writeable):
+            raise ValueError("out[%r] must be a writable C-contiguous float64 array of %d values"
+                             % (name, n))
+        return a.ctypes.data
+
     def macros(self, device=False, out=None):
         """rho, ux, uy, T, p, lambda of the current state; with out (a dict of
         preallocated host or CUDA tensors/arrays) the results land there."""
         names = ("rho", "ux", "uy", "T", "p", "lam")
         if out is not None:
-            ptrs = [(out[k].data_ptr() if _is_torch(out[k]) else out[k].ctypes.data)
-                    if k in out else None for k in names]
+            ptrs = [self._out_ptr(out[k], k, device) if k in out else None for k in names]
             self._check(self._api.macros(self._h, *[ctypes.c_void_p(p) for p in ptrs],
                                               1 if device else 0))
             return out
@@ -535,11 +553,16 @@ class Solver:
         return buf
 
     def set_state(self, buf):
-        if _is_torch(buf):
-            if buf.numel() != self.state_bytes():
-                raise ValueError("state buffer has the wrong size")
+        if _is_torch(buf) and buf.is_cuda:
+            import torch
+            if not (buf.dtype == torch.uint8 and buf.is_contiguous()
+                    and buf.numel() == self.state_bytes()):
+                raise ValueError("a CUDA state buffer must be a contiguous uint8 tensor of %d "
+                                 "bytes" % self.state_bytes())
             self._check(self._api.set_state(self._h, ctypes.c_void_p(buf.data_ptr()), 1))
             return
+        if _is_torch(buf):
+            buf = buf.numpy()
         buf = np.ascontiguousarray(buf, np.uint8)
         if buf.size != self.state_bytes():
             raise ValueError("state buffer has %d bytes, expected %d" % (buf.size,

@@ -100,3 +100,33 @@ def test_d2v24_side_conditions_are_checked(kw):
     with pytest.raises(lbkm.LbkmError) as e:
         lbkm.Solver24(stream=0, **base)
     assert e.value.code == 1
+
+
+def _shell(nx, ny):
+    # a Solver's Python side without a handle: only the buffer checks run
+    s = lbkm.Solver.__new__(lbkm.Solver)
+    s.nx, s.ny = nx, ny
+    return s
+
+
+def test_macros_output_buffers_are_checked_before_any_call():
+    """Solver.macros(out=...) hands the library raw pointers that it fills with ny * nx
+    doubles, so a buffer of another dtype, size, layout or device is refused first."""
+    import numpy as np
+    import torch
+    s = _shell(8, 3)
+    assert s._out_ptr(np.zeros((3, 8)), "rho", False) != 0
+    assert s._out_ptr(torch.zeros((3, 8), dtype=torch.float64), "rho", False) != 0
+    bad = [np.zeros((3, 8), np.float32), np.zeros((3, 7)), np.zeros((8, 3)).T,
+           torch.zeros((3, 8)), torch.zeros((3, 9), dtype=torch.float64),
+           torch.zeros((8, 3), dtype=torch.float64).t()]
+    ro = np.zeros((3, 8))
+    ro.flags.writeable = False
+    bad.append(ro)
+    for b in bad:
+        with pytest.raises(ValueError):
+            s._out_ptr(b, "rho", False)
+    with pytest.raises(ValueError):  # host buffers where the call writes device memory
+        s._out_ptr(np.zeros((3, 8)), "rho", True)
+    with pytest.raises(ValueError):
+        s._out_ptr(torch.zeros((3, 8), dtype=torch.float64), "rho", True)
