@@ -497,7 +497,7 @@ def run_d2v24(args):
     return 0
 
 
-def measure_adjoint(n_grad=1):
+def measure_adjoint(n_grad=1, steps=None):
     """Config 5: dJ/d(S, Q, omega1, omega2, rho0) of a 4000-step 1-D detonation of 8192
     cells (profile mismatch + integrated TNE), checkpoints every 64 steps, through
     lbkm_grad (host wall clock per gradient); against the plain FP64 forward run of the
@@ -508,7 +508,7 @@ def measure_adjoint(n_grad=1):
     cfg = li.adjoint()
     base, tgt = cfg["base"], cfg["target"]
     q, fl = base["params"], base["fields"]
-    steps = base["steps"]
+    steps = base["steps"] if steps is None else steps
     stream = torch.cuda.Stream()
 
     def solver(p, prec=lbkm.F64):
@@ -562,7 +562,7 @@ def measure_adjoint(n_grad=1):
     n_scalar = 16 + 3               # S_1..S_16, Q, omega1, omega2
     n_entries = n_scalar + nx       # and the initial density field
     fd = 2 * ms_fwd * 1e-3          # one central difference = two forward runs
-    return {"workload": "adjoint_8192x1_detonation_4000_steps", "checkpoint_every":
+    return {"workload": "adjoint_%dx1_detonation_%d_steps" % (nx, steps), "checkpoint_every":
             cfg["checkpoint_every"], "w_tne": cfg["w_tne"], "J": g["J"],
             "gradient_ms": sec * 1e3, "plain_f64_forward_ms": ms_fwd,
             "objective_only_ms": sec_j * 1e3, "objective_only_J": j_only,
@@ -596,8 +596,8 @@ def run_adjoint(args):
     torch.cuda.set_device(local)
     n_grad = max(1, min(args.steps, 3))
     with ClockSampler(local) as clk:
-        a = measure_adjoint(n_grad)
-    nx, steps = 8192, 4000
+        a = measure_adjoint(n_grad, args.adjoint_steps)
+    nx, steps = 8192, args.adjoint_steps
     line = {"metric": METRIC, "value": nx * steps / (a["gradient_ms"] * 1e-3) / 1e6,
             "unit": "Mcell-updates/s (forward-equivalent, per gradient)", "n_gpus": 1,
             "steps": n_grad, "warmup": 1, "ms_per_step": a["gradient_ms"],
@@ -658,6 +658,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--side", type=int, default=N_CELLS_SIDE)
+    ap.add_argument("--adjoint-steps", type=int, default=4000,
+                    help="steps of the adjoint workload (4000; fewer only for profiling)")
     ap.add_argument("--workload", default="reactive2d",
                     choices=["reactive2d", "batched", "detonation", "adjoint", "d2v24"])
     args = ap.parse_args()
