@@ -1069,10 +1069,24 @@ cudaError_t launch_one_step(const lbkm24* h, int from, cudaStream_t st)
     return e;
 }
 
+// streaming multiprocessors of the current device (152 on GB300, the value taken if the
+// query fails)
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1) {
+        cudaGetLastError();
+        return 152;
+    }
+    return sms;
+}
+
 int elementwise_blocks(int64_t n)
 {
-    int64_t b = (n + 255) / 256;
-    return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+    const int64_t b = (n + 255) / 256, cap = (int64_t)sm_count() * 16;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 lbkm_status check(lbkm24_t h)
@@ -1235,7 +1249,7 @@ lbkm_status lbkm24_create(const lbkm24_params* pin, void* cuda_stream, lbkm24_t*
     }
     // 1-D grids too short to give every SM a block of 128 cells run blocks of one warp:
     // the step is latency-bound there, and more SMs each take fewer cells
-    const bool narrow = p.ny == 1 && (p.nx + BT - 1) / BT < 2 * 152;
+    const bool narrow = p.ny == 1 && (p.nx + BT - 1) / BT < 2 * sm_count();
     h->block = p.ny > 1 ? dim3(32, BT / 32) : dim3(narrow ? 32 : BT, 1);
     h->grid = dim3((p.nx + h->block.x - 1) / h->block.x, (p.ny + h->block.y - 1) / h->block.y);
     h->nblocks = (int)(h->grid.x * h->grid.y);
