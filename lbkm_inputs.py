@@ -240,6 +240,29 @@ def d2v24_detonation(nx=5000, steps=78000, omega1=1e3, dx=2e-4, dt=5e-6, S=None,
                 name="d2v24_detonation_nx%d" % nx)
 
 
+# The paper leaves the rate constant of its Sec. VI detonations unstated. With omega1 = 13
+# its case (i) reaches, at t = 0.35, a pressure peak of 2.405 at x = 0.784 (printed: 2.3985
+# at 0.8345); from omega1 ~ 18 upwards a weak reaction front, lit inside the thick shock of
+# the R_i = 1e2 gas, outruns the detonation and the peak stays at the initial interface.
+D2V24_SEC6_OMEGA1 = 13.0
+
+
+def d2v24_tne_study(case=1, omega1=D2V24_SEC6_OMEGA1):
+    """The detonations of Sec. VI with D2V24, run to t = 0.35 from the initial state of
+    Sec. IV.A on x in [0, 1): case 1, R_i = 1e2 with v = (2.7, 2.2, 1.2), eta = (1.5,
+    0.5, 5.0), dx = 1e-3, dt = 1e-5; case 2, R_i = 1e3 with v = (2.7, 2.6, 1.9), eta =
+    (5.0, 0.0, 1.7), dx = 2e-4, dt = 2e-6; case 3, R_i = 1e4 with the case-2 set, dx =
+    4e-5, dt = 4e-6. All R_i equal (the section's collision parameters); I = 3, Q = 1,
+    T_ig = 1.1 as in Sec. IV.A."""
+    R, v, dx, dt = {1: (1e2, D2V24_TNE_V, 1e-3, 1e-5),
+                    2: (1e3, D2V24_TNE_V2, 2e-4, 2e-6),
+                    3: (1e4, D2V24_TNE_V2, 4e-5, 4e-6)}[case]
+    nx, steps = int(round(1.0 / dx)), int(round(0.35 / dt))
+    c = d2v24_detonation(nx=nx, steps=steps, omega1=omega1, dx=dx, dt=dt, S=np.full(24, R), v=v)
+    c["name"] = "d2v24_sec6_case%d" % case
+    return c
+
+
 def d2v24_shock_tube(which, steps=None):
     """The three shock tubes of Sec. IV.B with the paper's own D2V24 sets:
     Sod: (1, 1, 0) | (0.125, 0.8, 0) on [0, 1], 1000 cells, dt = 1e-5, t = 0.2, I = 3,
